@@ -1,0 +1,379 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle
+itself: published known-answer vectors, exact integer arithmetic, LAPACK
+(scipy GEQP3, numpy QR/Cholesky/triangular solves) on special cases that
+reduce to them, closed forms from the paper's theorems, and invariants.
+
+Each test names the passage it pins (Alg. = algorithm, Sec. = section).
+"""
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import oracle
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U = 2.0 ** -53
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# --------------------------------------------------------------------------
+# S: Philox4x32-10 and the SASO sampling rule (Sec. 3.3.1)
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    """Salmon et al. SC'11 Philox4x32-10, published known-answer vectors."""
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert oracle.philox4x32_10(w[:4], w[4:6]) == w[6:]
+        n += 1
+    assert n == 3
+
+
+@pytest.mark.parametrize("d,s", [(16, 4), (128, 4), (1280, 8), (5, 5), (7, 1)])
+def test_saso_columns_have_s_distinct_rows(d, s):
+    """Sec. 3.3.1: each column of S has exactly s nonzeros at distinct rows."""
+    for r in range(200):
+        rows, neg = oracle.saso_column(12345, r, d, s)
+        assert len(set(rows.tolist())) == s
+        assert rows.min() >= 0 and rows.max() < d
+        assert set(neg.tolist()) <= {0, 1}
+
+
+def test_saso_subsets_uniform():
+    """Sec. 3.3.1: the s locations are uniform over all s-subsets of [0, d):
+    chi-square over the C(6,2) = 15 subsets (Floyd's algorithm)."""
+    d, s, cols = 6, 2, 30000
+    counts = {}
+    for r in range(cols):
+        rows, _ = oracle.saso_column(777, r, d, s)
+        key = tuple(sorted(rows.tolist()))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 15
+    exp = cols / 15
+    chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
+    assert chi2 < 45.0  # 14 dof: p < 1e-4 for a correct sampler
+
+
+def test_saso_signs_balanced_and_row_marginals_uniform():
+    """Sec. 3.3.1: signs +-1 equally likely; each row equally likely."""
+    d, s, cols = 40, 4, 20000
+    hist = np.zeros(d)
+    negs = 0
+    for r in range(cols):
+        rows, neg = oracle.saso_column(99, r, d, s)
+        hist[rows] += 1
+        negs += int(neg.sum())
+    tot = cols * s
+    assert abs(negs / tot - 0.5) < 0.01
+    exp = tot / d
+    chi2 = float(((hist - exp) ** 2 / exp).sum())
+    assert chi2 < 90.0  # 39 dof
+
+
+def test_saso_seed_changes_operator():
+    a = oracle.saso_dense(1, 16, 64, 4)
+    b = oracle.saso_dense(2, 16, 64, 4)
+    assert not np.array_equal(a, b)
+    assert np.array_equal(a, oracle.saso_dense(1, 16, 64, 4))
+    assert oracle.saso_scale(4) == 0.5
+
+
+# --------------------------------------------------------------------------
+# Alg. 2 line 1: the sketch
+# --------------------------------------------------------------------------
+def test_sketch_exact_on_integer_matrix():
+    """On integer M with |M| <= 2^20 every partial sum is exact, so the sketch
+    must equal the exact product S M (Python integers) bit for bit; m spans
+    several 4096-row blocks and a ragged tail."""
+    rng = _rng(1)
+    m, n, d, s = 3 * 4096 + 123, 5, 16, 4
+    M = np.asfortranarray(rng.integers(-(2 ** 20), 2 ** 20, size=(m, n)).astype(np.float64))
+    Msk, st = oracle.sketch(M, d, s, seed=42)
+    assert st == 0
+    S2 = (oracle.saso_dense(42, d, m, s) * 2).astype(np.int64)   # entries +-1
+    exact = S2 @ M.astype(np.int64)                              # int64, exact
+    assert np.array_equal(Msk, exact.astype(np.float64) * 0.5)
+
+
+def test_sketch_matches_dense_product_general():
+    rng = _rng(2)
+    m, n, d, s = 5000, 7, 24, 8
+    M = np.asfortranarray(rng.standard_normal((m, n)))
+    Msk, st = oracle.sketch(M, d, s, seed=7)
+    S = oracle.saso_dense(7, d, m, s)
+    ref = S @ M
+    # sequential-sum error bound: (terms per row) * u * sum |S_ir M_rc|
+    bound = (m * s / d + 2) * U * (np.abs(S) @ np.abs(M))
+    assert (np.abs(Msk - ref) <= bound).all()
+
+
+def test_sketch_nonfinite_status():
+    M = np.asfortranarray(np.ones((100, 3)))
+    M[17, 1] = np.nan
+    _, st = oracle.sketch(M, 8, 2, seed=1)
+    assert st == 2
+
+
+# --------------------------------------------------------------------------
+# dot32 (the summation reading used inside the QRCP)
+# --------------------------------------------------------------------------
+def test_dot32_exact_on_integers_and_within_error_bound():
+    rng = _rng(3)
+    x = rng.integers(-1000, 1000, 333).astype(np.float64)
+    y = rng.integers(-1000, 1000, 333).astype(np.float64)
+    assert oracle.dot32(x, y) == float(int(x.astype(np.int64) @ y.astype(np.int64)))
+    x = rng.standard_normal(1001)
+    y = rng.standard_normal(1001)
+    exact = sum(Fraction(a) * Fraction(b) for a, b in zip(x.tolist(), y.tolist()))
+    bound = (1001 / 32 + 6) * U * float(np.abs(x) @ np.abs(y))
+    assert abs(Fraction(oracle.dot32(x, y)) - exact) <= Fraction(bound)
+
+
+# --------------------------------------------------------------------------
+# Alg. 2 line 2: QRCP (GEQP3 semantics)
+# --------------------------------------------------------------------------
+def _graded(d, n, seed):
+    rng = _rng(seed)
+    X = rng.standard_normal((d, n)) * np.logspace(0, -3, n)[rng.permutation(n)]
+    return np.asfortranarray(X)
+
+
+@pytest.mark.parametrize("d,n,seed", [(40, 13, 1), (128, 64, 2), (200, 150, 3), (9, 9, 4)])
+def test_qrcp_matches_lapack_geqp3(d, n, seed):
+    X = _graded(d, n, seed)
+    R, J, tau, piv, sec, _ = oracle.qrcp(X)
+    _, Rl, Jl = sl.qr(X, mode="economic", pivoting=True)
+    gap = (piv - np.maximum(sec, 0)) / piv
+    first_tie = int(np.argmax(gap < 1e-10)) if (gap < 1e-10).any() else n
+    assert first_tie >= n - 1
+    assert np.array_equal(J, Jl)
+    scale = np.abs(Rl).max()
+    assert np.abs(np.abs(R) - np.abs(Rl[:n, :])).max() <= 1e-12 * scale
+    # R^T R = X_J^T X_J (R^sk is the R factor of the pivoted sketch)
+    XJ = X[:, J]
+    assert np.abs(R.T @ R - XJ.T @ XJ).max() <= 1e-13 * np.abs(XJ.T @ XJ).max()
+    assert (np.diag(R) >= 0).all()
+    assert np.array_equal(np.triu(R), R)
+    # |R_jj| non-increasing under max-norm pivoting
+    dR = np.diag(R)
+    assert (dR[1:] <= dR[:-1] * (1 + 1e-12)).all()
+
+
+def test_qrcp_lowest_index_on_exact_ties():
+    """Businger-Golub pivoting with the BLAS idamax convention: the first of
+    equal maxima.  Columns 1..3 are signed permutations of one vector of
+    powers of two (exactly equal norms), column 0 is smaller."""
+    base = np.array([4.0, 2.0, 1.0, 0.5, 0.25, 8.0])
+    X = np.zeros((6, 4))
+    X[:, 0] = base / 4
+    X[:, 1] = base[[1, 0, 2, 3, 4, 5]]
+    X[:, 2] = -base[[5, 4, 3, 2, 1, 0]]
+    X[:, 3] = base
+    R, J, *_ = oracle.qrcp(np.asfortranarray(X))
+    assert J[0] == 1
+
+
+# --------------------------------------------------------------------------
+# Alg. 2 line 3: rank (Sec. 4.3)
+# --------------------------------------------------------------------------
+def test_rank_tol_counts_leading_diagonal():
+    R = np.diag([2.0, 1.0, 1e-3, 1e-10, 1e-9, 1e-15])
+    assert oracle.rank_tol(R, 1e-9) == 3       # 1e-10/2 < 1e-9 stops the count
+    assert oracle.rank_tol(R, 1e-12) == 5
+    assert oracle.rank_tol(R, 0.6) == 1
+    assert oracle.rank_tol(np.zeros((3, 3)), 1e-9) == 0
+
+
+def test_rank_stage1_closed_form():
+    """eq. initial_numerical_rank: k_o = min{l : ||C_l||_F <= u max|R|}."""
+    n = 6
+    R = np.triu(np.ones((n, n))) * 0.0
+    diag = [1.0, 0.5, 0.25, 1e-17, 1e-18, 0.0]
+    R[np.arange(n), np.arange(n)] = diag
+    # ||C_3||_F = sqrt(1e-34 + 1e-36) <= u * 1 ; ||C_2|| = 0.25 > u
+    assert oracle.rank_stage1(R) == 3
+    R[2, 5] = 1e-3   # in row 2 -> C_2 only
+    assert oracle.rank_stage1(R) == 3
+    R[3, 4] = 1e-10  # C_3 now above u
+    assert oracle.rank_stage1(R) == 4
+
+
+def test_rank_stage2_cond_diag():
+    """eq. updated_numerical_rank with cond(diag): largest l with
+    max/min of the first l diagonal entries of R^pre <= 10."""
+    Rp = np.diag([1.0, 1.2, 0.9, 0.2, 0.09, 5.0])
+    assert oracle.rank_stage2(6, Rp) == 4      # 1.2/0.09 > 10 at l = 5
+    assert oracle.rank_stage2(3, Rp) == 3
+    assert oracle.rank_stage2(6, np.diag([1.0, 0.1, 0.0999, 1, 1, 1])) == 2
+
+
+# --------------------------------------------------------------------------
+# Alg. 2 lines 4-8 kernels against LAPACK
+# --------------------------------------------------------------------------
+def test_trsm_matches_triangular_solve():
+    rng = _rng(5)
+    m, n, k = 300, 20, 12
+    B = np.asfortranarray(rng.standard_normal((m, n)))
+    T = np.triu(rng.standard_normal((k, k))) + 4 * np.eye(k)
+    cols = rng.permutation(n)[:k]
+    X = oracle.trsm_rut(B, T, cols)
+    ref = sl.solve_triangular(T, B[:, cols].T, trans="T", lower=False).T
+    assert np.abs(X - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_gram_matches_product_several_blocks():
+    rng = _rng(6)
+    m, k = 3 * 4096 + 77, 9
+    X = np.asfortranarray(rng.standard_normal((m, k)))
+    G = oracle.gram(X)
+    assert np.array_equal(G, G.T)
+    assert np.abs(G - X.T @ X).max() <= 1e-13 * m
+    Xi = np.asfortranarray(rng.integers(-50, 50, (m, k)).astype(np.float64))
+    assert np.array_equal(oracle.gram(Xi), (Xi.astype(np.int64).T @ Xi.astype(np.int64)).astype(float))
+
+
+def test_potrf_matches_cholesky_and_reports_failure():
+    rng = _rng(7)
+    k = 15
+    Bm = rng.standard_normal((40, k))
+    G = Bm.T @ Bm
+    R, fail = oracle.potrf_upper(G)
+    assert fail == -1
+    assert np.abs(R - np.linalg.cholesky(G).T).max() <= 1e-13 * np.abs(R).max()
+    # Remark 3: column 9 depends on columns 0..8 -> failure at 9, leading block valid
+    Bm[:, 9] = Bm[:, :9] @ rng.standard_normal(9)
+    G = Bm.T @ Bm
+    G[9, 9] -= 1e-6 * G[9, 9]
+    R, fail = oracle.potrf_upper(G)
+    assert fail == 9
+    L = R[:9, :9]
+    assert np.abs(L.T @ L - G[:9, :9]).max() <= 1e-12 * np.abs(G).max()
+
+
+def test_trmm_matches_product():
+    rng = _rng(8)
+    k, n = 7, 11
+    Rp = np.triu(rng.standard_normal((k, k)))
+    Rs = np.triu(rng.standard_normal((k, n)))
+    R = oracle.trmm_upper(Rp, Rs)
+    assert np.abs(R - Rp @ Rs).max() <= 1e-14 * 10
+    assert np.array_equal(np.triu(R), R)
+
+
+# --------------------------------------------------------------------------
+# The whole method
+# --------------------------------------------------------------------------
+def test_identity_sketch_reduces_to_geqp3():
+    """With S = I (d = m is allowed, Alg. 2 input n <= d <= m) CQRRPT is QRCP
+    of M itself: J equals LAPACK GEQP3's pivots and |R| equals |R_geqp3|."""
+    X = _graded(90, 17, 11)
+    res = oracle.cqrrpt_core_sketched(X, X, tol=1e-14)
+    _, Rl, Jl = sl.qr(X, mode="economic", pivoting=True)
+    assert res.k == 17
+    assert np.array_equal(res.J, Jl)
+    assert np.abs(res.R - np.abs(Rl) * np.sign(res.R)).max() <= 1e-12 * np.abs(Rl).max()
+    assert np.abs(np.abs(res.R) - np.abs(Rl)).max() <= 1e-12 * np.abs(Rl).max()
+
+
+def test_full_rank_is_unique_positive_qr_of_pivoted_matrix():
+    """Full rank: (Q, R) with diag(R) > 0 is the unique QR of M[:, J]."""
+    m, n = 3000, 24
+    A = W.planted(m, n, W.logspaced(n, -3.0), 5).numpy()
+    A = np.asfortranarray(A)
+    res = oracle.cqrrpt(A, 1.25, 4, 1e-12, 17)
+    assert res.status == 0 and res.k == n
+    Qn, Rn = np.linalg.qr(A[:, res.J])
+    sg = np.sign(np.diag(Rn))
+    Qn = Qn * sg
+    Rn = (Rn.T * sg).T
+    assert np.abs(res.R - Rn).max() <= 1e-12 * np.abs(Rn).max()
+    assert np.abs(res.Q - Qn).max() <= 1e-11
+
+
+def test_theorem1_sketch_of_residual_vanishes():
+    """Thm. 1: S (M_n - Q_k R_k) = 0 when rank(SM) = rank(M)."""
+    m, n, gamma, s, seed = 2048, 16, 1.5, 3, 5
+    A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -4.0), 9).numpy())
+    res = oracle.cqrrpt(A, gamma, s, 1e-12, seed)
+    d = oracle.sketch_dim(n, gamma)
+    S = oracle.saso_dense(seed, d, m, s)
+    D = A[:, res.J] - res.Q @ res.R
+    assert np.linalg.norm(S @ D) <= 1e-14 * np.linalg.norm(S @ A) * 10
+
+
+def test_theorem2_spectrum_of_preconditioned_matrix():
+    """Thm. 2: sigma_i(M^pre) = 1 / sigma_{k-i+1}(S U), U an orthonormal basis
+    of range(M)."""
+    m, n, gamma, s, seed = 4096, 20, 1.25, 4, 3
+    U_ = W.haar(m, n, 21).numpy()
+    V_ = W.haar(n, n, 22).numpy()
+    A = np.asfortranarray((U_ * W.logspaced(n, -4.0).numpy()) @ V_.T)
+    res = oracle.cqrrpt(A, gamma, s, 1e-12, seed)
+    assert res.k == n
+    Mpre = oracle.trsm_rut(A, res.Rsk[:n, :n], res.J[:n])
+    d = oracle.sketch_dim(n, gamma)
+    S = oracle.saso_dense(seed, d, m, s)
+    sv_pre = np.linalg.svd(Mpre, compute_uv=False)
+    sv_su = np.linalg.svd(S @ U_, compute_uv=False)
+    assert np.abs(sv_pre - 1.0 / sv_su[::-1]).max() <= 1e-9 * sv_pre.max()
+
+
+def test_invariants_full_rank_cond_1e8():
+    """Full-rank m = 4096, n = 64, cond 1e8, d = 2n, 4 nnz/col, tol 1e-12:
+    k = n, R upper-trapezoidal with positive diagonal,
+    ||M[:,J] - QR||_F/||M||_F <= 1e-13 and ||Q^T Q - I||_2 <= 1e-13."""
+    w = W.single_small()
+    A = np.asfortranarray(w.matrix().numpy())
+    res = oracle.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    assert res.status == 0 and res.k == 64
+    assert np.array_equal(np.triu(res.R), res.R) and (np.diag(res.R) > 0).all()
+    assert np.linalg.norm(A[:, res.J] - res.Q @ res.R) / np.linalg.norm(A) <= 1e-13
+    assert np.linalg.norm(res.Q.T @ res.Q - np.eye(64), 2) <= 1e-13
+    assert sorted(res.J.tolist()) == list(range(64))
+
+
+@pytest.mark.parametrize("m,n,rank,gamma,s", [(8192, 96, 60, 1.25, 8), (4100, 33, 20, 1.25, 4)])
+def test_planted_rank_recovered(m, n, rank, gamma, s):
+    sv = np.zeros(n)
+    sv[:rank] = W.logspaced(rank, -6.0).numpy()
+    A = np.asfortranarray(W.planted(m, n, sv, 31, noise=1e-15).numpy())
+    res = oracle.cqrrpt(A, gamma, s, 1e-9, 77)
+    assert res.k == rank
+    assert np.linalg.norm(res.Q.T @ res.Q - np.eye(rank), 2) <= 1e-13
+    noise = 1e-15 * math.sqrt(m * n)
+    assert np.linalg.norm(A[:, res.J] - res.Q @ res.R) / np.linalg.norm(A) <= \
+        max(1e-13, 10 * noise / np.linalg.norm(A))
+
+
+def test_default_rank_rule_and_degenerate_cases():
+    rng = _rng(12)
+    # zero matrix -> k = 0, status 1
+    res = oracle.cqrrpt(np.zeros((64, 4), order="F"), 1.25, 2, -1.0, 1)
+    assert res.status == 1 and res.k == 0
+    # n = 1
+    A = np.asfortranarray(rng.standard_normal((50, 1)))
+    res = oracle.cqrrpt(A, 1.0, 1, -1.0, 3)
+    assert res.k == 1 and abs(res.R[0, 0] - np.linalg.norm(A)) <= 1e-14 * np.linalg.norm(A)
+    # d == m (gamma n = m)
+    A = np.asfortranarray(rng.standard_normal((20, 16)))
+    res = oracle.cqrrpt(A, 1.25, 3, -1.0, 4)
+    assert res.k == 16
+    assert np.linalg.norm(A[:, res.J] - res.Q @ res.R) <= 1e-13 * np.linalg.norm(A)
+    # invalid arguments
+    assert oracle.cqrrpt(A, 2.0, 3, -1.0, 4).status == -5      # d > m
+    assert oracle.cqrrpt(A, 0.9, 3, -1.0, 4).status == -5      # gamma < 1
+    assert oracle.cqrrpt(A, 1.0, 17, -1.0, 4).status == -6     # nnz > d
+    # non-finite input
+    A[3, 2] = np.inf
+    assert oracle.cqrrpt(A, 1.0, 2, -1.0, 4).status == 2

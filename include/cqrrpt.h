@@ -1,0 +1,172 @@
+/*
+ * cqrrpt.h -- C ABI of the GB300 (sm_103a) CQRRPT library.
+ *
+ * CQRRPT ("CholeskyQR with Randomization and Pivoting for Tall matrices",
+ * Melnichenko, Balabanov, Murray, Demmel, Mahoney, Luszczek; arXiv
+ * 2311.08316) computes a column-pivoted QR decomposition M[:, J] = Q_k R_k
+ * of a tall m x n matrix M (Def. 1 of the paper, Sec. 1.4):
+ *   Alg. 1: d = ceil(gamma n), sample a d x m sketching operator S;
+ *   Alg. 2: M^sk = S M; [Q^sk, R^sk, J] = qrcp(M^sk); k = rank(R^sk);
+ *           M^pre = M[:, J[:k]] (R^sk[:k,:k])^{-1}; G = M^pre^T M^pre;
+ *           R^pre = chol(G); Q_k = M^pre (R^pre)^{-1}; R_k = R^pre R^sk[:k,:].
+ *
+ * Conventions for every entry point:
+ *   - matrices are FP64, column-major (LAPACK layout), with a leading
+ *     dimension argument; indices are 0-based (the paper's are 1-based);
+ *   - every matrix/vector pointer is a DEVICE pointer unless the argument
+ *     name ends in _host; the caller owns every buffer it passes; the
+ *     library only reads A and writes the outputs it is given;
+ *   - calls are enqueued on `stream` and return without waiting, unless a
+ *     _host output pointer is given, in which case the call waits for the
+ *     stream and returns the final status;
+ *   - a handle owns the library's device workspace and device status words;
+ *     it is not thread safe: use one handle per concurrently used stream;
+ *   - argument errors are returned immediately as -i (argument i, counting
+ *     the handle as argument 1), nothing is enqueued;
+ *   - results do not depend on the launch configuration: the arithmetic
+ *     order of every sum is fixed (see the library's design notes), so the
+ *     same inputs give bit-identical outputs on every call.
+ *
+ * The sketching operator is the SASO of Sec. 3.3.1: each of the m columns of
+ * S has exactly nnz_per_col nonzeros at distinct uniformly random rows, each
+ * +-1/sqrt(nnz_per_col); S is generated on the fly from `seed` by the
+ * counter-based Philox4x32-10 generator and never stored.
+ */
+#ifndef CQRRPT_H
+#define CQRRPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (>= 0); negative values -i flag argument i. */
+#define CQRRPT_OK 0
+#define CQRRPT_RANK_ZERO 1   /* k == 0: M is numerically zero; J is valid  */
+#define CQRRPT_NONFINITE 2   /* the sketch of M holds Inf/NaN; k = 0       */
+#define CQRRPT_CUDA_ERROR 3  /* a CUDA call or launch failed              */
+#define CQRRPT_NO_MEMORY 4   /* workspace allocation failed               */
+#define CQRRPT_TIMEOUT 5     /* a bounded device-side wait expired        */
+
+/* Precision of the O(m n^2) steps (Alg. 2 lines 4-7). */
+#define CQRRPT_FP64 0
+
+typedef struct cqrrpt_ctx* cqrrpt_handle;
+
+/* Create a handle bound to CUDA device `device` (made current for the
+ * call).  Returns 0 or CQRRPT_CUDA_ERROR. */
+int cqrrpt_create(cqrrpt_handle* h, int device);
+
+/* Release the handle and its workspace (waits for the device). */
+int cqrrpt_destroy(cqrrpt_handle h);
+
+/* Workspace bytes cqrrpt_d needs for an m x n problem. */
+int cqrrpt_workspace_size(int64_t m, int64_t n, double gamma, int nnz_per_col, int precision,
+                          size_t* bytes_host);
+
+/* Grow the handle's workspace to at least `bytes` now (a later call that
+ * fits allocates nothing).  Returns 0 or CQRRPT_NO_MEMORY. */
+int cqrrpt_reserve(cqrrpt_handle h, size_t bytes);
+
+/* Full CQRRPT, Alg. 1 + Alg. 2 (the paper's cqrrpt(M, gamma, F) with F the
+ * SASO family; defaults gamma = 1.25, nnz_per_col = 4, Sec. 6.1).
+ *   m, n          M is m x n, n <= ceil(gamma n) = d <= m, n <= 16384.
+ *   A, lda        M (read only), lda >= m.
+ *   gamma         sampling factor >= 1 (Alg. 1).
+ *   nnz_per_col   nonzeros per column of S, 1 <= nnz_per_col <= min(d, 32).
+ *   tol           rank rule (Alg. 2 line 3, Sec. 4.3): tol > 0 keeps the
+ *                 leading columns with R^sk[j,j] > tol R^sk[0,0];
+ *                 tol <= 0 runs the paper's two-stage estimate (stage 1:
+ *                 smallest l with ||R^sk[l:,l:]||_F <= u max|R^sk|; stage 2
+ *                 after the Cholesky: largest l with
+ *                 cond(diag(R^pre[:l,:l])) <= sqrt(100u/u) = 10).  In both
+ *                 cases a Cholesky breakdown at column j sets k = j
+ *                 (Remark 3).
+ *   seed          seed of S.
+ *   precision     CQRRPT_FP64.
+ *   Q, ldq        m x n capacity, ldq >= m; columns 0..k-1 receive Q_k
+ *                 (column j of M^pre is formed there first).
+ *   R, ldr        n x n capacity, ldr >= n; rows 0..k-1 receive R_k, upper
+ *                 trapezoidal with a positive diagonal.
+ *   J             n int64 entries: the full pivot vector, column j of
+ *                 M[:, J] is column J[j] of M.
+ *   k_dev         device int64 or NULL: receives k.
+ *   k_host        host int64 or NULL: if given, the call waits for the
+ *                 stream, stores k and returns the final status.
+ * Without k_host the return value covers argument and launch errors only;
+ * device-detected conditions (CQRRPT_RANK_ZERO, CQRRPT_NONFINITE,
+ * CQRRPT_TIMEOUT) are then read with cqrrpt_last_status. */
+int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, double gamma,
+             int nnz_per_col, double tol, uint64_t seed, int precision, double* Q, int64_t ldq,
+             double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
+             cudaStream_t stream);
+
+/* Wait for `stream` and return the device-detected status of the handle's
+ * last cqrrpt_d call (0, 1, 2 or 5) in *status_host, and its k in *k_host
+ * (either pointer may be NULL). */
+int cqrrpt_last_status(cqrrpt_handle h, cudaStream_t stream, int* status_host, int64_t* k_host);
+
+const char* cqrrpt_status_string(int status);
+
+/* ---- single steps of Alg. 2 (same kernels as cqrrpt_d) ------------------ */
+
+/* Line 1: M^sk = S M, S the SASO of (seed, d, nnz_per_col).  Ask: d x n,
+ * ldsk >= d.  Sum order: per block of 4096 rows ascending, blocks in
+ * ascending order, then one multiply by 1/sqrt(nnz_per_col). */
+int cqrrpt_sketch_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                    int64_t d, int nnz_per_col, uint64_t seed, double* Ask, int64_t ldsk,
+                    cudaStream_t stream);
+
+/* Line 2: QRCP of X (d x n, ldx >= d, overwritten with Householder data).
+ * J: n int64 pivots; Rsk: n x n (ldr >= n) sign-normalised R^sk (diagonal
+ * >= 0, zero below the diagonal). */
+int cqrrpt_qrcp_d(cqrrpt_handle h, int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J,
+                  double* Rsk, int64_t ldr, cudaStream_t stream);
+
+/* Line 3 (stage 1 only when tol <= 0): rank of R^sk into the device int64
+ * *k_dev. */
+int cqrrpt_rank_d(cqrrpt_handle h, int64_t n, const double* Rsk, int64_t ldr, double tol,
+                  int64_t* k_dev, cudaStream_t stream);
+
+/* Lines 4 and 7: X[:, 0:k] = B[:, cols[0:k]] T^{-1}, T upper triangular
+ * k x k; cols: k device int64 or NULL (identity); X may equal B when cols
+ * is NULL (in-place). */
+int cqrrpt_trsm_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, int64_t ldb,
+                  const int64_t* cols, const double* T, int64_t ldt, double* X, int64_t ldx,
+                  cudaStream_t stream);
+
+/* Line 5: G = X^T X (k x k, both triangles), X m x k. */
+int cqrrpt_gram_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_t ldx, double* G,
+                  int64_t ldg, cudaStream_t stream);
+
+/* Line 6: upper Cholesky of G (k x k, overwritten as working storage) into
+ * R (upper triangle written).  *fail_dev (device int64) receives -1 or the
+ * first column whose pivot is not positive (Remark 3). */
+int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R, int64_t ldr,
+                   int64_t* fail_dev, cudaStream_t stream);
+
+/* Line 8: R = Rpre (k x k upper) * Rsk[0:k, 0:n] (upper trapezoidal), zero
+ * below the diagonal. */
+int cqrrpt_trmm_d(cqrrpt_handle h, int64_t k, int64_t n, const double* Rpre, int64_t ldp,
+                  const double* Rsk, int64_t ldsk, double* R, int64_t ldr, cudaStream_t stream);
+
+/* ---- host helpers (no GPU needed) --------------------------------------- */
+
+/* d = ceil(gamma n) (Alg. 1). */
+int64_t cqrrpt_sketch_dim(int64_t n, double gamma);
+
+/* One Philox4x32-10 block (Salmon et al., SC'11) as used for S. */
+void cqrrpt_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Column r of S: rows[0..nnz) in draw order and neg[q] = 1 when nonzero q
+ * is negative (nnz_per_col <= 32). */
+void cqrrpt_saso_column(uint64_t seed, int64_t r, int64_t d, int nnz_per_col, int32_t* rows,
+                        uint8_t* neg);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CQRRPT_H */

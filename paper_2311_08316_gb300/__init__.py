@@ -1,0 +1,286 @@
+"""Python binding of the GB300 CQRRPT library (``libcqrrpt.so``, C ABI in
+``include/cqrrpt.h``).
+
+Argument marshalling only: every step of the factorisation runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  There
+is no CPU fallback: if the compiled library is missing or no CUDA device is
+present the calls raise.
+
+Matrices are ``torch.float64`` CUDA tensors in column-major layout (LAPACK):
+shape ``(rows, cols)`` with ``stride(0) == 1``; ``colmajor(x)`` converts.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcqrrpt.so")
+
+STATUS = {0: "ok", 1: "rank zero", 2: "non-finite input", 3: "CUDA error", 4: "out of memory",
+          5: "device wait timed out"}
+
+FP64 = 0
+
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_p = ctypes.c_void_p
+_d = ctypes.c_double
+_int = ctypes.c_int
+
+_lib = None
+
+
+class CqrrptError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libcqrrpt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise CqrrptError("libcqrrpt.so is not built (run paper_2311_08316_gb300/build.py); "
+                          "there is no fallback implementation")
+    L = ctypes.CDLL(LIB_PATH)
+    L.cqrrpt_create.argtypes = [ctypes.POINTER(_p), _int]
+    L.cqrrpt_destroy.argtypes = [_p]
+    L.cqrrpt_workspace_size.argtypes = [_i64, _i64, _d, _int, _int, ctypes.POINTER(ctypes.c_size_t)]
+    L.cqrrpt_reserve.argtypes = [_p, ctypes.c_size_t]
+    L.cqrrpt_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _int, _p, _i64, _p, _i64,
+                           _p, _p, ctypes.POINTER(_i64), _p]
+    L.cqrrpt_last_status.argtypes = [_p, _p, ctypes.POINTER(_int), ctypes.POINTER(_i64)]
+    L.cqrrpt_status_string.argtypes = [_int]
+    L.cqrrpt_status_string.restype = ctypes.c_char_p
+    L.cqrrpt_sketch_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _int, _u64, _p, _i64, _p]
+    L.cqrrpt_qrcp_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p]
+    L.cqrrpt_rank_d.argtypes = [_p, _i64, _p, _i64, _d, _p, _p]
+    L.cqrrpt_trsm_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_gram_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_potrf_d.argtypes = [_p, _i64, _p, _i64, _p, _i64, _p, _p]
+    L.cqrrpt_trmm_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
+    L.cqrrpt_sketch_dim.restype = _i64
+    L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
+    L.cqrrpt_saso_column.argtypes = [_u64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_uint8)]
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names every entry point of include/cqrrpt.h (for load checks)."""
+    return ["cqrrpt_create", "cqrrpt_destroy", "cqrrpt_workspace_size", "cqrrpt_reserve",
+            "cqrrpt_d", "cqrrpt_last_status", "cqrrpt_status_string", "cqrrpt_sketch_d",
+            "cqrrpt_qrcp_d", "cqrrpt_rank_d", "cqrrpt_trsm_d", "cqrrpt_gram_d", "cqrrpt_potrf_d",
+            "cqrrpt_trmm_d", "cqrrpt_sketch_dim", "cqrrpt_philox4x32_10", "cqrrpt_saso_column"]
+
+
+def _check(rc, what):
+    if rc != 0:
+        msg = lib().cqrrpt_status_string(rc).decode()
+        raise CqrrptError("%s failed with status %d (%s)" % (what, rc, msg))
+
+
+def colmajor(x):
+    """Column-major (Fortran-order) copy of a 2-D tensor."""
+    return x.t().contiguous().t()
+
+
+def colmajor_empty(rows, cols, device="cuda", dtype=torch.float64):
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def _ld(x, rows_needed=None):
+    if x.dim() != 2 or x.dtype != torch.float64 or not x.is_cuda:
+        raise CqrrptError("expected a 2-D float64 CUDA tensor")
+    if x.stride(0) != 1:
+        raise CqrrptError("expected a column-major tensor (stride(0) == 1); use colmajor()")
+    return max(x.stride(1), x.shape[0], 1)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Owns the library's device workspace for one device (one per stream)."""
+
+    def __init__(self, device=None):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        h = ctypes.c_void_p()
+        _check(lib().cqrrpt_create(ctypes.byref(h), dev), "cqrrpt_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().cqrrpt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, nbytes):
+        _check(lib().cqrrpt_reserve(self.h, int(nbytes)), "cqrrpt_reserve")
+
+    def last_status(self, stream=None):
+        st = _int()
+        k = _i64()
+        _check(lib().cqrrpt_last_status(self.h, _stream(stream), ctypes.byref(st), ctypes.byref(k)),
+               "cqrrpt_last_status")
+        return st.value, k.value
+
+
+_default = {}
+
+
+def default_handle():
+    dev = torch.cuda.current_device()
+    if dev not in _default:
+        _default[dev] = Handle(dev)
+    return _default[dev]
+
+
+def sketch_dim(n, gamma):
+    return int(lib().cqrrpt_sketch_dim(n, gamma))
+
+
+def workspace_size(m, n, gamma=1.25, nnz=4, precision=FP64):
+    b = ctypes.c_size_t()
+    _check(lib().cqrrpt_workspace_size(m, n, gamma, nnz, precision, ctypes.byref(b)),
+           "cqrrpt_workspace_size")
+    return b.value
+
+
+class Factorization:
+    """Q (m x k), R (k x n), J (n pivots), k, status; Qbuf/Rbuf hold the
+    full-capacity output buffers."""
+
+    def __init__(self, Qbuf, Rbuf, J, k, status):
+        self.Qbuf, self.Rbuf, self.J, self.k, self.status = Qbuf, Rbuf, J, k, status
+
+    @property
+    def Q(self):
+        return self.Qbuf[:, : self.k]
+
+    @property
+    def R(self):
+        return self.Rbuf[: self.k, :]
+
+
+def cqrrpt(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64, out=None, handle=None,
+           stream=None, sync=True, k_dev=None):
+    """Alg. 1 + Alg. 2 on the GPU.  A: m x n column-major float64 CUDA
+    tensor.  With sync=True waits and returns the final k and status; with
+    sync=False returns immediately (k and status are then None; read them
+    with handle.last_status())."""
+    h = handle or default_handle()
+    m, n = A.shape
+    lda = _ld(A)
+    if out is None:
+        Q = colmajor_empty(m, n, A.device)
+        R = colmajor_empty(n, n, A.device)
+        J = torch.empty(n, dtype=torch.int64, device=A.device)
+    else:
+        Q, R, J = out
+    k = _i64()
+    rc = lib().cqrrpt_d(h.h, m, n, A.data_ptr(), lda, gamma, nnz, tol, seed, precision,
+                        Q.data_ptr(), _ld(Q), R.data_ptr(), _ld(R), J.data_ptr(),
+                        None if k_dev is None else k_dev.data_ptr(),
+                        ctypes.byref(k) if sync else None, _stream(stream))
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_d")
+    if not sync:
+        return Factorization(Q, R, J, None, None)
+    return Factorization(Q, R, J, k.value, rc)
+
+
+def sketch(A, d, nnz, seed, handle=None, stream=None):
+    h = handle or default_handle()
+    m, n = A.shape
+    out = colmajor_empty(d, n, A.device)
+    _check(lib().cqrrpt_sketch_d(h.h, m, n, A.data_ptr(), _ld(A), d, nnz, seed, out.data_ptr(),
+                                 _ld(out), _stream(stream)), "cqrrpt_sketch_d")
+    return out
+
+
+def qrcp(X, handle=None, stream=None):
+    """QRCP of X (d x n, overwritten).  Returns (Rsk n x n, J)."""
+    h = handle or default_handle()
+    d, n = X.shape
+    J = torch.empty(n, dtype=torch.int64, device=X.device)
+    Rsk = colmajor_empty(n, n, X.device)
+    _check(lib().cqrrpt_qrcp_d(h.h, d, n, X.data_ptr(), _ld(X), J.data_ptr(), Rsk.data_ptr(),
+                               _ld(Rsk), _stream(stream)), "cqrrpt_qrcp_d")
+    return Rsk, J
+
+
+def rank(Rsk, tol, handle=None, stream=None):
+    h = handle or default_handle()
+    k = torch.zeros(1, dtype=torch.int64, device=Rsk.device)
+    _check(lib().cqrrpt_rank_d(h.h, Rsk.shape[1], Rsk.data_ptr(), _ld(Rsk), tol, k.data_ptr(),
+                               _stream(stream)), "cqrrpt_rank_d")
+    return k
+
+
+def trsm(B, T, cols=None, out=None, handle=None, stream=None):
+    """X = B[:, cols] T^{-1} (T upper triangular k x k)."""
+    h = handle or default_handle()
+    m = B.shape[0]
+    k = T.shape[0]
+    X = colmajor_empty(m, k, B.device) if out is None else out
+    _check(lib().cqrrpt_trsm_d(h.h, m, k, B.data_ptr(), _ld(B),
+                               None if cols is None else cols.data_ptr(), T.data_ptr(), _ld(T),
+                               X.data_ptr(), _ld(X), _stream(stream)), "cqrrpt_trsm_d")
+    return X
+
+
+def gram(X, handle=None, stream=None):
+    h = handle or default_handle()
+    m, k = X.shape
+    G = colmajor_empty(k, k, X.device)
+    _check(lib().cqrrpt_gram_d(h.h, m, k, X.data_ptr(), _ld(X), G.data_ptr(), _ld(G),
+                               _stream(stream)), "cqrrpt_gram_d")
+    return G
+
+
+def potrf(G, handle=None, stream=None):
+    """Upper Cholesky of G (G is overwritten).  Returns (R, fail tensor)."""
+    h = handle or default_handle()
+    k = G.shape[0]
+    R = torch.zeros((k, k), dtype=torch.float64, device=G.device).t()
+    fail = torch.empty(1, dtype=torch.int64, device=G.device)
+    _check(lib().cqrrpt_potrf_d(h.h, k, G.data_ptr(), _ld(G), R.data_ptr(), _ld(R),
+                                fail.data_ptr(), _stream(stream)), "cqrrpt_potrf_d")
+    return R, fail
+
+
+def trmm(Rpre, Rsk_k, handle=None, stream=None):
+    h = handle or default_handle()
+    k, n = Rsk_k.shape
+    R = colmajor_empty(k, n, Rpre.device)
+    _check(lib().cqrrpt_trmm_d(h.h, k, n, Rpre.data_ptr(), _ld(Rpre), Rsk_k.data_ptr(),
+                               _ld(Rsk_k), R.data_ptr(), _ld(R), _stream(stream)), "cqrrpt_trmm_d")
+    return R
+
+
+def philox4x32_10(ctr, key):
+    """The library's Philox block (host code path, no GPU needed)."""
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    kk = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().cqrrpt_philox4x32_10(c, kk, o)
+    return list(o)
+
+
+def saso_column(seed, r, d, nnz):
+    rows = (ctypes.c_int32 * nnz)()
+    neg = (ctypes.c_uint8 * nnz)()
+    lib().cqrrpt_saso_column(seed, r, d, nnz, rows, neg)
+    return list(rows), list(neg)

@@ -1,0 +1,378 @@
+// C ABI of the CQRRPT library (declared in include/cqrrpt.h): argument
+// checking, workspace planning and the stream-ordered pipeline of Alg. 2.
+// No entry point synchronises unless it is given a host output pointer.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/cqrrpt.h"
+#include "kernels.h"
+#include "saso.cuh"
+
+using namespace cqrrpt;
+
+struct cqrrpt_ctx {
+  int device = 0;
+  int num_sms = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  DeviceScalars* sc = nullptr;  // per-call device scalars
+  int64_t* pinned = nullptr;    // host-pinned readback (k, status)
+};
+
+namespace {
+
+struct Plan {
+  int64_t d, nb;
+  size_t region, x, qrcp, rsk, g, rpre, f2, total;
+};
+
+Plan plan_fp64(int64_t m, int64_t n, int64_t d, int nnz) {
+  Plan p;
+  p.d = d;
+  p.nb = (m + kRowBlock - 1) / kRowBlock;
+  const int64_t a = sketch_workspace_bytes(m, n, (int)d, nnz);
+  const int64_t b = gram_workspace_bytes(m, n);
+  p.region = (size_t)(a > b ? a : b);
+  p.x = (size_t)align256(d * n * 8);
+  p.qrcp = (size_t)qrcp_workspace_bytes(n);
+  p.rsk = (size_t)align256(n * n * 8);
+  p.g = p.rsk;
+  p.rpre = p.rsk;
+  p.f2 = (size_t)align256((n + 1) * 8);
+  p.total = p.region + p.x + p.qrcp + p.rsk + p.g + p.rpre + p.f2;
+  return p;
+}
+
+int ensure_ws(cqrrpt_handle h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return kOk;
+  if (h->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return kNoMemory;
+  }
+  h->ws_bytes = bytes;
+  return kOk;
+}
+
+int64_t sketch_dim(int64_t n, double gamma) { return (int64_t)std::ceil(gamma * (double)n); }
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+__global__ void copy_k_kernel(const DeviceScalars* sc, int64_t* out) { *out = sc->k; }
+__global__ void copy_fail_kernel(const DeviceScalars* sc, int64_t* out) { *out = sc->fail; }
+
+}  // namespace
+
+extern "C" {
+
+int cqrrpt_create(cqrrpt_handle* h, int device) {
+  if (!h) return -1;
+  *h = nullptr;
+  DevGuard g(device);
+  cqrrpt_ctx* c = new (std::nothrow) cqrrpt_ctx();
+  if (!c) return kNoMemory;
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&c->sc, sizeof(DeviceScalars)) != cudaSuccess ||
+      cudaMallocHost(&c->pinned, 64) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->sc) cudaFree(c->sc);
+    delete c;
+    return kCudaError;
+  }
+  cudaMemset(c->sc, 0, sizeof(DeviceScalars));
+  cudaDeviceSynchronize();
+  *h = c;
+  return kOk;
+}
+
+int cqrrpt_destroy(cqrrpt_handle h) {
+  if (!h) return -1;
+  DevGuard g(h->device);
+  cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->sc) cudaFree(h->sc);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  delete h;
+  return kOk;
+}
+
+int cqrrpt_workspace_size(int64_t m, int64_t n, double gamma, int nnz, int precision,
+                          size_t* bytes) {
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (!(gamma >= 1.0)) return -3;
+  const int64_t d = sketch_dim(n, gamma);
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -4;
+  if (precision != CQRRPT_FP64) return -5;
+  if (!bytes) return -6;
+  *bytes = plan_fp64(m, n, d, nnz).total;
+  return kOk;
+}
+
+int cqrrpt_reserve(cqrrpt_handle h, size_t bytes) {
+  if (!h) return -1;
+  DevGuard g(h->device);
+  return ensure_ws(h, bytes);
+}
+
+int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, double gamma,
+             int nnz, double tol, uint64_t seed, int precision, double* Q, int64_t ldq, double* R,
+             int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 16384) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -6;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -6;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
+  if (std::isnan(tol)) return -8;
+  if (precision != CQRRPT_FP64) return -10;
+  if (!Q) return -11;
+  if (ldq < m) return -12;
+  if (!R) return -13;
+  if (ldr < n) return -14;
+  if (!J) return -15;
+
+  DevGuard g(h->device);
+  const Plan p = plan_fp64(m, n, d, nnz);
+  int st = ensure_ws(h, p.total);
+  if (st != kOk) return st;
+  char* w = (char*)h->ws;
+  void* region = w; w += p.region;
+  double* X = (double*)w; w += p.x;
+  void* qw = w; w += p.qrcp;
+  double* Rsk = (double*)w; w += p.rsk;
+  double* G = (double*)w; w += p.g;
+  double* Rpre = (double*)w; w += p.rpre;
+  double* f2 = (double*)w;
+  DeviceScalars* sc = h->sc;
+  int* status = &sc->status;
+  const int ni = (int)n, di = (int)d;
+  const double scale = 1.0 / std::sqrt((double)nnz);
+
+  cudaError_t e = launch_init_scalars(sc, 0, stream);
+  if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
+  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
+  if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
+  if (e == cudaSuccess)
+    e = launch_trsm_rut(m, ni, &sc->k, A, lda, J, Rsk, n, Q, ldq, status, stream);
+  if (e == cudaSuccess) e = launch_gram(m, ni, &sc->k, Q, ldq, G, n, region, status, stream);
+  if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, n, sc, stream);
+  if (e == cudaSuccess) e = launch_rank_stage2(Rpre, n, !(tol > 0.0), sc, stream);
+  if (e == cudaSuccess)
+    e = launch_trsm_rut(m, ni, &sc->k, Q, ldq, nullptr, Rpre, n, Q, ldq, status, stream);
+  if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, Rsk, n, R, ldr, status, stream);
+  if (e == cudaSuccess) e = launch_finalize(sc, k_dev, nullptr, stream);
+  if (e != cudaSuccess) return kCudaError;
+  if (k_host) {
+    int st2 = kOk;
+    int64_t kk = 0;
+    int r = cqrrpt_last_status(h, stream, &st2, &kk);
+    if (r != kOk) return r;
+    *k_host = kk;
+    return st2;
+  }
+  return kOk;
+}
+
+int cqrrpt_last_status(cqrrpt_handle h, cudaStream_t stream, int* status_host, int64_t* k_host) {
+  if (!h) return -1;
+  DevGuard g(h->device);
+  int64_t* pk = h->pinned;
+  int* ps = (int*)(h->pinned + 1);
+  if (launch_finalize(h->sc, pk, ps, stream) != cudaSuccess) return kCudaError;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return kCudaError;
+  if (status_host) *status_host = *ps;
+  if (k_host) *k_host = *pk;
+  return kOk;
+}
+
+const char* cqrrpt_status_string(int status) {
+  switch (status) {
+    case kOk: return "success";
+    case kRankZero: return "numerical rank is zero";
+    case kNonFinite: return "non-finite values in the input (sketch)";
+    case kCudaError: return "CUDA error";
+    case kNoMemory: return "out of device memory";
+    case kTimeout: return "device-side wait timed out";
+    default: return status < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+int cqrrpt_sketch_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                    int64_t d, int nnz, uint64_t seed, double* Ask, int64_t ldsk,
+                    cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (d < 1 || d > 28000) return -6;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
+  if (!Ask) return -9;
+  if (ldsk < d) return -10;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)sketch_workspace_bytes(m, n, (int)d, nnz));
+  if (st != kOk) return st;
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  if (launch_sketch(m, n, A, lda, (int)d, nnz, seed, 1.0 / std::sqrt((double)nnz), Ask, ldsk,
+                    h->ws, &h->sc->status, stream) != cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int cqrrpt_qrcp_d(cqrrpt_handle h, int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J,
+                  double* Rsk, int64_t ldr, cudaStream_t stream) {
+  if (!h) return -1;
+  if (d < 1) return -2;
+  if (n < 1 || n > d || n > 16384) return -3;
+  if (!X) return -4;
+  if (ldx < d) return -5;
+  if (!J) return -6;
+  if (!Rsk) return -7;
+  if (ldr < n) return -8;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)qrcp_workspace_bytes(n));
+  if (st != kOk) return st;
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  if (launch_qrcp((int)d, (int)n, X, ldx, J, Rsk, ldr, h->ws, h->sc, h->num_sms, stream) !=
+      cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int cqrrpt_rank_d(cqrrpt_handle h, int64_t n, const double* Rsk, int64_t ldr, double tol,
+                  int64_t* k_dev, cudaStream_t stream) {
+  if (!h) return -1;
+  if (n < 1 || n > 16384) return -2;
+  if (!Rsk) return -3;
+  if (ldr < n) return -4;
+  if (std::isnan(tol)) return -5;
+  if (!k_dev) return -6;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)align256((n + 1) * 8));
+  if (st != kOk) return st;
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  if (launch_rank((int)n, Rsk, ldr, tol, h->sc, (double*)h->ws, stream) != cudaSuccess)
+    return kCudaError;
+  copy_k_kernel<<<1, 1, 0, stream>>>(h->sc, k_dev);
+  return cudaGetLastError() == cudaSuccess ? kOk : kCudaError;
+}
+
+int cqrrpt_trsm_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, int64_t ldb,
+                  const int64_t* cols, const double* T, int64_t ldt, double* X, int64_t ldx,
+                  cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (k < 1 || k > 16384) return -3;
+  if (!B) return -4;
+  if (ldb < m) return -5;
+  if (!T) return -7;
+  if (ldt < k) return -8;
+  if (!X) return -9;
+  if (ldx < m) return -10;
+  DevGuard g(h->device);
+  if (launch_init_scalars(h->sc, k, stream) != cudaSuccess) return kCudaError;
+  if (launch_trsm_rut(m, (int)k, &h->sc->k, B, ldb, cols, T, ldt, X, ldx, &h->sc->status,
+                      stream) != cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int cqrrpt_gram_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_t ldx, double* G,
+                  int64_t ldg, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (k < 1 || k > 16384) return -3;
+  if (!X) return -4;
+  if (ldx < m) return -5;
+  if (!G) return -6;
+  if (ldg < k) return -7;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)gram_workspace_bytes(m, k));
+  if (st != kOk) return st;
+  if (launch_init_scalars(h->sc, k, stream) != cudaSuccess) return kCudaError;
+  if (launch_gram(m, (int)k, &h->sc->k, X, ldx, G, ldg, h->ws, &h->sc->status, stream) !=
+      cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R, int64_t ldr,
+                   int64_t* fail_dev, cudaStream_t stream) {
+  if (!h) return -1;
+  if (k < 1 || k > 16384) return -2;
+  if (!G) return -3;
+  if (ldg < k) return -4;
+  if (!R) return -5;
+  if (ldr < k) return -6;
+  DevGuard g(h->device);
+  if (launch_init_scalars(h->sc, k, stream) != cudaSuccess) return kCudaError;
+  if (launch_potrf((int)k, G, ldg, R, ldr, h->sc, stream) != cudaSuccess) return kCudaError;
+  if (fail_dev) {
+    copy_fail_kernel<<<1, 1, 0, stream>>>(h->sc, fail_dev);
+    if (cudaGetLastError() != cudaSuccess) return kCudaError;
+  }
+  return kOk;
+}
+
+int cqrrpt_trmm_d(cqrrpt_handle h, int64_t k, int64_t n, const double* Rpre, int64_t ldp,
+                  const double* Rsk, int64_t ldsk, double* R, int64_t ldr, cudaStream_t stream) {
+  if (!h) return -1;
+  if (k < 1) return -2;
+  if (n < k || n > 16384) return -3;
+  if (!Rpre) return -4;
+  if (ldp < k) return -5;
+  if (!Rsk) return -6;
+  if (ldsk < k) return -7;
+  if (!R) return -8;
+  if (ldr < k) return -9;
+  DevGuard g(h->device);
+  if (launch_init_scalars(h->sc, k, stream) != cudaSuccess) return kCudaError;
+  if (launch_trmm((int)n, &h->sc->k, Rpre, ldp, Rsk, ldsk, R, ldr, &h->sc->status, stream) !=
+      cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int64_t cqrrpt_sketch_dim(int64_t n, double gamma) { return sketch_dim(n, gamma); }
+
+void cqrrpt_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const Philox4 r = philox4x32_10(ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1]);
+  for (int i = 0; i < 4; ++i) out[i] = r.v[i];
+}
+
+void cqrrpt_saso_column(uint64_t seed, int64_t r, int64_t d, int nnz, int32_t* rows,
+                        uint8_t* neg) {
+  int tr[kMaxNnzInline];
+  uint32_t bits = 0;
+  if (nnz < 1 || nnz > kMaxNnzInline || nnz > d) return;
+  saso_column(seed, r, (int)d, nnz, tr, &bits);
+  for (int q = 0; q < nnz; ++q) {
+    rows[q] = tr[q];
+    neg[q] = (uint8_t)((bits >> q) & 1u);
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,398 @@
+// Alg. 2 lines 2-3: column-pivoted Householder QR of the d x n sketch
+// (Businger-Golub max-norm pivoting, as LAPACK GEQP3 which the paper uses,
+// Sec. 3.2 and Appendix A.1) and the rank rule of Sec. 4.3.
+//
+// qrcp_kernel is one cooperative, persistent launch of G CTAs.  Physical
+// columns never move: CTA b owns the physical columns b, b+G, b+2G, ... for
+// the whole factorisation (one warp per column) and a position <-> column
+// map (phys/posof) records the swaps, so a pivot exchange moves no data.
+// Each of the n steps is:
+//   1. every CTA reduces the per-CTA candidates (largest partial norm,
+//      lowest position on exact ties) to the same pivot column P;
+//   2. the owner of P forms the reflector H = I - tau v v^T (v written over
+//      the column below the diagonal, beta on it); CTA 0 records the swap;
+//      -- grid barrier --
+//   3. every CTA applies H to its unpivoted columns (w = v^T x by dot32,
+//      x += v (-tau w) with one fma per element) and downdates their norms
+//      (LAPACK dlaqp2 rule with the Drmac-Bujanovic recompute safeguard),
+//      then publishes its candidate;  -- grid barrier --
+// All reads of data written by other CTAs bypass L1 (ld.global.cg).
+// Grid barriers spin a bounded number of times (status kTimeout on expiry).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cqrrpt {
+
+struct QrcpWork {
+  double* vn1;
+  double* vn2;
+  double* tau;
+  int* phys;
+  int* posof;
+  double* cand_val;
+  int* cand_pos;
+  int* cand_col;
+};
+
+static QrcpWork carve_qrcp(void* work, int n) {
+  char* p = (char*)work;
+  QrcpWork w;
+  w.vn1 = (double*)p; p += align256((int64_t)n * 8);
+  w.vn2 = (double*)p; p += align256((int64_t)n * 8);
+  w.tau = (double*)p; p += align256((int64_t)n * 8);
+  w.phys = (int*)p; p += align256((int64_t)n * 4);
+  w.posof = (int*)p; p += align256((int64_t)n * 4);
+  w.cand_val = (double*)p; p += align256(4096 * 8);
+  w.cand_pos = (int*)p; p += align256(4096 * 4);
+  w.cand_col = (int*)p; p += align256(4096 * 4);
+  return w;
+}
+
+int64_t qrcp_workspace_bytes(int64_t n) {
+  return 3 * align256(n * 8) + 2 * align256(n * 4) + align256(4096 * 8) + 2 * align256(4096 * 4);
+}
+
+// dot32 of x[0..len) with itself, by one warp (result in every lane).
+__device__ __forceinline__ double warp_dot32_self(const double* x, int len) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int i = lane; i < len; i += 32) {
+    const double v = __ldcg(x + i);
+    acc = __fma_rn(v, v, acc);
+  }
+  return warp_tree_sum32(acc);
+}
+
+// candidate order: larger value first, then lower position
+__device__ __forceinline__ bool cand_better(double va, int pa, double vb, int pb) {
+  return va > vb || (va == vb && pa < pb);
+}
+
+__global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(int d, int n, double* X, int64_t ldx,
+                                                            QrcpWork w, DeviceScalars* sc,
+                                                            double tol3z) {
+  const int G = gridDim.x, bid = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  int* status = &sc->status;
+  __shared__ int sh_P, sh_p;
+  __shared__ double sh_tau, sh_beta, sh_denom;
+  __shared__ int sh_nz;
+  __shared__ double red_val[kQrcpThreads / 32];
+  __shared__ int red_pos[kQrcpThreads / 32];
+  __shared__ int red_col[kQrcpThreads / 32];
+
+  if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
+
+  // initial norms of owned columns
+  for (int q = warp;; q += nwarps) {
+    const int c = bid + G * q;
+    if (c >= n) break;
+    const double s = warp_dot32_self(X + (int64_t)c * ldx, d);
+    if (lane == 0) {
+      const double v = __dsqrt_rn(s);
+      w.vn1[c] = v;
+      w.vn2[c] = v;
+      w.phys[c] = c;
+      w.posof[c] = c;
+    }
+  }
+
+  auto publish_candidate = [&](int j_done) {
+    // best owned column with position > j_done
+    double bv = -1.0;
+    int bp = 0x7fffffff, bc = -1;
+    for (int q = warp;; q += nwarps) {
+      const int c = bid + G * q;
+      if (c >= n) break;
+      const int pc = __ldcg(w.posof + c);
+      if (pc <= j_done) continue;
+      const double v = __ldcg(w.vn1 + c);
+      if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bc = c; }
+    }
+    if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 1; i < nwarps; ++i)
+        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bc = red_col[i]; }
+      w.cand_val[bid] = bv;
+      w.cand_pos[bid] = bp;
+      w.cand_col[bid] = bc;
+    }
+  };
+  // lane 0 of each warp holds its warp's best only; redo per-warp reduction
+  // inside publish: each lane of the warp scanned the same columns, so all
+  // lanes agree and lane 0's copy is representative.
+  __syncthreads();
+  publish_candidate(-1);
+  if (!grid_sync(&sc->bar, G, status)) return;
+
+  for (int j = 0; j < n; ++j) {
+    // 1. global pivot
+    if (warp == 0) {
+      double bv = -1.0;
+      int bp = 0x7fffffff, bc = -1;
+      for (int i = lane; i < G; i += 32) {
+        const double v = __ldcg(w.cand_val + i);
+        const int p = __ldcg(w.cand_pos + i);
+        const int c = __ldcg(w.cand_col + i);
+        if (c >= 0 && cand_better(v, p, bv, bp)) { bv = v; bp = p; bc = c; }
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int op = __shfl_down_sync(0xffffffffu, bp, off);
+        const int oc = __shfl_down_sync(0xffffffffu, bc, off);
+        if (oc >= 0 && cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+      }
+      if (lane == 0) { sh_P = bc; sh_p = bp; }
+    }
+    __syncthreads();
+    const int P = sh_P, p = sh_p;
+    if (P < 0) {
+      // no finite candidate anywhere (overflow to Inf/NaN inside the
+      // factorisation); every CTA sees the same P and leaves together
+      if (bid == 0 && threadIdx.x == 0) atomicExch(status, kNonFinite);
+      return;
+    }
+    double* colP = X + (int64_t)P * ldx;
+    // 2. reflector by the owner of P; swap record by CTA 0
+    if (P % G == bid) {
+      if (warp == 0) {
+        const double alpha = __ldcg(colP + j);
+        const double sumsq = (j + 1 < d) ? warp_dot32_self(colP + j + 1, d - j - 1) : 0.0;
+        if (lane == 0) {
+          if (sumsq == 0.0) {
+            sh_tau = 0.0;
+            sh_nz = 0;
+          } else {
+            const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
+            const double beta = (alpha >= 0.0) ? -nrm : nrm;
+            sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
+            sh_beta = beta;
+            sh_denom = __dsub_rn(alpha, beta);
+            sh_nz = 1;
+          }
+        }
+      }
+      __syncthreads();
+      if (sh_nz) {
+        const double denom = sh_denom;
+        for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x)
+          colP[r] = __ddiv_rn(__ldcg(colP + r), denom);
+        if (threadIdx.x == 0) colP[j] = sh_beta;
+      }
+      if (threadIdx.x == 0) w.tau[j] = sh_tau;
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+      const int Pj = __ldcg(w.phys + j);
+      w.phys[p] = Pj;
+      w.posof[Pj] = p;
+      w.phys[j] = P;
+      w.posof[P] = j;
+    }
+    if (!grid_sync(&sc->bar, G, status)) return;
+
+    // 3. apply H to owned unpivoted columns, downdate norms
+    const double tau = __ldcg(w.tau + j);
+    const int len = d - j;
+    for (int q = warp;; q += nwarps) {
+      const int c = bid + G * q;
+      if (c >= n) break;
+      if (__ldcg(w.posof + c) <= j) continue;
+      double* colc = X + (int64_t)c * ldx + j;
+      double acc = 0.0;
+      for (int i = lane; i < len; i += 32) {
+        const double vi = (i == 0) ? 1.0 : __ldcg(colP + j + i);
+        acc = __fma_rn(vi, __ldcg(colc + i), acc);
+      }
+      const double wsum = warp_tree_sum32(acc);
+      const double t = __dmul_rn(-tau, wsum);
+      for (int i = lane; i < len; i += 32) {
+        const double vi = (i == 0) ? 1.0 : __ldcg(colP + j + i);
+        colc[i] = __fma_rn(vi, t, __ldcg(colc + i));
+      }
+      __syncwarp();
+      const double v1 = __ldcg(w.vn1 + c);
+      if (v1 != 0.0) {
+        const double v2 = __ldcg(w.vn2 + c);
+        double temp = __ddiv_rn(fabs(__ldcg(colc)), v1);
+        temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
+        temp = temp > 0.0 ? temp : 0.0;
+        const double ratio = __ddiv_rn(v1, v2);
+        const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
+        if (temp2 <= tol3z) {
+          const double s = (j + 1 < d) ? warp_dot32_self(colc + 1, d - j - 1) : 0.0;
+          if (lane == 0) {
+            const double nv = (j + 1 < d) ? __dsqrt_rn(s) : 0.0;
+            w.vn1[c] = nv;
+            w.vn2[c] = nv;
+          }
+        } else if (lane == 0) {
+          w.vn1[c] = __dmul_rn(v1, __dsqrt_rn(temp));
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    publish_candidate(j);
+    if (!grid_sync(&sc->bar, G, status)) return;
+  }
+}
+
+// R^sk[i, q] = s_i X[i, phys[q]] for i <= q < n (0 below), s_i = -1 when the
+// diagonal X[i, phys[i]] is negative; J[q] = phys[q].
+__global__ void qrcp_gather_kernel(int n, const double* X, int64_t ldx, const int* phys,
+                                   int64_t* J, double* Rsk, int64_t ldr, const int* status) {
+  const int q = blockIdx.x;
+  if (*status != kOk) return;
+  const int pq = phys[q];
+  if (threadIdx.x == 0) J[q] = pq;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = 0.0;
+    if (i <= q) {
+      const double diag = X[(int64_t)phys[i] * ldx + i];
+      v = X[(int64_t)pq * ldx + i];
+      if (diag < 0.0) v = -v;
+    }
+    Rsk[(int64_t)q * ldr + i] = v;
+  }
+}
+
+cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double* Rsk,
+                        int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
+                        cudaStream_t stream) {
+  QrcpWork w = carve_qrcp(work, n);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, kQrcpThreads, 0);
+  if (e != cudaSuccess) return e;
+  int G = (n + 7) / 8;
+  if (G > num_sms * per_sm) G = num_sms * per_sm;
+  if (G > num_sms) G = num_sms;
+  if (G > 4096) G = 4096;
+  if (G < 1) G = 1;
+  const double tol3z = sqrt(ldexp(1.0, -53));
+  void* args[] = {&d, &n, &X, &ldx, &w, &sc, (void*)&tol3z};
+  e = cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(G), dim3(kQrcpThreads), args, 0,
+                                  stream);
+  if (e != cudaSuccess) return e;
+  qrcp_gather_kernel<<<n, 128, 0, stream>>>(n, X, ldx, w.phys, J, Rsk, ldr, &sc->status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rank (Sec. 4.3).  tol > 0: k = number of leading j with R_jj > tol R_00.
+// tol <= 0: stage 1, k_o = min{l : ||C_l||_F <= u max|R|}, with
+// ||C_l||^2 = ||R[l, l:]||^2 + ||C_{l+1}||^2 (row sums ascending by fma).
+// ---------------------------------------------------------------------------
+__global__ void rank_kernel(int n, const double* Rsk, int64_t ldr, double tol, DeviceScalars* sc,
+                            double* f2 /* n + 1 */) {
+  __shared__ double sh_max[1024];
+  __shared__ int sh_k;
+  if (sc->status != kOk) {
+    if (threadIdx.x == 0) sc->k = 0;
+    return;
+  }
+  if (tol > 0.0) {
+    if (threadIdx.x == 0) sh_k = n;
+    __syncthreads();
+    const double thresh = __dmul_rn(tol, Rsk[0]);
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      if (!(Rsk[(int64_t)j * ldr + j] > thresh)) atomicMin(&sh_k, j);
+    __syncthreads();
+    if (threadIdx.x == 0) sc->k = sh_k;
+    return;
+  }
+  // stage 1
+  double mx = 0.0;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    double rs = 0.0;
+    for (int c = l; c < n; ++c) {
+      const double v = Rsk[(int64_t)c * ldr + l];
+      rs = __fma_rn(v, v, rs);
+      const double a = fabs(v);
+      mx = a > mx ? a : mx;
+    }
+    f2[l] = rs;
+  }
+  sh_max[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double smax = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) smax = sh_max[i] > smax ? sh_max[i] : smax;
+    const double thresh = __dmul_rn(ldexp(1.0, -53), smax);
+    // suffix sums f2[l] = f2[l+1] + rs_l
+    double acc = 0.0;
+    f2[n] = 0.0;
+    for (int l = n - 1; l >= 0; --l) {
+      acc = __dadd_rn(acc, f2[l]);
+      f2[l] = acc;
+    }
+    int ko = n;
+    for (int l = 0; l <= n; ++l)
+      if (__dsqrt_rn(f2[l]) <= thresh) { ko = l; break; }
+    sc->k = ko;
+  }
+}
+
+cudaError_t launch_rank(int n, const double* Rsk, int64_t ldr, double tol, DeviceScalars* sc,
+                        double* f2, cudaStream_t stream) {
+  rank_kernel<<<1, 1024, 0, stream>>>(n, Rsk, ldr, tol, sc, f2);
+  return cudaGetLastError();
+}
+
+// Stage 2: k := min(k, fail) (Remark 3), then if requested the largest
+// l <= k with max/min of diag(R^pre)[0:l] <= 10.
+__global__ void rank_stage2_kernel(const double* Rpre, int64_t ldp, int stage2, DeviceScalars* sc) {
+  if (sc->status != kOk) { sc->k = 0; return; }
+  int64_t k = sc->k;
+  if (sc->fail >= 0 && sc->fail < k) k = sc->fail;
+  if (stage2 && k > 0) {
+    int64_t kk = 0;
+    double mx = 0.0, mn = 0.0;
+    for (int64_t l = 1; l <= k; ++l) {
+      const double dl = Rpre[(l - 1) * ldp + (l - 1)];
+      if (l == 1) { mx = dl; mn = dl; }
+      else { mx = dl > mx ? dl : mx; mn = dl < mn ? dl : mn; }
+      if (__ddiv_rn(mx, mn) <= 10.0) kk = l; else break;
+    }
+    k = kk;
+  }
+  sc->k = k;
+}
+
+cudaError_t launch_rank_stage2(const double* Rpre, int64_t ldp, bool stage2, DeviceScalars* sc,
+                               cudaStream_t stream) {
+  rank_stage2_kernel<<<1, 1, 0, stream>>>(Rpre, ldp, stage2 ? 1 : 0, sc);
+  return cudaGetLastError();
+}
+
+__global__ void init_scalars_kernel(DeviceScalars* sc, int64_t k) {
+  sc->k = k;
+  sc->fail = -1;
+  sc->status = kOk;
+  sc->pad = 0;
+  sc->bar.count = 0;
+  sc->bar.generation = 0;
+}
+
+cudaError_t launch_init_scalars(DeviceScalars* sc, int64_t k, cudaStream_t stream) {
+  init_scalars_kernel<<<1, 1, 0, stream>>>(sc, k);
+  return cudaGetLastError();
+}
+
+__global__ void finalize_kernel(DeviceScalars* sc, int64_t* k_out, int* status_out) {
+  int st = sc->status;
+  if (st == kOk && sc->k == 0) st = kRankZero;
+  if (st != kOk && st != kRankZero) sc->k = 0;
+  if (k_out) *k_out = sc->k;
+  if (status_out) *status_out = st;
+}
+
+cudaError_t launch_finalize(DeviceScalars* sc, int64_t* k_out, int* status_out,
+                            cudaStream_t stream) {
+  finalize_kernel<<<1, 1, 0, stream>>>(sc, k_out, status_out);
+  return cudaGetLastError();
+}
+
+}  // namespace cqrrpt

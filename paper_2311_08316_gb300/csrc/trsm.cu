@@ -1,0 +1,90 @@
+// Alg. 2 lines 4 and 7: X = B[:, cols] T^{-1} with T upper triangular
+// (k x k), by row-wise substitution:
+//   X[i, j] = (B[i, cols[j]] - sum_{t<j} X[i, t] T[t, j]) / T[j, j],
+// the sum in ascending t with one fma per term.  Line 4 uses the pivot
+// gather cols = J[0:k] and T = R^sk_11 (M^pre = M_k (A^sk_k)^{-1}); line 7
+// runs in place with cols = identity and T = R^pre (Q_k = M^pre (R^pre)^{-1}).
+//
+// One thread owns one row i.  Columns are solved in register blocks of
+// kTrsmJB: the block's partial sums are seeded with B, then receive the
+// terms t < j0 chunk by chunk (kTrsmTB rows of T staged in shared memory,
+// X[i, t] re-read from the thread's own, already solved row), then the
+// triangular part of the block in ascending t.  Every partial sum therefore
+// receives its terms in ascending t, so the result does not depend on the
+// blocking.  The kernel is bound by the FP64 pipe (one DFMA per term).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cqrrpt {
+
+__global__ void __launch_bounds__(kTrsmThreads) trsm_rut_kernel(
+    int64_t m, const int64_t* __restrict__ k_dev, const double* B, int64_t ldb,
+    const int64_t* __restrict__ cols, const double* __restrict__ T, int64_t ldt, double* X,
+    int64_t ldx, const int* __restrict__ status) {
+  __shared__ double Ts[kTrsmTB][kTrsmJB];
+  __shared__ double Td[kTrsmJB][kTrsmJB];
+  if (*status != kOk) return;
+  const int k = (int)*k_dev;
+  const int64_t i = blockIdx.x * (int64_t)kTrsmThreads + threadIdx.x;
+  const bool active = i < m;
+  for (int j0 = 0; j0 < k; j0 += kTrsmJB) {
+    const int jb = min(kTrsmJB, k - j0);
+    double s[kTrsmJB];
+#pragma unroll
+    for (int jj = 0; jj < kTrsmJB; ++jj) {
+      s[jj] = 0.0;
+      if (active && jj < jb) {
+        const int64_t bc = cols ? cols[j0 + jj] : (int64_t)(j0 + jj);
+        s[jj] = B[bc * ldb + i];
+      }
+    }
+    // terms t < j0
+    for (int t0 = 0; t0 < j0; t0 += kTrsmTB) {
+      const int tb = min(kTrsmTB, j0 - t0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < kTrsmTB * kTrsmJB; e += kTrsmThreads) {
+        const int tt = e / kTrsmJB, jj = e % kTrsmJB;
+        Ts[tt][jj] = (tt < tb && jj < jb) ? T[(int64_t)(j0 + jj) * ldt + (t0 + tt)] : 0.0;
+      }
+      __syncthreads();
+      if (active) {
+        for (int tt = 0; tt < tb; ++tt) {
+          const double x = -X[(int64_t)(t0 + tt) * ldx + i];
+#pragma unroll
+          for (int jj = 0; jj < kTrsmJB; ++jj) s[jj] = __fma_rn(x, Ts[tt][jj], s[jj]);
+        }
+      }
+    }
+    // triangular block
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTrsmJB * kTrsmJB; e += kTrsmThreads) {
+      const int tt = e / kTrsmJB, jj = e % kTrsmJB;
+      Td[tt][jj] = (tt < jb && jj < jb) ? T[(int64_t)(j0 + jj) * ldt + (j0 + tt)] : 1.0;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int jj = 0; jj < kTrsmJB; ++jj) {
+        if (jj < jb) {
+          const double x = __ddiv_rn(s[jj], Td[jj][jj]);
+          X[(int64_t)(j0 + jj) * ldx + i] = x;
+          const double nx = -x;
+#pragma unroll
+          for (int j2 = jj + 1; j2 < kTrsmJB; ++j2) s[j2] = __fma_rn(nx, Td[jj][j2], s[j2]);
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_trsm_rut(int64_t m, int kmax, const int64_t* k_dev, const double* B,
+                            int64_t ldb, const int64_t* cols, const double* T, int64_t ldt,
+                            double* X, int64_t ldx, const int* status, cudaStream_t stream) {
+  (void)kmax;
+  const unsigned grid = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
+  trsm_rut_kernel<<<grid, kTrsmThreads, 0, stream>>>(m, k_dev, B, ldb, cols, T, ldt, X, ldx,
+                                                     status);
+  return cudaGetLastError();
+}
+
+}  // namespace cqrrpt

@@ -1,0 +1,272 @@
+"""GPU <-> oracle parity, step by step and end to end, through the C ABI.
+
+The library and the oracle implement the same readings of the paper (the
+SASO generator, the blocked/ascending summation orders, dot32 inside the
+QRCP, the pivot tie-break, the sign convention), so every floating-point
+output is compared BIT FOR BIT, and J and k exactly.  Sizes span several
+4096-row blocks, several tiles of every kernel, and ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2311_08316_gb300 import build as cbuild
+    cbuild.build()
+    import paper_2311_08316_gb300 as lib
+    lib.lib()
+    return lib
+
+
+def gpu(a):
+    a = np.asfortranarray(a, dtype=np.float64)
+    t = torch.from_numpy(a.T.copy()).cuda()   # (n, m) contiguous == column-major (m, n)
+    return t.t()
+
+
+def host(t):
+    return np.asfortranarray(t.detach().cpu().numpy())
+
+
+def assert_bits(got, ref, what):
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    assert got.shape == ref.shape, (what, got.shape, ref.shape)
+    same = (got.view(np.uint64) == ref.view(np.uint64)) if got.dtype == np.float64 else (got == ref)
+    if not same.all():
+        idx = np.argwhere(~same)
+        i = tuple(idx[0])
+        diff = np.abs(got.astype(np.float64) - ref.astype(np.float64))
+        raise AssertionError("%s: %d of %d differ; first at %s got %r ref %r; max abs diff %g"
+                             % (what, len(idx), same.size, i, got[i], ref[i], diff.max()))
+
+
+def _rng(s):
+    return np.random.default_rng(s)
+
+
+# ---------------------------------------------------------------- line 1
+@pytest.mark.parametrize("m,n,d,s,seed", [
+    (4096, 64, 128, 4, 7),
+    (3 * 4096 + 123, 13, 40, 8, 11),
+    (4097, 5, 16, 1, 3),
+    (10000, 33, 42, 32, 2**40 + 9),
+    (300, 7, 300, 4, 5),
+])
+def test_sketch_bitexact(C, m, n, d, s, seed):
+    A = _rng(seed % 1000).standard_normal((m, n))
+    ref, st = oracle.sketch(A, d, s, seed)
+    got = C.sketch(gpu(A), d, s, seed)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert_bits(host(got), ref, "sketch")
+
+
+# ---------------------------------------------------------------- line 2
+@pytest.mark.parametrize("d,n,seed", [(128, 64, 1), (37, 29, 2), (200, 150, 3), (640, 512, 4),
+                                      (9, 9, 5), (1, 1, 6)])
+def test_qrcp_bitexact(C, d, n, seed):
+    rng = _rng(seed)
+    X = rng.standard_normal((d, n)) * np.logspace(0, -8, n)[rng.permutation(n)]
+    R_ref, J_ref, *_ = oracle.qrcp(X)
+    Xg = gpu(X)
+    Rsk, J = C.qrcp(Xg)
+    torch.cuda.synchronize()
+    assert_bits(host(J), J_ref, "J")
+    assert_bits(host(Rsk), R_ref, "R^sk")
+
+
+def test_qrcp_rank_deficient_and_ties(C):
+    rng = _rng(9)
+    d, n = 96, 80
+    X = rng.standard_normal((d, 40)) @ rng.standard_normal((40, n))
+    X[:, 5] = X[:, 3]           # exact duplicate columns: exact norm ties
+    X[:, 70] = 0.0              # zero column
+    R_ref, J_ref, *_ = oracle.qrcp(X)
+    Rsk, J = C.qrcp(gpu(X))
+    torch.cuda.synchronize()
+    assert_bits(host(J), J_ref, "J")
+    assert_bits(host(Rsk), R_ref, "R^sk")
+
+
+# ---------------------------------------------------------------- line 3
+def test_rank_rules(C):
+    rng = _rng(10)
+    X = rng.standard_normal((60, 50)) * np.logspace(0, -14, 50)
+    R_ref, *_ = oracle.qrcp(X)
+    Rg = gpu(R_ref)
+    for tol in (1e-3, 1e-9, 1e-12, 1e-16):
+        k = C.rank(Rg, tol)
+        torch.cuda.synchronize()
+        assert int(k.item()) == oracle.rank_tol(R_ref, tol)
+    k = C.rank(Rg, -1.0)
+    assert int(k.item()) == oracle.rank_stage1(R_ref)
+
+
+# ---------------------------------------------------------------- lines 4, 7
+@pytest.mark.parametrize("m,n,k", [(1000, 40, 37), (4096 + 17, 70, 70), (33, 20, 1), (500, 300, 290)])
+def test_trsm_bitexact(C, m, n, k):
+    rng = _rng(m + k)
+    B = rng.standard_normal((m, n))
+    T = np.triu(rng.standard_normal((k, k))) + 3 * np.eye(k)
+    cols = rng.permutation(n)[:k].astype(np.int64)
+    ref = oracle.trsm_rut(B, T, cols)
+    got = C.trsm(gpu(B), gpu(T), torch.from_numpy(cols).cuda())
+    torch.cuda.synchronize()
+    assert_bits(host(got), ref, "trsm gather")
+    # in place, identity columns
+    ref2 = oracle.trsm_rut(ref, T)
+    Xg = gpu(ref)
+    C.trsm(Xg, gpu(T), None, out=Xg)
+    torch.cuda.synchronize()
+    assert_bits(host(Xg), ref2, "trsm in place")
+
+
+# ---------------------------------------------------------------- line 5
+@pytest.mark.parametrize("m,k", [(4096, 64), (3 * 4096 + 77, 45), (100, 1), (9000, 130)])
+def test_gram_bitexact(C, m, k):
+    X = _rng(m).standard_normal((m, k))
+    ref = oracle.gram(X)
+    got = C.gram(gpu(X))
+    torch.cuda.synchronize()
+    assert_bits(host(got), ref, "gram")
+
+
+# ---------------------------------------------------------------- line 6
+@pytest.mark.parametrize("k", [1, 31, 32, 33, 100, 257])
+def test_potrf_bitexact(C, k):
+    B = _rng(k).standard_normal((2 * k + 3, k))
+    G = B.T @ B
+    ref, fail = oracle.potrf_upper(G)
+    R, f = C.potrf(gpu(G))
+    torch.cuda.synchronize()
+    assert fail == -1 and int(f.item()) == -1
+    assert_bits(np.triu(host(R)), ref, "potrf")
+
+
+def test_potrf_failure_column(C):
+    rng = _rng(77)
+    k = 70
+    B = rng.standard_normal((200, k))
+    B[:, 45] = B[:, :45] @ rng.standard_normal(45)
+    G = B.T @ B
+    G[45, 45] -= 1e-3 * G[45, 45]
+    ref, fail = oracle.potrf_upper(G)
+    R, f = C.potrf(gpu(G))
+    torch.cuda.synchronize()
+    assert fail == 45 and int(f.item()) == 45
+    assert_bits(np.triu(host(R))[:45, :45], ref[:45, :45], "potrf leading block")
+
+
+# ---------------------------------------------------------------- line 8
+@pytest.mark.parametrize("k,n", [(7, 11), (64, 64), (100, 130), (1, 5)])
+def test_trmm_bitexact(C, k, n):
+    rng = _rng(k * n)
+    Rp = np.triu(rng.standard_normal((k, k)))
+    Rs = np.triu(rng.standard_normal((k, n)))
+    ref = oracle.trmm_upper(Rp, Rs)
+    got = C.trmm(gpu(Rp), gpu(Rs))
+    torch.cuda.synchronize()
+    assert_bits(host(got), ref, "trmm")
+
+
+# ---------------------------------------------------------------- end to end
+def _compare_full(C, A, gamma, nnz, tol, seed):
+    ref = oracle.cqrrpt(A, gamma, nnz, tol, seed)
+    res = C.cqrrpt(gpu(A), gamma, nnz, tol, seed)
+    assert res.status == ref.status
+    assert res.k == ref.k
+    assert_bits(host(res.J), ref.J, "J")
+    if ref.k:
+        assert_bits(host(res.Q), ref.Q, "Q")
+        assert_bits(host(res.R), ref.R, "R")
+    return ref, res
+
+
+def test_cqrrpt_full_rank_cond1e8(C):
+    """m = 4096, n = 64, cond 1e8, d = 2n, 4 nnz/col, tol 1e-12."""
+    w = W.single_small()
+    A = np.asfortranarray(w.matrix().numpy())
+    ref, res = _compare_full(C, A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    assert res.k == 64
+
+
+@pytest.mark.parametrize("m,n,rank,gamma,nnz,tol", [
+    (16384, 128, 100, 1.25, 8, 1e-9),
+    (5000, 37, 37, 1.25, 4, -1.0),
+    (9000, 70, 35, 1.5, 3, -1.0),
+    (4096 * 2 + 1, 50, 50, 1.0, 1, 1e-12),
+])
+def test_cqrrpt_bitexact_shapes(C, m, n, rank, gamma, nnz, tol):
+    sv = np.zeros(n)
+    sv[:rank] = W.logspaced(rank, -7.0).numpy()
+    A = np.asfortranarray(W.planted(m, n, sv, m + n, noise=(1e-15 if rank < n else 0.0)).numpy())
+    ref, res = _compare_full(C, A, gamma, nnz, tol, 1000 + m)
+    if tol > 0 and rank < n:
+        assert res.k == rank
+
+
+def test_cqrrpt_degenerate(C):
+    # k = 0: zero matrix
+    res = C.cqrrpt(gpu(np.zeros((300, 6))), 1.25, 2, -1.0, 1)
+    assert res.status == 1 and res.k == 0
+    # n = 1
+    A = _rng(4).standard_normal((77, 1))
+    _compare_full(C, A, 1.0, 1, -1.0, 3)
+    # d == m
+    A = _rng(5).standard_normal((20, 16))
+    _compare_full(C, A, 1.25, 3, -1.0, 4)
+    # non-finite
+    A = _rng(6).standard_normal((500, 9))
+    A[13, 4] = np.nan
+    res = C.cqrrpt(gpu(A), 1.25, 4, -1.0, 4)
+    assert res.status == 2 and res.k == 0
+    # the handle is usable afterwards
+    A = _rng(7).standard_normal((500, 9))
+    _compare_full(C, A, 1.25, 4, -1.0, 8)
+
+
+def test_cqrrpt_invalid_arguments(C):
+    import ctypes
+    A = gpu(_rng(1).standard_normal((50, 10)))
+    with pytest.raises(C.CqrrptError):
+        C.cqrrpt(A, 6.0, 4, -1.0, 1)          # d = 60 > m
+    with pytest.raises(C.CqrrptError):
+        C.cqrrpt(A, 1.25, 40, -1.0, 1)        # nnz > 32
+    with pytest.raises(C.CqrrptError):
+        C.cqrrpt(A, 0.5, 4, -1.0, 1)          # gamma < 1
+    L = C.lib()
+    h = C.default_handle()
+    assert L.cqrrpt_d(h.h, 50, 10, None, 50, 1.25, 4, -1.0, 1, 0, None, 50, None, 10, None, None,
+                      None, None) == -4
+
+
+def test_cqrrpt_repeatable_across_calls_and_streams(C):
+    w = W.single_large(m=8192 + 300, n=96, rank=70)
+    A = gpu(np.asfortranarray(w.matrix().numpy()))
+    r1 = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        r2 = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, stream=s)
+    torch.cuda.synchronize()
+    assert r1.k == r2.k == 70
+    assert torch.equal(r1.J, r2.J)
+    assert torch.equal(r1.Q, r2.Q) and torch.equal(r1.R, r2.R)
+
+
+def test_cqrrpt_async_status(C):
+    A = gpu(_rng(3).standard_normal((800, 12)))
+    h = C.Handle()
+    res = C.cqrrpt(A, 1.25, 4, 1e-12, 5, handle=h, sync=False)
+    st, k = h.last_status()
+    assert st == 0 and k == 12
+    h.close()

@@ -1,0 +1,320 @@
+"""CQRRPT benchmark on GB300: one step = one full CQRRPT factorisation (sketch,
+QRCP of the sketch, rank, M^pre TRSM, Gram, Cholesky, Q TRSM, TRMM) of the
+plain-FP64 rank-deficient workload m = 131072, n = 1024, planted rank 800
+(singular values 1 -> 1e-6 geometric, zero after, plus 1e-15 Gaussian noise;
+SASO d = 1.25 n = 1280 with 8 nonzeros per column; tol 1e-9).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is factorisations/s over all ranks
+with A resident in HBM; `e2e` is the same metric through the public API with
+host buffers (pinned host -> device copy of A, device -> host copy of Q, R,
+J, k every step).  Under torchrun each rank factors its own independent
+problem (the factorisations do not exchange data): weak scaling, no
+collective on the data path.  `--impl reference` times the CPU oracle on a
+row sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+# FP64 peak of GB300 for an ALU-bound FP64 kernel: 152 SMs x 2 DFMA/clk x
+# 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s at the maximum SM clock).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# DRAM bytes per row of M for one trsm_rut_kernel launch at n = 1024, k = 800
+# (ncu capture of the m = 32768 case, scaled by rows; see profiles/); None
+# until a capture of the current kernel exists.
+TRSM_DRAM_BYTES_PER_ROW = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--rows", type=int, default=131072, help="m of the workload")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """Max of a float over all ranks (the slowest rank sets the step time)."""
+    if world == 1:
+        return float(x)
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    w = W.single_large(m=args.rows)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    m_s = min(32768, w.m)
+    A = np.asfortranarray(W.planted(w.m, w.n, w.sv, w.seed, w.noise, dev).cpu().numpy()[:m_s])
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = (m_s / w.m) / t
+    cores = os.cpu_count()
+    sample = ("oracle CQRRPT on the first %d of %d rows (n=%d, same gamma, nnz, tol, seed; "
+              "k=%d); factorisations/s extrapolated linearly in m" % (m_s, w.m, w.n, r.k))
+    line = {"metric": "cqrrpt_factorizations_per_s", "value": value, "unit": "factorizations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(w),
+            "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "factorizations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w):
+    return {"workload": w.name, "m": w.m, "n": w.n, "d": w.d, "nnz_per_col": w.nnz,
+            "gamma": w.gamma, "tol": w.tol, "planted_rank": w.rank, "precision": "fp64",
+            "l2": "inputs larger than L2 (A = %.2f GiB > 129 MB), no flush" % (w.m * w.n * 8 / 2**30)}
+
+
+# --------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        barrier(world)
+        return
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    import paper_2311_08316_gb300 as C
+    from paper_2311_08316_gb300 import build as cbuild
+    cbuild.build()
+
+    w = W.single_large(m=args.rows)
+    m, n = w.m, w.n
+    A = w.matrix("cuda")
+    h = C.Handle(local)
+    h.reserve(C.workspace_size(m, n, w.gamma, w.nnz))
+    Q = C.colmajor_empty(m, n)
+    R = C.colmajor_empty(n, n)
+    J = torch.empty(n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(sync):
+        return C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, out=(Q, R, J), handle=h,
+                        stream=stream, sync=sync)
+
+    res = None
+    for _ in range(args.warmup):
+        res = step(True)
+    assert res is not None and res.status == 0, res.status if res else None
+    k = res.k
+
+    # ---- timed region: A resident in HBM
+    h.set_profiling(True)
+    phases = {p: [] for p in C.PHASES}
+    step_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = C.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(False)
+        pt = h.phase_times()        # waits for this step's last phase event
+        for p, v in pt.items():
+            phases[p].append(v)
+        step_ms.append(sum(pt.values()))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = C.kernel_launches() - launches0
+    clk = clocks.stop()
+    h.set_profiling(False)
+    st, k2 = h.last_status()
+    assert st == 0 and k2 == k
+
+    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
+    ms_per_step = elapsed_ms / args.steps
+    value = world * args.steps / (elapsed_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (trsm_rut_kernel: lines 4 and 7)
+    trsm_ms = (statistics.mean(phases["trsm_pre"]) + statistics.mean(phases["trsm_q"])) / 2
+    trsm_flops = float(m) * k * k          # k^2/2 fma per row, 2 flop each
+    achieved = trsm_flops / (trsm_ms * 1e-3) / 1e9
+    roof = {"kernel": "trsm_rut_kernel", "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+            "traffic": (TRSM_DRAM_BYTES_PER_ROW * m) if TRSM_DRAM_BYTES_PER_ROW else None,
+            "algorithmic_flops_per_launch": trsm_flops,
+            "launch_ms": trsm_ms,
+            "peak_note": "FP64 ALU: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, nominal)"}
+    alg_flops = (2.0 * m * k * k + m * k * (k + 1) + 4.0 * w.d * n * k - 2.0 * k * k * (w.d + n)
+                 + 5.0 * k ** 3 / 3.0)   # paper's count (Sec. 3.2), plus sketch adds below
+    alg_flops += float(m) * w.nnz * n
+    phase_share = {p: statistics.mean(v) / (ms_per_step) for p, v in phases.items()}
+
+    # ---- e2e through the public API with host buffers
+    A_host = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    A_host.copy_(A)
+    Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    Jh = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    del A
+    Ad = C.colmajor_empty(m, n)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = C.cqrrpt_from_host(A_host, w.gamma, w.nnz, w.tol, w.sketch_seed, out_host=(Qh, Rh, Jh),
+                                 device_buffers=(Ad, Q, R, J), handle=h, stream=stream)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    assert out.k == k
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms), world)
+    h2d = m * n * 8
+    d2h = m * k * 8 + k * n * 8 + n * 8 + 8
+
+    line = {"metric": "cqrrpt_factorizations_per_s", "value": value, "unit": "factorizations/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(w),
+            "k": k,
+            "gflops_2mn2": value * 2.0 * m * n * n / 1e9,
+            "gflops_geqrf_basis": value * (2.0 * m * n * n - 2.0 * n ** 3 / 3.0) / 1e9,
+            "gflops_algorithmic": value * alg_flops / 1e9,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "phase_share": phase_share,
+            "roofline": roof,
+            "e2e": {"value": world * 1e3 / e2e_step, "unit": "factorizations/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_step},
+            "gpu_launches": int(launches),
+            "clocks": clk}
+
+    # ---- CPU baseline: the oracle on the full workload (rank 0, N = 1 only)
+    if rank == 0 and world == 1:
+        import oracle
+        Ahost = np.asfortranarray(A_host.numpy())
+        t0 = time.perf_counter()
+        ref = oracle.cqrrpt(Ahost, w.gamma, w.nnz, w.tol, w.sketch_seed)
+        t = time.perf_counter() - t0
+        same = (ref.k == out.k and np.array_equal(ref.J, Jh.numpy())
+                and np.array_equal(ref.Q.view(np.uint64),
+                                   np.asfortranarray(Qh[:, :k].numpy()).view(np.uint64))
+                and np.array_equal(ref.R.view(np.uint64),
+                                   np.asfortranarray(Rh[:k, :].numpy()).view(np.uint64)))
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": "factorizations/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "the full workload, one factorisation (%.1f s)" % t}
+        line["parity_vs_oracle"] = "bit-identical J, k, Q, R" if same else "MISMATCH"
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,21 @@ int cqrrpt_last_status(cqrrpt_handle h, cudaStream_t stream, int* status_host, i
 
 const char* cqrrpt_status_string(int status);
 
+/* ---- tracing ------------------------------------------------------------ */
+
+/* enable != 0: cqrrpt_d records a CUDA event between its phases (the
+ * per-subroutine runtime breakdown of the paper's Sec. 6.3 profiling). */
+int cqrrpt_set_profiling(cqrrpt_handle h, int enable);
+
+/* Waits for the last profiled cqrrpt_d and writes the device time in ms of
+ * its first `nphases` (<= 8) phases to ms_host, in this order: sketch,
+ * qrcp, rank, M^pre TRSM (line 4), Gram (line 5), Cholesky + rank stage 2
+ * (line 6), Q TRSM (line 7), TRMM (line 8). */
+int cqrrpt_phase_times(cqrrpt_handle h, float* ms_host, int nphases);
+
+/* Number of kernels this library has launched in this process. */
+long long cqrrpt_kernel_launches(void);
+
 /* ---- single steps of Alg. 2 (same kernels as cqrrpt_d) ------------------ */
 
 /* Line 1: M^sk = S M, S the SASO of (seed, d, nnz_per_col).  Ask: d x n,

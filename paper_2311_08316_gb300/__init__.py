@@ -60,6 +60,10 @@ def lib():
     L.cqrrpt_gram_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
     L.cqrrpt_potrf_d.argtypes = [_p, _i64, _p, _i64, _p, _i64, _p, _p]
     L.cqrrpt_trmm_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_set_profiling.argtypes = [_p, _int]
+    L.cqrrpt_phase_times.argtypes = [_p, ctypes.POINTER(ctypes.c_float), _int]
+    L.cqrrpt_kernel_launches.argtypes = []
+    L.cqrrpt_kernel_launches.restype = ctypes.c_longlong
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
     L.cqrrpt_sketch_dim.restype = _i64
     L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -74,7 +78,16 @@ def exported_symbols():
     return ["cqrrpt_create", "cqrrpt_destroy", "cqrrpt_workspace_size", "cqrrpt_reserve",
             "cqrrpt_d", "cqrrpt_last_status", "cqrrpt_status_string", "cqrrpt_sketch_d",
             "cqrrpt_qrcp_d", "cqrrpt_rank_d", "cqrrpt_trsm_d", "cqrrpt_gram_d", "cqrrpt_potrf_d",
-            "cqrrpt_trmm_d", "cqrrpt_sketch_dim", "cqrrpt_philox4x32_10", "cqrrpt_saso_column"]
+            "cqrrpt_trmm_d", "cqrrpt_sketch_dim", "cqrrpt_philox4x32_10", "cqrrpt_saso_column",
+            "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches"]
+
+
+PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().cqrrpt_kernel_launches())
 
 
 def _check(rc, what):
@@ -125,6 +138,15 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+    def set_profiling(self, enable=True):
+        _check(lib().cqrrpt_set_profiling(self.h, 1 if enable else 0), "cqrrpt_set_profiling")
+
+    def phase_times(self):
+        """Per-phase device ms of the last profiled cqrrpt call (dict)."""
+        ms = (ctypes.c_float * len(PHASES))()
+        _check(lib().cqrrpt_phase_times(self.h, ms, len(PHASES)), "cqrrpt_phase_times")
+        return dict(zip(PHASES, list(ms)))
 
     def reserve(self, nbytes):
         _check(lib().cqrrpt_reserve(self.h, int(nbytes)), "cqrrpt_reserve")
@@ -284,3 +306,37 @@ def saso_column(seed, r, d, nnz):
     neg = (ctypes.c_uint8 * nnz)()
     lib().cqrrpt_saso_column(seed, r, d, nnz, rows, neg)
     return list(rows), list(neg)
+
+
+def cqrrpt_from_host(A_host, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64, out_host=None,
+                     device_buffers=None, handle=None, stream=None):
+    """CQRRPT of a host-resident column-major float64 matrix: copies A to the
+    device, factors it, and copies Q[:, :k], R[:k, :], J back into host
+    buffers (pinned buffers make the copies asynchronous DMA).  Returns a
+    Factorization whose Qbuf/Rbuf/J are the host buffers."""
+    m, n = A_host.shape
+    if device_buffers is None:
+        Ad = colmajor_empty(m, n)
+        Q = colmajor_empty(m, n)
+        R = colmajor_empty(n, n)
+        J = torch.empty(n, dtype=torch.int64, device="cuda")
+    else:
+        Ad, Q, R, J = device_buffers
+    if out_host is None:
+        Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        Jh = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    else:
+        Qh, Rh, Jh = out_host
+    s = stream if stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        Ad.copy_(A_host, non_blocking=True)
+        res = cqrrpt(Ad, gamma, nnz, tol, seed, precision, out=(Q, R, J), handle=handle, stream=s,
+                     sync=True)
+        k = res.k
+        if k:
+            Qh[:, :k].copy_(Q[:, :k], non_blocking=True)
+            Rh[:k, :].copy_(R[:k, :], non_blocking=True)
+        Jh.copy_(J, non_blocking=True)
+    s.synchronize()
+    return Factorization(Qh, Rh, Jh, k, res.status)

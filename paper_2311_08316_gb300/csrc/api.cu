@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "../../include/cqrrpt.h"
@@ -12,6 +13,8 @@
 
 using namespace cqrrpt;
 
+constexpr int kPhases = 8;  // sketch, qrcp, rank, trsm(M^pre), gram, chol, trsm(Q), trmm
+
 struct cqrrpt_ctx {
   int device = 0;
   int num_sms = 0;
@@ -19,9 +22,21 @@ struct cqrrpt_ctx {
   size_t ws_bytes = 0;
   DeviceScalars* sc = nullptr;  // per-call device scalars
   int64_t* pinned = nullptr;    // host-pinned readback (k, status)
+  int profiling = 0;
+  cudaEvent_t ev[kPhases + 1] = {};
 };
 
+static std::atomic<long long> g_launches{0};
+
+namespace cqrrpt {
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace cqrrpt
+
 namespace {
+
+inline void mark(cqrrpt_handle h, int i, cudaStream_t s) {
+  if (h->profiling) cudaEventRecord(h->ev[i], s);
+}
 
 struct Plan {
   int64_t d, nb;
@@ -111,6 +126,8 @@ int cqrrpt_destroy(cqrrpt_handle h) {
   if (h->ws) cudaFree(h->ws);
   if (h->sc) cudaFree(h->sc);
   if (h->pinned) cudaFreeHost(h->pinned);
+  for (int i = 0; i <= kPhases; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   delete h;
   return kOk;
 }
@@ -172,17 +189,26 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
   const double scale = 1.0 / std::sqrt((double)nnz);
 
   cudaError_t e = launch_init_scalars(sc, 0, stream);
+  mark(h, 0, stream);
   if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
+  mark(h, 1, stream);
   if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
+  mark(h, 2, stream);
   if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
+  mark(h, 3, stream);
   if (e == cudaSuccess)
     e = launch_trsm_rut(m, ni, &sc->k, A, lda, J, Rsk, n, Q, ldq, status, stream);
+  mark(h, 4, stream);
   if (e == cudaSuccess) e = launch_gram(m, ni, &sc->k, Q, ldq, G, n, region, status, stream);
+  mark(h, 5, stream);
   if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, n, sc, stream);
   if (e == cudaSuccess) e = launch_rank_stage2(Rpre, n, !(tol > 0.0), sc, stream);
+  mark(h, 6, stream);
   if (e == cudaSuccess)
     e = launch_trsm_rut(m, ni, &sc->k, Q, ldq, nullptr, Rpre, n, Q, ldq, status, stream);
+  mark(h, 7, stream);
   if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, Rsk, n, R, ldr, status, stream);
+  mark(h, 8, stream);
   if (e == cudaSuccess) e = launch_finalize(sc, k_dev, nullptr, stream);
   if (e != cudaSuccess) return kCudaError;
   if (k_host) {
@@ -207,6 +233,31 @@ int cqrrpt_last_status(cqrrpt_handle h, cudaStream_t stream, int* status_host, i
   if (k_host) *k_host = *pk;
   return kOk;
 }
+
+int cqrrpt_set_profiling(cqrrpt_handle h, int enable) {
+  if (!h) return -1;
+  DevGuard g(h->device);
+  if (enable && !h->ev[0]) {
+    for (int i = 0; i <= kPhases; ++i)
+      if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return kCudaError;
+  }
+  h->profiling = enable ? 1 : 0;
+  return kOk;
+}
+
+int cqrrpt_phase_times(cqrrpt_handle h, float* ms_host, int nphases) {
+  if (!h) return -1;
+  if (!ms_host) return -2;
+  if (nphases < 1 || nphases > kPhases) return -3;
+  if (!h->profiling) return -1;
+  DevGuard g(h->device);
+  if (cudaEventSynchronize(h->ev[kPhases]) != cudaSuccess) return kCudaError;
+  for (int i = 0; i < nphases; ++i)
+    if (cudaEventElapsedTime(&ms_host[i], h->ev[i], h->ev[i + 1]) != cudaSuccess) return kCudaError;
+  return kOk;
+}
+
+long long cqrrpt_kernel_launches(void) { return g_launches.load(); }
 
 const char* cqrrpt_status_string(int status) {
   switch (status) {

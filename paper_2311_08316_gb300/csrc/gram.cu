@@ -110,6 +110,7 @@ cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double*
   const int64_t total = (int64_t)kmax * kmax;
   const unsigned cgrid = (unsigned)min64((total + 255) / 256, 152 * 16);
   gram_combine_kernel<<<cgrid, 256, 0, stream>>>(nb, kmax, k_dev, partial, G, ldg, status);
+  count_launches(2);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,8 @@ cudaError_t launch_trmm(int n, const int64_t* k_dev, const double* Rpre, int64_t
                         const int* status, cudaStream_t stream);
 
 // ---- small helpers -------------------------------------------------------
+// Process-wide count of kernels this library has launched.
+void count_launches(int n);
 cudaError_t launch_init_scalars(DeviceScalars* sc, int64_t k, cudaStream_t stream);
 cudaError_t launch_finalize(DeviceScalars* sc, int64_t* k_out, int* status_out,
                             cudaStream_t stream);

@@ -94,8 +94,10 @@ cudaError_t launch_potrf(int kmax, double* G, int64_t ldg, double* R, int64_t ld
                          DeviceScalars* sc, cudaStream_t stream) {
   for (int jb = 0; jb < kmax; jb += kCholNB) {
     potrf_diag_kernel<<<1, 32, 0, stream>>>(jb, G, ldg, R, ldr, sc);
+    count_launches(1);
     const int rest = kmax - jb - kCholNB;
     if (rest > 0) {
+      count_launches(2);
       potrf_panel_kernel<<<(rest + 127) / 128, 128, 0, stream>>>(jb, G, ldg, R, ldr, sc);
       dim3 grid((rest + 15) / 16, (rest + 15) / 16);
       potrf_update_kernel<<<grid, dim3(16, 16), 0, stream>>>(jb, G, ldg, R, ldr, sc);

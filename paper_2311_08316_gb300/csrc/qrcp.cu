@@ -277,6 +277,7 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
                                   stream);
   if (e != cudaSuccess) return e;
   qrcp_gather_kernel<<<n, 128, 0, stream>>>(n, X, ldx, w.phys, J, Rsk, ldr, &sc->status);
+  count_launches(2);
   return cudaGetLastError();
 }
 
@@ -338,6 +339,7 @@ __global__ void rank_kernel(int n, const double* Rsk, int64_t ldr, double tol, D
 cudaError_t launch_rank(int n, const double* Rsk, int64_t ldr, double tol, DeviceScalars* sc,
                         double* f2, cudaStream_t stream) {
   rank_kernel<<<1, 1024, 0, stream>>>(n, Rsk, ldr, tol, sc, f2);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -364,6 +366,7 @@ __global__ void rank_stage2_kernel(const double* Rpre, int64_t ldp, int stage2, 
 cudaError_t launch_rank_stage2(const double* Rpre, int64_t ldp, bool stage2, DeviceScalars* sc,
                                cudaStream_t stream) {
   rank_stage2_kernel<<<1, 1, 0, stream>>>(Rpre, ldp, stage2 ? 1 : 0, sc);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -378,6 +381,7 @@ __global__ void init_scalars_kernel(DeviceScalars* sc, int64_t k) {
 
 cudaError_t launch_init_scalars(DeviceScalars* sc, int64_t k, cudaStream_t stream) {
   init_scalars_kernel<<<1, 1, 0, stream>>>(sc, k);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -392,6 +396,7 @@ __global__ void finalize_kernel(DeviceScalars* sc, int64_t* k_out, int* status_o
 cudaError_t launch_finalize(DeviceScalars* sc, int64_t* k_out, int* status_out,
                             cudaStream_t stream) {
   finalize_kernel<<<1, 1, 0, stream>>>(sc, k_out, status_out);
+  count_launches(1);
   return cudaGetLastError();
 }
 

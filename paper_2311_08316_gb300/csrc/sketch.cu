@@ -180,6 +180,7 @@ cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, in
   const int64_t total = n * (int64_t)d;
   const unsigned cgrid = (unsigned)min64((total + 255) / 256, 152 * 16);
   sketch_combine_kernel<<<cgrid, 256, 0, stream>>>(nb, n, d, scale, partial, Msk, ldsk, status);
+  count_launches(3);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ cudaError_t launch_trmm(int n, const int64_t* k_dev, const double* Rpre, int64_t
                         const int* status, cudaStream_t stream) {
   dim3 grid((unsigned)((n + 127) / 128), (unsigned)n);
   trmm_kernel<<<grid, 128, 0, stream>>>(n, k_dev, Rpre, ldp, Rsk, ldsk, R, ldr, status);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,7 @@ cudaError_t launch_trsm_rut(int64_t m, int kmax, const int64_t* k_dev, const dou
   const unsigned grid = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
   trsm_rut_kernel<<<grid, kTrsmThreads, 0, stream>>>(m, k_dev, B, ldb, cols, T, ldt, X, ldx,
                                                      status);
+  count_launches(1);
   return cudaGetLastError();
 }
 

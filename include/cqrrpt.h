@@ -50,6 +50,8 @@ extern "C" {
 #define CQRRPT_CUDA_ERROR 3  /* a CUDA call or launch failed              */
 #define CQRRPT_NO_MEMORY 4   /* workspace allocation failed               */
 #define CQRRPT_TIMEOUT 5     /* a bounded device-side wait expired        */
+#define CQRRPT_TOO_LARGE 6   /* problem exceeds the fixed scratch of
+                                cqrrpt_sketch_noalloc_d                  */
 
 /* Precision of the O(m n^2) steps (Alg. 2 lines 4-7). */
 #define CQRRPT_FP64 0
@@ -134,6 +136,29 @@ long long cqrrpt_kernel_launches(void);
 int cqrrpt_sketch_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
                     int64_t d, int nnz_per_col, uint64_t seed, double* Ask, int64_t ldsk,
                     cudaStream_t stream);
+
+/* Line 1 without any allocation (the paper has no counterpart: this is a
+ * deployment variant).  For callers that cannot allocate device memory
+ * when they sketch -- code inside a pre-sized, locked memory pool, or hosts
+ * that may not create a handle because a handle owns a workspace -- this
+ * computes exactly what cqrrpt_sketch_d computes (same kernels, same bits)
+ * but needs no handle: its scratch is one file-scope device array of
+ * 32 MiB that every GPU loading this library holds until the process exits.
+ * It calls no cudaMalloc/cudaFree.  Problems whose sketch scratch exceeds
+ * cqrrpt_sketch_noalloc_max_bytes() (about (m/4096 + 1) * n * d * 8 bytes
+ * plus the S lists) return CQRRPT_TOO_LARGE.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls on a device share the array and it keeps the last call's contents;
+ * calls whose executions overlap on the GPU race on it and must not be
+ * issued.  Arguments as cqrrpt_sketch_d without the handle (argument
+ * numbers shift by one: m is argument 1).  The device is the current one. */
+int cqrrpt_sketch_noalloc_d(int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,
+                            int nnz_per_col, uint64_t seed, double* Ask, int64_t ldsk,
+                            cudaStream_t stream);
+
+/* Largest sketch scratch (bytes) cqrrpt_sketch_noalloc_d accepts. */
+size_t cqrrpt_sketch_noalloc_max_bytes(void);
 
 /* Line 2: QRCP of X (d x n, ldx >= d, overwritten with Householder data).
  * J: n int64 pivots; Rsk: n x n (ldr >= n) sign-normalised R^sk (diagonal

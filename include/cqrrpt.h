@@ -106,6 +106,37 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
              double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
              cudaStream_t stream);
 
+/* ---- batched CQRRPT ------------------------------------------------------ */
+
+/* Workspace bytes cqrrpt_batched_d needs for `batch` problems (m, n: host
+ * arrays of batch entries). */
+int cqrrpt_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, double gamma,
+                                  int nnz_per_col, size_t* bytes_host);
+
+/* Many independent problems of uneven sizes in one batched pass: one launch
+ * per phase of Alg. 2 covers every problem (the QRCP and the Cholesky give
+ * one CTA to each problem), and the whole sequence is captured once into a
+ * CUDA graph and replayed while the batch's launch shapes repeat.
+ *   batch                       number of problems >= 1.
+ *   m, n, lda, tol, seed, ldq, ldr      HOST arrays of `batch` entries.
+ *   A, Q, R, J                  HOST arrays of `batch` DEVICE pointers with
+ *                               the meaning and sizes of cqrrpt_d.
+ *   gamma, nnz_per_col, precision      shared by all problems.
+ *   k_dev, status_dev           DEVICE arrays of `batch` entries (or NULL):
+ *                               each problem's k and final status.
+ * Every problem's J, k, Q and R are bit-identical to cqrrpt_d on the same
+ * inputs.  The call returns after enqueueing (argument errors: -i for
+ * argument i, counting the handle as 1). */
+int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
+                     const double* const* A, const int64_t* lda, double gamma, int nnz_per_col,
+                     const double* tol, const uint64_t* seed, int precision, double* const* Q,
+                     const int64_t* ldq, double* const* R, const int64_t* ldr, int64_t* const* J,
+                     int64_t* k_dev, int* status_dev, cudaStream_t stream);
+
+/* enable = 0: cqrrpt_batched_d launches its kernels directly instead of
+ * through its cached CUDA graph. */
+int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable);
+
 /* Wait for `stream` and return the device-detected status of the handle's
  * last cqrrpt_d call (0, 1, 2 or 5) in *status_host, and its k in *k_host
  * (either pointer may be NULL). */

@@ -64,6 +64,11 @@ def lib():
     L.cqrrpt_phase_times.argtypes = [_p, ctypes.POINTER(ctypes.c_float), _int]
     L.cqrrpt_kernel_launches.argtypes = []
     L.cqrrpt_kernel_launches.restype = ctypes.c_longlong
+    L.cqrrpt_batched_d.argtypes = [_p, _int, _p, _p, _p, _p, _d, _int, _p, _p, _int, _p, _p, _p,
+                                   _p, _p, _p, _p, _p]
+    L.cqrrpt_batched_workspace_size.argtypes = [_int, _p, _p, _d, _int,
+                                                ctypes.POINTER(ctypes.c_size_t)]
+    L.cqrrpt_set_batch_graphs.argtypes = [_p, _int]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
     L.cqrrpt_sketch_dim.restype = _i64
     L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -79,7 +84,8 @@ def exported_symbols():
             "cqrrpt_d", "cqrrpt_last_status", "cqrrpt_status_string", "cqrrpt_sketch_d",
             "cqrrpt_qrcp_d", "cqrrpt_rank_d", "cqrrpt_trsm_d", "cqrrpt_gram_d", "cqrrpt_potrf_d",
             "cqrrpt_trmm_d", "cqrrpt_sketch_dim", "cqrrpt_philox4x32_10", "cqrrpt_saso_column",
-            "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches"]
+            "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches",
+            "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -340,3 +346,47 @@ def cqrrpt_from_host(A_host, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64
         Jh.copy_(J, non_blocking=True)
     s.synchronize()
     return Factorization(Qh, Rh, Jh, k, res.status)
+
+
+def _arr(ctype, values):
+    return (ctype * len(values))(*values)
+
+
+def cqrrpt_batched(As, gamma=1.25, nnz=4, tols=None, seeds=None, precision=FP64, outs=None,
+                   handle=None, stream=None, sync=True, graphs=True):
+    """Batched CQRRPT of independent column-major float64 CUDA matrices
+    (uneven sizes allowed) through cqrrpt_batched_d.  Returns a list of
+    Factorization; with sync=True their k and status are filled in."""
+    h = handle or default_handle()
+    L = lib()
+    b = len(As)
+    tols = [(-1.0 if tols is None else float(tols[i])) for i in range(b)] if not isinstance(tols, float) else [tols] * b
+    seeds = [int(i) for i in range(b)] if seeds is None else [int(s) for s in seeds]
+    if outs is None:
+        outs = [(colmajor_empty(A.shape[0], A.shape[1], A.device),
+                 colmajor_empty(A.shape[1], A.shape[1], A.device),
+                 torch.empty(A.shape[1], dtype=torch.int64, device=A.device)) for A in As]
+    kd = torch.zeros(b, dtype=torch.int64, device=As[0].device)
+    sd = torch.zeros(b, dtype=torch.int32, device=As[0].device)
+    P = ctypes.c_void_p
+    rc = L.cqrrpt_batched_d(
+        h.h, b, _arr(_i64, [A.shape[0] for A in As]), _arr(_i64, [A.shape[1] for A in As]),
+        _arr(P, [A.data_ptr() for A in As]), _arr(_i64, [_ld(A) for A in As]), gamma, nnz,
+        _arr(_d, tols), _arr(_u64, seeds), precision,
+        _arr(P, [o[0].data_ptr() for o in outs]), _arr(_i64, [_ld(o[0]) for o in outs]),
+        _arr(P, [o[1].data_ptr() for o in outs]), _arr(_i64, [_ld(o[1]) for o in outs]),
+        _arr(P, [o[2].data_ptr() for o in outs]), kd.data_ptr(), sd.data_ptr(), _stream(stream))
+    _check(rc, "cqrrpt_batched_d")
+    res = [Factorization(o[0], o[1], o[2], None, None) for o in outs]
+    if sync:
+        (stream or torch.cuda.current_stream()).synchronize()
+        ks = kd.cpu().tolist()
+        ss = sd.cpu().tolist()
+        for r, k, s in zip(res, ks, ss):
+            r.k, r.status = int(k), int(s)
+    return res, kd, sd
+
+
+def set_batch_graphs(enable, handle=None):
+    h = handle or default_handle()
+    _check(lib().cqrrpt_set_batch_graphs(h.h, 1 if enable else 0), "cqrrpt_set_batch_graphs")

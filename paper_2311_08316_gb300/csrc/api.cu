@@ -6,8 +6,10 @@
 #include <cstring>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "../../include/cqrrpt.h"
+#include "batched.h"
 #include "kernels.h"
 #include "saso.cuh"
 
@@ -24,6 +26,15 @@ struct cqrrpt_ctx {
   int64_t* pinned = nullptr;    // host-pinned readback (k, status)
   int profiling = 0;
   cudaEvent_t ev[kPhases + 1] = {};
+  // batched path: pinned staging of the launch tables, graph cache
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_ev = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_key[12] = {};
+  int graph_kernels = 0;
+  int use_graphs = 1;
 };
 
 static std::atomic<long long> g_launches{0};
@@ -128,6 +139,10 @@ int cqrrpt_destroy(cqrrpt_handle h) {
   if (h->pinned) cudaFreeHost(h->pinned);
   for (int i = 0; i <= kPhases; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->capture) cudaStreamDestroy(h->capture);
+  if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+  if (h->stage) cudaFreeHost(h->stage);
   delete h;
   return kOk;
 }
@@ -219,6 +234,152 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
     *k_host = kk;
     return st2;
   }
+  return kOk;
+}
+
+static int batch_check(int batch, const int64_t* m, const int64_t* n, const double* const* A,
+                       const int64_t* lda, double gamma, int nnz, const double* tol,
+                       const uint64_t* seed, int precision, double* const* Q, const int64_t* ldq,
+                       double* const* R, const int64_t* ldr, int64_t* const* J) {
+  if (batch < 1) return -2;
+  if (!m) return -3;
+  if (!n) return -4;
+  if (!A) return -5;
+  if (!lda) return -6;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -7;
+  if (!tol) return -9;
+  if (!seed) return -10;
+  if (precision != CQRRPT_FP64) return -11;
+  if (!Q) return -12;
+  if (!ldq) return -13;
+  if (!R) return -14;
+  if (!ldr) return -15;
+  if (!J) return -16;
+  for (int p = 0; p < batch; ++p) {
+    if (m[p] < 1) return -3;
+    if (n[p] < 1 || n[p] > 16384) return -4;
+    if (!A[p]) return -5;
+    if (lda[p] < m[p]) return -6;
+    const int64_t d = sketch_dim(n[p], gamma);
+    if (d > m[p] || d > 28000) return -7;
+    if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -8;
+    if (std::isnan(tol[p])) return -9;
+    if (!Q[p]) return -12;
+    if (ldq[p] < m[p]) return -13;
+    if (!R[p]) return -14;
+    if (ldr[p] < n[p]) return -15;
+    if (!J[p]) return -16;
+  }
+  return kOk;
+}
+
+int cqrrpt_batched_workspace_size(int batch, const int64_t* m, const int64_t* n, double gamma,
+                                  int nnz, size_t* bytes) {
+  if (batch < 1) return -1;
+  if (!m || !n) return -2;
+  if (!(gamma >= 1.0)) return -4;
+  if (!bytes) return -6;
+  int64_t total = align256((int64_t)batch * sizeof(DeviceScalars)) + batch_table_bytes(batch);
+  for (int p = 0; p < batch; ++p) {
+    if (m[p] < 1 || n[p] < 1) return -2;
+    const int64_t d = sketch_dim(n[p], gamma);
+    if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -5;
+    total += problem_workspace_bytes(m[p], n[p], d, nnz);
+  }
+  *bytes = (size_t)total;
+  return kOk;
+}
+
+int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable) {
+  if (!h) return -1;
+  h->use_graphs = enable ? 1 : 0;
+  return kOk;
+}
+
+int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
+                     const double* const* A, const int64_t* lda, double gamma, int nnz,
+                     const double* tol, const uint64_t* seed, int precision, double* const* Q,
+                     const int64_t* ldq, double* const* R, const int64_t* ldr, int64_t* const* J,
+                     int64_t* k_dev, int* status_dev, cudaStream_t stream) {
+  if (!h) return -1;
+  int st = batch_check(batch, m, n, A, lda, gamma, nnz, tol, seed, precision, Q, ldq, R, ldr, J);
+  if (st != kOk) return st;
+  DevGuard g(h->device);
+  size_t need = 0;
+  st = cqrrpt_batched_workspace_size(batch, m, n, gamma, nnz, &need);
+  if (st != kOk) return st;
+  st = ensure_ws(h, need);
+  if (st != kOk) return st;
+
+  std::vector<BatchProblem> probs((size_t)batch);
+  for (int p = 0; p < batch; ++p) {
+    BatchProblem& q = probs[(size_t)p];
+    q.m = m[p]; q.n = n[p]; q.d = sketch_dim(n[p], gamma); q.nnz = nnz; q.tol = tol[p];
+    q.seed = seed[p]; q.A = A[p]; q.lda = lda[p]; q.Q = Q[p]; q.ldq = ldq[p]; q.R = R[p];
+    q.ldr = ldr[p]; q.J = J[p];
+    q.k_out = k_dev ? k_dev + p : nullptr;
+    q.status_out = status_dev ? status_dev + p : nullptr;
+  }
+  char* ws = (char*)h->ws;
+  BatchPlan P;
+  P.scalars = (DeviceScalars*)ws;
+  P.tables = ws + align256((int64_t)batch * sizeof(DeviceScalars));
+  char* per_problem = P.tables + batch_table_bytes(batch);
+  batch_plan(P, batch, probs.data(), per_problem);
+
+  // stage the tables through pinned memory (wait until the previous copy
+  // out of the staging buffer has finished before overwriting it)
+  const size_t img = P.image.size();
+  if (!h->stage_ev && cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess)
+    return kCudaError;
+  if (cudaEventSynchronize(h->stage_ev) != cudaSuccess) return kCudaError;
+  if (img > h->stage_bytes) {
+    if (h->stage) cudaFreeHost(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    if (cudaMallocHost(&h->stage, img) != cudaSuccess) return kNoMemory;
+    h->stage_bytes = img;
+  }
+  memcpy(h->stage, P.image.data(), img);
+  if (cudaMemcpyAsync(P.tables, h->stage, img, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return kCudaError;
+  if (cudaEventRecord(h->stage_ev, stream) != cudaSuccess) return kCudaError;
+  if (sketch_set_attributes(P.max_d) != cudaSuccess) return kCudaError;
+
+  if (!h->use_graphs) return batch_launch(P, stream) == cudaSuccess ? kOk : kCudaError;
+
+  const int64_t key[12] = {batch, P.max_d, P.tiles_list, P.tiles_part, P.tiles_comb,
+                           P.tiles_gath, P.tiles_trsm, P.tiles_gp, P.tiles_gc, P.tiles_tm,
+                           (int64_t)(uintptr_t)P.tables, (int64_t)(uintptr_t)P.scalars};
+  if (!h->graph_exec || memcmp(key, h->graph_key, sizeof(key)) != 0) {
+    if (h->graph_exec) {
+      cudaGraphExecDestroy(h->graph_exec);
+      h->graph_exec = nullptr;
+    }
+    if (!h->capture && cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking) != cudaSuccess)
+      return kCudaError;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return kCudaError;
+    const long long before = g_launches.load();
+    cudaError_t e = batch_launch(P, h->capture);
+    const cudaError_t e2 = cudaStreamEndCapture(h->capture, &graph);
+    h->graph_kernels = (int)(g_launches.load() - before);
+    g_launches.store(before);  // captured, not launched
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return kCudaError;
+    }
+    e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->graph_exec = nullptr;
+      return kCudaError;
+    }
+    memcpy(h->graph_key, key, sizeof(key));
+  }
+  if (cudaGraphLaunch(h->graph_exec, stream) != cudaSuccess) return kCudaError;
+  count_launches(h->graph_kernels);
   return kOk;
 }
 

@@ -1,0 +1,178 @@
+// Batched CQRRPT: many independent, uneven problems factored by one batched
+// launch per phase of Alg. 2 (14 launches for the whole batch, replayed as
+// one CUDA graph when the batch's launch shapes repeat).
+//
+// Each batched kernel maps CTA b to (problem p, tile t) through a prefix
+// table of per-problem tile counts and runs the same body as the
+// single-problem kernel, so every problem's J, k, Q and R are bit-identical
+// to a standalone cqrrpt_d call on the same inputs, whatever else shares the
+// batch.  The QRCP and the Cholesky give one CTA to each problem (block
+// barriers only: nothing waits on another CTA).
+//
+// The per-phase descriptor tables and tile prefix tables are written into a
+// pinned host staging buffer and copied to the workspace with one
+// cudaMemcpyAsync per call; the copy is ordered before the launches on the
+// caller's stream.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/cqrrpt.h"
+#include "batched.h"
+#include "kernels.h"
+
+namespace cqrrpt {
+
+namespace {
+
+struct Layout {
+  // byte offsets inside the batch region
+  size_t tables, scalars, per_problem;
+  size_t total;
+};
+
+template <class T>
+size_t push_table(std::vector<char>& buf, const std::vector<T>& v) {
+  const size_t off = (buf.size() + 255) & ~size_t(255);
+  buf.resize(off + v.size() * sizeof(T));
+  if (!v.empty()) memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+  return off;
+}
+
+}  // namespace
+
+int64_t problem_workspace_bytes(int64_t m, int64_t n, int64_t d, int nnz) {
+  const int64_t a = sketch_workspace_bytes(m, n, (int)d, nnz);
+  const int64_t b = gram_workspace_bytes(m, n);
+  int64_t t = (a > b ? a : b);
+  t += align256(d * n * 8);
+  t += qrcp_workspace_bytes(n);
+  t += 3 * align256(n * n * 8);
+  t += align256((n + 1) * 8);
+  return t;
+}
+
+int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base) {
+  DeviceScalars* scalars = P.scalars;
+  char* tables = P.tables;
+  P = BatchPlan();
+  P.scalars = scalars;
+  P.tables = tables;
+  P.nprob = batch;
+  // per-problem workspace
+  char* w = ws_base;
+  std::vector<SketchDesc> sk(batch);
+  std::vector<QrcpDesc> qr(batch);
+  std::vector<RankDesc> rk(batch);
+  std::vector<TrsmDesc> t1(batch), t2(batch);
+  std::vector<GramDesc> gr(batch);
+  std::vector<PotrfDesc> po(batch);
+  std::vector<Stage2Desc> s2(batch);
+  std::vector<TrmmDesc> tm(batch);
+  std::vector<FinalDesc> fi(batch);
+  std::vector<int64_t> b_list(batch + 1), b_part(batch + 1), b_comb(batch + 1),
+      b_gath(batch + 1), b_trsm(batch + 1), b_gp(batch + 1), b_gc(batch + 1), b_tm(batch + 1);
+  DeviceScalars* sc = P.scalars;
+  b_list[0] = b_part[0] = b_comb[0] = b_gath[0] = b_trsm[0] = b_gp[0] = b_gc[0] = b_tm[0] = 0;
+  int max_d = 1;
+  for (int p = 0; p < batch; ++p) {
+    const BatchProblem& q = probs[p];
+    const int64_t m = q.m, n = q.n, d = q.d;
+    if (d > max_d) max_d = (int)d;
+    const int64_t a = sketch_workspace_bytes(m, n, (int)d, q.nnz);
+    const int64_t b = gram_workspace_bytes(m, n);
+    char* region = w;
+    w += (a > b ? a : b);
+    double* X = (double*)w; w += align256(d * n * 8);
+    void* qw = w; w += qrcp_workspace_bytes(n);
+    double* Rsk = (double*)w; w += align256(n * n * 8);
+    double* G = (double*)w; w += align256(n * n * 8);
+    double* Rpre = (double*)w; w += align256(n * n * 8);
+    double* f2 = (double*)w; w += align256((n + 1) * 8);
+    DeviceScalars* s = sc + p;
+    SketchDesc& S = sk[p];
+    S = SketchDesc{};
+    S.m = m; S.n = n; S.d = (int)d; S.s = q.nnz; S.seed = q.seed;
+    S.scale = 1.0 / std::sqrt((double)q.nnz);
+    S.M = q.A; S.ldm = q.lda; S.Msk = X; S.ldsk = d; S.status = &s->status;
+    sketch_carve(S, region);
+    qr[p] = QrcpDesc{(int)d, (int)n, X, d, qrcp_carve(qw, (int)n), q.J, Rsk, n, s};
+    rk[p] = RankDesc{(int)n, Rsk, n, q.tol, f2, s};
+    t1[p] = TrsmDesc{m, &s->k, q.A, q.lda, q.J, Rsk, n, q.Q, q.ldq, &s->status};
+    gr[p] = GramDesc{m, (int)n, &s->k, q.Q, q.ldq, (double*)region, G, n, &s->status};
+    po[p] = PotrfDesc{(int)n, G, n, Rpre, n, s};
+    s2[p] = Stage2Desc{Rpre, n, q.tol > 0.0 ? 0 : 1, s};
+    t2[p] = TrsmDesc{m, &s->k, q.Q, q.ldq, nullptr, Rpre, n, q.Q, q.ldq, &s->status};
+    tm[p] = TrmmDesc{(int)n, &s->k, Rpre, n, Rsk, n, q.R, q.ldr, &s->status};
+    fi[p] = FinalDesc{s, q.k_out, q.status_out};
+    b_list[p + 1] = b_list[p] + sketch_list_tiles(S);
+    b_part[p + 1] = b_part[p] + sketch_partial_tiles(S);
+    b_comb[p + 1] = b_comb[p] + sketch_combine_tiles(S);
+    b_gath[p + 1] = b_gath[p] + n;
+    b_trsm[p + 1] = b_trsm[p] + trsm_tiles(m);
+    b_gp[p + 1] = b_gp[p] + gram_partial_tiles(m, (int)n);
+    b_gc[p + 1] = b_gc[p] + gram_combine_tiles((int)n);
+    b_tm[p + 1] = b_tm[p] + trmm_tiles((int)n);
+  }
+  P.max_d = max_d;
+  P.tiles_list = b_list[batch];
+  P.tiles_part = b_part[batch];
+  P.tiles_comb = b_comb[batch];
+  P.tiles_gath = b_gath[batch];
+  P.tiles_trsm = b_trsm[batch];
+  P.tiles_gp = b_gp[batch];
+  P.tiles_gc = b_gc[batch];
+  P.tiles_tm = b_tm[batch];
+  // table image (host), then offsets become device pointers into P.tables
+  std::vector<char>& img = P.image;
+  img.clear();
+  const size_t o_sk = push_table(img, sk), o_qr = push_table(img, qr), o_rk = push_table(img, rk),
+               o_t1 = push_table(img, t1), o_t2 = push_table(img, t2), o_gr = push_table(img, gr),
+               o_po = push_table(img, po), o_s2 = push_table(img, s2), o_tm = push_table(img, tm),
+               o_fi = push_table(img, fi);
+  const size_t o_bl = push_table(img, b_list), o_bp = push_table(img, b_part),
+               o_bc = push_table(img, b_comb), o_bg = push_table(img, b_gath),
+               o_bt = push_table(img, b_trsm), o_bgp = push_table(img, b_gp),
+               o_bgc = push_table(img, b_gc), o_btm = push_table(img, b_tm);
+  char* T = P.tables;
+  P.sk = (const SketchDesc*)(T + o_sk);
+  P.qr = (const QrcpDesc*)(T + o_qr);
+  P.rk = (const RankDesc*)(T + o_rk);
+  P.t1 = (const TrsmDesc*)(T + o_t1);
+  P.t2 = (const TrsmDesc*)(T + o_t2);
+  P.gr = (const GramDesc*)(T + o_gr);
+  P.po = (const PotrfDesc*)(T + o_po);
+  P.s2 = (const Stage2Desc*)(T + o_s2);
+  P.tm = (const TrmmDesc*)(T + o_tm);
+  P.fi = (const FinalDesc*)(T + o_fi);
+  P.base_list = (const int64_t*)(T + o_bl);
+  P.base_part = (const int64_t*)(T + o_bp);
+  P.base_comb = (const int64_t*)(T + o_bc);
+  P.base_gath = (const int64_t*)(T + o_bg);
+  P.base_trsm = (const int64_t*)(T + o_bt);
+  P.base_gp = (const int64_t*)(T + o_bgp);
+  P.base_gc = (const int64_t*)(T + o_bgc);
+  P.base_tm = (const int64_t*)(T + o_btm);
+  return 0;
+}
+
+cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s) {
+  const int np = P.nprob;
+  cudaError_t e = launch_init_scalars_batched(P.scalars, np, s);
+  if (e == cudaSuccess) e = launch_sketch_batched(0, P.sk, P.base_list, np, P.tiles_list, P.max_d, s);
+  if (e == cudaSuccess) e = launch_sketch_batched(1, P.sk, P.base_part, np, P.tiles_part, P.max_d, s);
+  if (e == cudaSuccess) e = launch_sketch_batched(2, P.sk, P.base_comb, np, P.tiles_comb, P.max_d, s);
+  if (e == cudaSuccess) e = launch_qrcp_batched(P.qr, np, P.base_gath, P.tiles_gath, s);
+  if (e == cudaSuccess) e = launch_rank_batched(P.rk, np, s);
+  if (e == cudaSuccess) e = launch_trsm_rut_batched(P.t1, P.base_trsm, np, P.tiles_trsm, s);
+  if (e == cudaSuccess) e = launch_gram_batched(0, P.gr, P.base_gp, np, P.tiles_gp, s);
+  if (e == cudaSuccess) e = launch_gram_batched(1, P.gr, P.base_gc, np, P.tiles_gc, s);
+  if (e == cudaSuccess) e = launch_potrf_batched(P.po, np, s);
+  if (e == cudaSuccess) e = launch_rank_stage2_batched(P.s2, np, s);
+  if (e == cudaSuccess) e = launch_trsm_rut_batched(P.t2, P.base_trsm, np, P.tiles_trsm, s);
+  if (e == cudaSuccess) e = launch_trmm_batched(P.tm, P.base_tm, np, P.tiles_tm, s);
+  if (e == cudaSuccess) e = launch_finalize_batched(P.fi, np, s);
+  return e;
+}
+
+}  // namespace cqrrpt

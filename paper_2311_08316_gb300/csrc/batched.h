@@ -1,0 +1,68 @@
+// Host-side planning of a batched CQRRPT (see batched.cu).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "kernels.h"
+
+namespace cqrrpt {
+
+// One problem of a batch (all pointers are device pointers).
+struct BatchProblem {
+  int64_t m, n, d;
+  int nnz;
+  double tol;
+  uint64_t seed;
+  const double* A;
+  int64_t lda;
+  double* Q;
+  int64_t ldq;
+  double* R;
+  int64_t ldr;
+  int64_t* J;
+  int64_t* k_out;     // device, may be null
+  int* status_out;    // device, may be null
+};
+
+struct BatchPlan {
+  int nprob = 0, max_d = 1;
+  int64_t tiles_list = 0, tiles_part = 0, tiles_comb = 0, tiles_gath = 0, tiles_trsm = 0,
+          tiles_gp = 0, tiles_gc = 0, tiles_tm = 0;
+  DeviceScalars* scalars = nullptr;  // device, nprob entries
+  char* tables = nullptr;            // device image of `image`
+  std::vector<char> image;           // host image of the tables
+  const SketchDesc* sk = nullptr;
+  const QrcpDesc* qr = nullptr;
+  const RankDesc* rk = nullptr;
+  const TrsmDesc* t1 = nullptr;
+  const TrsmDesc* t2 = nullptr;
+  const GramDesc* gr = nullptr;
+  const PotrfDesc* po = nullptr;
+  const Stage2Desc* s2 = nullptr;
+  const TrmmDesc* tm = nullptr;
+  const FinalDesc* fi = nullptr;
+  const int64_t *base_list = nullptr, *base_part = nullptr, *base_comb = nullptr,
+                *base_gath = nullptr, *base_trsm = nullptr, *base_gp = nullptr,
+                *base_gc = nullptr, *base_tm = nullptr;
+};
+
+// workspace of one problem inside a batch
+int64_t problem_workspace_bytes(int64_t m, int64_t n, int64_t d, int nnz);
+// upper bound of the table image for `batch` problems
+inline int64_t batch_table_bytes(int batch) {
+  const int64_t descs = 10 * 256 + (int64_t)batch * (sizeof(SketchDesc) + sizeof(QrcpDesc) +
+                                                      sizeof(RankDesc) + 2 * sizeof(TrsmDesc) +
+                                                      sizeof(GramDesc) + sizeof(PotrfDesc) +
+                                                      sizeof(Stage2Desc) + sizeof(TrmmDesc) +
+                                                      sizeof(FinalDesc));
+  const int64_t bases = 8 * (256 + (int64_t)(batch + 1) * 8);
+  return align256(descs + bases + 256);
+}
+// Fills P (P.scalars and P.tables must be set by the caller beforehand) and
+// carves every problem's workspace from ws_base onward.
+int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base);
+// Enqueues the 14 batched launches.
+cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s);
+cudaError_t sketch_set_attributes(int max_d);
+
+}  // namespace cqrrpt

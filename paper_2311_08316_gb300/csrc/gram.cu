@@ -2,42 +2,51 @@
 // the CholeskyQR step, Sec. 2.1).
 //
 // The sum over the m rows is blocked: for each row block b of kRowBlock rows
-// gram_partial_kernel forms P_b[a, c] = sum_{r in b} X[r, a] X[r, c] in
-// ascending r with one fma per term (a <= c); gram_combine_kernel then adds
-// the blocks in ascending order, G[a, c] = ((P_0 + P_1) + P_2) + ..., and
-// mirrors the upper triangle.  One CTA computes one kGramTile x kGramTile
-// output tile of one row block; each of its 64 threads owns a 4 x 4
-// register tile, and rows are staged kGramRows at a time in shared memory.
-// The kernel is bound by the FP64 pipe.
+// gram_partial forms P_b[a, c] = sum_{r in b} X[r, a] X[r, c] in ascending r
+// with one fma per term (a <= c); gram_combine then adds the blocks in
+// ascending order, G[a, c] = ((P_0 + P_1) + P_2) + ..., and mirrors the
+// upper triangle.  One CTA computes one kGramTile x kGramTile output tile of
+// one row block; each of its 64 threads owns a 4 x 4 register tile, and rows
+// are staged kGramRows at a time in shared memory.  The kernel is bound by
+// the FP64 pipe.  Single-problem and batched launches share the bodies.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace cqrrpt {
 
-int64_t gram_workspace_bytes(int64_t m, int64_t n) {
-  const int64_t nb = (m + kRowBlock - 1) / kRowBlock;
-  return align256(nb * n * n * 8);
+static __host__ __device__ int64_t gram_nblocks(int64_t m) {
+  return (m + kRowBlock - 1) / kRowBlock;
+}
+static __host__ __device__ int64_t gram_ntri(int kmax) {
+  const int64_t t1 = (kmax + kGramTile - 1) / kGramTile;
+  return t1 * (t1 + 1) / 2;
 }
 
-__global__ void __launch_bounds__(64) gram_partial_kernel(int64_t m, int n_ld,
-                                                          const int64_t* __restrict__ k_dev,
-                                                          const double* __restrict__ X, int64_t ldx,
-                                                          double* partial,
-                                                          const int* __restrict__ status) {
+int64_t gram_workspace_bytes(int64_t m, int64_t n) { return align256(gram_nblocks(m) * n * n * 8); }
+int64_t gram_partial_tiles(int64_t m, int kmax) { return gram_nblocks(m) * gram_ntri(kmax); }
+int64_t gram_combine_tiles(int kmax) {
+  return ((int64_t)kmax * kmax + kCombineThreads - 1) / kCombineThreads;
+}
+
+__device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& D) {
   __shared__ double Xa[kGramTile][kGramRows + 1];  // [col][row]
   __shared__ double Xc[kGramTile][kGramRows + 1];
-  if (*status != kOk) return;
-  const int k = (int)*k_dev;
-  // tile index -> (ta, tc) with ta <= tc
+  if (*D.status != kOk) return;
+  const int k = (int)*D.k_dev;
+  const int64_t ntri = gram_ntri(D.n_ld);
+  const int64_t b = tile / ntri;
+  int t = (int)(tile - b * ntri);
+  // triangular tile index -> (ta, tc) with ta <= tc, for the device k
   const int tiles_1d = (k + kGramTile - 1) / kGramTile;
-  int t = blockIdx.x, ta = 0;
+  int ta = 0;
   while (ta < tiles_1d && t >= tiles_1d - ta) { t -= tiles_1d - ta; ++ta; }
   if (ta >= tiles_1d) return;
   const int tc = ta + t;
-  const int64_t b = blockIdx.y;
   const int64_t r0 = b * kRowBlock;
-  const int rows = (int)min64(kRowBlock, m - r0);
+  const int rows = (int)min64(kRowBlock, D.m - r0);
   if (rows <= 0) return;
+  const double* X = D.X;
+  const int64_t ldx = D.ldx;
   const int a0 = ta * kGramTile, c0 = tc * kGramTile;
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
   double acc[4][4];
@@ -69,7 +78,8 @@ __global__ void __launch_bounds__(64) gram_partial_kernel(int64_t m, int n_ld,
         for (int v = 0; v < 4; ++v) acc[u][v] = __fma_rn(va[u], vc[v], acc[u][v]);
     }
   }
-  double* P = partial + b * (int64_t)n_ld * n_ld;
+  const int n_ld = D.n_ld;
+  double* P = D.partial + b * (int64_t)n_ld * n_ld;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -79,38 +89,61 @@ __global__ void __launch_bounds__(64) gram_partial_kernel(int64_t m, int n_ld,
     }
 }
 
-__global__ void gram_combine_kernel(int64_t nblocks, int n_ld, const int64_t* __restrict__ k_dev,
-                                    const double* __restrict__ partial, double* G, int64_t ldg,
-                                    const int* __restrict__ status) {
-  if (*status != kOk) return;
-  const int k = (int)*k_dev;
-  const int64_t total = (int64_t)k * k;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx / k), a = (int)(idx - (int64_t)c * k);
-    if (a > c) continue;
-    const int64_t off = (int64_t)c * n_ld + a;
-    double tsum = 0.0;
-    for (int64_t b = 0; b < nblocks; ++b)
-      tsum = __dadd_rn(tsum, partial[b * (int64_t)n_ld * n_ld + off]);
-    G[(int64_t)c * ldg + a] = tsum;
-    G[(int64_t)a * ldg + c] = tsum;
-  }
+__device__ __forceinline__ void gram_combine_body(int64_t tile, const GramDesc& D) {
+  if (*D.status != kOk) return;
+  const int k = (int)*D.k_dev;
+  const int n_ld = D.n_ld;
+  const int64_t nblocks = gram_nblocks(D.m);
+  const int64_t idx = tile * kCombineThreads + threadIdx.x;
+  if (idx >= (int64_t)k * k) return;
+  const int c = (int)(idx / k), a = (int)(idx - (int64_t)c * k);
+  if (a > c) return;
+  const int64_t off = (int64_t)c * n_ld + a;
+  double tsum = 0.0;
+  for (int64_t b = 0; b < nblocks; ++b)
+    tsum = __dadd_rn(tsum, D.partial[b * (int64_t)n_ld * n_ld + off]);
+  D.G[(int64_t)c * D.ldg + a] = tsum;
+  D.G[(int64_t)a * D.ldg + c] = tsum;
+}
+
+__global__ void __launch_bounds__(64) gram_partial_kernel(GramDesc D) {
+  gram_partial_body(blockIdx.x, D);
+}
+__global__ void __launch_bounds__(kCombineThreads) gram_combine_kernel(GramDesc D) {
+  gram_combine_body(blockIdx.x, D);
+}
+__global__ void __launch_bounds__(64) gram_partial_batched_kernel(const GramDesc* D,
+                                                                  const int64_t* base, int np) {
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  gram_partial_body(t, D[p]);
+}
+__global__ void __launch_bounds__(kCombineThreads) gram_combine_batched_kernel(const GramDesc* D,
+                                                                               const int64_t* base,
+                                                                               int np) {
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  gram_combine_body(t, D[p]);
 }
 
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
                         cudaStream_t stream) {
-  const int64_t nb = (m + kRowBlock - 1) / kRowBlock;
-  const int t1 = (kmax + kGramTile - 1) / kGramTile;
-  const int tiles = t1 * (t1 + 1) / 2;
-  double* partial = (double*)work;
-  dim3 grid((unsigned)tiles, (unsigned)nb);
-  gram_partial_kernel<<<grid, 64, 0, stream>>>(m, kmax, k_dev, X, ldx, partial, status);
-  const int64_t total = (int64_t)kmax * kmax;
-  const unsigned cgrid = (unsigned)min64((total + 255) / 256, 152 * 16);
-  gram_combine_kernel<<<cgrid, 256, 0, stream>>>(nb, kmax, k_dev, partial, G, ldg, status);
+  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status};
+  gram_partial_kernel<<<(unsigned)gram_partial_tiles(m, kmax), 64, 0, stream>>>(D);
+  gram_combine_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
   count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* base, int np,
+                                int64_t total_tiles, cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  if (phase == 0)
+    gram_partial_batched_kernel<<<(unsigned)total_tiles, 64, 0, stream>>>(D, base, np);
+  else
+    gram_combine_batched_kernel<<<(unsigned)total_tiles, kCombineThreads, 0, stream>>>(D, base, np);
+  count_launches(1);
   return cudaGetLastError();
 }
 

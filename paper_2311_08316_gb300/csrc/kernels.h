@@ -1,12 +1,13 @@
-// Internal launch interface between the C-ABI layer (api.cu) and the kernel
-// translation units.  Every launcher enqueues on `stream`, never
-// synchronises, and returns the launch error (cudaSuccess if none).
-// Ranks and status words live in device memory so that a whole
-// factorisation can be enqueued without a host round trip.
+// Internal launch interface between the C-ABI layer (api.cu, batched.cu) and
+// the kernel translation units.  Every launcher enqueues on `stream`, never
+// synchronises, and returns the launch error (cudaSuccess if none).  Ranks
+// and status words live in device memory so that a whole factorisation can
+// be enqueued without a host round trip.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "batch.cuh"
 #include "common.cuh"
 
 namespace cqrrpt {
@@ -20,70 +21,92 @@ constexpr int kTrsmTB = 64;       // TRSM: rows of T staged per chunk
 constexpr int kGramTile = 32;     // SYRK: output tile edge
 constexpr int kGramRows = 32;     // SYRK: rows staged per chunk
 constexpr int kCholNB = 32;       // Cholesky panel width
+constexpr int kCombineThreads = 256;
 
 inline int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
-// Device scalars of one factorisation.
-struct DeviceScalars {
-  int64_t k;         // current rank (rank rule, then Remark 3, then stage 2)
-  int64_t fail;      // Cholesky failure column or -1
-  int status;        // kOk / kNonFinite / kTimeout ...
-  int pad;
-  GridBarrier bar;
-};
+// Process-wide count of kernels this library has launched.
+void count_launches(int n);
 
 // ---- Alg. 2 line 1 -------------------------------------------------------
 int64_t sketch_workspace_bytes(int64_t m, int64_t n, int d, int s);
+// Carves the scratch of one sketch out of `work` into D.
+void sketch_carve(SketchDesc& D, void* work);
 cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, int d, int s,
                           uint64_t seed, double scale, double* Msk, int64_t ldsk, void* work,
                           int* status, cudaStream_t stream);
+int64_t sketch_list_tiles(const SketchDesc& D);
+int64_t sketch_partial_tiles(const SketchDesc& D);
+int64_t sketch_combine_tiles(const SketchDesc& D);
+// phase 0: lists, 1: partial sums, 2: combine
+cudaError_t launch_sketch_batched(int phase, const SketchDesc* D, const int64_t* base, int nprob,
+                                  int64_t total_tiles, int max_d, cudaStream_t stream);
 
 // ---- Alg. 2 line 2 -------------------------------------------------------
 int64_t qrcp_workspace_bytes(int64_t n);
+QrcpWork qrcp_carve(void* work, int n);
 // X (d x n, ld ldx) is overwritten; J (n, int64) receives the pivots;
 // Rsk (n x n, ld ldr) receives the sign-normalised upper triangle.
 cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double* Rsk,
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
                         cudaStream_t stream);
+// one CTA per problem (no grid barrier), then the gather
+cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gather_base,
+                                int64_t gather_tiles, cudaStream_t stream);
 
 // ---- Alg. 2 line 3 -------------------------------------------------------
 // tol > 0: leading count of R_jj > tol R_00; tol <= 0: stage 1.
 // f2: n + 1 doubles of scratch.
 cudaError_t launch_rank(int n, const double* Rsk, int64_t ldr, double tol, DeviceScalars* sc,
                         double* f2, cudaStream_t stream);
+cudaError_t launch_rank_batched(const RankDesc* D, int nprob, cudaStream_t stream);
 // stage 2 on R^pre after the Cholesky (k := min(k, fail) first).
 cudaError_t launch_rank_stage2(const double* Rpre, int64_t ldp, bool stage2, DeviceScalars* sc,
                                cudaStream_t stream);
+cudaError_t launch_rank_stage2_batched(const Stage2Desc* D, int nprob, cudaStream_t stream);
 
 // ---- Alg. 2 lines 4 and 7 ------------------------------------------------
 // X[:, 0:k] = B[:, cols[0:k]] * T^{-1}; cols may be null (identity); X may
-// alias B when cols is null.  k read from *k_dev; kmax bounds the grid.
+// alias B when cols is null.  k read from *k_dev.
+int64_t trsm_tiles(int64_t m);
 cudaError_t launch_trsm_rut(int64_t m, int kmax, const int64_t* k_dev, const double* B,
                             int64_t ldb, const int64_t* cols, const double* T, int64_t ldt,
                             double* X, int64_t ldx, const int* status, cudaStream_t stream);
+cudaError_t launch_trsm_rut_batched(const TrsmDesc* D, const int64_t* base, int nprob,
+                                    int64_t total_tiles, cudaStream_t stream);
 
 // ---- Alg. 2 line 5 -------------------------------------------------------
 int64_t gram_workspace_bytes(int64_t m, int64_t n);
+int64_t gram_partial_tiles(int64_t m, int kmax);
+int64_t gram_combine_tiles(int kmax);
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
                         cudaStream_t stream);
+// phase 0: partial tiles, 1: combine
+cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* base, int nprob,
+                                int64_t total_tiles, cudaStream_t stream);
 
 // ---- Alg. 2 line 6 -------------------------------------------------------
 // Factors G (overwritten as working storage) into R (upper); on a
 // non-positive pivot at column j records sc->fail = j (Remark 3).
 cudaError_t launch_potrf(int kmax, double* G, int64_t ldg, double* R, int64_t ldr,
                          DeviceScalars* sc, cudaStream_t stream);
+// one CTA per problem runs every panel
+cudaError_t launch_potrf_batched(const PotrfDesc* D, int nprob, cudaStream_t stream);
 
 // ---- Alg. 2 line 8 -------------------------------------------------------
+int64_t trmm_tiles(int n);
 cudaError_t launch_trmm(int n, const int64_t* k_dev, const double* Rpre, int64_t ldp,
                         const double* Rsk, int64_t ldsk, double* R, int64_t ldr,
                         const int* status, cudaStream_t stream);
+cudaError_t launch_trmm_batched(const TrmmDesc* D, const int64_t* base, int nprob,
+                                int64_t total_tiles, cudaStream_t stream);
 
 // ---- small helpers -------------------------------------------------------
-// Process-wide count of kernels this library has launched.
-void count_launches(int n);
 cudaError_t launch_init_scalars(DeviceScalars* sc, int64_t k, cudaStream_t stream);
+cudaError_t launch_init_scalars_batched(DeviceScalars* sc, int nprob, cudaStream_t stream);
 cudaError_t launch_finalize(DeviceScalars* sc, int64_t* k_out, int* status_out,
                             cudaStream_t stream);
+cudaError_t launch_finalize_batched(const FinalDesc* D, int nprob, cudaStream_t stream);
 
 }  // namespace cqrrpt

@@ -2,39 +2,29 @@
 // (Businger-Golub max-norm pivoting, as LAPACK GEQP3 which the paper uses,
 // Sec. 3.2 and Appendix A.1) and the rank rule of Sec. 4.3.
 //
-// qrcp_kernel is one cooperative, persistent launch of G CTAs.  Physical
-// columns never move: CTA b owns the physical columns b, b+G, b+2G, ... for
-// the whole factorisation (one warp per column) and a position <-> column
-// map (phys/posof) records the swaps, so a pivot exchange moves no data.
-// Each of the n steps is:
+// The QRCP of one problem runs on G CTAs that stay resident for all n steps
+// (one cooperative launch for a single large problem; G = 1 and one CTA per
+// problem for a batch).  Physical columns never move: CTA b owns the physical
+// columns b, b+G, b+2G, ... for the whole factorisation (one warp per
+// column) and a position <-> column map (phys/posof) records the swaps, so a
+// pivot exchange moves no data.  Each of the n steps is:
 //   1. every CTA reduces the per-CTA candidates (largest partial norm,
 //      lowest position on exact ties) to the same pivot column P;
 //   2. the owner of P forms the reflector H = I - tau v v^T (v written over
 //      the column below the diagonal, beta on it); CTA 0 records the swap;
-//      -- grid barrier --
+//      -- barrier --
 //   3. every CTA applies H to its unpivoted columns (w = v^T x by dot32,
 //      x += v (-tau w) with one fma per element) and downdates their norms
 //      (LAPACK dlaqp2 rule with the Drmac-Bujanovic recompute safeguard),
-//      then publishes its candidate;  -- grid barrier --
-// All reads of data written by other CTAs bypass L1 (ld.global.cg).
-// Grid barriers spin a bounded number of times (status kTimeout on expiry).
+//      then publishes its candidate;  -- barrier --
+// All reads of data written by other CTAs bypass L1 (ld.global.cg).  Grid
+// barriers spin a bounded number of times (status kTimeout on expiry).
 #include "common.cuh"
 #include "kernels.h"
 
 namespace cqrrpt {
 
-struct QrcpWork {
-  double* vn1;
-  double* vn2;
-  double* tau;
-  int* phys;
-  int* posof;
-  double* cand_val;
-  int* cand_pos;
-  int* cand_col;
-};
-
-static QrcpWork carve_qrcp(void* work, int n) {
+QrcpWork qrcp_carve(void* work, int n) {
   char* p = (char*)work;
   QrcpWork w;
   w.vn1 = (double*)p; p += align256((int64_t)n * 8);
@@ -68,19 +58,22 @@ __device__ __forceinline__ bool cand_better(double va, int pa, double vb, int pb
   return va > vb || (va == vb && pa < pb);
 }
 
-__global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(int d, int n, double* X, int64_t ldx,
-                                                            QrcpWork w, DeviceScalars* sc,
-                                                            double tol3z) {
-  const int G = gridDim.x, bid = blockIdx.x;
+__device__ __forceinline__ void qrcp_body(const int G, const int bid, const QrcpDesc& D,
+                                          double tol3z) {
+  const int d = D.d, n = D.n;
+  double* X = D.X;
+  const int64_t ldx = D.ldx;
+  const QrcpWork& w = D.w;
+  DeviceScalars* sc = D.sc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   int* status = &sc->status;
   __shared__ int sh_P, sh_p;
   __shared__ double sh_tau, sh_beta, sh_denom;
   __shared__ int sh_nz;
-  __shared__ double red_val[kQrcpThreads / 32];
-  __shared__ int red_pos[kQrcpThreads / 32];
-  __shared__ int red_col[kQrcpThreads / 32];
+  __shared__ double red_val[32];
+  __shared__ int red_pos[32];
+  __shared__ int red_col[32];
 
   if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
 
@@ -98,8 +91,9 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(int d, int n, double
     }
   }
 
+  // each warp scans its owned columns (all lanes alike), then thread 0
+  // reduces the warps and publishes the CTA's candidate
   auto publish_candidate = [&](int j_done) {
-    // best owned column with position > j_done
     double bv = -1.0;
     int bp = 0x7fffffff, bc = -1;
     for (int q = warp;; q += nwarps) {
@@ -120,9 +114,6 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(int d, int n, double
       w.cand_col[bid] = bc;
     }
   };
-  // lane 0 of each warp holds its warp's best only; redo per-warp reduction
-  // inside publish: each lane of the warp scanned the same columns, so all
-  // lanes agree and lane 0's copy is representative.
   __syncthreads();
   publish_candidate(-1);
   if (!grid_sync(&sc->bar, G, status)) return;
@@ -240,29 +231,47 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(int d, int n, double
   }
 }
 
+__global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(QrcpDesc D, double tol3z) {
+  qrcp_body(gridDim.x, blockIdx.x, D, tol3z);
+}
+
+__global__ void __launch_bounds__(1024) qrcp_batched_kernel(const QrcpDesc* D, double tol3z) {
+  qrcp_body(1, 0, D[blockIdx.x], tol3z);
+}
+
 // R^sk[i, q] = s_i X[i, phys[q]] for i <= q < n (0 below), s_i = -1 when the
 // diagonal X[i, phys[i]] is negative; J[q] = phys[q].
-__global__ void qrcp_gather_kernel(int n, const double* X, int64_t ldx, const int* phys,
-                                   int64_t* J, double* Rsk, int64_t ldr, const int* status) {
-  const int q = blockIdx.x;
-  if (*status != kOk) return;
+__device__ __forceinline__ void qrcp_gather_body(int q, const QrcpDesc& D) {
+  if (D.sc->status != kOk) return;
+  const int n = D.n;
+  const int* phys = D.w.phys;
   const int pq = phys[q];
-  if (threadIdx.x == 0) J[q] = pq;
+  if (threadIdx.x == 0) D.J[q] = pq;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double v = 0.0;
     if (i <= q) {
-      const double diag = X[(int64_t)phys[i] * ldx + i];
-      v = X[(int64_t)pq * ldx + i];
+      const double diag = D.X[(int64_t)phys[i] * D.ldx + i];
+      v = D.X[(int64_t)pq * D.ldx + i];
       if (diag < 0.0) v = -v;
     }
-    Rsk[(int64_t)q * ldr + i] = v;
+    D.Rsk[(int64_t)q * D.ldr + i] = v;
   }
 }
+
+__global__ void qrcp_gather_kernel(QrcpDesc D) { qrcp_gather_body(blockIdx.x, D); }
+
+__global__ void qrcp_gather_batched_kernel(const QrcpDesc* D, const int64_t* base, int np) {
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  qrcp_gather_body((int)t, D[p]);
+}
+
+static double tol3z_value() { return sqrt(ldexp(1.0, -53)); }
 
 cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double* Rsk,
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
                         cudaStream_t stream) {
-  QrcpWork w = carve_qrcp(work, n);
+  QrcpDesc D{d, n, X, ldx, qrcp_carve(work, n), J, Rsk, ldr, sc};
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, kQrcpThreads, 0);
   if (e != cudaSuccess) return e;
@@ -271,12 +280,21 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   if (G > num_sms) G = num_sms;
   if (G > 4096) G = 4096;
   if (G < 1) G = 1;
-  const double tol3z = sqrt(ldexp(1.0, -53));
-  void* args[] = {&d, &n, &X, &ldx, &w, &sc, (void*)&tol3z};
+  const double tol3z = tol3z_value();
+  void* args[] = {&D, (void*)&tol3z};
   e = cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(G), dim3(kQrcpThreads), args, 0,
                                   stream);
   if (e != cudaSuccess) return e;
-  qrcp_gather_kernel<<<n, 128, 0, stream>>>(n, X, ldx, w.phys, J, Rsk, ldr, &sc->status);
+  qrcp_gather_kernel<<<n, 128, 0, stream>>>(D);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gather_base,
+                                int64_t gather_tiles, cudaStream_t stream) {
+  if (nprob <= 0) return cudaSuccess;
+  qrcp_batched_kernel<<<nprob, 512, 0, stream>>>(D, tol3z_value());
+  qrcp_gather_batched_kernel<<<(unsigned)gather_tiles, 128, 0, stream>>>(D, gather_base, nprob);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -286,18 +304,22 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
 // tol <= 0: stage 1, k_o = min{l : ||C_l||_F <= u max|R|}, with
 // ||C_l||^2 = ||R[l, l:]||^2 + ||C_{l+1}||^2 (row sums ascending by fma).
 // ---------------------------------------------------------------------------
-__global__ void rank_kernel(int n, const double* Rsk, int64_t ldr, double tol, DeviceScalars* sc,
-                            double* f2 /* n + 1 */) {
+__device__ __forceinline__ void rank_body(const RankDesc& D) {
   __shared__ double sh_max[1024];
   __shared__ int sh_k;
+  DeviceScalars* sc = D.sc;
+  const int n = D.n;
+  const double* Rsk = D.Rsk;
+  const int64_t ldr = D.ldr;
+  double* f2 = D.f2;
   if (sc->status != kOk) {
     if (threadIdx.x == 0) sc->k = 0;
     return;
   }
-  if (tol > 0.0) {
+  if (D.tol > 0.0) {
     if (threadIdx.x == 0) sh_k = n;
     __syncthreads();
-    const double thresh = __dmul_rn(tol, Rsk[0]);
+    const double thresh = __dmul_rn(D.tol, Rsk[0]);
     for (int j = threadIdx.x; j < n; j += blockDim.x)
       if (!(Rsk[(int64_t)j * ldr + j] > thresh)) atomicMin(&sh_k, j);
     __syncthreads();
@@ -336,24 +358,38 @@ __global__ void rank_kernel(int n, const double* Rsk, int64_t ldr, double tol, D
   }
 }
 
+__global__ void __launch_bounds__(1024) rank_kernel(RankDesc D) { rank_body(D); }
+__global__ void __launch_bounds__(1024) rank_batched_kernel(const RankDesc* D) {
+  rank_body(D[blockIdx.x]);
+}
+
 cudaError_t launch_rank(int n, const double* Rsk, int64_t ldr, double tol, DeviceScalars* sc,
                         double* f2, cudaStream_t stream) {
-  rank_kernel<<<1, 1024, 0, stream>>>(n, Rsk, ldr, tol, sc, f2);
+  RankDesc D{n, Rsk, ldr, tol, f2, sc};
+  rank_kernel<<<1, 1024, 0, stream>>>(D);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank_batched(const RankDesc* D, int nprob, cudaStream_t stream) {
+  if (nprob <= 0) return cudaSuccess;
+  rank_batched_kernel<<<nprob, 1024, 0, stream>>>(D);
   count_launches(1);
   return cudaGetLastError();
 }
 
 // Stage 2: k := min(k, fail) (Remark 3), then if requested the largest
 // l <= k with max/min of diag(R^pre)[0:l] <= 10.
-__global__ void rank_stage2_kernel(const double* Rpre, int64_t ldp, int stage2, DeviceScalars* sc) {
+__device__ __forceinline__ void stage2_body(const Stage2Desc& D) {
+  DeviceScalars* sc = D.sc;
   if (sc->status != kOk) { sc->k = 0; return; }
   int64_t k = sc->k;
   if (sc->fail >= 0 && sc->fail < k) k = sc->fail;
-  if (stage2 && k > 0) {
+  if (D.stage2 && k > 0) {
     int64_t kk = 0;
     double mx = 0.0, mn = 0.0;
     for (int64_t l = 1; l <= k; ++l) {
-      const double dl = Rpre[(l - 1) * ldp + (l - 1)];
+      const double dl = D.Rpre[(l - 1) * D.ldp + (l - 1)];
       if (l == 1) { mx = dl; mn = dl; }
       else { mx = dl > mx ? dl : mx; mn = dl < mn ? dl : mn; }
       if (__ddiv_rn(mx, mn) <= 10.0) kk = l; else break;
@@ -363,14 +399,28 @@ __global__ void rank_stage2_kernel(const double* Rpre, int64_t ldp, int stage2, 
   sc->k = k;
 }
 
+__global__ void rank_stage2_kernel(Stage2Desc D) { stage2_body(D); }
+__global__ void rank_stage2_batched_kernel(const Stage2Desc* D, int np) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < np) stage2_body(D[p]);
+}
+
 cudaError_t launch_rank_stage2(const double* Rpre, int64_t ldp, bool stage2, DeviceScalars* sc,
                                cudaStream_t stream) {
-  rank_stage2_kernel<<<1, 1, 0, stream>>>(Rpre, ldp, stage2 ? 1 : 0, sc);
+  Stage2Desc D{Rpre, ldp, stage2 ? 1 : 0, sc};
+  rank_stage2_kernel<<<1, 1, 0, stream>>>(D);
   count_launches(1);
   return cudaGetLastError();
 }
 
-__global__ void init_scalars_kernel(DeviceScalars* sc, int64_t k) {
+cudaError_t launch_rank_stage2_batched(const Stage2Desc* D, int nprob, cudaStream_t stream) {
+  if (nprob <= 0) return cudaSuccess;
+  rank_stage2_batched_kernel<<<(nprob + 127) / 128, 128, 0, stream>>>(D, nprob);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ void init_scalars_body(DeviceScalars* sc, int64_t k) {
   sc->k = k;
   sc->fail = -1;
   sc->status = kOk;
@@ -379,13 +429,26 @@ __global__ void init_scalars_kernel(DeviceScalars* sc, int64_t k) {
   sc->bar.generation = 0;
 }
 
+__global__ void init_scalars_kernel(DeviceScalars* sc, int64_t k) { init_scalars_body(sc, k); }
+__global__ void init_scalars_batched_kernel(DeviceScalars* sc, int np) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < np) init_scalars_body(sc + p, 0);
+}
+
 cudaError_t launch_init_scalars(DeviceScalars* sc, int64_t k, cudaStream_t stream) {
   init_scalars_kernel<<<1, 1, 0, stream>>>(sc, k);
   count_launches(1);
   return cudaGetLastError();
 }
 
-__global__ void finalize_kernel(DeviceScalars* sc, int64_t* k_out, int* status_out) {
+cudaError_t launch_init_scalars_batched(DeviceScalars* sc, int nprob, cudaStream_t stream) {
+  if (nprob <= 0) return cudaSuccess;
+  init_scalars_batched_kernel<<<(nprob + 127) / 128, 128, 0, stream>>>(sc, nprob);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ void finalize_body(DeviceScalars* sc, int64_t* k_out, int* status_out) {
   int st = sc->status;
   if (st == kOk && sc->k == 0) st = kRankZero;
   if (st != kOk && st != kRankZero) sc->k = 0;
@@ -393,9 +456,24 @@ __global__ void finalize_kernel(DeviceScalars* sc, int64_t* k_out, int* status_o
   if (status_out) *status_out = st;
 }
 
+__global__ void finalize_kernel(DeviceScalars* sc, int64_t* k_out, int* status_out) {
+  finalize_body(sc, k_out, status_out);
+}
+__global__ void finalize_batched_kernel(const FinalDesc* D, int np) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < np) finalize_body(D[p].sc, D[p].k_out, D[p].status_out);
+}
+
 cudaError_t launch_finalize(DeviceScalars* sc, int64_t* k_out, int* status_out,
                             cudaStream_t stream) {
   finalize_kernel<<<1, 1, 0, stream>>>(sc, k_out, status_out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(const FinalDesc* D, int nprob, cudaStream_t stream) {
+  if (nprob <= 0) return cudaSuccess;
+  finalize_batched_kernel<<<(nprob + 127) / 128, 128, 0, stream>>>(D, nprob);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -1,21 +1,19 @@
 // Alg. 2 line 1: the sketch M^sk = S M with the SASO S of Sec. 3.3.1.
 //
 // Three kernels:
-//   saso_lists_kernel     per row block (kRowBlock rows) of M, the SASO
-//                         columns of that block regrouped by target row i:
-//                         for each i the rows r of the block with S[i,r] != 0
-//                         in ascending r, with their signs (a CSR of the
-//                         block of S by target row).
-//   sketch_partial_kernel per (row block b, group of kSkCols columns): stages
-//                         the block of M in shared memory (coalesced), then
-//                         one thread per target row i walks its list and
-//                         accumulates +-M[r, c] in ascending r from +0.0,
-//                         giving P_b[i, c].
-//   sketch_combine_kernel M^sk[i, c] = scale * (P_0 + P_1 + ...) in
-//                         ascending block order from +0.0; flags non-finite
-//                         results.
+//   saso_lists     per row block (kRowBlock rows) of M, the SASO columns of
+//                  that block regrouped by target row i: for each i the rows
+//                  r of the block with S[i,r] != 0 in ascending r, with their
+//                  signs (a CSR of the block of S by target row).
+//   sketch_partial per (row block b, group of kSkCols columns): stages the
+//                  block of M in shared memory (coalesced), then one thread
+//                  per target row i walks its list and accumulates +-M[r, c]
+//                  in ascending r from +0.0, giving P_b[i, c].
+//   sketch_combine M^sk[i, c] = scale * (P_0 + P_1 + ...) in ascending block
+//                  order from +0.0; flags non-finite results.
 // The arithmetic (FP64 additions in that order, one final scale) is fixed by
-// the data, not by the launch shape.
+// the data, not by the launch shape.  Each kernel exists as a single-problem
+// launch and a batched launch (CTA -> (problem, tile)) over the same body.
 #include "common.cuh"
 #include "kernels.h"
 #include "saso.cuh"
@@ -23,23 +21,21 @@
 namespace cqrrpt {
 
 // entries: (r_local << 1) | negative
-__global__ void saso_lists_kernel(int64_t m, int d, int s, uint64_t seed, int* seg_start,
-                                  uint32_t* entries) {
-  extern __shared__ int sh_lists[];
+__device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, int* sh_lists) {
+  const int d = D.d, s = D.s;
   int* count = sh_lists;          // d
   int* start = sh_lists + d;      // d + 1
-  const int64_t b = blockIdx.x;
   const int64_t r0 = b * kRowBlock;
-  const int rows = (int)min64(kRowBlock, m - r0);
-  int* gstart = seg_start + b * (int64_t)(d + 1);
-  uint32_t* gent = entries + b * (int64_t)kRowBlock * s;
+  const int rows = (int)min64(kRowBlock, D.m - r0);
+  int* gstart = D.seg_start + b * (int64_t)(d + 1);
+  uint32_t* gent = D.entries + b * (int64_t)kRowBlock * s;
 
   for (int i = threadIdx.x; i < d; i += blockDim.x) count[i] = 0;
   __syncthreads();
   int tr[kMaxNnzInline];
   uint32_t neg;
   for (int rl = threadIdx.x; rl < rows; rl += blockDim.x) {
-    saso_column(seed, r0 + rl, d, s, tr, &neg);
+    saso_column(D.seed, r0 + rl, d, s, tr, &neg);
     for (int q = 0; q < s; ++q) atomicAdd(&count[tr[q]], 1);
   }
   __syncthreads();
@@ -65,7 +61,7 @@ __global__ void saso_lists_kernel(int64_t m, int d, int s, uint64_t seed, int* s
   for (int i = threadIdx.x; i < d; i += blockDim.x) count[i] = start[i];  // cursors
   __syncthreads();
   for (int rl = threadIdx.x; rl < rows; rl += blockDim.x) {
-    saso_column(seed, r0 + rl, d, s, tr, &neg);
+    saso_column(D.seed, r0 + rl, d, s, tr, &neg);
     for (int q = 0; q < s; ++q) {
       const int pos = atomicAdd(&count[tr[q]], 1);
       gent[pos] = ((uint32_t)rl << 1) | ((neg >> q) & 1u);
@@ -87,25 +83,24 @@ __global__ void saso_lists_kernel(int64_t m, int d, int s, uint64_t seed, int* s
   }
 }
 
-__global__ void __launch_bounds__(kSkThreads) sketch_partial_kernel(
-    int64_t m, int64_t n, const double* __restrict__ M, int64_t ldm, int d, int s,
-    const int* __restrict__ seg_start, const uint32_t* __restrict__ entries, double* partial) {
-  extern __shared__ double tile[];  // [kRowBlock][kSkCols], row-major
-  const int64_t b = blockIdx.x;
-  const int64_t c0 = (int64_t)blockIdx.y * kSkCols;
+__device__ __forceinline__ void sketch_partial_body(int64_t b, int64_t cg, const SketchDesc& D,
+                                                    double* tile /* [kRowBlock][kSkCols] */) {
+  const int d = D.d;
+  const int64_t n = D.n;
+  const int64_t c0 = cg * kSkCols;
   const int64_t r0 = b * kRowBlock;
-  const int rows = (int)min64(kRowBlock, m - r0);
+  const int rows = (int)min64(kRowBlock, D.m - r0);
   const int ncols = (int)min64(kSkCols, n - c0);
   for (int cc = 0; cc < kSkCols; ++cc) {
     if (cc < ncols) {
-      const double* col = M + (c0 + cc) * ldm + r0;
+      const double* col = D.M + (c0 + cc) * D.ldm + r0;
       for (int rl = threadIdx.x; rl < rows; rl += blockDim.x) tile[rl * kSkCols + cc] = col[rl];
     }
   }
   __syncthreads();
-  const int* st = seg_start + b * (int64_t)(d + 1);
-  const uint32_t* ent = entries + b * (int64_t)kRowBlock * s;
-  double* P = partial + b * n * (int64_t)d;  // P_b: d x n, ld d
+  const int* st = D.seg_start + b * (int64_t)(d + 1);
+  const uint32_t* ent = D.entries + b * (int64_t)kRowBlock * D.s;
+  double* P = D.partial + b * n * (int64_t)d;  // P_b: d x n, ld d
   for (int i = threadIdx.x; i < d; i += blockDim.x) {
     double acc[kSkCols];
 #pragma unroll
@@ -126,25 +121,68 @@ __global__ void __launch_bounds__(kSkThreads) sketch_partial_kernel(
   }
 }
 
-__global__ void sketch_combine_kernel(int64_t nblocks, int64_t n, int d, double scale,
-                                      const double* __restrict__ partial, double* Msk, int64_t ldsk,
-                                      int* status) {
-  const int64_t total = n * (int64_t)d;
+__device__ __forceinline__ void sketch_combine_body(int64_t tile, const SketchDesc& D) {
+  const int d = D.d;
+  const int64_t total = D.n * (int64_t)d;
+  const int64_t nblocks = (D.m + kRowBlock - 1) / kRowBlock;
+  const int64_t idx = tile * kCombineThreads + threadIdx.x;
   bool bad = false;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
+  if (idx < total) {
     const int64_t c = idx / d, i = idx - c * d;
     double t = 0.0;
-    for (int64_t b = 0; b < nblocks; ++b) t = __dadd_rn(t, partial[b * total + idx]);
-    const double v = __dmul_rn(t, scale);
-    Msk[c * ldsk + i] = v;
-    bad |= !isfinite(v);
+    for (int64_t b = 0; b < nblocks; ++b) t = __dadd_rn(t, D.partial[b * total + idx]);
+    const double v = __dmul_rn(t, D.scale);
+    D.Msk[c * D.ldsk + i] = v;
+    bad = !isfinite(v);
   }
-  if (bad) atomicExch(status, kNonFinite);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(D.status, kNonFinite);
 }
 
+// ---- single-problem kernels -------------------------------------------------
+__global__ void saso_lists_kernel(SketchDesc D) {
+  extern __shared__ int sh_lists[];
+  saso_lists_body(blockIdx.x, D, sh_lists);
+}
+
+__global__ void __launch_bounds__(kSkThreads) sketch_partial_kernel(SketchDesc D, int64_t ncg) {
+  extern __shared__ double tile[];
+  sketch_partial_body(blockIdx.x / ncg, blockIdx.x % ncg, D, tile);
+}
+
+__global__ void __launch_bounds__(kCombineThreads) sketch_combine_kernel(SketchDesc D) {
+  sketch_combine_body(blockIdx.x, D);
+}
+
+// ---- batched kernels --------------------------------------------------------
+__global__ void saso_lists_batched_kernel(const SketchDesc* D, const int64_t* base, int np) {
+  extern __shared__ int sh_lists[];
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  saso_lists_body(t, D[p], sh_lists);
+}
+
+__global__ void __launch_bounds__(kSkThreads) sketch_partial_batched_kernel(const SketchDesc* D,
+                                                                            const int64_t* base,
+                                                                            int np) {
+  extern __shared__ double tile[];
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  const int64_t ncg = (D[p].n + kSkCols - 1) / kSkCols;
+  sketch_partial_body(t / ncg, t % ncg, D[p], tile);
+}
+
+__global__ void __launch_bounds__(kCombineThreads) sketch_combine_batched_kernel(
+    const SketchDesc* D, const int64_t* base, int np) {
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  sketch_combine_body(t, D[p]);
+}
+
+// ---- host side --------------------------------------------------------------
+static int64_t nblocks_of(int64_t m) { return (m + kRowBlock - 1) / kRowBlock; }
+
 int64_t sketch_workspace_bytes(int64_t m, int64_t n, int d, int s) {
-  const int64_t nb = (m + kRowBlock - 1) / kRowBlock;
+  const int64_t nb = nblocks_of(m);
   int64_t bytes = 0;
   bytes += align256(nb * (int64_t)(d + 1) * 4);
   bytes += align256(nb * (int64_t)kRowBlock * s * 4);
@@ -152,35 +190,81 @@ int64_t sketch_workspace_bytes(int64_t m, int64_t n, int d, int s) {
   return bytes;
 }
 
+void sketch_carve(SketchDesc& D, void* work) {
+  const int64_t nb = nblocks_of(D.m);
+  char* p = (char*)work;
+  D.seg_start = (int*)p;
+  p += align256(nb * (int64_t)(D.d + 1) * 4);
+  D.entries = (uint32_t*)p;
+  p += align256(nb * (int64_t)kRowBlock * D.s * 4);
+  D.partial = (double*)p;
+}
+
+int64_t sketch_list_tiles(const SketchDesc& D) { return nblocks_of(D.m); }
+int64_t sketch_partial_tiles(const SketchDesc& D) {
+  return nblocks_of(D.m) * ((D.n + kSkCols - 1) / kSkCols);
+}
+int64_t sketch_combine_tiles(const SketchDesc& D) {
+  return (D.n * (int64_t)D.d + kCombineThreads - 1) / kCombineThreads;
+}
+
+static cudaError_t set_smem_attrs(size_t lists_bytes) {
+  cudaError_t e = cudaSuccess;
+  if (lists_bytes > 48 * 1024) {
+    e = cudaFuncSetAttribute(saso_lists_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lists_bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(saso_lists_batched_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists_bytes);
+    if (e != cudaSuccess) return e;
+  }
+  const int tile_bytes = kRowBlock * kSkCols * (int)sizeof(double);
+  e = cudaFuncSetAttribute(sketch_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tile_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sketch_partial_batched_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes);
+  return e;
+}
+
 cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, int d, int s,
                           uint64_t seed, double scale, double* Msk, int64_t ldsk, void* work,
                           int* status, cudaStream_t stream) {
-  const int64_t nb = (m + kRowBlock - 1) / kRowBlock;
-  char* p = (char*)work;
-  int* seg_start = (int*)p;
-  p += align256(nb * (int64_t)(d + 1) * 4);
-  uint32_t* entries = (uint32_t*)p;
-  p += align256(nb * (int64_t)kRowBlock * s * 4);
-  double* partial = (double*)p;
-
+  SketchDesc D{};
+  D.m = m; D.n = n; D.d = d; D.s = s; D.seed = seed; D.scale = scale;
+  D.M = M; D.ldm = ldm; D.Msk = Msk; D.ldsk = ldsk; D.status = status;
+  sketch_carve(D, work);
   const size_t sh_lists = (size_t)(2 * d + 1) * sizeof(int);
-  if (sh_lists > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(saso_lists_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_lists);
-    if (e != cudaSuccess) return e;
-  }
-  saso_lists_kernel<<<(unsigned)nb, 256, sh_lists, stream>>>(m, d, s, seed, seg_start, entries);
-  const size_t sh_tile = (size_t)kRowBlock * kSkCols * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(sketch_partial_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_tile);
+  cudaError_t e = set_smem_attrs(sh_lists);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)nb, (unsigned)((n + kSkCols - 1) / kSkCols));
-  sketch_partial_kernel<<<grid, kSkThreads, sh_tile, stream>>>(m, n, M, ldm, d, s, seg_start,
-                                                                entries, partial);
-  const int64_t total = n * (int64_t)d;
-  const unsigned cgrid = (unsigned)min64((total + 255) / 256, 152 * 16);
-  sketch_combine_kernel<<<cgrid, 256, 0, stream>>>(nb, n, d, scale, partial, Msk, ldsk, status);
+  saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), 256, sh_lists, stream>>>(D);
+  const int64_t ncg = (n + kSkCols - 1) / kSkCols;
+  sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), kSkThreads,
+                          kRowBlock * kSkCols * sizeof(double), stream>>>(D, ncg);
+  sketch_combine_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(D);
   count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t sketch_set_attributes(int max_d) {
+  return set_smem_attrs((size_t)(2 * max_d + 1) * sizeof(int));
+}
+
+// The shared-memory attributes must have been set by sketch_set_attributes
+// (outside any stream capture).
+cudaError_t launch_sketch_batched(int phase, const SketchDesc* D, const int64_t* base, int np,
+                                  int64_t total_tiles, int max_d, cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const size_t sh_lists = (size_t)(2 * max_d + 1) * sizeof(int);
+  if (phase == 0)
+    saso_lists_batched_kernel<<<(unsigned)total_tiles, 256, sh_lists, stream>>>(D, base, np);
+  else if (phase == 1)
+    sketch_partial_batched_kernel<<<(unsigned)total_tiles, kSkThreads,
+                                    kRowBlock * kSkCols * sizeof(double), stream>>>(D, base, np);
+  else
+    sketch_combine_batched_kernel<<<(unsigned)total_tiles, kCombineThreads, 0, stream>>>(D, base,
+                                                                                        np);
+  count_launches(1);
   return cudaGetLastError();
 }
 

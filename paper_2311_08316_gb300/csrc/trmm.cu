@@ -10,27 +10,52 @@
 
 namespace cqrrpt {
 
-__global__ void trmm_kernel(int n, const int64_t* __restrict__ k_dev, const double* __restrict__ Rp,
-                            int64_t ldp, const double* __restrict__ Rs, int64_t lds, double* R,
-                            int64_t ldr, const int* __restrict__ status) {
-  if (*status != kOk) return;
-  const int k = (int)*k_dev;
-  const int c = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kTrmmThreads = 128;
+
+int64_t trmm_tiles(int n) { return (int64_t)((n + kTrmmThreads - 1) / kTrmmThreads) * n; }
+
+// tile -> (column c, row chunk)
+__device__ __forceinline__ void trmm_body(int64_t tile, const TrmmDesc& D) {
+  if (*D.status != kOk) return;
+  const int n = D.n;
+  const int k = (int)*D.k_dev;
+  const int chunks = (n + kTrmmThreads - 1) / kTrmmThreads;
+  const int c = (int)(tile / chunks);
+  const int i = (int)(tile % chunks) * kTrmmThreads + threadIdx.x;
   if (i >= k || c >= n) return;
   double s = 0.0;
   if (c >= i) {
     const int tend = min(c, k - 1);
-    for (int t = i; t <= tend; ++t) s = __fma_rn(Rp[(int64_t)t * ldp + i], Rs[(int64_t)c * lds + t], s);
+    for (int t = i; t <= tend; ++t)
+      s = __fma_rn(D.Rp[(int64_t)t * D.ldp + i], D.Rs[(int64_t)c * D.lds + t], s);
   }
-  R[(int64_t)c * ldr + i] = s;
+  D.R[(int64_t)c * D.ldr + i] = s;
+}
+
+__global__ void __launch_bounds__(kTrmmThreads) trmm_kernel(TrmmDesc D) {
+  trmm_body(blockIdx.x, D);
+}
+
+__global__ void __launch_bounds__(kTrmmThreads) trmm_batched_kernel(const TrmmDesc* D,
+                                                                     const int64_t* base, int np) {
+  int64_t t;
+  const int p = find_problem(base, np, blockIdx.x, &t);
+  trmm_body(t, D[p]);
 }
 
 cudaError_t launch_trmm(int n, const int64_t* k_dev, const double* Rpre, int64_t ldp,
                         const double* Rsk, int64_t ldsk, double* R, int64_t ldr,
                         const int* status, cudaStream_t stream) {
-  dim3 grid((unsigned)((n + 127) / 128), (unsigned)n);
-  trmm_kernel<<<grid, 128, 0, stream>>>(n, k_dev, Rpre, ldp, Rsk, ldsk, R, ldr, status);
+  TrmmDesc D{n, k_dev, Rpre, ldp, Rsk, ldsk, R, ldr, status};
+  trmm_kernel<<<(unsigned)trmm_tiles(n), kTrmmThreads, 0, stream>>>(D);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trmm_batched(const TrmmDesc* D, const int64_t* base, int nprob,
+                                int64_t total_tiles, cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  trmm_batched_kernel<<<(unsigned)total_tiles, kTrmmThreads, 0, stream>>>(D, base, nprob);
   count_launches(1);
   return cudaGetLastError();
 }

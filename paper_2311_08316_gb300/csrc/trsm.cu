@@ -12,20 +12,28 @@
 // triangular part of the block in ascending t.  Every partial sum therefore
 // receives its terms in ascending t, so the result does not depend on the
 // blocking.  The kernel is bound by the FP64 pipe (one DFMA per term).
+//
+// The single-problem kernel and the batched kernel (one launch over many
+// independent problems; CTA -> (problem, row tile) through a prefix table)
+// share the same body.
+#include "batch.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
 namespace cqrrpt {
 
-__global__ void __launch_bounds__(kTrsmThreads) trsm_rut_kernel(
-    int64_t m, const int64_t* __restrict__ k_dev, const double* B, int64_t ldb,
-    const int64_t* __restrict__ cols, const double* __restrict__ T, int64_t ldt, double* X,
-    int64_t ldx, const int* __restrict__ status) {
+__device__ __forceinline__ void trsm_rut_body(int64_t tile, const TrsmDesc& D) {
   __shared__ double Ts[kTrsmTB][kTrsmJB];
   __shared__ double Td[kTrsmJB][kTrsmJB];
-  if (*status != kOk) return;
-  const int k = (int)*k_dev;
-  const int64_t i = blockIdx.x * (int64_t)kTrsmThreads + threadIdx.x;
+  if (*D.status != kOk) return;
+  const int k = (int)*D.k_dev;
+  const int64_t m = D.m;
+  const double* B = D.B;
+  const int64_t* cols = D.cols;
+  const double* T = D.T;
+  double* X = D.X;
+  const int64_t ldb = D.ldb, ldt = D.ldt, ldx = D.ldx;
+  const int64_t i = tile * (int64_t)kTrsmThreads + threadIdx.x;
   const bool active = i < m;
   for (int j0 = 0; j0 < k; j0 += kTrsmJB) {
     const int jb = min(kTrsmJB, k - j0);
@@ -77,13 +85,35 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_rut_kernel(
   }
 }
 
+__global__ void __launch_bounds__(kTrsmThreads) trsm_rut_kernel(TrsmDesc D) {
+  trsm_rut_body(blockIdx.x, D);
+}
+
+__global__ void __launch_bounds__(kTrsmThreads) trsm_rut_batched_kernel(const TrsmDesc* D,
+                                                                         const int64_t* base,
+                                                                         int nprob) {
+  int64_t local;
+  const int p = find_problem(base, nprob, blockIdx.x, &local);
+  trsm_rut_body(local, D[p]);
+}
+
+int64_t trsm_tiles(int64_t m) { return (m + kTrsmThreads - 1) / kTrsmThreads; }
+
 cudaError_t launch_trsm_rut(int64_t m, int kmax, const int64_t* k_dev, const double* B,
                             int64_t ldb, const int64_t* cols, const double* T, int64_t ldt,
                             double* X, int64_t ldx, const int* status, cudaStream_t stream) {
   (void)kmax;
-  const unsigned grid = (unsigned)((m + kTrsmThreads - 1) / kTrsmThreads);
-  trsm_rut_kernel<<<grid, kTrsmThreads, 0, stream>>>(m, k_dev, B, ldb, cols, T, ldt, X, ldx,
-                                                     status);
+  TrsmDesc D{m, k_dev, B, ldb, cols, T, ldt, X, ldx, status};
+  trsm_rut_kernel<<<(unsigned)trsm_tiles(m), kTrsmThreads, 0, stream>>>(D);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_rut_batched(const TrsmDesc* D_dev, const int64_t* base_dev, int nprob,
+                                    int64_t total_tiles, cudaStream_t stream) {
+  if (total_tiles <= 0) return cudaSuccess;
+  trsm_rut_batched_kernel<<<(unsigned)total_tiles, kTrsmThreads, 0, stream>>>(D_dev, base_dev,
+                                                                             nprob);
   count_launches(1);
   return cudaGetLastError();
 }

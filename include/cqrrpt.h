@@ -53,8 +53,22 @@ extern "C" {
 #define CQRRPT_TOO_LARGE 6   /* problem exceeds the fixed scratch of
                                 cqrrpt_sketch_noalloc_d                  */
 
-/* Precision of the O(m n^2) steps (Alg. 2 lines 4-7). */
+/* Precision of the O(m n^2) steps (Alg. 2 lines 4, 5 and 7).  In every
+ * mode the sketch, the QRCP of the sketch, the rank rule, the Cholesky and
+ * R = R^pre R^sk run in FP64, so J and k are the same in all modes.
+ *   CQRRPT_FP64       FP64 FMA, fixed summation order: bit-identical to the
+ *                     library's documented arithmetic on every call.
+ *   CQRRPT_SPLITBF16  lines 4, 5, 7 on the BF16 tensor cores through an
+ *                     error-free split of every operand into eight 7-bit
+ *                     digits (56 bits) with exact FP32 accumulation of
+ *                     chunks of 1024 terms, summed in FP64: FP64-level
+ *                     accuracy, not bit-identical to CQRRPT_FP64.
+ *   CQRRPT_SPLITBF16_CHOLQR2  as CQRRPT_SPLITBF16, followed by a second
+ *                     Cholesky-QR pass on Q (G2 = Q^T Q, R2 = chol(G2),
+ *                     Q := Q R2^{-1}, R := R2 R) in the same arithmetic. */
 #define CQRRPT_FP64 0
+#define CQRRPT_SPLITBF16 2
+#define CQRRPT_SPLITBF16_CHOLQR2 3
 
 typedef struct cqrrpt_ctx* cqrrpt_handle;
 
@@ -137,6 +151,67 @@ int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t
  * through its cached CUDA graph. */
 int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable);
 
+/* ---- serving: continuous batching ---------------------------------------- */
+
+/* One request: a host matrix and host output buffers (pinned host memory
+ * makes the copies asynchronous).  All pointers are HOST pointers. */
+typedef struct {
+  int64_t m, n;         /* n <= ceil(gamma n) <= m                          */
+  const double* A_host; /* m x n, column-major, lda >= m                     */
+  int64_t lda;
+  double tol;           /* rank rule as in cqrrpt_d                          */
+  uint64_t seed;        /* seed of S                                         */
+  int precision;        /* CQRRPT_FP64 or a CQRRPT_SPLITBF16 mode            */
+  double* Q_host;       /* m x n capacity, ldq >= m (first k columns valid)  */
+  int64_t ldq;
+  double* R_host;       /* n x n capacity, ldr >= n (first k rows valid)     */
+  int64_t ldr;
+  int64_t* J_host;      /* n pivots                                          */
+} cqrrpt_request;
+
+typedef struct {
+  int64_t k;
+  int status;           /* as cqrrpt_d                                        */
+  double latency_us;    /* submit -> results in the host buffers              */
+  double queue_us;      /* submit -> admitted (device memory reserved)        */
+} cqrrpt_result;
+
+typedef struct cqrrpt_server_s* cqrrpt_server;
+
+/* A server that factors submitted requests with continuous batching: a
+ * scheduler thread admits requests in arrival order while their device
+ * footprint (A, Q, R, J and, for FP64 requests, the batched workspace) fits
+ * hbm_budget_bytes (one allocation made here) and at most max_inflight are in
+ * flight, copies their inputs in while the previous wave runs, and launches
+ * one batched pass over every admitted FP64 request whose input has arrived
+ * (split-BF16 requests run one at a time through cqrrpt_d after it).  Results
+ * are bit-identical to standalone calls.  The server owns `h` until
+ * cqrrpt_server_destroy (split-BF16 requests use its workspace).  The current
+ * device is used. */
+int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight, double gamma,
+                         int nnz_per_col, cqrrpt_server* server);
+
+/* Non-blocking: queues the request and returns its ticket.  The request's
+ * buffers must stay valid until its completion is polled.  A request whose
+ * footprint exceeds the whole budget returns CQRRPT_NO_MEMORY. */
+int cqrrpt_server_submit(cqrrpt_server s, const cqrrpt_request* req, uint64_t* ticket);
+
+/* *done = 1 once the request's results are in its host buffers; then *out
+ * (if not NULL) receives k, status and latencies and the ticket is retired. */
+int cqrrpt_server_poll(cqrrpt_server s, uint64_t ticket, int* done, cqrrpt_result* out);
+
+/* Waits until no request is queued or in flight (timeout_us < 0: no limit).
+ * Returns CQRRPT_TIMEOUT when the limit passes first. */
+int cqrrpt_server_drain(cqrrpt_server s, int64_t timeout_us);
+
+/* Counters: batched waves launched, requests completed, in flight, queued. */
+int cqrrpt_server_stats(cqrrpt_server s, int64_t* waves, int64_t* completed, int64_t* inflight,
+                        int64_t* queued);
+
+/* Finishes every queued and in-flight request, stops the scheduler and frees
+ * the server's memory. */
+int cqrrpt_server_destroy(cqrrpt_server s);
+
 /* Wait for `stream` and return the device-detected status of the handle's
  * last cqrrpt_d call (0, 1, 2 or 5) in *status_host, and its k in *k_host
  * (either pointer may be NULL). */
@@ -218,6 +293,20 @@ int cqrrpt_gram_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_
  * first column whose pivot is not positive (Remark 3). */
 int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R, int64_t ldr,
                    int64_t* fail_dev, cudaStream_t stream);
+
+/* Line 5 in the CQRRPT_SPLITBF16 arithmetic: G = X^T X (k x k) as 36 BF16
+ * tensor-core products of 7-bit digit planes, exact FP32 chunk sums of 1024
+ * terms added in FP64. */
+int cqrrpt_gram_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_t ldx,
+                        double* G, int64_t ldg, cudaStream_t stream);
+
+/* Lines 4 and 7 in the CQRRPT_SPLITBF16 arithmetic: X = B[:, cols] T^{-1}
+ * (recursive halving; off-diagonal blocks as split-BF16 products, 32 x 32
+ * diagonal blocks applied through their FP64 inverses).  X may equal B when
+ * cols is NULL. */
+int cqrrpt_trsm_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, int64_t ldb,
+                        const int64_t* cols, const double* T, int64_t ldt, double* X,
+                        int64_t ldx, cudaStream_t stream);
 
 /* Line 8: R = Rpre (k x k upper) * Rsk[0:k, 0:n] (upper trapezoidal), zero
  * below the diagonal. */

@@ -69,6 +69,8 @@ def lib():
     L.cqrrpt_batched_workspace_size.argtypes = [_int, _p, _p, _d, _int,
                                                 ctypes.POINTER(ctypes.c_size_t)]
     L.cqrrpt_set_batch_graphs.argtypes = [_p, _int]
+    L.cqrrpt_gram_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_trsm_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p, _i64, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
     L.cqrrpt_sketch_dim.restype = _i64
     L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -85,7 +87,8 @@ def exported_symbols():
             "cqrrpt_qrcp_d", "cqrrpt_rank_d", "cqrrpt_trsm_d", "cqrrpt_gram_d", "cqrrpt_potrf_d",
             "cqrrpt_trmm_d", "cqrrpt_sketch_dim", "cqrrpt_philox4x32_10", "cqrrpt_saso_column",
             "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches",
-            "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs"]
+            "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs",
+            "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -390,3 +393,112 @@ def cqrrpt_batched(As, gamma=1.25, nnz=4, tols=None, seeds=None, precision=FP64,
 def set_batch_graphs(enable, handle=None):
     h = handle or default_handle()
     _check(lib().cqrrpt_set_batch_graphs(h.h, 1 if enable else 0), "cqrrpt_set_batch_graphs")
+
+
+SPLITBF16 = 2
+SPLITBF16_CHOLQR2 = 3
+
+
+def gram_split(X, handle=None, stream=None):
+    """G = X^T X in the split-BF16 (FP64-accurate tensor-core) arithmetic."""
+    h = handle or default_handle()
+    m, k = X.shape
+    G = colmajor_empty(k, k, X.device)
+    _check(lib().cqrrpt_gram_split_d(h.h, m, k, X.data_ptr(), _ld(X), G.data_ptr(), _ld(G),
+                                     _stream(stream)), "cqrrpt_gram_split_d")
+    return G
+
+
+def trsm_split(B, T, cols=None, out=None, handle=None, stream=None):
+    """X = B[:, cols] T^{-1} in the split-BF16 arithmetic."""
+    h = handle or default_handle()
+    m = B.shape[0]
+    k = T.shape[0]
+    X = colmajor_empty(m, k, B.device) if out is None else out
+    _check(lib().cqrrpt_trsm_split_d(h.h, m, k, B.data_ptr(), _ld(B),
+                                     None if cols is None else cols.data_ptr(), T.data_ptr(),
+                                     _ld(T), X.data_ptr(), _ld(X), _stream(stream)),
+           "cqrrpt_trsm_split_d")
+    return X
+
+
+# ---- serving ----------------------------------------------------------------
+class Request(ctypes.Structure):
+    _fields_ = [("m", _i64), ("n", _i64), ("A_host", _p), ("lda", _i64), ("tol", _d),
+                ("seed", _u64), ("precision", _int), ("Q_host", _p), ("ldq", _i64),
+                ("R_host", _p), ("ldr", _i64), ("J_host", _p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("k", _i64), ("status", _int), ("latency_us", _d), ("queue_us", _d)]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_ready", False):
+        L.cqrrpt_server_create.argtypes = [_p, ctypes.c_size_t, _int, _d, _int, ctypes.POINTER(_p)]
+        L.cqrrpt_server_submit.argtypes = [_p, ctypes.POINTER(Request), ctypes.POINTER(_u64)]
+        L.cqrrpt_server_poll.argtypes = [_p, _u64, ctypes.POINTER(_int), ctypes.POINTER(Result)]
+        L.cqrrpt_server_drain.argtypes = [_p, _i64]
+        L.cqrrpt_server_stats.argtypes = [_p] + [ctypes.POINTER(_i64)] * 4
+        L.cqrrpt_server_destroy.argtypes = [_p]
+        L._server_ready = True
+    return L
+
+
+class Server:
+    """Continuous-batching server over cqrrpt_server_*.  Requests carry host
+    (ideally pinned) column-major float64 tensors; results land in the
+    request's host output tensors.  The handle is owned by the server."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=64, gamma=1.25, nnz=4, handle=None):
+        L = _server_lib()
+        self.handle = handle or Handle()
+        s = ctypes.c_void_p()
+        _check(L.cqrrpt_server_create(self.handle.h, int(hbm_budget_bytes), max_inflight, gamma,
+                                      nnz, ctypes.byref(s)), "cqrrpt_server_create")
+        self.s = s
+        self._keep = {}
+
+    def submit(self, A_host, tol=-1.0, seed=0, precision=FP64, out=None):
+        m, n = A_host.shape
+        if A_host.stride(0) != 1:
+            raise CqrrptError("A_host must be column-major")
+        if out is None:
+            out = (torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
+                   torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
+                   torch.empty(n, dtype=torch.int64, pin_memory=True))
+        Qh, Rh, Jh = out
+        req = Request(m, n, A_host.data_ptr(), max(A_host.stride(1), m), tol, seed, precision,
+                      Qh.data_ptr(), max(Qh.stride(1), m), Rh.data_ptr(), max(Rh.stride(1), n),
+                      Jh.data_ptr())
+        t = _u64()
+        _check(_server_lib().cqrrpt_server_submit(self.s, ctypes.byref(req), ctypes.byref(t)),
+               "cqrrpt_server_submit")
+        self._keep[t.value] = (A_host, out)
+        return t.value
+
+    def poll(self, ticket):
+        """None while running, else (Factorization on host buffers, Result)."""
+        done = _int()
+        res = Result()
+        _check(_server_lib().cqrrpt_server_poll(self.s, ticket, ctypes.byref(done),
+                                                ctypes.byref(res)), "cqrrpt_server_poll")
+        if not done.value:
+            return None
+        _, (Qh, Rh, Jh) = self._keep.pop(ticket)
+        return Factorization(Qh, Rh, Jh, res.k, res.status), res
+
+    def drain(self, timeout_us=-1):
+        _check(_server_lib().cqrrpt_server_drain(self.s, int(timeout_us)), "cqrrpt_server_drain")
+
+    def stats(self):
+        v = [_i64() for _ in range(4)]
+        _check(_server_lib().cqrrpt_server_stats(self.s, *[ctypes.byref(x) for x in v]),
+               "cqrrpt_server_stats")
+        return dict(zip(["waves", "completed", "inflight", "queued"], [x.value for x in v]))
+
+    def close(self):
+        if self.s:
+            _server_lib().cqrrpt_server_destroy(self.s)
+            self.s = None

@@ -11,6 +11,7 @@
 #include "../../include/cqrrpt.h"
 #include "batched.h"
 #include "kernels.h"
+#include "ozaki.h"
 #include "saso.cuh"
 
 using namespace cqrrpt;
@@ -105,6 +106,129 @@ struct DevGuard {
 __global__ void copy_k_kernel(const DeviceScalars* sc, int64_t* out) { *out = sc->k; }
 __global__ void copy_fail_kernel(const DeviceScalars* sc, int64_t* out) { *out = sc->fail; }
 
+bool precision_ok(int p) {
+  return p == CQRRPT_FP64 || p == CQRRPT_SPLITBF16 || p == CQRRPT_SPLITBF16_CHOLQR2;
+}
+
+// Workspace of the split-BF16 modes: the sketch scratch and the tensor-core
+// scratch share one region; then M^sk, QRCP work, R^sk, G, R^pre, f2, a copy
+// of the first-pass R and the device scalars of the second pass.
+Plan plan_for(int64_t m, int64_t n, int64_t d, int nnz, int precision) {
+  if (precision == CQRRPT_FP64) return plan_fp64(m, n, d, nnz);
+  Plan p = plan_fp64(m, n, d, nnz);
+  int64_t region = sketch_workspace_bytes(m, n, (int)d, nnz);
+  const int64_t t = oz_trsm_inv_workspace(m, (int)n);
+  const int64_t gw = oz_gram_workspace(m, (int)n, nullptr);
+  region = region > t ? region : t;
+  region = region > gw ? region : gw;
+  p.region = (size_t)align256(region);
+  p.total = p.region + p.x + p.qrcp + p.rsk + p.g + p.rpre + p.f2 + p.rsk +
+            (size_t)align256(sizeof(DeviceScalars));
+  return p;
+}
+
+int read_k(cqrrpt_handle h, DeviceScalars* sc, cudaStream_t s, int64_t* k, int* st) {
+  if (launch_finalize(sc, h->pinned, (int*)(h->pinned + 1), s) != cudaSuccess) return kCudaError;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return kCudaError;
+  *k = h->pinned[0];
+  *st = *(int*)(h->pinned + 1);
+  return kOk;
+}
+
+// Split-BF16 pipeline: FP64 sketch, QRCP, rank, Cholesky and TRMM; lines 4,
+// 5 and 7 as FP64-accurate tensor-core products (ozaki.cu).  The recursive
+// TRSM needs k on the host, so this path reads k back twice (after the rank
+// rule and after the Cholesky).
+int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,
+              int nnz, double tol, uint64_t seed, int precision, double* Q, int64_t ldq, double* R,
+              int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host, cudaStream_t stream) {
+  const Plan p = plan_for(m, n, d, nnz, precision);
+  int st = ensure_ws(h, p.total);
+  if (st != kOk) return st;
+  char* w = (char*)h->ws;
+  void* region = w; w += p.region;
+  double* X = (double*)w; w += p.x;
+  void* qw = w; w += p.qrcp;
+  double* Rsk = (double*)w; w += p.rsk;
+  double* G = (double*)w; w += p.g;
+  double* Rpre = (double*)w; w += p.rpre;
+  double* f2 = (double*)w; w += p.f2;
+  double* R1 = (double*)w; w += p.rsk;
+  DeviceScalars* sc2 = (DeviceScalars*)w;
+  DeviceScalars* sc = h->sc;
+  int* status = &sc->status;
+  const int ni = (int)n, di = (int)d;
+  const double scale = 1.0 / std::sqrt((double)nnz);
+
+  cudaError_t e = launch_init_scalars(sc, 0, stream);
+  mark(h, 0, stream);
+  if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
+  mark(h, 1, stream);
+  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
+  mark(h, 2, stream);
+  if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
+  mark(h, 3, stream);
+  if (e != cudaSuccess) return kCudaError;
+  int64_t k = 0;
+  int dst = kOk;
+  if ((st = read_k(h, sc, stream, &k, &dst)) != kOk) return st;
+  if (dst == kOk && k > 0) {
+    // line 4: M^pre = M[:, J[:k]] (R^sk_11)^{-1} into Q
+    e = oz_trsm(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream);
+    mark(h, 4, stream);
+    // line 5: G = M^pre^T M^pre
+    if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream);
+    mark(h, 5, stream);
+    // line 6 (FP64) and the rank rule's stage 2
+    if (e == cudaSuccess) e = launch_potrf((int)k, G, n, Rpre, n, sc, stream);
+    if (e == cudaSuccess) e = launch_rank_stage2(Rpre, n, !(tol > 0.0), sc, stream);
+    if (e != cudaSuccess) return kCudaError;
+    if ((st = read_k(h, sc, stream, &k, &dst)) != kOk) return st;
+    mark(h, 6, stream);
+    if (dst == kOk && k > 0) {
+      // line 7: Q_k = M^pre (R^pre)^{-1}, in place; R^pre is well conditioned
+      // (Theorem 2), so one product with its FP64 inverse
+      e = oz_trsm_inv(m, (int)k, Q, ldq, Rpre, n, region, stream);
+      mark(h, 7, stream);
+      // line 8: R_k = R^pre R^sk_k
+      double* Rout = (precision == CQRRPT_SPLITBF16_CHOLQR2) ? R1 : R;
+      const int64_t ldo = (precision == CQRRPT_SPLITBF16_CHOLQR2) ? n : ldr;
+      if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, Rsk, n, Rout, ldo, status, stream);
+      if (e == cudaSuccess && precision == CQRRPT_SPLITBF16_CHOLQR2) {
+        // second Cholesky-QR pass on Q: G2 = Q^T Q, R2 = chol(G2),
+        // Q := Q R2^{-1}, R := R2 R1.  A breakdown here keeps the first pass.
+        e = launch_init_scalars(sc2, k, stream);
+        if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream);
+        if (e == cudaSuccess) e = launch_potrf((int)k, G, n, Rpre, n, sc2, stream);
+        if (e == cudaSuccess) {
+          copy_fail_kernel<<<1, 1, 0, stream>>>(sc2, h->pinned + 4);
+          count_launches(1);
+          e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && cudaStreamSynchronize(stream) != cudaSuccess) return kCudaError;
+        if (e == cudaSuccess && h->pinned[4] < 0) {
+          e = oz_trsm_inv(m, (int)k, Q, ldq, Rpre, n, region, stream);
+          if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, R1, n, R, ldr, status, stream);
+        } else if (e == cudaSuccess) {
+          // second pass broke down: keep the first pass's R
+          e = cudaMemcpy2DAsync(R, ldr * sizeof(double), R1, n * sizeof(double),
+                                (size_t)k * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice,
+                                stream);
+        }
+      }
+      mark(h, 8, stream);
+    }
+  }
+  if (e == cudaSuccess) e = launch_finalize(sc, k_dev, nullptr, stream);
+  if (e != cudaSuccess) return kCudaError;
+  if (k_host) {
+    if ((st = read_k(h, sc, stream, &k, &dst)) != kOk) return st;
+    *k_host = k;
+    return dst;
+  }
+  return kOk;
+}
+
 }  // namespace
 
 extern "C" {
@@ -154,9 +278,9 @@ int cqrrpt_workspace_size(int64_t m, int64_t n, double gamma, int nnz, int preci
   if (!(gamma >= 1.0)) return -3;
   const int64_t d = sketch_dim(n, gamma);
   if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -4;
-  if (precision != CQRRPT_FP64) return -5;
+  if (!precision_ok(precision)) return -5;
   if (!bytes) return -6;
-  *bytes = plan_fp64(m, n, d, nnz).total;
+  *bytes = plan_for(m, n, d, nnz, precision).total;
   return kOk;
 }
 
@@ -179,7 +303,7 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
   if (d > m || d > 28000) return -6;
   if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
   if (std::isnan(tol)) return -8;
-  if (precision != CQRRPT_FP64) return -10;
+  if (!precision_ok(precision)) return -10;
   if (!Q) return -11;
   if (ldq < m) return -12;
   if (!R) return -13;
@@ -187,6 +311,9 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
   if (!J) return -15;
 
   DevGuard g(h->device);
+  if (precision != CQRRPT_FP64)
+    return run_split(h, m, n, A, lda, d, nnz, tol, seed, precision, Q, ldq, R, ldr, J, k_dev,
+                     k_host, stream);
   const Plan p = plan_fp64(m, n, d, nnz);
   int st = ensure_ws(h, p.total);
   if (st != kOk) return st;
@@ -547,6 +674,41 @@ int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R
     if (cudaGetLastError() != cudaSuccess) return kCudaError;
   }
   return kOk;
+}
+
+int cqrrpt_gram_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_t ldx,
+                        double* G, int64_t ldg, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (k < 1 || k > 16384) return -3;
+  if (!X) return -4;
+  if (ldx < m) return -5;
+  if (!G) return -6;
+  if (ldg < k) return -7;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)oz_gram_workspace(m, (int)k, nullptr));
+  if (st != kOk) return st;
+  return oz_gram(m, (int)k, X, ldx, G, ldg, h->ws, stream) == cudaSuccess ? kOk : kCudaError;
+}
+
+int cqrrpt_trsm_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, int64_t ldb,
+                        const int64_t* cols, const double* T, int64_t ldt, double* X,
+                        int64_t ldx, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (k < 1 || k > 16384) return -3;
+  if (!B) return -4;
+  if (ldb < m) return -5;
+  if (!T) return -7;
+  if (ldt < k) return -8;
+  if (!X) return -9;
+  if (ldx < m) return -10;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)oz_trsm_workspace(m, (int)k));
+  if (st != kOk) return st;
+  return oz_trsm(m, (int)k, B, ldb, cols, T, ldt, X, ldx, h->ws, stream) == cudaSuccess
+             ? kOk
+             : kCudaError;
 }
 
 int cqrrpt_trmm_d(cqrrpt_handle h, int64_t k, int64_t n, const double* Rpre, int64_t ldp,

@@ -52,7 +52,8 @@ int64_t problem_workspace_bytes(int64_t m, int64_t n, int64_t d, int nnz) {
   return t;
 }
 
-int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base) {
+int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base,
+               char* const* ws_each) {
   DeviceScalars* scalars = P.scalars;
   char* tables = P.tables;
   P = BatchPlan();
@@ -81,6 +82,7 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     if (d > max_d) max_d = (int)d;
     const int64_t a = sketch_workspace_bytes(m, n, (int)d, q.nnz);
     const int64_t b = gram_workspace_bytes(m, n);
+    if (ws_each) w = ws_each[p];  // problem p's own workspace
     char* region = w;
     w += (a > b ? a : b);
     double* X = (double*)w; w += align256(d * n * 8);

@@ -59,8 +59,10 @@ inline int64_t batch_table_bytes(int batch) {
   return align256(descs + bases + 256);
 }
 // Fills P (P.scalars and P.tables must be set by the caller beforehand) and
-// carves every problem's workspace from ws_base onward.
-int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base);
+// carves every problem's workspace from ws_base onward, or, when ws_each is
+// given, problem p's workspace (problem_workspace_bytes) from ws_each[p].
+int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base,
+               char* const* ws_each = nullptr);
 // Enqueues the 14 batched launches.
 cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s);
 cudaError_t sketch_set_attributes(int max_d);

@@ -16,7 +16,7 @@ constexpr int kSkCols = 4;        // sketch: columns per CTA
 constexpr int kSkThreads = 512;   // sketch: threads per CTA
 constexpr int kQrcpThreads = 256;
 constexpr int kTrsmThreads = 128;
-constexpr int kTrsmJB = 16;       // TRSM: columns solved per register block
+constexpr int kTrsmJB = 32;       // TRSM: columns solved per register block
 constexpr int kTrsmTB = 64;       // TRSM: rows of T staged per chunk
 constexpr int kGramTile = 32;     // SYRK: output tile edge
 constexpr int kGramRows = 32;     // SYRK: rows staged per chunk

@@ -1,0 +1,110 @@
+"""The continuous-batching server (cqrrpt_server_*).
+
+Requests submitted while others are on the GPU join later waves; every
+result must be the same as a standalone factorisation of the same request
+(bit for bit: the batched kernels run the single-problem arithmetic), the
+HBM budget must bound admission (requests wait, none is lost), and a request
+that can never fit is refused at submission.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2311_08316_gb300 import build as cbuild
+    cbuild.build()
+    import paper_2311_08316_gb300 as lib
+    lib.lib()
+    return lib
+
+
+def pinned_colmajor(a):
+    a = np.asfortranarray(a, dtype=np.float64)
+    t = torch.from_numpy(a.T.copy()).pin_memory()
+    return t.t()
+
+
+def requests(count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(4, 70))
+        m = int(rng.integers(max(2 * n, 100), 12000))
+        r = int(rng.integers(max(1, n // 2), n + 1))
+        sv = np.zeros(n)
+        sv[:r] = W.logspaced(r, -float(rng.uniform(2, 10))).numpy()
+        A = W.planted(m, n, sv, seed * 100 + i, noise=(1e-15 if r < n else 0.0)).numpy()
+        out.append((np.asfortranarray(A), 1e-9 if r < n else 1e-12, 4000 + i))
+    return out
+
+
+def test_server_results_equal_standalone(C):
+    reqs = requests(24, 1)
+    srv = C.Server(hbm_budget_bytes=2 << 30, max_inflight=16)
+    tickets = []
+    for i, (A, tol, seed) in enumerate(reqs):
+        tickets.append(srv.submit(pinned_colmajor(A), tol, seed))
+        if i % 5 == 0:
+            time.sleep(0.002)   # arrivals spread over the first waves
+    srv.drain(timeout_us=120_000_000)
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs)
+    assert stats["waves"] >= 2
+    for t, (A, tol, seed) in zip(tickets, reqs):
+        got = srv.poll(t)
+        assert got is not None
+        fac, res = got
+        ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+        assert res.status == ref.status and res.k == ref.k
+        assert res.latency_us > 0 and res.queue_us >= 0
+        assert np.array_equal(fac.J.numpy(), ref.J)
+        Q = np.asfortranarray(fac.Q.numpy())
+        R = np.asfortranarray(fac.R.numpy())
+        assert np.array_equal(Q.view(np.uint64), ref.Q.view(np.uint64))
+        assert np.array_equal(R.view(np.uint64), ref.R.view(np.uint64))
+    srv.close()
+
+
+def test_server_budget_admission_and_refusal(C):
+    reqs = requests(10, 2)
+    # budget for about two of these requests at a time
+    srv = C.Server(hbm_budget_bytes=48 << 20, max_inflight=8)
+    tickets = [srv.submit(pinned_colmajor(A), tol, seed) for A, tol, seed in reqs]
+    srv.drain(timeout_us=120_000_000)
+    assert srv.stats()["completed"] == len(reqs)
+    for t, (A, tol, seed) in zip(tickets, reqs):
+        fac, res = srv.poll(t)
+        one = C.cqrrpt(torch.from_numpy(A.T.copy()).cuda().t(), 1.25, 4, tol, seed)
+        assert res.k == one.k
+        assert np.array_equal(fac.R.numpy(), one.R.cpu().numpy())
+    big = np.ones((200000, 64), order="F")
+    with pytest.raises(C.CqrrptError):
+        srv.submit(pinned_colmajor(big), -1.0, 1)      # footprint > whole budget
+    srv.close()
+
+
+def test_server_mixed_precision_requests(C):
+    reqs = requests(6, 3)
+    srv = C.Server(hbm_budget_bytes=1 << 30, max_inflight=8)
+    tickets = [srv.submit(pinned_colmajor(A), tol, seed, precision=(2 if i % 2 else 0))
+               for i, (A, tol, seed) in enumerate(reqs)]
+    srv.drain(timeout_us=120_000_000)
+    for i, (t, (A, tol, seed)) in enumerate(zip(tickets, reqs)):
+        fac, res = srv.poll(t)
+        ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+        assert res.k == ref.k and np.array_equal(fac.J.numpy(), ref.J)
+        Q = fac.Q.numpy()
+        R = fac.R.numpy()
+        AJ = A[:, ref.J]
+        assert np.linalg.norm(AJ - Q @ R) / np.linalg.norm(A) <= 1e-12
+        assert np.linalg.norm(Q.T @ Q - np.eye(res.k), 2) <= 1e-12
+    srv.close()

@@ -239,6 +239,204 @@ __global__ void __launch_bounds__(1024) qrcp_batched_kernel(const QrcpDesc* D, d
   qrcp_body(1, 0, D[blockIdx.x], tol3z);
 }
 
+// dot32 of x[0..len) with itself from shared memory, by one warp.
+__device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  for (int i = lane; i < len; i += 32) acc = __fma_rn(x[i], x[i], acc);
+  return warp_tree_sum32(acc);
+}
+
+// Same steps and arithmetic as qrcp_body, with every CTA's owned columns
+// held in shared memory for the whole factorisation (cache[q * d + r] is
+// row r of physical column bid + G q) and the reflector vector of each step
+// staged once per CTA in shared memory; the pivot column's reflector is also
+// written to global memory for the other CTAs, and all owned columns are
+// written back at the end.  Used when the owned columns fit.
+__global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, double tol3z) {
+  extern __shared__ double cache[];
+  const int G = gridDim.x, bid = blockIdx.x;
+  const int d = D.d, n = D.n;
+  double* X = D.X;
+  const int64_t ldx = D.ldx;
+  const QrcpWork& w = D.w;
+  DeviceScalars* sc = D.sc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  int* status = &sc->status;
+  const int nown = bid < n ? (n - bid + G - 1) / G : 0;
+  double* vbuf = cache + (int64_t)nown * d;
+  __shared__ int sh_P, sh_p;
+  __shared__ double sh_tau, sh_beta, sh_denom;
+  __shared__ int sh_nz;
+  __shared__ double red_val[32];
+  __shared__ int red_pos[32];
+  __shared__ int red_col[32];
+
+  if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
+
+  for (int q = 0; q < nown; ++q) {
+    const double* src = X + (int64_t)(bid + G * q) * ldx;
+    for (int r = threadIdx.x; r < d; r += blockDim.x) cache[(int64_t)q * d + r] = src[r];
+  }
+  __syncthreads();
+  for (int q = warp; q < nown; q += nwarps) {
+    const int c = bid + G * q;
+    const double s = warp_dot32_self_smem(cache + (int64_t)q * d, d);
+    if (lane == 0) {
+      const double v = __dsqrt_rn(s);
+      w.vn1[c] = v;
+      w.vn2[c] = v;
+      w.phys[c] = c;
+      w.posof[c] = c;
+    }
+  }
+
+  auto publish_candidate = [&](int j_done) {
+    double bv = -1.0;
+    int bp = 0x7fffffff, bc = -1;
+    for (int q = warp; q < nown; q += nwarps) {
+      const int c = bid + G * q;
+      const int pc = __ldcg(w.posof + c);
+      if (pc <= j_done) continue;
+      const double v = __ldcg(w.vn1 + c);
+      if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bc = c; }
+    }
+    if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 1; i < nwarps; ++i)
+        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bc = red_col[i]; }
+      w.cand_val[bid] = bv;
+      w.cand_pos[bid] = bp;
+      w.cand_col[bid] = bc;
+    }
+  };
+  __syncthreads();
+  publish_candidate(-1);
+  bool ok = grid_sync(&sc->bar, G, status);
+
+  for (int j = 0; ok && j < n; ++j) {
+    // 1. global pivot
+    if (warp == 0) {
+      double bv = -1.0;
+      int bp = 0x7fffffff, bc = -1;
+      for (int i = lane; i < G; i += 32) {
+        const double v = __ldcg(w.cand_val + i);
+        const int p = __ldcg(w.cand_pos + i);
+        const int c = __ldcg(w.cand_col + i);
+        if (c >= 0 && cand_better(v, p, bv, bp)) { bv = v; bp = p; bc = c; }
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int op = __shfl_down_sync(0xffffffffu, bp, off);
+        const int oc = __shfl_down_sync(0xffffffffu, bc, off);
+        if (oc >= 0 && cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+      }
+      if (lane == 0) { sh_P = bc; sh_p = bp; }
+    }
+    __syncthreads();
+    const int P = sh_P, p = sh_p;
+    if (P < 0) {
+      if (bid == 0 && threadIdx.x == 0) atomicExch(status, kNonFinite);
+      ok = false;
+      break;
+    }
+    // 2. reflector by the owner of P (from its cache); swap record by CTA 0
+    if (P % G == bid) {
+      double* colP = cache + (int64_t)((P - bid) / G) * d;
+      if (warp == 0) {
+        const double alpha = colP[j];
+        const double sumsq = (j + 1 < d) ? warp_dot32_self_smem(colP + j + 1, d - j - 1) : 0.0;
+        if (lane == 0) {
+          if (sumsq == 0.0) {
+            sh_tau = 0.0;
+            sh_nz = 0;
+          } else {
+            const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
+            const double beta = (alpha >= 0.0) ? -nrm : nrm;
+            sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
+            sh_beta = beta;
+            sh_denom = __dsub_rn(alpha, beta);
+            sh_nz = 1;
+          }
+        }
+      }
+      __syncthreads();
+      double* gP = X + (int64_t)P * ldx;
+      if (sh_nz) {
+        const double denom = sh_denom;
+        for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x) {
+          const double v = __ddiv_rn(colP[r], denom);
+          colP[r] = v;
+          gP[r] = v;
+        }
+        if (threadIdx.x == 0) { colP[j] = sh_beta; gP[j] = sh_beta; }
+      } else {
+        for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x) gP[r] = colP[r];
+      }
+      if (threadIdx.x == 0) w.tau[j] = sh_tau;
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+      const int Pj = __ldcg(w.phys + j);
+      w.phys[p] = Pj;
+      w.posof[Pj] = p;
+      w.phys[j] = P;
+      w.posof[P] = j;
+    }
+    if (!grid_sync(&sc->bar, G, status)) { ok = false; break; }
+
+    // 3. stage v, apply H to owned unpivoted columns, downdate norms
+    const double tau = __ldcg(w.tau + j);
+    const int len = d - j;
+    const double* gP = X + (int64_t)P * ldx + j;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = (i == 0) ? 1.0 : __ldcg(gP + i);
+    __syncthreads();
+    for (int q = warp; q < nown; q += nwarps) {
+      const int c = bid + G * q;
+      if (__ldcg(w.posof + c) <= j) continue;
+      double* colc = cache + (int64_t)q * d + j;
+      double acc = 0.0;
+      for (int i = lane; i < len; i += 32) acc = __fma_rn(vbuf[i], colc[i], acc);
+      const double wsum = warp_tree_sum32(acc);
+      const double t = __dmul_rn(-tau, wsum);
+      for (int i = lane; i < len; i += 32) colc[i] = __fma_rn(vbuf[i], t, colc[i]);
+      __syncwarp();
+      const double v1 = __ldcg(w.vn1 + c);
+      if (v1 != 0.0) {
+        const double v2 = __ldcg(w.vn2 + c);
+        double temp = __ddiv_rn(fabs(colc[0]), v1);
+        temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
+        temp = temp > 0.0 ? temp : 0.0;
+        const double ratio = __ddiv_rn(v1, v2);
+        const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
+        if (temp2 <= tol3z) {
+          const double s = (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1) : 0.0;
+          if (lane == 0) {
+            const double nv = (j + 1 < d) ? __dsqrt_rn(s) : 0.0;
+            w.vn1[c] = nv;
+            w.vn2[c] = nv;
+          }
+        } else if (lane == 0) {
+          w.vn1[c] = __dmul_rn(v1, __dsqrt_rn(temp));
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    publish_candidate(j);
+    if (!grid_sync(&sc->bar, G, status)) { ok = false; break; }
+  }
+  // write the owned columns back (also after an early exit, so that global
+  // memory holds this CTA's last state)
+  __syncthreads();
+  for (int q = 0; q < nown; ++q) {
+    double* dst = X + (int64_t)(bid + G * q) * ldx;
+    for (int r = threadIdx.x; r < d; r += blockDim.x) dst[r] = cache[(int64_t)q * d + r];
+  }
+}
+
 // R^sk[i, q] = s_i X[i, phys[q]] for i <= q < n (0 below), s_i = -1 when the
 // diagonal X[i, phys[i]] is negative; J[q] = phys[q].
 __device__ __forceinline__ void qrcp_gather_body(int q, const QrcpDesc& D) {
@@ -282,8 +480,26 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   if (G < 1) G = 1;
   const double tol3z = tol3z_value();
   void* args[] = {&D, (void*)&tol3z};
-  e = cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(G), dim3(kQrcpThreads), args, 0,
-                                  stream);
+  // owned columns resident in shared memory when they fit
+  const int64_t nown = (n + G - 1) / G;
+  const size_t smem = (size_t)(nown * d + d) * sizeof(double);
+  bool cached = smem <= 200 * 1024;
+  if (cached) {
+    e = cudaFuncSetAttribute(qrcp_cached_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    int per_sm_c = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, qrcp_cached_kernel,
+                                                        kQrcpThreads, smem);
+    cached = (e == cudaSuccess && per_sm_c >= 1 && G <= num_sms * per_sm_c);
+    cudaGetLastError();
+  }
+  if (cached)
+    e = cudaLaunchCooperativeKernel((const void*)qrcp_cached_kernel, dim3(G), dim3(kQrcpThreads),
+                                    args, smem, stream);
+  else
+    e = cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(G), dim3(kQrcpThreads), args, 0,
+                                    stream);
   if (e != cudaSuccess) return e;
   qrcp_gather_kernel<<<n, 128, 0, stream>>>(D);
   count_launches(2);

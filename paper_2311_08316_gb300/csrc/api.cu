@@ -174,7 +174,8 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
   if ((st = read_k(h, sc, stream, &k, &dst)) != kOk) return st;
   if (dst == kOk && k > 0) {
     // line 4: M^pre = M[:, J[:k]] (R^sk_11)^{-1} into Q
-    e = oz_trsm(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream);
+    // (row-wise FP64 inverse of the row-graded R^sk_11, then one product)
+    e = oz_trsm_inv(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream);
     mark(h, 4, stream);
     // line 5: G = M^pre^T M^pre
     if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream);
@@ -188,7 +189,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
     if (dst == kOk && k > 0) {
       // line 7: Q_k = M^pre (R^pre)^{-1}, in place; R^pre is well conditioned
       // (Theorem 2), so one product with its FP64 inverse
-      e = oz_trsm_inv(m, (int)k, Q, ldq, Rpre, n, region, stream);
+      e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream);
       mark(h, 7, stream);
       // line 8: R_k = R^pre R^sk_k
       double* Rout = (precision == CQRRPT_SPLITBF16_CHOLQR2) ? R1 : R;
@@ -207,7 +208,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
         }
         if (e == cudaSuccess && cudaStreamSynchronize(stream) != cudaSuccess) return kCudaError;
         if (e == cudaSuccess && h->pinned[4] < 0) {
-          e = oz_trsm_inv(m, (int)k, Q, ldq, Rpre, n, region, stream);
+          e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream);
           if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, R1, n, R, ldr, status, stream);
         } else if (e == cudaSuccess) {
           // second pass broke down: keep the first pass's R

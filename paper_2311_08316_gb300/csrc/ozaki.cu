@@ -3,7 +3,7 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 2012; tensor-core
 // use as in Mukunoki, Ozaki, Ogita & Imamura, ICCS 2020).  Used by the
-// split-BF16 precision mode for Alg. 2 lines 4, 5 and 7, the O(m n^2) steps
+// split-BF16 precision modes for Alg. 2 lines 4, 5 and 7, the O(m n^2) steps
 // (the paper's two-roundoff model, Sec. 4.1, lets line 4 run in a
 // different arithmetic; here all three keep FP64-level accuracy).
 //
@@ -15,19 +15,23 @@
 // exact in BF16.  Truncation error: below 2^(e-56) per entry.
 //
 // Product.  C = A B = 2^(ea_i + eb_j) sum_{p,q} 2^(-7(p+q)) (D_p E_q)_{ij};
-// pairs with p + q <= 9 are kept (36 BF16 products); the dropped levels are
-// below 9 * 2^-56 relative to the scales.  Each digit product is an integer
-// of magnitude < 2^14, so an FP32 tensor-core accumulation of up to 1024
-// such terms is exact; after every chunk of at most 1024 K-terms the FP32
-// accumulator is added to an FP64 accumulator with one fma by
-// 2^(-7(p+q)).  The only roundings are those FP64 additions and the final
-// scaling, so the error is that of an FP64 dot product of length K/1024 over
-// exact partial sums (plus the 2^-53-level truncation above).
+// pairs with p + q <= 9 are kept (36 BF16 products, taken level by level,
+// level s = p + q); the dropped levels are below 9 * 2^-56 relative to the
+// scales.  Each digit product is an integer of magnitude < 2^14, so an FP32
+// tensor-core accumulation of up to 1024 such terms is exact.  After every
+// chunk of at most 1024 K-terms the FP32 accumulator is converted exactly to
+// an integer and added to a 64-bit integer accumulator of the level (exact);
+// when a level is complete its integer sum T_s (< 2^53) is converted exactly
+// and added, scaled by 2^(-7s), to an FP64 accumulator.  The roundings are
+// those eight FP64 additions and the final scaling.  No FP64 arithmetic runs
+// in the inner loop (the FP64 pipe is scarce on GB300).
 //
 // The tensor-core engine is warp-level mma.sync m16n8k16 (bf16 x bf16 ->
 // f32): CTA tile 64 x 128, 8 warps of 32 x 32, K staged 32 at a time through
-// a 3-stage cp.async pipeline with ldmatrix fragment loads.  All operands are
-// "K-contiguous": A is stored as M rows of K digits, B as N rows of K digits.
+// a 4-stage cp.async pipeline, ldmatrix fragment loads double-buffered over
+// the two k16 steps of a stage; the FP64 accumulators of the tile live in
+// shared memory.  All operands are "K-contiguous": A is stored as M rows of K
+// digits, B as N rows of K digits.
 #include <cmath>
 
 #include "common.cuh"
@@ -135,6 +139,8 @@ __global__ void oz_split_rows_kernel(const double* __restrict__ X, int64_t ldx, 
 // ---------------------------------------------------------------------------
 constexpr int kBM = 64, kBN = 128, kBK = 32, kStages = 3, kPad = 8;
 constexpr int kLdS = kBK + kPad;  // shared row stride (bf16)
+constexpr int kLdC = kBN + 1;     // FP64 tile row stride (doubles)
+constexpr size_t kOzSmem = (size_t)kStages * (kBM + kBN) * kLdS * 2 + (size_t)kBM * kLdC * 8;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -163,21 +169,49 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsi
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// pair index -> (p, q), both 1-based, p + q <= kOzLevels
-__device__ __forceinline__ void pair_of(int idx, int& p, int& q) {
-  p = 1;
-  int cnt = kOzLevels - 1;  // pairs with this p: q = 1 .. kOzLevels - p
-  while (idx >= cnt) {
-    idx -= cnt;
-    ++p;
-    cnt = kOzLevels - p;
+// pair index -> (p, q) in level order: level s = p + q = 2, 3, ..., 9; inside
+// a level p ascends.  Level s starts at index (s-2)(s-1)/2.
+__device__ __forceinline__ void pair_of(int idx, int& p, int& q, int& s, bool& level_end) {
+  s = 2;
+  while ((s - 1) * s / 2 <= idx) ++s;
+  const int first = (s - 2) * (s - 1) / 2;
+  p = idx - first + 1;
+  q = s - p;
+  level_end = (p == s - 1);
+}
+
+struct Frag {
+  unsigned a[2][4];
+  unsigned b[4][2];
+};
+
+__device__ __forceinline__ void load_frags(Frag& f, const __nv_bfloat16 (*As)[kLdS],
+                                           const __nv_bfloat16 (*Bs)[kLdS], int wm, int wn,
+                                           int kk, int lane) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int row = wm * 32 + i * 16 + (lane & 15);
+    const int col = kk + (lane >> 4) * 8;
+    ldmatrix_x4(f.a[i][0], f.a[i][1], f.a[i][2], f.a[i][3], &As[row][col]);
   }
-  q = idx + 1;
+#pragma unroll
+  for (int j2 = 0; j2 < 2; ++j2) {
+    const int row = wn * 32 + j2 * 16 + (lane & 7) + ((lane >> 4) << 3);
+    const int col = kk + ((lane >> 3) & 1) * 8;
+    unsigned r0, r1, r2, r3;
+    ldmatrix_x4(r0, r1, r2, r3, &Bs[row][col]);
+    f.b[2 * j2][0] = r0; f.b[2 * j2][1] = r1;
+    f.b[2 * j2 + 1][0] = r2; f.b[2 * j2 + 1][1] = r3;
+  }
 }
 
 __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(OzGemm G) {
-  __shared__ __align__(16) __nv_bfloat16 As[kStages][kBM][kLdS];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kStages][kBN][kLdS];
+  extern __shared__ __align__(16) unsigned char oz_smem[];
+  typedef __nv_bfloat16 RowA[kLdS];
+  RowA* As = (RowA*)oz_smem;                                  // [kStages * kBM]
+  RowA* Bs = (RowA*)(oz_smem + (size_t)kStages * kBM * kLdS * 2);  // [kStages * kBN]
+  double* Cs = (double*)(oz_smem + (size_t)kStages * (kBM + kBN) * kLdS * 2);  // [kBM][kLdC]
+
   const int tiles_m = (int)((G.M + kBM - 1) / kBM);
   const int tiles_n = (G.N + kBN - 1) / kBN;
   const int tile = blockIdx.x;
@@ -194,18 +228,20 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(OzGemm G) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps, each 32 x 32
+  for (int e = threadIdx.x; e < kBM * kLdC; e += 256) Cs[e] = 0.0;
   float acc[2][4][4];
-  double acc64[2][4][4];
+  long long lev[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) { acc[i][j][v] = 0.f; acc64[i][j][v] = 0.0; }
+      for (int v = 0; v < 4; ++v) { acc[i][j][v] = 0.f; lev[i][j][v] = 0; }
 
   auto load_stage = [&](int it, int buf) {
-    int p, q;
-    pair_of(it / nstage_k, p, q);
+    int p, q, s;
+    bool le;
+    pair_of(it / nstage_k, p, q, s, le);
     const int64_t k0 = kbeg + (int64_t)(it % nstage_k) * kBK;
     const __nv_bfloat16* Ap = G.A + (int64_t)(p - 1) * G.a_plane;
     const __nv_bfloat16* Bq = G.B + (int64_t)(q - 1) * G.b_plane;
@@ -213,7 +249,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(OzGemm G) {
       const int row = threadIdx.x >> 2, ch = threadIdx.x & 3;
       const int64_t gm = m0 + row;
       const bool ok = gm < G.M;
-      cp_async16(&As[buf][row][ch * 8], Ap + (ok ? gm : 0) * G.Kpad + k0 + ch * 8, ok);
+      cp_async16(&As[buf * kBM + row][ch * 8], Ap + (ok ? gm : 0) * G.Kpad + k0 + ch * 8, ok);
     }
 #pragma unroll
     for (int rep = 0; rep < 2; ++rep) {  // B: 128 rows x 32 k = 512 chunks
@@ -221,7 +257,8 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(OzGemm G) {
       const int row = idx >> 2, ch = idx & 3;
       const int gn = n0 + row;
       const bool ok = gn < G.N;
-      cp_async16(&Bs[buf][row][ch * 8], Bq + (int64_t)(ok ? gn : 0) * G.Kpad + k0 + ch * 8, ok);
+      cp_async16(&Bs[buf * kBN + row][ch * 8], Bq + (int64_t)(ok ? gn : 0) * G.Kpad + k0 + ch * 8,
+                 ok);
     }
   };
 
@@ -231,6 +268,7 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(OzGemm G) {
     if (s < total) load_stage(s, s);
     cp_async_commit();
   }
+  const int g = lane >> 2, t4 = lane & 3;
   for (int it = 0; it < total; ++it) {
     cp_async_wait<kStages - 2>();
     __syncthreads();
@@ -238,61 +276,68 @@ __global__ void __launch_bounds__(256, 2) oz_gemm_kernel(OzGemm G) {
     if (nxt < total) load_stage(nxt, nxt % kStages);
     cp_async_commit();
     const int buf = it % kStages;
+    const RowA* Ab = As + buf * kBM;
+    const RowA* Bb = Bs + buf * kBN;
+    Frag f0, f1;
+    load_frags(f0, Ab, Bb, wm, wn, 0, lane);
+    load_frags(f1, Ab, Bb, wm, wn, 16, lane);
 #pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      unsigned af[2][4], bfr[4][2];
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int row = wm * 32 + i * 16 + (lane & 15);
-        const int col = kk + (lane >> 4) * 8;
-        ldmatrix_x4(af[i][0], af[i][1], af[i][2], af[i][3], &As[buf][row][col]);
-      }
+      for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], f0.a[i], f0.b[j]);
 #pragma unroll
-      for (int j2 = 0; j2 < 2; ++j2) {
-        const int row = wn * 32 + j2 * 16 + (lane & 7) + ((lane >> 4) << 3);
-        const int col = kk + ((lane >> 3) & 1) * 8;
-        unsigned r0, r1, r2, r3;
-        ldmatrix_x4(r0, r1, r2, r3, &Bs[buf][row][col]);
-        bfr[2 * j2][0] = r0; bfr[2 * j2][1] = r1;
-        bfr[2 * j2 + 1][0] = r2; bfr[2 * j2 + 1][1] = r3;
-      }
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-    }
-    // drain after every chunk of kOzChunk K-terms and at the end of a pair
+      for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], f1.a[i], f1.b[j]);
+    // FP32 -> exact integer after every chunk of kOzChunk K-terms and at the
+    // end of a pair; integer level sum -> FP64 tile at the end of a level
     const int sk = it % nstage_k;
     const bool pair_end = (sk == nstage_k - 1);
     if (pair_end || ((sk + 1) * kBK) % kOzChunk == 0) {
-      int p, q;
-      pair_of(it / nstage_k, p, q);
-      const double scale = ldexp(1.0, -7 * (p + q));
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            acc64[i][j][v] = __fma_rn((double)acc[i][j][v], scale, acc64[i][j][v]);
+            lev[i][j][v] += (long long)__float2int_rn(acc[i][j][v]);
             acc[i][j][v] = 0.f;
           }
+      int p, q, s;
+      bool level_end;
+      pair_of(it / nstage_k, p, q, s, level_end);
+      if (pair_end && level_end) {
+        const double scale = ldexp(1.0, -7 * s);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int row = wm * 32 + i * 16 + g + ((v >> 1) << 3);
+              const int col = wn * 32 + j * 8 + 2 * t4 + (v & 1);
+              double* c = &Cs[row * kLdC + col];
+              *c = __fma_rn((double)lev[i][j][v], scale, *c);
+              lev[i][j][v] = 0;
+            }
+      }
     }
   }
   cp_async_wait<0>();
 
   // epilogue: scale by 2^(ea_i + eb_j) and store / subtract / write partial
-  const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const int64_t row = m0 + wm * 32 + i * 16 + g + ((v >> 1) << 3);
-        const int col = n0 + wn * 32 + j * 8 + 2 * t + (v & 1);
+        const int lr = wm * 32 + i * 16 + g + ((v >> 1) << 3);
+        const int lc = wn * 32 + j * 8 + 2 * t4 + (v & 1);
+        const int64_t row = m0 + lr;
+        const int col = n0 + lc;
         if (row >= G.M || col >= G.N) continue;
-        const double val = ldexp(acc64[i][j][v], G.ea[row] + G.eb[col]);
+        const double val = ldexp(Cs[lr * kLdC + lc], G.ea[row] + G.eb[col]);
         double* c = G.C + (int64_t)ks * G.c_slice + (int64_t)col * G.ldc + row;
         if (G.mode == kOzStore) *c = val;
         else *c = __dsub_rn(*c, val);
@@ -324,6 +369,23 @@ __global__ void oz_gather_kernel(const double* __restrict__ B, int64_t ldb,
     X[(int64_t)j * ldx + r] = B[src * ldb + r];
 }
 
+// W = T^{-1} for upper triangular T (k x k), row by row: row i of W solves
+// w^T T = e_i^T left to right (w_j = 0 for j < i), so the computed W has a
+// small right residual, |W T - I| <= c u |W| |T| -- the residual that enters
+// M_k - M^pre R^sk_11 when line 4 is applied as M_k W.  One thread per row.
+__global__ void oz_trinv_rows_kernel(const double* __restrict__ T, int64_t ldt, int k,
+                                     double* __restrict__ W, int64_t ldw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  for (int j = 0; j < i; ++j) W[(int64_t)j * ldw + i] = 0.0;
+  for (int j = i; j < k; ++j) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int t = i; t < j; ++t)
+      s = __fma_rn(-W[(int64_t)t * ldw + i], T[(int64_t)j * ldt + t], s);
+    W[(int64_t)j * ldw + i] = __ddiv_rn(s, T[(int64_t)j * ldt + j]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -334,10 +396,17 @@ int64_t oz_plane_bytes(int64_t rows, int64_t kpad) {
 }
 
 cudaError_t oz_gemm_launch(const OzGemm& G, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   const int64_t tiles_m = (G.M + kBM - 1) / kBM;
   const int64_t tiles_n = (G.N + kBN - 1) / kBN;
   const int64_t nks = (G.Kpad + G.kslice - 1) / G.kslice;
-  oz_gemm_kernel<<<(unsigned)(tiles_m * tiles_n * nks), 256, 0, s>>>(G);
+  oz_gemm_kernel<<<(unsigned)(tiles_m * tiles_n * nks), 256, kOzSmem, s>>>(G);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -387,7 +456,7 @@ cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, 
   oz_split_cols_kernel<<<sg, 256, 0, s>>>(X, ldx, m, k, kpad, e, D, plane);
   OzGemm G{};
   G.M = k; G.N = k; G.Kpad = kpad;
-  G.kslice = round_up((kpad / kOzChunk + nslices - 1) / nslices, 1) * kOzChunk;
+  G.kslice = ((kpad / kOzChunk + nslices - 1) / nslices) * kOzChunk;
   G.A = D; G.a_plane = plane; G.B = D; G.b_plane = plane;
   G.ea = e; G.eb = e;
   G.C = P; G.ldc = k; G.c_slice = (int64_t)k * k;
@@ -397,7 +466,7 @@ cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, 
   const int64_t ns = (kpad + G.kslice - 1) / G.kslice;
   oz_combine_sym_kernel<<<(unsigned)(((int64_t)k * k + 255) / 256), 256, 0, s>>>(P, G.c_slice, (int)ns,
                                                                                 k, Gm, ldg);
-  count_launches(4);
+  count_launches(3);
   return cudaGetLastError();
 }
 
@@ -438,6 +507,18 @@ struct TrsmCtx {
   int64_t* widths;
   int* status;
 };
+
+void carve_trsm(TrsmCtx& c, int64_t m, int k, void* work) {
+  const int64_t kp = round_up(k, kBK);
+  const int64_t big = kp > 1024 ? kp : 1024;
+  char* w = (char*)work;
+  c.DA = (__nv_bfloat16*)w; w += (int64_t)kOzDigits * oz_plane_bytes(m, big);
+  c.DB = (__nv_bfloat16*)w; w += (int64_t)kOzDigits * oz_plane_bytes(k, big);
+  c.ea = (int*)w; w += align256(m * 4);
+  c.eb = (int*)w; w += align256((int64_t)k * 4);
+  c.widths = (int64_t*)w; w += align256(((int64_t)k / kOzTrsmNB + 2) * 8);
+  c.status = (int*)w;
+}
 
 // C[:, 0:n] (m x n, ld ldc) op= Xs[:, 0:kk] * Ts (kk x n); mode store/sub.
 cudaError_t oz_mul(const TrsmCtx& c, const double* Xs, int64_t ldxs, int kk, const double* Ts,
@@ -481,17 +562,9 @@ cudaError_t solve(const TrsmCtx& c, int a, int b, cudaStream_t s) {
 cudaError_t oz_trsm(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                     const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
                     cudaStream_t s) {
-  const int64_t kp = round_up(k, kBK);
-  const int64_t big = kp > 1024 ? kp : 1024;
-  char* w = (char*)work;
   TrsmCtx c{};
   c.m = m; c.k = k; c.X = X; c.ldx = ldx; c.T = T; c.ldt = ldt;
-  c.DA = (__nv_bfloat16*)w; w += (int64_t)kOzDigits * oz_plane_bytes(m, big);
-  c.DB = (__nv_bfloat16*)w; w += (int64_t)kOzDigits * oz_plane_bytes(k, big);
-  c.ea = (int*)w; w += align256(m * 4);
-  c.eb = (int*)w; w += align256((int64_t)k * 4);
-  c.widths = (int64_t*)w; w += align256(((int64_t)k / kOzTrsmNB + 2) * 8);
-  c.status = (int*)w;
+  carve_trsm(c, m, k, work);
   if (B != X || cols) {
     dim3 g((unsigned)min64((m + 255) / 256, 256), (unsigned)k);
     oz_gather_kernel<<<g, 256, 0, s>>>(B, ldb, cols, m, X, ldx);
@@ -505,51 +578,32 @@ cudaError_t oz_trsm(int64_t m, int k, const double* B, int64_t ldb, const int64_
   return solve(c, 0, k, s);
 }
 
-}  // namespace cqrrpt
-
-namespace cqrrpt {
-
-// W = T^{-1} for upper triangular T (k x k): column j solves T w = e_j by
-// back substitution in FP64, one thread per column.
-__global__ void oz_trinv_kernel(const double* __restrict__ T, int64_t ldt, int k,
-                                double* __restrict__ W, int64_t ldw) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= k) return;
-  double* wj = W + (int64_t)j * ldw;
-  for (int i = j + 1; i < k; ++i) wj[i] = 0.0;
-  for (int i = j; i >= 0; --i) {
-    double s = (i == j) ? 1.0 : 0.0;
-    for (int t = i + 1; t <= j; ++t) s = __fma_rn(-T[(int64_t)t * ldt + i], wj[t], s);
-    wj[i] = __ddiv_rn(s, T[(int64_t)i * ldt + i]);
-  }
-}
-
 int64_t oz_trsm_inv_workspace(int64_t m, int k) {
   return oz_trsm_workspace(m, k) + align256((int64_t)k * k * 8);
 }
 
-// X := X T^{-1} as one split-BF16 product with the FP64 inverse of T.  Only
-// for well-conditioned T (the Cholesky factor R^pre of Alg. 2 line 6, whose
-// condition number the preconditioning keeps near 1, Theorem 2): the
-// product's error is then u * cond(T) relative, like a substitution's.
-cudaError_t oz_trsm_inv(int64_t m, int k, double* X, int64_t ldx, const double* T, int64_t ldt,
-                        void* work, cudaStream_t s) {
-  const int64_t kp = round_up(k, kBK);
-  const int64_t big = kp > 1024 ? kp : 1024;
-  char* w = (char*)work;
+// X := B[:, cols] T^{-1} as one split-BF16 product with W = T^{-1} computed
+// row by row in FP64 (small right residual |W T - I|).  Accurate when that
+// residual times the row grading of T is small: for R^pre (condition near 1,
+// Theorem 2) and for the row-graded R^sk of a max-norm QRCP (R = D U with
+// |U_ij| <= 1 above a unit diagonal), where |W||T| = |U^{-1}||U|.
+cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
+                        const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
+                        cudaStream_t s) {
   TrsmCtx c{};
   c.m = m; c.k = k; c.X = X; c.ldx = ldx; c.T = T; c.ldt = ldt;
-  c.DA = (__nv_bfloat16*)w; w += (int64_t)kOzDigits * oz_plane_bytes(m, big);
-  c.DB = (__nv_bfloat16*)w; w += (int64_t)kOzDigits * oz_plane_bytes(k, big);
-  c.ea = (int*)w; w += align256(m * 4);
-  c.eb = (int*)w; w += align256((int64_t)k * 4);
-  c.widths = (int64_t*)w; w += align256(((int64_t)k / kOzTrsmNB + 2) * 8);
-  c.status = (int*)w; w += 256;
-  double* W = (double*)w;
-  oz_trinv_kernel<<<(k + 127) / 128, 128, 0, s>>>(T, ldt, k, W, k);
+  carve_trsm(c, m, k, work);
+  double* W = (double*)((char*)work + oz_trsm_workspace(m, k));
+  if (B != X || cols) {
+    dim3 g((unsigned)min64((m + 255) / 256, 256), (unsigned)k);
+    oz_gather_kernel<<<g, 256, 0, s>>>(B, ldb, cols, m, X, ldx);
+    count_launches(1);
+  }
+  oz_trinv_rows_kernel<<<(k + 127) / 128, 128, 0, s>>>(T, ldt, k, W, k);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // the split reads X before the product overwrites it (separate planes)
   return oz_mul(c, X, ldx, k, W, k, k, X, ldx, kOzStore, s);
 }
 

@@ -38,10 +38,11 @@ int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out);
 cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* G, int64_t ldg,
                     void* work, cudaStream_t s);
 int64_t oz_trsm_workspace(int64_t m, int k);
-// X := X T^{-1} through the FP64 inverse of a well-conditioned T
+// X := B[:, cols] T^{-1} through the FP64 (row-wise) inverse of T
 int64_t oz_trsm_inv_workspace(int64_t m, int k);
-cudaError_t oz_trsm_inv(int64_t m, int k, double* X, int64_t ldx, const double* T, int64_t ldt,
-                        void* work, cudaStream_t s);
+cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
+                        const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
+                        cudaStream_t s);
 cudaError_t oz_trsm(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                     const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
                     cudaStream_t s);

@@ -48,11 +48,17 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--rows", type=int, default=131072, help="m of the workload")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "mixed"],
+    p.add_argument("--workload", default="single",
+                   choices=["single", "batched", "mixed", "serve"],
                    help="single: the rank-800 131072 x 1024 problem (headline); batched: 512 "
                         "uneven problems in one batched pass; mixed: 1048576 x 512, cond 1e10, "
-                        "split-BF16 modes against FP64")
+                        "split-BF16 modes against FP64; serve: a Poisson stream of mixed-size "
+                        "requests through the continuous-batching server")
     p.add_argument("--batch", type=int, default=512)
+    p.add_argument("--requests", type=int, default=600, help="serve: requests in the open loop")
+    p.add_argument("--pool", type=int, default=32, help="serve: distinct matrices")
+    p.add_argument("--load", type=float, default=0.7,
+                   help="serve: offered rate as a fraction of the closed-loop capacity")
     return p.parse_args()
 
 
@@ -82,6 +88,21 @@ def max_over_ranks(x, world, device="cpu"):
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_workload(w, rank):
+    """Rank r's own problem of the same shape: matrix and S seeds shifted by
+    r (rank 0 keeps the published seeds), so ranks factor independent inputs."""
+    if rank == 0:
+        return w
+    import dataclasses
+    return dataclasses.replace(w, seed=w.seed + 7919 * rank,
+                               sketch_seed=w.sketch_seed + 7919 * rank)
+
+
+def rank_batch(count, rank):
+    """Rank r's own batch of `count` uneven problems (independent seeds)."""
+    return W.batch_uneven(count=count, seed=W.BASE_SEED + 3 + 104729 * rank)
 
 
 # --------------------------------------------------------------- clocks
@@ -187,7 +208,7 @@ def cqrrpt_flops(m, n, d, k, s):
 def run_batched(args, world, rank, local, C):
     """512 independent problems (m ~ U[4096, 65536], n ~ U[32, 256], rank ~
     U[n/2, n]) factored by one batched pass (one graph launch) per step."""
-    ws = W.batch_uneven(count=args.batch)
+    ws = rank_batch(args.batch, rank)
     mats = [w.matrix("cuda") for w in ws]
     outs = [(C.colmajor_empty(w.m, w.n), C.colmajor_empty(w.n, w.n),
              torch.empty(w.n, dtype=torch.int64, device="cuda")) for w in ws]
@@ -200,7 +221,11 @@ def run_batched(args, world, rank, local, C):
         return C.cqrrpt_batched(mats, 1.25, 4, tols, seeds, outs=outs, handle=h, stream=stream,
                                 sync=sync)
 
-    for _ in range(args.warmup):
+    # the first warm-up step runs the autotuner (tile shapes per width bucket)
+    res, kd, sd, tune_us = C.cqrrpt_batched(mats, 1.25, 4, tols, seeds, outs=outs, handle=h,
+                                            stream=stream, autotune=True)
+    tuned = C.get_batch_tuning(handle=h)
+    for _ in range(max(0, args.warmup - 1)):
         res, kd, sd = step(True)
     ks = [r.k for r in res]
     assert all(r.status == 0 for r in res), [r.status for r in res]
@@ -234,6 +259,9 @@ def run_batched(args, world, rank, local, C):
                        "sum_2mn2": sum(2.0 * w.m * w.n * w.n for w in ws),
                        "gamma": 1.25, "nnz_per_col": 4, "precision": "fp64",
                        "launch": "one CUDA graph of per-phase batched kernels per step",
+                       "autotuned": {"trsm_jb": tuned[0], "gram_tile": tuned[1],
+                                     "bucket": "min((n-1)//32, 15)",
+                                     "times_us": {str(b): v for b, v in tune_us.items()}},
                        "l2": "inputs larger than L2 (sum of A = %.1f GB), no flush"
                              % (sum(w.m * w.n * 8 for w in ws) / 1e9)},
             "gflops_2mn2": value * sum(2.0 * w.m * w.n * w.n for w in ws) / len(ws) / 1e9,
@@ -279,7 +307,7 @@ def run_mixed(args, world, rank, local, C):
     with and without a second Cholesky-QR pass) timed against the FP64
     mode on the same inputs; accuracy of each against the FP64 result (which
     is bit-identical to the oracle)."""
-    w = W.mixed_tall(m=args.rows if args.rows != 131072 else (1 << 20))
+    w = rank_workload(W.mixed_tall(m=args.rows if args.rows != 131072 else (1 << 20)), rank)
     A = w.matrix("cuda")
     m, n = w.m, w.n
     h = C.Handle(local)
@@ -338,6 +366,180 @@ def run_mixed(args, world, rank, local, C):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, world, rank, local, C):
+    """Continuous-batching server under a Poisson stream.  Requests are drawn
+    from a pool of `--pool` matrices of the serving mix (m = 2^U[12,20],
+    n = 2^U[4,9], cond 10^U[2,12], 30% planted rank with 1e-15 noise); each
+    request has its own sketch seed and precision (FP64 or split-BF16, 50/50).
+    First the closed-loop capacity (every request queued at once), then the
+    open loop at `--load` x capacity; latency is arrival -> results in the
+    request's host buffers (host copies included), measured by the server."""
+    import oracle
+    rng = np.random.default_rng(W.BASE_SEED + 5)
+    pool = W.serving_requests(args.pool)
+    hosts, outs = [], []
+    for w, _ in pool:
+        A = w.matrix("cuda")
+        Ah = torch.empty((w.n, w.m), dtype=torch.float64, pin_memory=True).t()
+        Ah.copy_(A)
+        del A
+        hosts.append(Ah)
+        # one output set per pool entry, shared by its non-sampled requests
+        # (their results are not read; sampled requests get their own)
+        outs.append((torch.empty((w.n, w.m), dtype=torch.float64, pin_memory=True).t(),
+                     torch.empty((w.n, w.n), dtype=torch.float64, pin_memory=True).t(),
+                     torch.empty(w.n, dtype=torch.int64, pin_memory=True)))
+    torch.cuda.synchronize()
+    h = C.Handle(local)
+    srv = C.Server(hbm_budget_bytes=120 << 30, max_inflight=64, handle=h)
+
+    def make(count, seed_base):
+        reqs = []
+        for i in range(count):
+            e = int(rng.integers(len(pool)))
+            prec = C.SPLITBF16 if rng.random() < 0.5 else C.FP64
+            reqs.append((e, prec, seed_base + i))
+        return reqs
+
+    def submit(req, out=None):
+        e, prec, seed = req
+        w = pool[e][0]
+        return srv.submit(hosts[e], w.tol, seed, precision=prec, out=out or outs[e])
+
+    # warm-up: every pool entry once in each precision (sizes the workspace)
+    for e in range(len(pool)):
+        for prec in (C.FP64, C.SPLITBF16):
+            submit((e, prec, 7))
+    srv.drain(timeout_us=600_000_000)
+    assert srv.stats()["completed"] == 2 * len(pool)
+
+    # closed loop: capacity
+    cap_reqs = make(max(len(pool), args.requests // 2), 10**7)
+    t0 = time.perf_counter()
+    tk = [submit(r) for r in cap_reqs]
+    srv.drain(timeout_us=600_000_000)
+    cap_s = time.perf_counter() - t0
+    for t in tk:
+        assert srv.poll(t) is not None
+    capacity = len(cap_reqs) / cap_s
+
+    # open loop: Poisson arrivals at load x capacity
+    rate = args.load * capacity
+    reqs = make(args.requests, 2 * 10**7)
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    # parity sample: the four smallest FP64 requests and two split-BF16 ones
+    order = sorted(range(len(reqs)), key=lambda i: pool[reqs[i][0]][0].m * pool[reqs[i][0]][0].n)
+    sample = [i for i in order if reqs[i][1] == C.FP64][:4] + \
+             [i for i in order if reqs[i][1] != C.FP64][:2]
+    own = {}
+    for i in sample:
+        w = pool[reqs[i][0]][0]
+        own[i] = (torch.empty((w.n, w.m), dtype=torch.float64, pin_memory=True).t(),
+                  torch.empty((w.n, w.n), dtype=torch.float64, pin_memory=True).t(),
+                  torch.empty(w.n, dtype=torch.int64, pin_memory=True))
+    tickets = [None] * len(reqs)
+    results = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = C.kernel_launches()
+
+    def feeder():
+        t_next = time.perf_counter()
+        for i, r in enumerate(reqs):
+            t_next += gaps[i]
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = submit(r, own.get(i))
+
+    th = threading.Thread(target=feeder)
+    t_start = time.perf_counter()
+    th.start()
+    pending = set(range(len(reqs)))
+    t_last = t_start
+    while pending:
+        for i in list(pending):
+            if tickets[i] is None:
+                continue
+            got = srv.poll(tickets[i])
+            if got is not None:
+                fac, res = got
+                results[i] = res
+                if i in own:
+                    own[i] = (fac.Q.numpy()[:, :res.k].copy(), fac.R.numpy()[:res.k].copy(),
+                              fac.J.numpy().copy(), res.k, res.status)
+                pending.discard(i)
+                t_last = time.perf_counter()
+        time.sleep(0.0002)
+    th.join()
+    wall = t_last - t_start
+    launches = C.kernel_launches() - launches0
+    clk = clocks.stop()
+    stats = srv.stats()
+    srv.close()
+
+    lat = np.array([results[i].latency_us for i in range(len(reqs))]) / 1e3
+    que = np.array([results[i].queue_us for i in range(len(reqs))]) / 1e3
+    isfp = np.array([reqs[i][1] == C.FP64 for i in range(len(reqs))])
+    assert all(results[i].status in (0, 1) for i in range(len(reqs)))
+    ws = [pool[r[0]][0] for r in reqs]
+    ks = [results[i].k for i in range(len(reqs))]
+    throughput = len(reqs) / wall
+    flops = sum(cqrrpt_flops(w.m, w.n, w.d, k, w.nnz) for w, k in zip(ws, ks))
+    h2d = statistics.mean(w.m * w.n * 8 for w in ws)
+    d2h = statistics.mean(w.m * k * 8 + k * w.n * 8 + w.n * 8 + 8 for w, k in zip(ws, ks))
+
+    # parity: sampled FP64 requests bit-identical to the oracle; split-BF16
+    # ones: same J and k as the oracle, FP64-level residuals
+    par = []
+    for i in sample:
+        Qs, Rs, Js, k, st = own[i]
+        w = pool[reqs[i][0]][0]
+        A = np.asfortranarray(hosts[reqs[i][0]].numpy())
+        ref = oracle.cqrrpt(A, w.gamma, w.nnz, w.tol, reqs[i][2])
+        ok = ref.k == k and np.array_equal(ref.J, Js)
+        if reqs[i][1] == C.FP64:
+            ok = ok and np.array_equal(ref.Q.view(np.uint64), np.asfortranarray(Qs).view(np.uint64)) \
+                and np.array_equal(ref.R.view(np.uint64), np.asfortranarray(Rs).view(np.uint64))
+        else:
+            AJ = A[:, Js]
+            rec = np.linalg.norm(AJ - Qs @ Rs) / np.linalg.norm(A)
+            orth = np.linalg.norm(Qs.T @ Qs - np.eye(k), 2)
+            ok = ok and rec <= 1e-12 and orth <= 1e-12
+        par.append(bool(ok))
+
+    def pct(a):
+        return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)),
+                "mean": float(a.mean())} if len(a) else None
+
+    line = {"metric": "cqrrpt_requests_per_s", "value": throughput, "unit": "requests/s",
+            "n_gpus": world, "steps": len(reqs), "warmup": 2 * len(pool),
+            "ms_per_step": wall * 1e3 / len(reqs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 / bf16 digits -> f64", "data": "synthetic",
+            "config": {"workload": "cqrrpt_serving_poisson_m2^12-2^20_n16-512_cond1e2-1e12",
+                       "requests": len(reqs), "pool_matrices": len(pool),
+                       "mean_A_bytes": h2d, "hbm_budget_bytes": 120 << 30, "max_inflight": 64,
+                       "offered_rate_per_s": rate, "load": args.load,
+                       "precision_mix": "fp64 / splitbf16 50/50",
+                       "l2": "inputs copied from host per request (mean %.0f MB), no flush"
+                             % (h2d / 1e6)},
+            "capacity_requests_per_s": capacity,
+            "latency_ms": {"all": pct(lat), "fp64": pct(lat[isfp]), "splitbf16": pct(lat[~isfp]),
+                           "queue": pct(que)},
+            "gflops_algorithmic": flops / wall / 1e9,
+            "gflops_2mn2": sum(2.0 * w.m * w.n * w.n for w in ws) / wall / 1e9,
+            "waves": stats["waves"],
+            "e2e": {"value": throughput, "unit": "requests/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "note": "the serving loop is end to end: pinned host in, host out"},
+            "parity_vs_oracle": ("%d/%d sampled requests match (fp64 bit-identical, split-BF16 "
+                                 "same J/k and residuals <= 1e-12)" % (sum(par), len(par))),
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -360,8 +562,12 @@ def main():
         run_mixed(args, world, rank, local, C)
         barrier(world)
         return
+    if args.workload == "serve":
+        run_serve(args, world, rank, local, C)
+        barrier(world)
+        return
 
-    w = W.single_large(m=args.rows)
+    w = rank_workload(W.single_large(m=args.rows), rank)
     m, n = w.m, w.n
     A = w.matrix("cuda")
     h = C.Handle(local)

@@ -102,7 +102,7 @@ int cqrrpt_reserve(cqrrpt_handle h, size_t bytes);
  *                 cases a Cholesky breakdown at column j sets k = j
  *                 (Remark 3).
  *   seed          seed of S.
- *   precision     CQRRPT_FP64.
+ *   precision     CQRRPT_FP64, CQRRPT_SPLITBF16 or CQRRPT_SPLITBF16_CHOLQR2.
  *   Q, ldq        m x n capacity, ldq >= m; columns 0..k-1 receive Q_k
  *                 (column j of M^pre is formed there first).
  *   R, ldr        n x n capacity, ldr >= n; rows 0..k-1 receive R_k, upper
@@ -151,6 +151,41 @@ int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t
  * through its cached CUDA graph. */
 int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable);
 
+/* Autotuner of the batched path.  The two O(m n^2) batched kernels have
+ * tile shapes chosen per problem width bucket b = min((n - 1) / 32, 15):
+ * the widest register block of the substitution of Alg. 2 lines 4 and 7
+ * (16 or 32 columns) and the output tile of the Gram partial sums of line 5
+ * (16 x 16 or 32 x 32).  This call factors the batch once with the handle's
+ * current shapes, then, for every bucket present, times both shapes of both
+ * kernels on that bucket's problems (best of 3 launches, CUDA events),
+ * stores the faster shape per bucket and kernel in the handle (every later
+ * cqrrpt_batched_d and server wave on the handle uses it), and factors the
+ * batch again with the chosen shapes: on return the outputs are those of
+ * cqrrpt_batched_d.  The shapes change the blocking only, never the order
+ * of any sum, so outputs are bit-identical whatever is chosen.  Waits for
+ * the stream.
+ *   arguments 1-18      as cqrrpt_batched_d.
+ *   times_us_host       HOST array of 64 doubles or NULL: for bucket b,
+ *                       [4b + 0, 4b + 1] = TRSM time with 16 / 32 columns,
+ *                       [4b + 2, 4b + 3] = Gram time with 16 / 32 tiles
+ *                       (microseconds; 0 for buckets absent from the batch).
+ * Returns 0, an argument error, CQRRPT_NO_MEMORY or CQRRPT_CUDA_ERROR. */
+int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
+                            const double* const* A, const int64_t* lda, double gamma,
+                            int nnz_per_col, const double* tol, const uint64_t* seed,
+                            int precision, double* const* Q, const int64_t* ldq,
+                            double* const* R, const int64_t* ldr, int64_t* const* J,
+                            int64_t* k_dev, int* status_dev, double* times_us_host,
+                            cudaStream_t stream);
+
+/* The handle's batched tile shapes: HOST arrays of 16 entries (either may be
+ * NULL), TRSM column block (16 or 32) and Gram tile edge (16 or 32) per
+ * width bucket.  set_tuning returns -2 / -3 for a value other than 16 or
+ * 32 and then changes nothing.  A new handle starts with 32-column blocks
+ * and 16 x 16 Gram tiles for n <= 64, 32 x 32 above. */
+int cqrrpt_batched_get_tuning(cqrrpt_handle h, int* trsm_jb_host, int* gram_tile_host);
+int cqrrpt_batched_set_tuning(cqrrpt_handle h, const int* trsm_jb_host, const int* gram_tile_host);
+
 /* ---- serving: continuous batching ---------------------------------------- */
 
 /* One request: a host matrix and host output buffers (pinned host memory
@@ -180,14 +215,17 @@ typedef struct cqrrpt_server_s* cqrrpt_server;
 
 /* A server that factors submitted requests with continuous batching: a
  * scheduler thread admits requests in arrival order while their device
- * footprint (A, Q, R, J and, for FP64 requests, the batched workspace) fits
- * hbm_budget_bytes (one allocation made here) and at most max_inflight are in
- * flight, copies their inputs in while the previous wave runs, and launches
- * one batched pass over every admitted FP64 request whose input has arrived
- * (split-BF16 requests run one at a time through cqrrpt_d after it).  Results
- * are bit-identical to standalone calls.  The server owns `h` until
- * cqrrpt_server_destroy (split-BF16 requests use its workspace).  The current
- * device is used. */
+ * footprint (A, Q, R, J and, for requests of the batched route, the batched
+ * workspace) fits hbm_budget_bytes (one allocation made here) and at most
+ * max_inflight are in flight, and copies their inputs in while earlier work
+ * runs.  Whenever the GPU is free it starts the next unit of work, chosen by
+ * the oldest request whose input has arrived: either one batched pass over
+ * every arrived FP64 request with n <= 256 (requests that arrived while the
+ * previous pass ran join the next one), or a single-problem run (cqrrpt_d on
+ * the whole GPU) of a split-BF16 request or of an FP64 request with n > 256.
+ * Results are bit-identical to standalone calls of the same precision.  The
+ * server owns `h` until cqrrpt_server_destroy (single-problem runs use its
+ * workspace, outside the budget).  The current device is used. */
 int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight, double gamma,
                          int nnz_per_col, cqrrpt_server* server);
 

@@ -69,6 +69,10 @@ def lib():
     L.cqrrpt_batched_workspace_size.argtypes = [_int, _p, _p, _d, _int,
                                                 ctypes.POINTER(ctypes.c_size_t)]
     L.cqrrpt_set_batch_graphs.argtypes = [_p, _int]
+    L.cqrrpt_batched_autotune.argtypes = [_p, _int, _p, _p, _p, _p, _d, _int, _p, _p, _int, _p,
+                                          _p, _p, _p, _p, _p, _p, ctypes.POINTER(_d), _p]
+    L.cqrrpt_batched_get_tuning.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
+    L.cqrrpt_batched_set_tuning.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
     L.cqrrpt_gram_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
     L.cqrrpt_trsm_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p, _i64, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
@@ -88,6 +92,7 @@ def exported_symbols():
             "cqrrpt_trmm_d", "cqrrpt_sketch_dim", "cqrrpt_philox4x32_10", "cqrrpt_saso_column",
             "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches",
             "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs",
+            "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d"]
 
 
@@ -356,10 +361,13 @@ def _arr(ctype, values):
 
 
 def cqrrpt_batched(As, gamma=1.25, nnz=4, tols=None, seeds=None, precision=FP64, outs=None,
-                   handle=None, stream=None, sync=True, graphs=True):
+                   handle=None, stream=None, sync=True, graphs=True, autotune=False):
     """Batched CQRRPT of independent column-major float64 CUDA matrices
-    (uneven sizes allowed) through cqrrpt_batched_d.  Returns a list of
-    Factorization; with sync=True their k and status are filled in."""
+    (uneven sizes allowed) through cqrrpt_batched_d (cqrrpt_batched_autotune
+    with autotune=True: the handle's tile shapes are re-tuned on this batch,
+    and the tuning times are returned as a fourth element).  Returns
+    (list of Factorization, k device tensor, status device tensor); with
+    sync=True the Factorizations' k and status are filled in."""
     h = handle or default_handle()
     L = lib()
     b = len(As)
@@ -372,14 +380,18 @@ def cqrrpt_batched(As, gamma=1.25, nnz=4, tols=None, seeds=None, precision=FP64,
     kd = torch.zeros(b, dtype=torch.int64, device=As[0].device)
     sd = torch.zeros(b, dtype=torch.int32, device=As[0].device)
     P = ctypes.c_void_p
-    rc = L.cqrrpt_batched_d(
-        h.h, b, _arr(_i64, [A.shape[0] for A in As]), _arr(_i64, [A.shape[1] for A in As]),
-        _arr(P, [A.data_ptr() for A in As]), _arr(_i64, [_ld(A) for A in As]), gamma, nnz,
-        _arr(_d, tols), _arr(_u64, seeds), precision,
-        _arr(P, [o[0].data_ptr() for o in outs]), _arr(_i64, [_ld(o[0]) for o in outs]),
-        _arr(P, [o[1].data_ptr() for o in outs]), _arr(_i64, [_ld(o[1]) for o in outs]),
-        _arr(P, [o[2].data_ptr() for o in outs]), kd.data_ptr(), sd.data_ptr(), _stream(stream))
-    _check(rc, "cqrrpt_batched_d")
+    args = [h.h, b, _arr(_i64, [A.shape[0] for A in As]), _arr(_i64, [A.shape[1] for A in As]),
+            _arr(P, [A.data_ptr() for A in As]), _arr(_i64, [_ld(A) for A in As]), gamma, nnz,
+            _arr(_d, tols), _arr(_u64, seeds), precision,
+            _arr(P, [o[0].data_ptr() for o in outs]), _arr(_i64, [_ld(o[0]) for o in outs]),
+            _arr(P, [o[1].data_ptr() for o in outs]), _arr(_i64, [_ld(o[1]) for o in outs]),
+            _arr(P, [o[2].data_ptr() for o in outs]), kd.data_ptr(), sd.data_ptr()]
+    times = None
+    if autotune:
+        times = (_d * 64)()
+        _check(L.cqrrpt_batched_autotune(*args, times, _stream(stream)), "cqrrpt_batched_autotune")
+    else:
+        _check(L.cqrrpt_batched_d(*args, _stream(stream)), "cqrrpt_batched_d")
     res = [Factorization(o[0], o[1], o[2], None, None) for o in outs]
     if sync:
         (stream or torch.cuda.current_stream()).synchronize()
@@ -387,7 +399,28 @@ def cqrrpt_batched(As, gamma=1.25, nnz=4, tols=None, seeds=None, precision=FP64,
         ss = sd.cpu().tolist()
         for r, k, s in zip(res, ks, ss):
             r.k, r.status = int(k), int(s)
+    if autotune:
+        t = list(times)
+        return res, kd, sd, {b_: {"trsm_us": (t[4 * b_], t[4 * b_ + 1]),
+                                  "gram_us": (t[4 * b_ + 2], t[4 * b_ + 3])}
+                             for b_ in range(16) if t[4 * b_ + 1] > 0}
     return res, kd, sd
+
+
+def get_batch_tuning(handle=None):
+    """(trsm_jb[16], gram_tile[16]) of the handle, per width bucket
+    min((n - 1) // 32, 15)."""
+    h = handle or default_handle()
+    a, g = (_int * 16)(), (_int * 16)()
+    _check(lib().cqrrpt_batched_get_tuning(h.h, a, g), "cqrrpt_batched_get_tuning")
+    return list(a), list(g)
+
+
+def set_batch_tuning(trsm_jb=None, gram_tile=None, handle=None):
+    h = handle or default_handle()
+    a = (_int * 16)(*trsm_jb) if trsm_jb is not None else None
+    g = (_int * 16)(*gram_tile) if gram_tile is not None else None
+    _check(lib().cqrrpt_batched_set_tuning(h.h, a, g), "cqrrpt_batched_set_tuning")
 
 
 def set_batch_graphs(enable, handle=None):

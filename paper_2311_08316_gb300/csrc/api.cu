@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <vector>
@@ -36,12 +37,18 @@ struct cqrrpt_ctx {
   int64_t graph_key[12] = {};
   int graph_kernels = 0;
   int use_graphs = 1;
+  BatchTuning tune = default_tuning();  // tile shapes of the batched kernels
 };
 
 static std::atomic<long long> g_launches{0};
 
 namespace cqrrpt {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// k and status of the handle's last call into caller slots, stream-ordered
+int handle_finalize(cqrrpt_handle h, int64_t* k_out, int* status_out, cudaStream_t s) {
+  return launch_finalize(h->sc, k_out, status_out, s) == cudaSuccess ? kOk : kCudaError;
+}
+const BatchTuning* handle_tuning(cqrrpt_handle h) { return &h->tune; }
 }  // namespace cqrrpt
 
 namespace {
@@ -424,21 +431,16 @@ int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable) {
   return kOk;
 }
 
-int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
-                     const double* const* A, const int64_t* lda, double gamma, int nnz,
-                     const double* tol, const uint64_t* seed, int precision, double* const* Q,
-                     const int64_t* ldq, double* const* R, const int64_t* ldr, int64_t* const* J,
-                     int64_t* k_dev, int* status_dev, cudaStream_t stream) {
-  if (!h) return -1;
-  int st = batch_check(batch, m, n, A, lda, gamma, nnz, tol, seed, precision, Q, ldq, R, ldr, J);
-  if (st != kOk) return st;
-  DevGuard g(h->device);
-  size_t need = 0;
-  st = cqrrpt_batched_workspace_size(batch, m, n, gamma, nnz, &need);
-  if (st != kOk) return st;
-  st = ensure_ws(h, need);
-  if (st != kOk) return st;
+}  // extern "C"
 
+namespace {
+
+std::vector<BatchProblem> batch_problems(int batch, const int64_t* m, const int64_t* n,
+                                         const double* const* A, const int64_t* lda, double gamma,
+                                         int nnz, const double* tol, const uint64_t* seed,
+                                         double* const* Q, const int64_t* ldq, double* const* R,
+                                         const int64_t* ldr, int64_t* const* J, int64_t* k_dev,
+                                         int* status_dev) {
   std::vector<BatchProblem> probs((size_t)batch);
   for (int p = 0; p < batch; ++p) {
     BatchProblem& q = probs[(size_t)p];
@@ -448,15 +450,28 @@ int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t
     q.k_out = k_dev ? k_dev + p : nullptr;
     q.status_out = status_dev ? status_dev + p : nullptr;
   }
-  char* ws = (char*)h->ws;
-  BatchPlan P;
-  P.scalars = (DeviceScalars*)ws;
-  P.tables = ws + align256((int64_t)batch * sizeof(DeviceScalars));
-  char* per_problem = P.tables + batch_table_bytes(batch);
-  batch_plan(P, batch, probs.data(), per_problem);
+  return probs;
+}
 
-  // stage the tables through pinned memory (wait until the previous copy
-  // out of the staging buffer has finished before overwriting it)
+// Workspace layout of a batched call: device scalars, tables, then each
+// problem's workspace in order.
+struct BatchWs {
+  DeviceScalars* scalars;
+  char* tables;
+  char* per_problem;
+};
+BatchWs batch_ws(cqrrpt_handle h, int batch) {
+  char* ws = (char*)h->ws;
+  BatchWs b;
+  b.scalars = (DeviceScalars*)ws;
+  b.tables = ws + align256((int64_t)batch * sizeof(DeviceScalars));
+  b.per_problem = b.tables + batch_table_bytes(batch);
+  return b;
+}
+
+// Copies the plan's tables to the device through the pinned staging buffer
+// (after the previous copy out of it has finished).
+int stage_tables(cqrrpt_handle h, const BatchPlan& P, cudaStream_t stream) {
   const size_t img = P.image.size();
   if (!h->stage_ev && cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess)
     return kCudaError;
@@ -472,6 +487,18 @@ int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t
   if (cudaMemcpyAsync(P.tables, h->stage, img, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return kCudaError;
   if (cudaEventRecord(h->stage_ev, stream) != cudaSuccess) return kCudaError;
+  return kOk;
+}
+
+int batched_run(cqrrpt_handle h, std::vector<BatchProblem>& probs, cudaStream_t stream) {
+  const int batch = (int)probs.size();
+  const BatchWs W = batch_ws(h, batch);
+  BatchPlan P;
+  P.scalars = W.scalars;
+  P.tables = W.tables;
+  batch_plan(P, batch, probs.data(), W.per_problem, nullptr, &h->tune);
+  int st = stage_tables(h, P, stream);
+  if (st != kOk) return st;
   if (sketch_set_attributes(P.max_d) != cudaSuccess) return kCudaError;
 
   if (!h->use_graphs) return batch_launch(P, stream) == cudaSuccess ? kOk : kCudaError;
@@ -508,6 +535,160 @@ int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t
   }
   if (cudaGraphLaunch(h->graph_exec, stream) != cudaSuccess) return kCudaError;
   count_launches(h->graph_kernels);
+  return kOk;
+}
+
+// Times the line-4 TRSM and the Gram partial kernel of the problems in
+// `sub` (indices into probs) with every problem at shape `v`; best of
+// `reps` runs each (microseconds).
+int time_bucket(cqrrpt_handle h, const std::vector<BatchProblem>& probs,
+                const std::vector<int>& sub, int v, const BatchWs& W,
+                const std::vector<char*>& ws_each, cudaStream_t stream, double* t_trsm,
+                double* t_gram) {
+  std::vector<BatchProblem> sp;
+  std::vector<char*> sw;
+  std::vector<int> si;
+  for (int i : sub) {
+    sp.push_back(probs[(size_t)i]);
+    sw.push_back(ws_each[(size_t)i]);
+    si.push_back(i);
+  }
+  BatchTuning T;
+  for (int b = 0; b < kTuneBuckets; ++b) T.trsm_jb[b] = T.gram_tile[b] = v;
+  BatchPlan P;
+  P.scalars = W.scalars;
+  P.tables = W.tables;
+  batch_plan(P, (int)sp.size(), sp.data(), nullptr, sw.data(), &T, si.data());
+  int st = stage_tables(h, P, stream);
+  if (st != kOk) return st;
+  cudaEvent_t ev[3];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return kCudaError;
+  const int reps = 3;
+  *t_trsm = *t_gram = 1e300;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(ev[0], stream);
+    if (e == cudaSuccess)
+      e = launch_trsm_rut_batched(P.t1, P.base_trsm, P.nprob, P.tiles_trsm, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], stream);
+    if (e == cudaSuccess) e = launch_gram_batched(0, P.gr, P.base_gp, P.nprob, P.tiles_gp, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    if (e == cudaSuccess) {
+      *t_trsm = std::min(*t_trsm, 1e3 * (double)a);
+      *t_gram = std::min(*t_gram, 1e3 * (double)b);
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  return e == cudaSuccess ? kOk : kCudaError;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
+                     const double* const* A, const int64_t* lda, double gamma, int nnz,
+                     const double* tol, const uint64_t* seed, int precision, double* const* Q,
+                     const int64_t* ldq, double* const* R, const int64_t* ldr, int64_t* const* J,
+                     int64_t* k_dev, int* status_dev, cudaStream_t stream) {
+  if (!h) return -1;
+  int st = batch_check(batch, m, n, A, lda, gamma, nnz, tol, seed, precision, Q, ldq, R, ldr, J);
+  if (st != kOk) return st;
+  DevGuard g(h->device);
+  size_t need = 0;
+  st = cqrrpt_batched_workspace_size(batch, m, n, gamma, nnz, &need);
+  if (st != kOk) return st;
+  st = ensure_ws(h, need);
+  if (st != kOk) return st;
+  std::vector<BatchProblem> probs = batch_problems(batch, m, n, A, lda, gamma, nnz, tol, seed, Q,
+                                                   ldq, R, ldr, J, k_dev, status_dev);
+  return batched_run(h, probs, stream);
+}
+
+int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
+                            const double* const* A, const int64_t* lda, double gamma, int nnz,
+                            const double* tol, const uint64_t* seed, int precision,
+                            double* const* Q, const int64_t* ldq, double* const* R,
+                            const int64_t* ldr, int64_t* const* J, int64_t* k_dev,
+                            int* status_dev, double* times_us_host, cudaStream_t stream) {
+  if (!h) return -1;
+  int st = batch_check(batch, m, n, A, lda, gamma, nnz, tol, seed, precision, Q, ldq, R, ldr, J);
+  if (st != kOk) return st;
+  DevGuard g(h->device);
+  size_t need = 0;
+  st = cqrrpt_batched_workspace_size(batch, m, n, gamma, nnz, &need);
+  if (st != kOk) return st;
+  st = ensure_ws(h, need);
+  if (st != kOk) return st;
+  std::vector<BatchProblem> probs = batch_problems(batch, m, n, A, lda, gamma, nnz, tol, seed, Q,
+                                                   ldq, R, ldr, J, k_dev, status_dev);
+  // 1. one pass with the current shapes: R^sk, J and k of every problem
+  if ((st = batched_run(h, probs, stream)) != kOk) return st;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return kCudaError;
+  // 2. per width bucket and shape: time the line-4 TRSM (it rewrites M^pre
+  //    into Q from M, J and R^sk, the same values every time) and the Gram
+  //    partial sums of that M^pre
+  const BatchWs W = batch_ws(h, batch);
+  std::vector<char*> ws_each((size_t)batch);
+  char* w = W.per_problem;
+  std::vector<std::vector<int>> members(kTuneBuckets);
+  for (int p = 0; p < batch; ++p) {
+    ws_each[(size_t)p] = w;
+    w += problem_workspace_bytes(probs[(size_t)p].m, probs[(size_t)p].n, probs[(size_t)p].d, nnz);
+    members[(size_t)tune_bucket(probs[(size_t)p].n)].push_back(p);
+  }
+  if (times_us_host)
+    for (int i = 0; i < 4 * kTuneBuckets; ++i) times_us_host[i] = 0.0;
+  BatchTuning T = h->tune;
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    if (members[(size_t)b].empty()) continue;
+    double tt[2], tg[2];
+    const int shapes[2] = {16, 32};
+    for (int v = 0; v < 2; ++v) {
+      st = time_bucket(h, probs, members[(size_t)b], shapes[v], W, ws_each, stream, &tt[v], &tg[v]);
+      if (st != kOk) return st;
+    }
+    T.trsm_jb[b] = tt[0] < tt[1] ? 16 : 32;
+    T.gram_tile[b] = tg[0] < tg[1] ? 16 : 32;
+    if (times_us_host) {
+      times_us_host[4 * b + 0] = tt[0];
+      times_us_host[4 * b + 1] = tt[1];
+      times_us_host[4 * b + 2] = tg[0];
+      times_us_host[4 * b + 3] = tg[1];
+    }
+  }
+  h->tune = T;
+  // 3. the batch again with the chosen shapes (the outputs of the call)
+  if ((st = batched_run(h, probs, stream)) != kOk) return st;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return kCudaError;
+  return kOk;
+}
+
+int cqrrpt_batched_get_tuning(cqrrpt_handle h, int* trsm_jb_host, int* gram_tile_host) {
+  if (!h) return -1;
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    if (trsm_jb_host) trsm_jb_host[b] = h->tune.trsm_jb[b];
+    if (gram_tile_host) gram_tile_host[b] = h->tune.gram_tile[b];
+  }
+  return kOk;
+}
+
+int cqrrpt_batched_set_tuning(cqrrpt_handle h, const int* trsm_jb_host,
+                              const int* gram_tile_host) {
+  if (!h) return -1;
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    if (trsm_jb_host && trsm_jb_host[b] != 16 && trsm_jb_host[b] != 32) return -2;
+    if (gram_tile_host && gram_tile_host[b] != 16 && gram_tile_host[b] != 32) return -3;
+  }
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    if (trsm_jb_host) h->tune.trsm_jb[b] = trsm_jb_host[b];
+    if (gram_tile_host) h->tune.gram_tile[b] = gram_tile_host[b];
+  }
   return kOk;
 }
 

@@ -76,6 +76,7 @@ struct TrsmDesc {
   double* X;
   int64_t ldx;
   const int* status;
+  int jb;  // widest register block of columns: 16 or 32 (0 = 32)
 };
 
 struct GramDesc {
@@ -88,6 +89,7 @@ struct GramDesc {
   double* G;
   int64_t ldg;
   const int* status;
+  int tile;  // output tile edge: 16 or 32 (0 = 32)
 };
 
 struct PotrfDesc {

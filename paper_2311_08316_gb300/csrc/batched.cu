@@ -52,8 +52,18 @@ int64_t problem_workspace_bytes(int64_t m, int64_t n, int64_t d, int nnz) {
   return t;
 }
 
+BatchTuning default_tuning() {
+  BatchTuning t;
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    t.trsm_jb[b] = 32;
+    t.gram_tile[b] = b < 2 ? 16 : 32;
+  }
+  return t;
+}
+
 int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base,
-               char* const* ws_each) {
+               char* const* ws_each, const BatchTuning* tune, const int* scalar_index) {
+  const BatchTuning TU = tune ? *tune : default_tuning();
   DeviceScalars* scalars = P.scalars;
   char* tables = P.tables;
   P = BatchPlan();
@@ -91,7 +101,10 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     double* G = (double*)w; w += align256(n * n * 8);
     double* Rpre = (double*)w; w += align256(n * n * 8);
     double* f2 = (double*)w; w += align256((n + 1) * 8);
-    DeviceScalars* s = sc + p;
+    DeviceScalars* s = sc + (scalar_index ? scalar_index[p] : p);
+    const int bucket = tune_bucket(n);
+    const int jb = TU.trsm_jb[bucket] == 16 ? 16 : 32;
+    const int gt = TU.gram_tile[bucket] == 16 ? 16 : 32;
     SketchDesc& S = sk[p];
     S = SketchDesc{};
     S.m = m; S.n = n; S.d = (int)d; S.s = q.nnz; S.seed = q.seed;
@@ -100,11 +113,11 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     sketch_carve(S, region);
     qr[p] = QrcpDesc{(int)d, (int)n, X, d, qrcp_carve(qw, (int)n), q.J, Rsk, n, s};
     rk[p] = RankDesc{(int)n, Rsk, n, q.tol, f2, s};
-    t1[p] = TrsmDesc{m, &s->k, q.A, q.lda, q.J, Rsk, n, q.Q, q.ldq, &s->status};
-    gr[p] = GramDesc{m, (int)n, &s->k, q.Q, q.ldq, (double*)region, G, n, &s->status};
+    t1[p] = TrsmDesc{m, &s->k, q.A, q.lda, q.J, Rsk, n, q.Q, q.ldq, &s->status, jb};
+    gr[p] = GramDesc{m, (int)n, &s->k, q.Q, q.ldq, (double*)region, G, n, &s->status, gt};
     po[p] = PotrfDesc{(int)n, G, n, Rpre, n, s};
     s2[p] = Stage2Desc{Rpre, n, q.tol > 0.0 ? 0 : 1, s};
-    t2[p] = TrsmDesc{m, &s->k, q.Q, q.ldq, nullptr, Rpre, n, q.Q, q.ldq, &s->status};
+    t2[p] = TrsmDesc{m, &s->k, q.Q, q.ldq, nullptr, Rpre, n, q.Q, q.ldq, &s->status, jb};
     tm[p] = TrmmDesc{(int)n, &s->k, Rpre, n, Rsk, n, q.R, q.ldr, &s->status};
     fi[p] = FinalDesc{s, q.k_out, q.status_out};
     b_list[p + 1] = b_list[p] + sketch_list_tiles(S);
@@ -112,7 +125,7 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     b_comb[p + 1] = b_comb[p] + sketch_combine_tiles(S);
     b_gath[p + 1] = b_gath[p] + n;
     b_trsm[p + 1] = b_trsm[p] + trsm_tiles(m);
-    b_gp[p + 1] = b_gp[p] + gram_partial_tiles(m, (int)n);
+    b_gp[p + 1] = b_gp[p] + gram_partial_tiles(m, (int)n, gt);
     b_gc[p + 1] = b_gc[p] + gram_combine_tiles((int)n);
     b_tm[p + 1] = b_tm[p] + trmm_tiles((int)n);
   }

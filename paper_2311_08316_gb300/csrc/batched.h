@@ -46,6 +46,22 @@ struct BatchPlan {
                 *base_gc = nullptr, *base_tm = nullptr;
 };
 
+// Tile shapes of the batched O(m n^2) kernels, per problem width bucket
+// b = min((n - 1) / 32, kTuneBuckets - 1): the TRSM's widest register block
+// (16 or 32 columns) and the Gram's output tile edge (16 or 32).  Only the
+// blocking changes, never the arithmetic.
+constexpr int kTuneBuckets = 16;
+struct BatchTuning {
+  int trsm_jb[kTuneBuckets];
+  int gram_tile[kTuneBuckets];
+};
+inline int tune_bucket(int64_t n) {
+  const int64_t b = (n - 1) / 32;
+  return (int)(b < kTuneBuckets - 1 ? b : kTuneBuckets - 1);
+}
+// untuned shapes: 32-column TRSM blocks; 16 x 16 Gram tiles up to n = 64
+BatchTuning default_tuning();
+
 // workspace of one problem inside a batch
 int64_t problem_workspace_bytes(int64_t m, int64_t n, int64_t d, int nnz);
 // upper bound of the table image for `batch` problems
@@ -61,8 +77,11 @@ inline int64_t batch_table_bytes(int batch) {
 // Fills P (P.scalars and P.tables must be set by the caller beforehand) and
 // carves every problem's workspace from ws_base onward, or, when ws_each is
 // given, problem p's workspace (problem_workspace_bytes) from ws_each[p].
+// Problem p uses the device scalars P.scalars[p], or P.scalars[scalar_index[p]]
+// when scalar_index is given; tile shapes come from `tune` (NULL: defaults).
 int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base,
-               char* const* ws_each = nullptr);
+               char* const* ws_each = nullptr, const BatchTuning* tune = nullptr,
+               const int* scalar_index = nullptr);
 // Enqueues the 14 batched launches.
 cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s);
 cudaError_t sketch_set_attributes(int max_d);

@@ -5,10 +5,14 @@
 // gram_partial forms P_b[a, c] = sum_{r in b} X[r, a] X[r, c] in ascending r
 // with one fma per term (a <= c); gram_combine then adds the blocks in
 // ascending order, G[a, c] = ((P_0 + P_1) + P_2) + ..., and mirrors the
-// upper triangle.  One CTA computes one kGramTile x kGramTile output tile of
-// one row block; each of its 64 threads owns a 4 x 4 register tile, and rows
-// are staged kGramRows at a time in shared memory.  The kernel is bound by
-// the FP64 pipe.  Single-problem and batched launches share the bodies.
+// upper triangle.  One CTA computes one output tile of one row block
+// (kGramTile x kGramTile, or 16 x 16 where a batched problem's descriptor
+// asks for it: less padding when k is small; the batched autotuner picks the
+// edge per problem size); its 64 threads own 4 x 4 (2 x 2) register tiles,
+// and rows are staged kGramRows at a time in shared memory.  Each entry is
+// the same ascending-r fma chain whatever the tile, so the tile does not
+// change the result.  The kernel is bound by the FP64 pipe.  Single-problem
+// and batched launches share the bodies.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,27 +21,35 @@ namespace cqrrpt {
 static __host__ __device__ int64_t gram_nblocks(int64_t m) {
   return (m + kRowBlock - 1) / kRowBlock;
 }
-static __host__ __device__ int64_t gram_ntri(int kmax) {
-  const int64_t t1 = (kmax + kGramTile - 1) / kGramTile;
+static __host__ __device__ int gram_tile_edge(int tile) { return tile == 16 ? 16 : kGramTile; }
+static __host__ __device__ int64_t gram_ntri(int kmax, int tile) {
+  const int e = gram_tile_edge(tile);
+  const int64_t t1 = (kmax + e - 1) / e;
   return t1 * (t1 + 1) / 2;
 }
 
 int64_t gram_workspace_bytes(int64_t m, int64_t n) { return align256(gram_nblocks(m) * n * n * 8); }
-int64_t gram_partial_tiles(int64_t m, int kmax) { return gram_nblocks(m) * gram_ntri(kmax); }
+int64_t gram_partial_tiles(int64_t m, int kmax, int tile) {
+  return gram_nblocks(m) * gram_ntri(kmax, tile);
+}
 int64_t gram_combine_tiles(int kmax) {
   return ((int64_t)kmax * kmax + kCombineThreads - 1) / kCombineThreads;
 }
 
-__device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& D) {
-  __shared__ double Xa[kGramTile][kGramRows + 1];  // [col][row]
-  __shared__ double Xc[kGramTile][kGramRows + 1];
-  if (*D.status != kOk) return;
+// One TILE x TILE output tile of one row block; 64 threads in an 8 x 8
+// grid, each with a (TILE/8) x (TILE/8) register tile.
+typedef double GramStage[kGramTile][kGramRows + 1];  // [col][row]
+
+template <int TILE>
+__device__ __forceinline__ void gram_partial_tile(int64_t tile, const GramDesc& D, GramStage& Xa,
+                                                  GramStage& Xc) {
+  constexpr int R = TILE / 8;
   const int k = (int)*D.k_dev;
-  const int64_t ntri = gram_ntri(D.n_ld);
+  const int64_t ntri = gram_ntri(D.n_ld, TILE);
   const int64_t b = tile / ntri;
   int t = (int)(tile - b * ntri);
   // triangular tile index -> (ta, tc) with ta <= tc, for the device k
-  const int tiles_1d = (k + kGramTile - 1) / kGramTile;
+  const int tiles_1d = (k + TILE - 1) / TILE;
   int ta = 0;
   while (ta < tiles_1d && t >= tiles_1d - ta) { t -= tiles_1d - ta; ++ta; }
   if (ta >= tiles_1d) return;
@@ -47,18 +59,18 @@ __device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& 
   if (rows <= 0) return;
   const double* X = D.X;
   const int64_t ldx = D.ldx;
-  const int a0 = ta * kGramTile, c0 = tc * kGramTile;
+  const int a0 = ta * TILE, c0 = tc * TILE;
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < R; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < R; ++v) acc[u][v] = 0.0;
 
   for (int rr0 = 0; rr0 < rows; rr0 += kGramRows) {
     const int nr = min(kGramRows, rows - rr0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kGramTile * kGramRows; e += 64) {
+    for (int e = threadIdx.x; e < TILE * kGramRows; e += 64) {
       const int col = e / kGramRows, row = e % kGramRows;
       const int64_t r = r0 + rr0 + row;
       const bool rok = row < nr;
@@ -67,26 +79,35 @@ __device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& 
     }
     __syncthreads();
     for (int row = 0; row < nr; ++row) {
-      double va[4], vc[4];
+      double va[R], vc[R];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) va[u] = Xa[ty * 4 + u][row];
+      for (int u = 0; u < R; ++u) va[u] = Xa[ty * R + u][row];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) vc[v] = Xc[tx * 4 + v][row];
+      for (int v = 0; v < R; ++v) vc[v] = Xc[tx * R + v][row];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = __fma_rn(va[u], vc[v], acc[u][v]);
+        for (int v = 0; v < R; ++v) acc[u][v] = __fma_rn(va[u], vc[v], acc[u][v]);
     }
   }
   const int n_ld = D.n_ld;
   double* P = D.partial + b * (int64_t)n_ld * n_ld;
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < R; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int a = a0 + ty * 4 + u, c = c0 + tx * 4 + v;
+    for (int v = 0; v < R; ++v) {
+      const int a = a0 + ty * R + u, c = c0 + tx * R + v;
       if (a < k && c < k && a <= c) P[(int64_t)c * n_ld + a] = acc[u][v];
     }
+}
+
+__device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& D) {
+  __shared__ GramStage Xa, Xc;
+  if (*D.status != kOk) return;
+  if (D.tile == 16)
+    gram_partial_tile<16>(tile, D, Xa, Xc);
+  else
+    gram_partial_tile<kGramTile>(tile, D, Xa, Xc);
 }
 
 __device__ __forceinline__ void gram_combine_body(int64_t tile, const GramDesc& D) {
@@ -129,8 +150,8 @@ __global__ void __launch_bounds__(kCombineThreads) gram_combine_batched_kernel(c
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
                         cudaStream_t stream) {
-  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status};
-  gram_partial_kernel<<<(unsigned)gram_partial_tiles(m, kmax), 64, 0, stream>>>(D);
+  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status, kGramTile};
+  gram_partial_kernel<<<(unsigned)gram_partial_tiles(m, kmax, kGramTile), 64, 0, stream>>>(D);
   gram_combine_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
   count_launches(2);
   return cudaGetLastError();

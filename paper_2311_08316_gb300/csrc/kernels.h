@@ -77,7 +77,7 @@ cudaError_t launch_trsm_rut_batched(const TrsmDesc* D, const int64_t* base, int 
 
 // ---- Alg. 2 line 5 -------------------------------------------------------
 int64_t gram_workspace_bytes(int64_t m, int64_t n);
-int64_t gram_partial_tiles(int64_t m, int kmax);
+int64_t gram_partial_tiles(int64_t m, int kmax, int tile);
 int64_t gram_combine_tiles(int kmax);
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,

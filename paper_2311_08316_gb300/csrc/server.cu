@@ -7,11 +7,14 @@
 //     arena over one allocation made at creation -- and at most max_inflight
 //     are in flight; the host -> device copy of an admitted request's A is
 //     issued at once on a copy stream, overlapping the running wave;
-//   * whenever no wave is running, launches one batched pass (the batched
-//     kernels of batched.cu) over every admitted FP64 request whose input has
-//     arrived -- requests that arrived while the previous wave ran join the
-//     next one -- and runs split-BF16 requests through the single-problem
-//     path after it;
+//   * whenever no wave is running, either launches one batched pass (the
+//     batched kernels of batched.cu) over every admitted small FP64 request
+//     whose input has arrived -- requests that arrived while the previous
+//     wave ran join the next one -- or, when the oldest arrived request is
+//     routed to the single-problem path (split-BF16 precision, or n above
+//     kBatchMaxN, where the one-CTA-per-problem QRCP and Cholesky of the
+//     batched kernels would serialise), runs that request alone on the whole
+//     GPU;
 //   * when a wave completes, copies each result (Q, R, J, k, status) back on
 //     the copy stream, frees the request's arena block when the copy is done
 //     and records the completion time.
@@ -35,6 +38,9 @@
 #include "saso.cuh"
 
 namespace cqrrpt {
+
+int handle_finalize(cqrrpt_handle h, int64_t* k_out, int* status_out, cudaStream_t s);
+const BatchTuning* handle_tuning(cqrrpt_handle h);
 
 namespace {
 
@@ -105,7 +111,17 @@ struct Req {
   cqrrpt_result res{};
 };
 
-size_t footprint(const cqrrpt_request& r, int64_t d, int nnz, int precision) {
+// Widest problem a batched wave takes; wider ones (and every split-BF16
+// request) run alone through cqrrpt_d with the multi-CTA QRCP and Cholesky.
+constexpr int64_t kBatchMaxN = 256;
+
+bool single_route(const cqrrpt_request& r) {
+  return r.precision != CQRRPT_FP64 || r.n > kBatchMaxN;
+}
+
+// Device bytes a request holds while in flight.  Requests on the single
+// path use the handle's workspace instead of their own.
+size_t footprint(const cqrrpt_request& r, int64_t d, int nnz) {
   const int64_t m = r.m, n = r.n;
   size_t b = 0;
   b += (size_t)align256(m * n * 8);      // A
@@ -113,7 +129,7 @@ size_t footprint(const cqrrpt_request& r, int64_t d, int nnz, int precision) {
   b += (size_t)align256(n * n * 8);      // R
   b += (size_t)align256(n * 8);          // J
   b += 256;                              // k, status
-  if (precision == CQRRPT_FP64) b += (size_t)problem_workspace_bytes(m, n, d, nnz);
+  if (!single_route(r)) b += (size_t)problem_workspace_bytes(m, n, d, nnz);
   return b;
 }
 
@@ -208,7 +224,7 @@ bool Server::step() {
       Req* q = pending.front();
       const cqrrpt_request& r = q->r;
       size_t off = 0;
-      const size_t bytes = footprint(r, q->d, nnz, r.precision);
+      const size_t bytes = footprint(r, q->d, nnz);
       if (!arena.alloc(bytes, &off)) break;
       pending.pop_front();
       q->off = off;
@@ -235,16 +251,25 @@ bool Server::step() {
       progress = true;
     }
   }
-  // launch a wave over every admitted request whose input has arrived
+  // launch the next unit of work: the oldest arrived request decides
+  // between a batched wave and a single-path run
   if (!wave_running) {
-    std::vector<Req*> ready, single;
+    std::vector<Req*> ready;
+    Req* solo = nullptr;
+    double ready_first = 0.0;
     {
       std::lock_guard<std::mutex> lock(mu);
-      for (Req* q : inflight)
-        if (q->state == kStaging && cudaEventQuery(q->h2d) == cudaSuccess)
-          (q->r.precision == CQRRPT_FP64 ? ready : single).push_back(q);
+      for (Req* q : inflight) {
+        if (q->state != kStaging || cudaEventQuery(q->h2d) != cudaSuccess) continue;
+        if (single_route(q->r)) {
+          if (!solo || q->t_submit < solo->t_submit) solo = q;
+        } else {
+          if (ready.empty() || q->t_submit < ready_first) ready_first = q->t_submit;
+          ready.push_back(q);
+        }
+      }
     }
-    if (!ready.empty()) {
+    if (!ready.empty() && !(solo && solo->t_submit < ready_first)) {
       std::vector<BatchProblem> probs(ready.size());
       std::vector<char*> wss(ready.size());
       for (size_t i = 0; i < ready.size(); ++i) {
@@ -258,7 +283,7 @@ bool Server::step() {
       BatchPlan P;
       P.scalars = (DeviceScalars*)fixed;
       P.tables = fixed + align256((int64_t)max_inflight * sizeof(DeviceScalars));
-      batch_plan(P, (int)ready.size(), probs.data(), nullptr, wss.data());
+      batch_plan(P, (int)ready.size(), probs.data(), nullptr, wss.data(), handle_tuning(h));
       const size_t img = P.image.size();
       cudaEventSynchronize(stage_ev);
       if (img > stage_bytes) {
@@ -282,24 +307,26 @@ bool Server::step() {
       wave_running = true;
       ++waves;
       progress = true;
-    } else if (!single.empty()) {
-      // split-BF16 requests: the single-problem path, one at a time
-      Req* q = single.front();
+    } else if (solo) {
+      Req* q = solo;
       {
         std::lock_guard<std::mutex> lock(mu);
         q->state = kRunning;
         wave.assign(1, q);
       }
+      // FP64 requests are enqueued without a host wait; the split-BF16
+      // pipeline reads k back on the way (its recursive products are sized
+      // on the host).  k and status land in the request's device slots.
       const int rc = run_single(h, q->r, gamma, nnz, q->A, q->Q, q->R, q->J, compute);
-      // k and status of the handle's last call into the request's slots
-      int st = 0;
-      int64_t k = 0;
-      cqrrpt_last_status(h, compute, &st, &k);
-      if (rc != kOk && rc != kRankZero && rc != kNonFinite) st = rc;
-      *q->k_host = k;
-      *q->st_host = st;
-      cudaMemcpyAsync(q->k_dev, q->k_host, sizeof(int64_t), cudaMemcpyHostToDevice, compute);
-      cudaMemcpyAsync(q->st_dev, q->st_host, sizeof(int), cudaMemcpyHostToDevice, compute);
+      if (rc != kOk && rc != kRankZero && rc != kNonFinite) {
+        *q->k_host = 0;
+        *q->st_host = rc;
+        cudaMemcpyAsync(q->k_dev, q->k_host, sizeof(int64_t), cudaMemcpyHostToDevice, compute);
+        cudaMemcpyAsync(q->st_dev, q->st_host, sizeof(int), cudaMemcpyHostToDevice, compute);
+      } else if (handle_finalize(h, q->k_dev, q->st_dev, compute) != kOk) {
+        error = kCudaError;
+        return false;
+      }
       cudaEventRecord(wave_done, compute);
       wave_running = true;
       ++waves;
@@ -401,7 +428,7 @@ int cqrrpt_server_submit(cqrrpt_server S, const cqrrpt_request* r, uint64_t* tic
     return -2;
   const int64_t d = (int64_t)std::ceil(s.gamma * (double)r->n);
   if (d > r->m || d > 28000 || s.nnz > d) return -2;
-  if (footprint(*r, d, s.nnz, r->precision) > s.arena.size) return kNoMemory;
+  if (footprint(*r, d, s.nnz) > s.arena.size) return kNoMemory;
   Req* q = new Req();
   q->r = *r;
   q->d = d;

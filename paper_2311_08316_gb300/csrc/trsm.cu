@@ -6,12 +6,15 @@
 // runs in place with cols = identity and T = R^pre (Q_k = M^pre (R^pre)^{-1}).
 //
 // One thread owns one row i.  Columns are solved in register blocks of
-// kTrsmJB: the block's partial sums are seeded with B, then receive the
-// terms t < j0 chunk by chunk (kTrsmTB rows of T staged in shared memory,
-// X[i, t] re-read from the thread's own, already solved row), then the
-// triangular part of the block in ascending t.  Every partial sum therefore
-// receives its terms in ascending t, so the result does not depend on the
-// blocking.  The kernel is bound by the FP64 pipe (one DFMA per term).
+// kTrsmJB columns (16 where a batched problem's descriptor asks for it; the
+// batched autotuner picks the width per problem size), the last k mod that
+// width in blocks of 16, 8, 4, 2, 1.  A block's partial sums are seeded
+// with B, then receive the terms t < j0 chunk by chunk (kTrsmTB rows of T
+// staged in shared memory, X[i, t] re-read from the thread's own, already
+// solved row), then the triangular part of the block in ascending t.  Every
+// partial sum therefore receives its terms in ascending t, so the result
+// does not depend on the blocking.  The kernel is bound by the FP64 pipe
+// (one DFMA per term).
 //
 // The single-problem kernel and the batched kernel (one launch over many
 // independent problems; CTA -> (problem, row tile) through a prefix table)
@@ -22,79 +25,98 @@
 
 namespace cqrrpt {
 
-__device__ __forceinline__ void trsm_rut_body(int64_t tile, const TrsmDesc& D) {
-  __shared__ double Ts[kTrsmTB][kTrsmJB];
-  __shared__ double Td[kTrsmJB][kTrsmJB];
-  if (*D.status != kOk) return;
-  const int k = (int)*D.k_dev;
-  const int64_t m = D.m;
+// Columns j0 .. j0 + JB - 1 of the thread's row i (all of them exist).
+template <int JB>
+__device__ __forceinline__ void trsm_rut_block(int j0, int64_t i, bool active, double* Ts,
+                                               double* Td, const TrsmDesc& D) {
   const double* B = D.B;
   const int64_t* cols = D.cols;
   const double* T = D.T;
   double* X = D.X;
   const int64_t ldb = D.ldb, ldt = D.ldt, ldx = D.ldx;
-  const int64_t i = tile * (int64_t)kTrsmThreads + threadIdx.x;
-  const bool active = i < m;
-  for (int j0 = 0; j0 < k; j0 += kTrsmJB) {
-    const int jb = min(kTrsmJB, k - j0);
-    double s[kTrsmJB];
+  double s[JB];
 #pragma unroll
-    for (int jj = 0; jj < kTrsmJB; ++jj) {
-      s[jj] = 0.0;
-      if (active && jj < jb) {
-        const int64_t bc = cols ? cols[j0 + jj] : (int64_t)(j0 + jj);
-        s[jj] = B[bc * ldb + i];
-      }
+  for (int jj = 0; jj < JB; ++jj) {
+    s[jj] = 0.0;
+    if (active) {
+      const int64_t bc = cols ? cols[j0 + jj] : (int64_t)(j0 + jj);
+      s[jj] = B[bc * ldb + i];
     }
-    // terms t < j0
-    for (int t0 = 0; t0 < j0; t0 += kTrsmTB) {
-      const int tb = min(kTrsmTB, j0 - t0);
-      __syncthreads();
-      for (int e = threadIdx.x; e < kTrsmTB * kTrsmJB; e += kTrsmThreads) {
-        const int tt = e / kTrsmJB, jj = e % kTrsmJB;
-        Ts[tt][jj] = (tt < tb && jj < jb) ? T[(int64_t)(j0 + jj) * ldt + (t0 + tt)] : 0.0;
-      }
-      __syncthreads();
-      if (active) {
-        for (int tt = 0; tt < tb; ++tt) {
-          const double x = -X[(int64_t)(t0 + tt) * ldx + i];
-#pragma unroll
-          for (int jj = 0; jj < kTrsmJB; ++jj) s[jj] = __fma_rn(x, Ts[tt][jj], s[jj]);
-        }
-      }
-    }
-    // triangular block
+  }
+  // terms t < j0
+  for (int t0 = 0; t0 < j0; t0 += kTrsmTB) {
+    const int tb = min(kTrsmTB, j0 - t0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kTrsmJB * kTrsmJB; e += kTrsmThreads) {
-      const int tt = e / kTrsmJB, jj = e % kTrsmJB;
-      Td[tt][jj] = (tt < jb && jj < jb) ? T[(int64_t)(j0 + jj) * ldt + (j0 + tt)] : 1.0;
+    for (int e = threadIdx.x; e < tb * JB; e += kTrsmThreads) {
+      const int tt = e / JB, jj = e % JB;
+      Ts[tt * JB + jj] = T[(int64_t)(j0 + jj) * ldt + (t0 + tt)];
     }
     __syncthreads();
     if (active) {
+      for (int tt = 0; tt < tb; ++tt) {
+        const double x = -X[(int64_t)(t0 + tt) * ldx + i];
 #pragma unroll
-      for (int jj = 0; jj < kTrsmJB; ++jj) {
-        if (jj < jb) {
-          const double x = __ddiv_rn(s[jj], Td[jj][jj]);
-          X[(int64_t)(j0 + jj) * ldx + i] = x;
-          const double nx = -x;
-#pragma unroll
-          for (int j2 = jj + 1; j2 < kTrsmJB; ++j2) s[j2] = __fma_rn(nx, Td[jj][j2], s[j2]);
-        }
+        for (int jj = 0; jj < JB; ++jj) s[jj] = __fma_rn(x, Ts[tt * JB + jj], s[jj]);
       }
+    }
+  }
+  // triangular block
+  __syncthreads();
+  for (int e = threadIdx.x; e < JB * JB; e += kTrsmThreads) {
+    const int tt = e / JB, jj = e % JB;
+    Td[tt * JB + jj] = T[(int64_t)(j0 + jj) * ldt + (j0 + tt)];
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) {
+      const double x = __ddiv_rn(s[jj], Td[jj * JB + jj]);
+      X[(int64_t)(j0 + jj) * ldx + i] = x;
+      const double nx = -x;
+#pragma unroll
+      for (int j2 = jj + 1; j2 < JB; ++j2) s[j2] = __fma_rn(nx, Td[jj * JB + j2], s[j2]);
     }
   }
 }
 
+// Blocks of JBMAX columns, then the remainder k mod JBMAX as blocks of
+// halving width (16, 8, 4, 2, 1), so no block computes a column that does not
+// exist.
+// Ts (kTrsmTB x kTrsmJB) and Td (kTrsmJB x kTrsmJB): shared staging.
+template <int JBMAX>
+__device__ __forceinline__ void trsm_rut_body(int64_t tile, const TrsmDesc& D, double* Ts,
+                                              double* Td) {
+  static_assert(JBMAX == 16 || JBMAX == 32, "column block of 16 or 32");
+  if (*D.status != kOk) return;
+  const int k = (int)*D.k_dev;
+  const int64_t i = tile * (int64_t)kTrsmThreads + threadIdx.x;
+  const bool active = i < D.m;
+  int j0 = 0;
+  for (; j0 + JBMAX <= k; j0 += JBMAX) trsm_rut_block<JBMAX>(j0, i, active, Ts, Td, D);
+  if (JBMAX > 16 && k - j0 >= 16) { trsm_rut_block<16>(j0, i, active, Ts, Td, D); j0 += 16; }
+  if (k - j0 >= 8) { trsm_rut_block<8>(j0, i, active, Ts, Td, D); j0 += 8; }
+  if (k - j0 >= 4) { trsm_rut_block<4>(j0, i, active, Ts, Td, D); j0 += 4; }
+  if (k - j0 >= 2) { trsm_rut_block<2>(j0, i, active, Ts, Td, D); j0 += 2; }
+  if (k - j0 >= 1) trsm_rut_block<1>(j0, i, active, Ts, Td, D);
+}
+
 __global__ void __launch_bounds__(kTrsmThreads) trsm_rut_kernel(TrsmDesc D) {
-  trsm_rut_body(blockIdx.x, D);
+  __shared__ double Ts[kTrsmTB * kTrsmJB];
+  __shared__ double Td[kTrsmJB * kTrsmJB];
+  trsm_rut_body<kTrsmJB>(blockIdx.x, D, Ts, Td);
 }
 
 __global__ void __launch_bounds__(kTrsmThreads) trsm_rut_batched_kernel(const TrsmDesc* D,
                                                                          const int64_t* base,
                                                                          int nprob) {
   int64_t local;
+  __shared__ double Ts[kTrsmTB * kTrsmJB];
+  __shared__ double Td[kTrsmJB * kTrsmJB];
   const int p = find_problem(base, nprob, blockIdx.x, &local);
-  trsm_rut_body(local, D[p]);
+  if (D[p].jb == 16)
+    trsm_rut_body<16>(local, D[p], Ts, Td);
+  else
+    trsm_rut_body<32>(local, D[p], Ts, Td);
 }
 
 int64_t trsm_tiles(int64_t m) { return (m + kTrsmThreads - 1) / kTrsmThreads; }
@@ -103,7 +125,7 @@ cudaError_t launch_trsm_rut(int64_t m, int kmax, const int64_t* k_dev, const dou
                             int64_t ldb, const int64_t* cols, const double* T, int64_t ldt,
                             double* X, int64_t ldx, const int* status, cudaStream_t stream) {
   (void)kmax;
-  TrsmDesc D{m, k_dev, B, ldb, cols, T, ldt, X, ldx, status};
+  TrsmDesc D{m, k_dev, B, ldb, cols, T, ldt, X, ldx, status, kTrsmJB};
   trsm_rut_kernel<<<(unsigned)trsm_tiles(m), kTrsmThreads, 0, stream>>>(D);
   count_launches(1);
   return cudaGetLastError();

@@ -105,3 +105,47 @@ def test_batched_per_problem_status(C):
     assert torch.equal(res[0].Q, res[3].Q)
     ref = oracle.cqrrpt(good, 1.25, 3, -1.0, 1)
     assert bits_equal(host(res[0].R), ref.R)
+
+
+def test_batched_tile_shapes_do_not_change_results(C):
+    # every TRSM column block (16 / 32, with the 16-8-4-2-1 remainder) and
+    # Gram tile (16 / 32) gives the oracle's bits; widths cover several
+    # buckets and k mod 32 of every residue class a few times
+    mats, tols = make_batch(12, 6)
+    mats += [np.asfortranarray(W.planted(700, n, W.logspaced(n, -5.0), 60 + n).numpy())
+             for n in (31, 33, 47, 64, 65, 97, 130)]
+    tols += [1e-12] * 7
+    seeds = [900 + i for i in range(len(mats))]
+    As = [gpu(A) for A in mats]
+    refs = [oracle.cqrrpt(A, 1.25, 4, t, s) for A, t, s in zip(mats, tols, seeds)]
+    h = C.Handle()
+    for jb, gt in [(16, 16), (32, 32), (16, 32), (32, 16)]:
+        C.set_batch_tuning([jb] * 16, [gt] * 16, handle=h)
+        res, _, _ = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, handle=h)
+        for i, (r, ref) in enumerate(zip(res, refs)):
+            assert r.k == ref.k and bits_equal(host(r.J), ref.J), (jb, gt, i)
+            assert bits_equal(host(r.Q), ref.Q) and bits_equal(host(r.R), ref.R), (jb, gt, i)
+    with pytest.raises(C.CqrrptError):
+        C.set_batch_tuning([24] * 16, None, handle=h)
+
+
+def test_batched_autotune_picks_shapes_and_keeps_results(C):
+    mats, tols = make_batch(16, 7)
+    seeds = [300 + i for i in range(len(mats))]
+    As = [gpu(A) for A in mats]
+    h = C.Handle()
+    res, _, _, times = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, handle=h, autotune=True)
+    buckets = {min((A.shape[1] - 1) // 32, 15) for A in mats}
+    assert set(times) == buckets
+    jb, gt = C.get_batch_tuning(handle=h)
+    for b, t in times.items():
+        assert all(x > 0 for x in t["trsm_us"] + t["gram_us"])
+        assert jb[b] == (16 if t["trsm_us"][0] < t["trsm_us"][1] else 32)
+        assert gt[b] == (16 if t["gram_us"][0] < t["gram_us"][1] else 32)
+    again, _, _ = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, handle=h)
+    for i, (A, r, r2) in enumerate(zip(mats, res, again)):
+        ref = oracle.cqrrpt(A, 1.25, 4, tols[i], seeds[i])
+        assert r.k == ref.k and r2.k == ref.k
+        for x in (r, r2):
+            assert bits_equal(host(x.J), ref.J)
+            assert bits_equal(host(x.Q), ref.Q) and bits_equal(host(x.R), ref.R)

@@ -108,3 +108,29 @@ def test_server_mixed_precision_requests(C):
         assert np.linalg.norm(AJ - Q @ R) / np.linalg.norm(A) <= 1e-12
         assert np.linalg.norm(Q.T @ Q - np.eye(res.k), 2) <= 1e-12
     srv.close()
+
+
+def test_server_wide_fp64_requests_take_single_path(C):
+    # n > 256 runs alone through the multi-CTA path; narrow ones are batched.
+    # Either way the result is bit-identical to the oracle, and arrival order
+    # decides which unit of work starts next.
+    rng = np.random.default_rng(4)
+    reqs = []
+    for i, n in enumerate([300, 40, 280, 64, 260, 17]):
+        m = int(rng.integers(2 * n, 5000))
+        A = W.planted(m, n, W.logspaced(n, -6.0), 9000 + i).numpy()
+        reqs.append((np.asfortranarray(A), 1e-12, 7000 + i))
+    srv = C.Server(hbm_budget_bytes=1 << 30, max_inflight=8)
+    tickets = [srv.submit(pinned_colmajor(A), tol, seed) for A, tol, seed in reqs]
+    srv.drain(timeout_us=120_000_000)
+    assert srv.stats()["completed"] == len(reqs)
+    for t, (A, tol, seed) in zip(tickets, reqs):
+        fac, res = srv.poll(t)
+        ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+        assert res.status == ref.status and res.k == ref.k
+        assert np.array_equal(fac.J.numpy(), ref.J)
+        Q = np.asfortranarray(fac.Q.numpy())
+        R = np.asfortranarray(fac.R.numpy())
+        assert np.array_equal(Q.view(np.uint64), ref.Q.view(np.uint64))
+        assert np.array_equal(R.view(np.uint64), ref.R.view(np.uint64))
+    srv.close()

@@ -157,3 +157,33 @@ def batch_uneven(count=512, seed=BASE_SEED + 3, m_lo=4096, m_hi=65536, n_lo=32, 
         out.append(Workload("batch%d" % i, m, n, 1.25, 4, tol, seed + 100 + 3 * i,
                             seed + 10**6 + i, sv=sv, rank=(r if r < n else 0)))
     return out
+
+
+def serving_requests(count, seed=BASE_SEED + 4, m_exp=(12, 20), n_exp=(4, 9), cond_exp=(2, 12),
+                     deficient=0.3, mixed=0.5):
+    """A stream of independent requests: m = round(2^U[12, 20]),
+    n = round(2^U[4, 9]), sv log-spaced 1 -> 10^-U[2, 12]; a fraction
+    `deficient` has planted rank r ~ U[n/2, n-1] (sv zero after r, plus
+    1e-15 Gaussian noise, tol 1e-9), the rest is full rank (tol 1e-12);
+    gamma 1.25, 4 nnz/col; a fraction `mixed` asks for split-BF16 precision
+    (flag `mixed` on the Workload).  Returns a list of (Workload, mixed)."""
+    g = torch.Generator()
+    g.manual_seed(seed)
+    out = []
+    for i in range(count):
+        u = torch.rand(4, generator=g, dtype=torch.float64)
+        m = int(round(2.0 ** (m_exp[0] + (m_exp[1] - m_exp[0]) * float(u[0]))))
+        n = int(round(2.0 ** (n_exp[0] + (n_exp[1] - n_exp[0]) * float(u[1]))))
+        m = max(m, int(math.ceil(1.25 * n)))
+        lo = -(cond_exp[0] + (cond_exp[1] - cond_exp[0]) * float(u[2]))
+        if float(u[3]) < deficient and n >= 2:
+            r = int(torch.randint(max(1, n // 2), n, (1,), generator=g))
+            sv = torch.zeros(n, dtype=torch.float64)
+            sv[:r] = logspaced(r, lo)
+            noise, tol = 1e-15, 1e-9
+        else:
+            r, sv, noise, tol = 0, logspaced(n, lo), 0.0, 1e-12
+        mx = bool(float(torch.rand(1, generator=g, dtype=torch.float64)) < mixed)
+        out.append((Workload("req%d" % i, m, n, 1.25, 4, tol, seed + 100 + 3 * i,
+                             seed + 10**6 + i, sv=sv, noise=noise, rank=r), mx))
+    return out

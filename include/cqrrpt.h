@@ -60,8 +60,9 @@ extern "C" {
  *                     library's documented arithmetic on every call.
  *   CQRRPT_SPLITBF16  lines 4, 5, 7 on the BF16 tensor cores through an
  *                     error-free split of every operand into eight 7-bit
- *                     digits (56 bits) with exact FP32 accumulation of
- *                     chunks of 1024 terms, summed in FP64: FP64-level
+ *                     digits (56 bits), exact FP32 accumulation of chunks of
+ *                     1024 terms, exact 64-bit integer combination of the
+ *                     digit levels, two FP64 roundings per entry: FP64-level
  *                     accuracy, not bit-identical to CQRRPT_FP64.
  *   CQRRPT_SPLITBF16_CHOLQR2  as CQRRPT_SPLITBF16, followed by a second
  *                     Cholesky-QR pass on Q (G2 = Q^T Q, R2 = chol(G2),
@@ -333,15 +334,18 @@ int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R
                    int64_t* fail_dev, cudaStream_t stream);
 
 /* Line 5 in the CQRRPT_SPLITBF16 arithmetic: G = X^T X (k x k) as 36 BF16
- * tensor-core products of 7-bit digit planes, exact FP32 chunk sums of 1024
- * terms added in FP64. */
+ * tensor-core products of 7-bit digit planes: exact FP32 chunk sums of 1024
+ * terms, combined exactly in 64-bit integers (two groups of four levels),
+ * each group rounded once to FP64.  A bounded device wait that expires is
+ * reported as CQRRPT_TIMEOUT by cqrrpt_last_status. */
 int cqrrpt_gram_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_t ldx,
                         double* G, int64_t ldg, cudaStream_t stream);
 
 /* Lines 4 and 7 in the CQRRPT_SPLITBF16 arithmetic: X = B[:, cols] T^{-1}
- * (recursive halving; off-diagonal blocks as split-BF16 products, 32 x 32
- * diagonal blocks applied through their FP64 inverses).  X may equal B when
- * cols is NULL. */
+ * (recursive halving; off-diagonal blocks as split-BF16 products, 32-column
+ * diagonal blocks by FP64 row-wise substitution): backward stable for any
+ * upper triangular T.  X may equal B when cols is NULL.  A bounded device
+ * wait that expires is reported as CQRRPT_TIMEOUT by cqrrpt_last_status. */
 int cqrrpt_trsm_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, int64_t ldb,
                         const int64_t* cols, const double* T, int64_t ldt, double* X,
                         int64_t ldx, cudaStream_t stream);

@@ -182,10 +182,10 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
   if (dst == kOk && k > 0) {
     // line 4: M^pre = M[:, J[:k]] (R^sk_11)^{-1} into Q
     // (row-wise FP64 inverse of the row-graded R^sk_11, then one product)
-    e = oz_trsm_inv(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream);
+    e = oz_trsm_inv(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream, status);
     mark(h, 4, stream);
     // line 5: G = M^pre^T M^pre
-    if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream);
+    if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream, status);
     mark(h, 5, stream);
     // line 6 (FP64) and the rank rule's stage 2
     if (e == cudaSuccess) e = launch_potrf((int)k, G, n, Rpre, n, sc, stream);
@@ -196,7 +196,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
     if (dst == kOk && k > 0) {
       // line 7: Q_k = M^pre (R^pre)^{-1}, in place; R^pre is well conditioned
       // (Theorem 2), so one product with its FP64 inverse
-      e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream);
+      e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream, status);
       mark(h, 7, stream);
       // line 8: R_k = R^pre R^sk_k
       double* Rout = (precision == CQRRPT_SPLITBF16_CHOLQR2) ? R1 : R;
@@ -206,7 +206,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
         // second Cholesky-QR pass on Q: G2 = Q^T Q, R2 = chol(G2),
         // Q := Q R2^{-1}, R := R2 R1.  A breakdown here keeps the first pass.
         e = launch_init_scalars(sc2, k, stream);
-        if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream);
+        if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream, status);
         if (e == cudaSuccess) e = launch_potrf((int)k, G, n, Rpre, n, sc2, stream);
         if (e == cudaSuccess) {
           copy_fail_kernel<<<1, 1, 0, stream>>>(sc2, h->pinned + 4);
@@ -215,7 +215,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
         }
         if (e == cudaSuccess && cudaStreamSynchronize(stream) != cudaSuccess) return kCudaError;
         if (e == cudaSuccess && h->pinned[4] < 0) {
-          e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream);
+          e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream, status);
           if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, R1, n, R, ldr, status, stream);
         } else if (e == cudaSuccess) {
           // second pass broke down: keep the first pass's R
@@ -870,7 +870,10 @@ int cqrrpt_gram_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, 
   DevGuard g(h->device);
   int st = ensure_ws(h, (size_t)oz_gram_workspace(m, (int)k, nullptr));
   if (st != kOk) return st;
-  return oz_gram(m, (int)k, X, ldx, G, ldg, h->ws, stream) == cudaSuccess ? kOk : kCudaError;
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  return oz_gram(m, (int)k, X, ldx, G, ldg, h->ws, stream, &h->sc->status) == cudaSuccess
+             ? kOk
+             : kCudaError;
 }
 
 int cqrrpt_trsm_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, int64_t ldb,
@@ -888,7 +891,9 @@ int cqrrpt_trsm_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* B, 
   DevGuard g(h->device);
   int st = ensure_ws(h, (size_t)oz_trsm_workspace(m, (int)k));
   if (st != kOk) return st;
-  return oz_trsm(m, (int)k, B, ldb, cols, T, ldt, X, ldx, h->ws, stream) == cudaSuccess
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  return oz_trsm(m, (int)k, B, ldb, cols, T, ldt, X, ldx, h->ws, stream, &h->sc->status) ==
+                 cudaSuccess
              ? kOk
              : kCudaError;
 }

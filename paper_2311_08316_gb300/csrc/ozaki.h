@@ -31,20 +31,24 @@ struct OzGemm {
   int64_t c_slice;    // offset between the partial results of two K slices
   int mode;           // kOzStore: C = v; kOzSub: C = C - v
   int upper_only;     // skip tiles strictly below the diagonal
+  int* err;           // device status word (or null): set to CQRRPT_TIMEOUT
+                      // when a bounded wait of the engine expires
 };
 
+// tcgen05 engine (ozaki_tc.cu)
+cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s);
 cudaError_t oz_gemm_launch(const OzGemm& G, cudaStream_t s);
 int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out);
 cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* G, int64_t ldg,
-                    void* work, cudaStream_t s);
+                    void* work, cudaStream_t s, int* status = nullptr);
 int64_t oz_trsm_workspace(int64_t m, int k);
 // X := B[:, cols] T^{-1} through the FP64 (row-wise) inverse of T
 int64_t oz_trsm_inv_workspace(int64_t m, int k);
 cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                         const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
-                        cudaStream_t s);
+                        cudaStream_t s, int* status = nullptr);
 cudaError_t oz_trsm(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                     const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
-                    cudaStream_t s);
+                    cudaStream_t s, int* status = nullptr);
 
 }  // namespace cqrrpt

@@ -1,0 +1,490 @@
+// The split-BF16 product engine on the 5th-generation tensor cores
+// (tcgen05.mma, operands staged by TMA, accumulators in tensor memory).
+//
+// Computes, for one OzGemm (see ozaki.h),
+//   C[i, j] (op)= 2^(ea_i + eb_j) sum_{p+q<=9} 2^(-7(p+q)) sum_k A_p[i][k] B_q[j][k]
+// with the same exactness argument as the rest of the split path: a BF16
+// product of two 7-bit digits is an integer below 2^14, so an FP32 sum of
+// at most 1024 of them (one "chunk") is exact.
+//
+// CTA tile 128 x 128 of C for one K slice; 192 threads:
+//   warp 0      TMA producer: for every digit pair (p, q) in level order
+//               (level s = p + q = 2..9, p ascending inside a level) and
+//               every 64-wide K stage, loads the 128 x 64 tiles of A_p and
+//               B_q (128-byte swizzle) into a 6-deep shared-memory ring;
+//   warp 1      allocates the 512 tensor-memory columns, and one thread
+//               issues the MMAs (M = 128, N = 128, K = 16; four per stage)
+//               into one of two FP32 accumulators (columns 0-127, 128-255):
+//               one accumulator per chunk, so chunk c + 1 runs while chunk c
+//               is drained;
+//   warps 2-5   drain each finished chunk (one TMEM lane = one row of C per
+//               thread): FP32 -> exact int32 -> added into a 64-bit integer
+//               accumulator kept in tensor memory (columns 256-383 low
+//               words, 384-511 high words).  The eight levels are combined
+//               there exactly, in two groups, by Horner's rule:
+//                 group 1 = levels 2..5:  G = ((L2 2^7 + L3) 2^7 + L4) 2^7 + L5
+//                 group 2 = levels 6..9   (same),
+//               i.e. at the first chunk of each level after the first of a
+//               group G := 2^7 G before the level's chunks are added.  With
+//               L_s <= (s - 1) K 127^2 both groups stay below 2^58 for any
+//               K <= 2^20, so they are exact in int64.  At the end of a group
+//               G is rounded once to FP64, scaled by 2^(ea + eb - 7 s_last)
+//               and stored into C (group 1: C = v, or C - v; group 2:
+//               C + v, or C - v).
+// Pipelines are tied by mbarriers: full/empty per stage, full/empty per
+// accumulator.  Every wait is bounded (2 s of wall time); on expiry the
+// thread records CQRRPT_TIMEOUT in *G.err, the roles stop issuing work, the
+// MMA thread waits (bounded) for its MMAs, the producer for its copies, and
+// the tensor memory is released before the CTA exits; CTAs that start after
+// the status word is set return at once.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "ozaki.h"
+
+namespace cqrrpt {
+
+namespace {
+
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64, kTcStages = 6;
+constexpr int kTcTileBytes = kTcBM * kTcBK * 2;            // 16 KB, one operand tile
+constexpr int kTcStageBytes = 2 * kTcTileBytes;             // A + B
+constexpr int kTcChunkStages = kOzChunk / kTcBK;            // 16 stages = 1024 K terms
+constexpr int kTcThreads = 192;
+constexpr uint32_t kTcTmemCols = 512;
+constexpr uint32_t kTcGroupLo = 256, kTcGroupHi = 384;      // TMEM columns
+constexpr int kTcBarriers = 2 * kTcStages + 4 + 1;          // full, empty, acc full/empty, done
+constexpr size_t kTcSmem = 1024 /* alignment slack */ + (size_t)kTcStages * kTcStageBytes +
+                           kTcBarriers * 8 + 16;
+
+// level order of the 36 digit pairs
+__constant__ unsigned char kTcPairP[kOzPairs] = {1, 1, 2, 1, 2, 3, 1, 2, 3, 4, 1, 2,
+                                                 3, 4, 5, 1, 2, 3, 4, 5, 6, 1, 2, 3,
+                                                 4, 5, 6, 7, 1, 2, 3, 4, 5, 6, 7, 8};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase of parity `parity` to complete: gives up after
+// kTcWaitNs of wall time (a pipeline step of this kernel takes microseconds)
+// or kSpinLimit polls, whichever comes first.
+constexpr unsigned long long kTcWaitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kTcWaitNs) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: rows of 64 BF16 (128 B), 8-row core groups 1024 B apart
+// (stride byte offset), leading byte offset unused (1), descriptor version 1,
+// layout type 2 = 128-byte swizzle.  The tile base is 1024-byte aligned.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcBN >> 3) << 17) |
+                              ((uint32_t)(kTcBM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(kTcIdesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+#define OZ_R32(a) \
+  "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), \
+  "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), \
+  "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), \
+  "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), \
+  "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31])
+#define OZ_W32(a) \
+  "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), \
+  "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), \
+  "r"(a[15]), "r"(a[16]), "r"(a[17]), "r"(a[18]), "r"(a[19]), "r"(a[20]), "r"(a[21]), \
+  "r"(a[22]), "r"(a[23]), "r"(a[24]), "r"(a[25]), "r"(a[26]), "r"(a[27]), "r"(a[28]), \
+  "r"(a[29]), "r"(a[30]), "r"(a[31])
+#define OZ_REGLIST32                                                                      \
+  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, " \
+  "%19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}"
+#define OZ_REGLIST32_FROM1                                                                   \
+  "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, " \
+  "%20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32}"
+
+// 32 consecutive columns of the thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " OZ_REGLIST32 ", [%32];"
+               : OZ_R32(r)
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], " OZ_REGLIST32_FROM1 ";" ::"r"(taddr),
+               OZ_W32(r)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void record_timeout(int* err) {
+  if (err) atomicExch(err, kTimeout);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    oz_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 OzGemm G) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle tiles: 1024-aligned
+  const uint32_t a_tiles = base;
+  const uint32_t b_tiles = base + kTcStages * kTcTileBytes;
+  const uint32_t bars = base + kTcStages * kTcStageBytes;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (kTcStages + s); };
+  auto accf_bar = [&](int b) { return bars + 8u * (2 * kTcStages + b); };
+  auto acce_bar = [&](int b) { return bars + 8u * (2 * kTcStages + 2 + b); };
+  const uint32_t done_bar = bars + 8u * (2 * kTcStages + 4);
+  uint32_t* tmem_slot = (uint32_t*)(tc_smem_raw + (bars - raw) + 8u * kTcBarriers);
+
+  // tile of this CTA
+  const int64_t tiles_m = (G.M + kTcBM - 1) / kTcBM;
+  const int64_t tiles_n = (G.N + kTcBN - 1) / kTcBN;
+  const int64_t tile = blockIdx.x;
+  const int64_t tm = tile % tiles_m, tn = (tile / tiles_m) % tiles_n;
+  const int64_t ks = tile / (tiles_m * tiles_n);
+  const int64_t m0 = tm * kTcBM;
+  const int n0 = (int)(tn * kTcBN);
+  if (G.upper_only && m0 >= n0 + kTcBN) return;  // uniform: before any barrier
+  const int64_t kbeg = ks * G.kslice;
+  const int64_t kend = min64(kbeg + G.kslice, G.Kpad);
+  if (kbeg >= kend) return;
+  // an earlier failure (of this launch or a previous step): nothing to do
+  if (G.err && *(volatile const int*)G.err != kOk) return;
+  const int nk = (int)((kend - kbeg + kTcBK - 1) / kTcBK);  // K stages per pair
+  const int nchunks = (nk + kTcChunkStages - 1) / kTcChunkStages;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    int issued = 0;
+    for (int pi = 0; pi < kOzPairs && ok; ++pi) {
+      const int p = kTcPairP[pi];
+      int s = 2;
+      while ((s - 1) * s / 2 <= pi) ++s;
+      const int q = s - p;
+      for (int kst = 0; kst < nk; ++kst) {
+        if (!mbar_wait(empty_bar(stage), phase ^ 1u)) {
+          record_timeout(G.err);
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(full_bar(stage), kTcStageBytes);
+        const int kx = (int)(kbeg + (int64_t)kst * kTcBK);
+        tma_load_3d(a_tiles + stage * kTcTileBytes, &tmA, full_bar(stage), kx, (int)m0, p - 1);
+        tma_load_3d(b_tiles + stage * kTcTileBytes, &tmB, full_bar(stage), kx, n0, q - 1);
+        ++issued;
+        if (++stage == kTcStages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    if (!ok) {
+      // copies still in flight land before the CTA exits: wait for the
+      // full barrier of each of the last (up to kTcStages) issued loads
+      int st = stage;
+      uint32_t ph = phase;
+      for (int i = 0; i < kTcStages && i < issued; ++i) {
+        if (--st < 0) {
+          st = kTcStages - 1;
+          ph ^= 1u;
+        }
+        mbar_wait(full_bar(st), ph);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t use[2] = {0u, 0u};
+    int buf = 0;
+    bool ok = true;
+    bool any = false;
+    for (int pi = 0; pi < kOzPairs && ok; ++pi) {
+      for (int c = 0; c < nchunks && ok; ++c) {
+        if (!mbar_wait(acce_bar(buf), use[buf] ^ 1u)) {
+          record_timeout(G.err);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * kTcBN);
+        const int st_n = min(kTcChunkStages, nk - c * kTcChunkStages);
+        for (int j = 0; j < st_n; ++j) {
+          if (!mbar_wait(full_bar(stage), phase)) {
+            record_timeout(G.err);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = sw128_desc(a_tiles + stage * kTcTileBytes);
+          const uint64_t bd = sw128_desc(b_tiles + stage * kTcTileBytes);
+#pragma unroll
+          for (int kk = 0; kk < kTcBK / 16; ++kk)  // K = 16 per MMA: +32 bytes
+            umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                      (j > 0 || kk > 0) ? 1u : 0u);
+          umma_commit(empty_bar(stage));
+          any = true;
+          if (++stage == kTcStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(accf_bar(buf));
+        use[buf] ^= 1u;
+        buf ^= 1;
+      }
+    }
+    // every MMA issued by this thread has completed before the TMEM goes
+    if (any) {
+      umma_commit(done_bar);
+      if (!mbar_wait(done_bar, 0)) record_timeout(G.err);
+    }
+  } else if (warp >= 2) {
+    // ---- drain: one row of the tile per thread
+    const int quarter = warp & 3;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int64_t row = m0 + quarter * 32 + lane;
+    const bool row_ok = row < G.M;
+    const int ea = row_ok ? G.ea[row] : 0;
+    double* Cbase = G.C + ks * G.c_slice + (row_ok ? row : 0);
+    uint32_t fph[2] = {0u, 0u};
+    int buf = 0;
+    bool ok = true;
+    for (int pi = 0; pi < kOzPairs && ok; ++pi) {
+      int s = 2;
+      while ((s - 1) * s / 2 <= pi) ++s;
+      const bool first_pair_of_level = pi == (s - 2) * (s - 1) / 2;
+      const bool last_pair_of_level = pi == (s - 1) * s / 2 - 1;
+      const bool group_first_level = (s == 2 || s == 6);
+      const bool group_last_level = (s == 5 || s == 9);
+      for (int c = 0; c < nchunks; ++c) {
+        if (!mbar_wait(accf_bar(buf), fph[buf])) {
+          record_timeout(G.err);
+          ok = false;
+          break;
+        }
+        fph[buf] ^= 1u;
+        tc_fence_after();
+        const bool start_level = first_pair_of_level && c == 0;
+        const bool fresh = start_level && group_first_level;
+        const bool emit = group_last_level && last_pair_of_level && c == nchunks - 1;
+#pragma unroll 1
+        for (int piece = 0; piece < kTcBN / 32; ++piece) {
+          uint32_t fa[32], lo[32], hi[32];
+          tmem_ld32(lane_addr + (uint32_t)(buf * kTcBN + piece * 32), fa);
+          if (!fresh) {
+            tmem_ld32(lane_addr + kTcGroupLo + (uint32_t)(piece * 32), lo);
+            tmem_ld32(lane_addr + kTcGroupHi + (uint32_t)(piece * 32), hi);
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            long long g = fresh ? 0ll
+                                : (long long)(((unsigned long long)hi[i] << 32) |
+                                              (unsigned long long)lo[i]);
+            if (start_level && !fresh) g *= 128;  // Horner step, exact (< 2^58)
+            g += (long long)__float2int_rn(__uint_as_float(fa[i]));
+            lo[i] = (uint32_t)((unsigned long long)g & 0xFFFFFFFFull);
+            hi[i] = (uint32_t)((unsigned long long)g >> 32);
+          }
+          if (emit) {
+            // the group is complete: one FP64 rounding, scale, store
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int col = n0 + piece * 32 + i;
+              if (!row_ok || col >= G.N) continue;
+              const long long g =
+                  (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
+              const double v = ldexp(__ll2double_rn(g), ea + G.eb[col] - 7 * s);
+              double* cp = Cbase + (int64_t)col * G.ldc;
+              if (G.mode == kOzSub) *cp = __dsub_rn(*cp, v);
+              else if (s == 5) *cp = v;
+              else *cp = __dadd_rn(*cp, v);
+            }
+          } else {
+            tmem_st32(lane_addr + kTcGroupLo + (uint32_t)(piece * 32), lo);
+            tmem_st32(lane_addr + kTcGroupHi + (uint32_t)(piece * 32), hi);
+          }
+        }
+        if (!emit) tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce_bar(buf));
+        buf ^= 1;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTcTmemCols)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3-D map over digit planes [8][rows][kpad] (BF16), box 64 (K) x 128 rows x
+// 1 plane, 128-byte swizzle, zero fill outside.
+bool plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t kpad,
+               int64_t plane) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)kOzDigits};
+  const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)plane * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // TMA: 16-byte aligned bases, row strides and plane strides
+  // (several K slices: slice boundaries on stage boundaries; one slice may
+  // end mid-stage, TMA fills zeros past Kpad)
+  const bool sliced = G.kslice < G.Kpad;
+  if (((uintptr_t)G.A & 15) || ((uintptr_t)G.B & 15) || (G.Kpad % 8) || (G.a_plane % 8) ||
+      (G.b_plane % 8) || G.kslice <= 0 || (sliced && (G.kslice % kTcBK)))
+    return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap ma;
+  alignas(64) CUtensorMap mb;
+  if (!plane_map(&ma, G.A, G.M, G.Kpad, G.a_plane) ||
+      !plane_map(&mb, G.B, G.N, G.Kpad, G.b_plane))
+    return cudaErrorInvalidValue;
+  const int64_t tiles_m = (G.M + kTcBM - 1) / kTcBM;
+  const int64_t tiles_n = (G.N + kTcBN - 1) / kTcBN;
+  const int64_t nks = (G.Kpad + G.kslice - 1) / G.kslice;
+  oz_tc_kernel<<<(unsigned)(tiles_m * tiles_n * nks), kTcThreads, kTcSmem, s>>>(ma, mb, G);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace cqrrpt

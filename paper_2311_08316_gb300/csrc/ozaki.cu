@@ -158,18 +158,29 @@ __global__ void oz_gather_kernel(const double* __restrict__ B, int64_t ldb,
 // W = T^{-1} for upper triangular T (k x k), row by row: row i of W solves
 // w^T T = e_i^T left to right (w_j = 0 for j < i), so the computed W has a
 // small right residual, |W T - I| <= c u |W| |T| -- the residual that enters
-// M_k - M^pre R^sk_11 when line 4 is applied as M_k W.  One thread per row.
-__global__ void oz_trinv_rows_kernel(const double* __restrict__ T, int64_t ldt, int k,
-                                     double* __restrict__ W, int64_t ldw) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// M_k - M^pre R^sk_11 when line 4 is applied as M_k W.  One warp per row:
+// for each j the dot product sum_{i<=t<j} w_t T[t, j] is split over the 32
+// lanes (T's column j is contiguous: coalesced) and reduced by a fixed
+// shuffle tree; the row being built lives in shared memory.
+constexpr int kTrinvWarps = 8;  // at most; fewer when k rows do not fit
+__global__ void __launch_bounds__(kTrinvWarps * 32)
+    oz_trinv_rows_kernel(const double* __restrict__ T, int64_t ldt, int k, double* __restrict__ W,
+                         int64_t ldw) {
+  extern __shared__ double trinv_rows[];  // [warps][k]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (int)(blockDim.x >> 5) + warp;
   if (i >= k) return;
-  for (int j = 0; j < i; ++j) W[(int64_t)j * ldw + i] = 0.0;
+  double* w = trinv_rows + (int64_t)warp * k;
   for (int j = i; j < k; ++j) {
-    double s = (i == j) ? 1.0 : 0.0;
-    for (int t = i; t < j; ++t)
-      s = __fma_rn(-W[(int64_t)t * ldw + i], T[(int64_t)j * ldt + t], s);
-    W[(int64_t)j * ldw + i] = __ddiv_rn(s, T[(int64_t)j * ldt + j]);
+    const double* tc = T + (int64_t)j * ldt;
+    double part = 0.0;
+    for (int t = i + lane; t < j; t += 32) part = __fma_rn(w[t], tc[t], part);
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) part = __dadd_rn(part, __shfl_xor_sync(0xffffffffu, part, off));
+    if (lane == 0) w[j] = __ddiv_rn(((i == j) ? 1.0 : 0.0) - part, tc[j]);
+    __syncwarp();
   }
+  for (int j = lane; j < k; j += 32) W[(int64_t)j * ldw + i] = j < i ? 0.0 : w[j];
 }
 
 // ---------------------------------------------------------------------------
@@ -379,7 +390,17 @@ cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const in
     oz_gather_kernel<<<g, 256, 0, s>>>(B, ldb, cols, m, X, ldx);
     count_launches(1);
   }
-  oz_trinv_rows_kernel<<<(k + 127) / 128, 128, 0, s>>>(T, ldt, k, W, k);
+  // one row of W per warp in shared memory: as many warps as fit 200 KB
+  int warps = (int)(200 * 1024 / ((int64_t)k * (int64_t)sizeof(double)));
+  warps = warps < 1 ? 1 : (warps > kTrinvWarps ? kTrinvWarps : warps);
+  const size_t trinv_smem = (size_t)warps * k * sizeof(double);
+  if (trinv_smem > 48 * 1024) {
+    cudaError_t ea = cudaFuncSetAttribute(oz_trinv_rows_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)trinv_smem);
+    if (ea != cudaSuccess) return ea;
+  }
+  oz_trinv_rows_kernel<<<(k + warps - 1) / warps, warps * 32, trinv_smem, s>>>(T, ldt, k, W, k);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

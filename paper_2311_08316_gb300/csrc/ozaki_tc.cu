@@ -18,19 +18,23 @@
 //               one accumulator per chunk, so chunk c + 1 runs while chunk c
 //               is drained;
 //   warps 2-5   drain each finished chunk (one TMEM lane = one row of C per
-//               thread): FP32 -> exact int32 -> added into a 64-bit integer
-//               accumulator kept in tensor memory (columns 256-383 low
-//               words, 384-511 high words).  The eight levels are combined
-//               there exactly, in two groups, by Horner's rule:
-//                 group 1 = levels 2..5:  G = ((L2 2^7 + L3) 2^7 + L4) 2^7 + L5
-//                 group 2 = levels 6..9   (same),
-//               i.e. at the first chunk of each level after the first of a
-//               group G := 2^7 G before the level's chunks are added.  With
-//               L_s <= (s - 1) K 127^2 both groups stay below 2^58 for any
-//               K <= 2^20, so they are exact in int64.  At the end of a group
-//               G is rounded once to FP64, scaled by 2^(ea + eb - 7 s_last)
-//               and stored into C (group 1: C = v, or C - v; group 2:
-//               C + v, or C - v).
+//               thread): FP32 -> exact int32 -> shifted by 7 (s_g - s) bits
+//               and added into a 64-bit integer accumulator kept in tensor
+//               memory (columns 256-383 low words, 384-511 high words), one
+//               group of levels at a time:
+//                 group 1 = levels 2..5 (s_g = 5), group 2 = levels 6..9
+//                 (s_g = 9): G = sum over the group's pairs and chunks of
+//                 2^(7 (s_g - s)) * chunk sum.
+//               Integer addition is exact, so the order of pairs and chunks
+//               is free; with L_s <= (s - 1) K 127^2 both groups stay below
+//               2^58 for any K <= 2^20.  At the end of a group G is rounded
+//               once to FP64, scaled by 2^(ea + eb - 7 s_g) and stored into C
+//               (group 1: C = v, or C - v; group 2: C + v, or C - v).
+// Work order inside a CTA: group, then 1024-term K chunk, then the group's
+// pairs (level order), then the chunk's 64-wide K stages, so that the digit
+// planes of one chunk are reused by every pair of the group while they are
+// hot in L2.  CTA order: the column tiles of one row block are consecutive
+// (they share the row block's A planes), K slices outermost.
 // Pipelines are tied by mbarriers: full/empty per stage, full/empty per
 // accumulator.  Every wait is bounded (2 s of wall time); on expiry the
 // thread records CQRRPT_TIMEOUT in *G.err, the roles stop issuing work, the
@@ -60,6 +64,8 @@ constexpr int kTcBarriers = 2 * kTcStages + 4 + 1;          // full, empty, acc 
 constexpr size_t kTcSmem = 1024 /* alignment slack */ + (size_t)kTcStages * kTcStageBytes +
                            kTcBarriers * 8 + 16;
 
+// first pair index of each group of levels (2..5, 6..9), and the end
+__constant__ int kTcGroupFirst[3] = {0, 10, 36};
 // level order of the 36 digit pairs
 __constant__ unsigned char kTcPairP[kOzPairs] = {1, 1, 2, 1, 2, 3, 1, 2, 3, 4, 1, 2,
                                                  3, 4, 5, 1, 2, 3, 4, 5, 6, 1, 2, 3,
@@ -214,7 +220,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int64_t tiles_m = (G.M + kTcBM - 1) / kTcBM;
   const int64_t tiles_n = (G.N + kTcBN - 1) / kTcBN;
   const int64_t tile = blockIdx.x;
-  const int64_t tm = tile % tiles_m, tn = (tile / tiles_m) % tiles_n;
+  const int64_t tn = tile % tiles_n, tm = (tile / tiles_n) % tiles_m;
   const int64_t ks = tile / (tiles_m * tiles_n);
   const int64_t m0 = tm * kTcBM;
   const int n0 = (int)(tn * kTcBN);
@@ -258,12 +264,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint32_t phase = 0;
     bool ok = true;
     int issued = 0;
-    for (int pi = 0; pi < kOzPairs && ok; ++pi) {
+    for (int grp = 0; grp < 2 && ok; ++grp)
+    for (int c = 0; c < nchunks && ok; ++c)
+    for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1] && ok; ++pi) {
       const int p = kTcPairP[pi];
       int s = 2;
       while ((s - 1) * s / 2 <= pi) ++s;
       const int q = s - p;
-      for (int kst = 0; kst < nk; ++kst) {
+      const int kst_end = min(nk, (c + 1) * kTcChunkStages);
+      for (int kst = c * kTcChunkStages; kst < kst_end; ++kst) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u)) {
           record_timeout(G.err);
           ok = false;
@@ -301,8 +310,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int buf = 0;
     bool ok = true;
     bool any = false;
-    for (int pi = 0; pi < kOzPairs && ok; ++pi) {
-      for (int c = 0; c < nchunks && ok; ++c) {
+    for (int grp = 0; grp < 2 && ok; ++grp)
+    for (int c = 0; c < nchunks && ok; ++c) {
+      for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1] && ok; ++pi) {
         if (!mbar_wait(acce_bar(buf), use[buf] ^ 1u)) {
           record_timeout(G.err);
           ok = false;
@@ -353,14 +363,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint32_t fph[2] = {0u, 0u};
     int buf = 0;
     bool ok = true;
-    for (int pi = 0; pi < kOzPairs && ok; ++pi) {
-      int s = 2;
-      while ((s - 1) * s / 2 <= pi) ++s;
-      const bool first_pair_of_level = pi == (s - 2) * (s - 1) / 2;
-      const bool last_pair_of_level = pi == (s - 1) * s / 2 - 1;
-      const bool group_first_level = (s == 2 || s == 6);
-      const bool group_last_level = (s == 5 || s == 9);
-      for (int c = 0; c < nchunks; ++c) {
+    for (int grp = 0; grp < 2 && ok; ++grp)
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int s_g = grp == 0 ? 5 : 9;  // last level of the group
+      for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1]; ++pi) {
+        int s = 2;
+        while ((s - 1) * s / 2 <= pi) ++s;
         if (!mbar_wait(accf_bar(buf), fph[buf])) {
           record_timeout(G.err);
           ok = false;
@@ -368,9 +376,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         fph[buf] ^= 1u;
         tc_fence_after();
-        const bool start_level = first_pair_of_level && c == 0;
-        const bool fresh = start_level && group_first_level;
-        const bool emit = group_last_level && last_pair_of_level && c == nchunks - 1;
+        const bool fresh = c == 0 && pi == kTcGroupFirst[grp];
+        const bool emit = c == nchunks - 1 && pi == kTcGroupFirst[grp + 1] - 1;
+        const long long weight = 1ll << (7 * (s_g - s));
 #pragma unroll 1
         for (int piece = 0; piece < kTcBN / 32; ++piece) {
           uint32_t fa[32], lo[32], hi[32];
@@ -385,8 +393,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             long long g = fresh ? 0ll
                                 : (long long)(((unsigned long long)hi[i] << 32) |
                                               (unsigned long long)lo[i]);
-            if (start_level && !fresh) g *= 128;  // Horner step, exact (< 2^58)
-            g += (long long)__float2int_rn(__uint_as_float(fa[i]));
+            g += (long long)__float2int_rn(__uint_as_float(fa[i])) * weight;  // exact, < 2^58
             lo[i] = (uint32_t)((unsigned long long)g & 0xFFFFFFFFull);
             hi[i] = (uint32_t)((unsigned long long)g >> 32);
           }
@@ -398,10 +405,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               if (!row_ok || col >= G.N) continue;
               const long long g =
                   (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
-              const double v = ldexp(__ll2double_rn(g), ea + G.eb[col] - 7 * s);
+              const double v = ldexp(__ll2double_rn(g), ea + G.eb[col] - 7 * s_g);
               double* cp = Cbase + (int64_t)col * G.ldc;
               if (G.mode == kOzSub) *cp = __dsub_rn(*cp, v);
-              else if (s == 5) *cp = v;
+              else if (grp == 0) *cp = v;
               else *cp = __dadd_rn(*cp, v);
             }
           } else {

@@ -12,8 +12,8 @@
 
 namespace cqrrpt {
 
-constexpr int kSkCols = 4;        // sketch: columns per CTA
-constexpr int kSkThreads = 512;   // sketch: threads per CTA
+constexpr int kSkCols = 2;        // sketch: columns per CTA
+constexpr int kSkThreads = 1024;  // sketch: threads per CTA, at most
 constexpr int kQrcpThreads = 256;
 constexpr int kTrsmThreads = 128;
 constexpr int kTrsmJB = 32;       // TRSM: columns solved per register block

@@ -7,21 +7,22 @@
 // product of two 7-bit digits is an integer below 2^14, so an FP32 sum of
 // at most 1024 of them (one "chunk") is exact.
 //
-// CTA tile 128 x 128 of C for one K slice; 192 threads:
-//   warp 0      TMA producer: for every digit pair (p, q) in level order
-//               (level s = p + q = 2..9, p ascending inside a level) and
-//               every 64-wide K stage, loads the 128 x 64 tiles of A_p and
-//               B_q (128-byte swizzle) into a 6-deep shared-memory ring;
+// CTA tile 128 x 128 of C for one K slice; 18 warps (at most 96 registers a
+// thread, so that five warps fit one SM sub-partition's register file):
+//   warp 0      TMA producer: for every digit pair (p, q) and every 64-wide
+//               K stage, loads the 128 x 64 tiles of A_p and B_q (128-byte
+//               swizzle) into a 6-deep shared-memory ring;
 //   warp 1      allocates the 512 tensor-memory columns, and one thread
 //               issues the MMAs (M = 128, N = 128, K = 16; four per stage)
 //               into one of two FP32 accumulators (columns 0-127, 128-255):
 //               one accumulator per chunk, so chunk c + 1 runs while chunk c
 //               is drained;
-//   warps 2-5   drain each finished chunk (one TMEM lane = one row of C per
-//               thread): FP32 -> exact int32 -> shifted by 7 (s_g - s) bits
-//               and added into a 64-bit integer accumulator kept in tensor
-//               memory (columns 256-383 low words, 384-511 high words), one
-//               group of levels at a time:
+//   warps 2-17  drain each finished chunk: four warps per TMEM lane quarter
+//               (32 rows of C), each owning 32 columns in two pieces of 16,
+//               one row per thread.  FP32 -> exact int32 -> times
+//               2^(7 (s_g - s)) -> added into a 64-bit integer sum kept in
+//               tensor memory (columns 256-383 low words, 384-511 high
+//               words), one group of levels at a time:
 //                 group 1 = levels 2..5 (s_g = 5), group 2 = levels 6..9
 //                 (s_g = 9): G = sum over the group's pairs and chunks of
 //                 2^(7 (s_g - s)) * chunk sum.
@@ -57,10 +58,13 @@ constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64, kTcStages = 6;
 constexpr int kTcTileBytes = kTcBM * kTcBK * 2;            // 16 KB, one operand tile
 constexpr int kTcStageBytes = 2 * kTcTileBytes;             // A + B
 constexpr int kTcChunkStages = kOzChunk / kTcBK;            // 16 stages = 1024 K terms
-constexpr int kTcThreads = 192;
+constexpr int kTcDrainWarps = 16;                          // 4 per TMEM lane quarter
+constexpr int kTcThreads = 32 * (2 + kTcDrainWarps);        // 18 warps: <= 96 registers
+constexpr int kTcAccBufs = 2;                               // FP32 accumulators in TMEM
 constexpr uint32_t kTcTmemCols = 512;
-constexpr uint32_t kTcGroupLo = 256, kTcGroupHi = 384;      // TMEM columns
-constexpr int kTcBarriers = 2 * kTcStages + 4 + 1;          // full, empty, acc full/empty, done
+constexpr uint32_t kTcGroupLo = kTcAccBufs * kTcBN;         // 256: low words of the sums
+constexpr uint32_t kTcGroupHi = kTcGroupLo + kTcBN;         // 384: high words
+constexpr int kTcBarriers = 2 * kTcStages + 2 * kTcAccBufs + 1;  // full, empty, acc full/empty, done
 constexpr size_t kTcSmem = 1024 /* alignment slack */ + (size_t)kTcStages * kTcStageBytes +
                            kTcBarriers * 8 + 16;
 
@@ -159,48 +163,48 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-#define OZ_R32(a) \
-  "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), \
-  "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), \
-  "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), \
-  "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), \
-  "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31])
-#define OZ_W32(a) \
-  "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), \
-  "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), \
-  "r"(a[15]), "r"(a[16]), "r"(a[17]), "r"(a[18]), "r"(a[19]), "r"(a[20]), "r"(a[21]), \
-  "r"(a[22]), "r"(a[23]), "r"(a[24]), "r"(a[25]), "r"(a[26]), "r"(a[27]), "r"(a[28]), \
-  "r"(a[29]), "r"(a[30]), "r"(a[31])
-#define OZ_REGLIST32                                                                      \
-  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, " \
-  "%19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}"
-#define OZ_REGLIST32_FROM1                                                                   \
-  "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, " \
-  "%20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32}"
+#define OZ_R16(r)                                                                          \
+  "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),     \
+      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), \
+      "=r"(r[14]), "=r"(r[15])
+#define OZ_W16(r)                                                                           \
+  "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),  \
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),     \
+      "r"(r[15])
 
-// 32 consecutive columns of the thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " OZ_REGLIST32 ", [%32];"
-               : OZ_R32(r)
-               : "r"(taddr));
+// 16 consecutive 32-bit columns of the thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : OZ_R16(r)
+      : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], " OZ_REGLIST32_FROM1 ";" ::"r"(taddr),
-               OZ_W32(r)
-               : "memory");
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      OZ_W16(r)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+// x * 2^e, rounded once (as ldexp): one multiplication by the exact power
+// of two when 2^e is a normal double, ldexp otherwise.
+__device__ __forceinline__ double scale2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
+  return ldexp(x, e);
 }
 
 __device__ __forceinline__ void record_timeout(int* err) {
   if (err) atomicExch(err, kTimeout);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __maxnreg__(96)
     oz_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  OzGemm G) {
   extern __shared__ unsigned char tc_smem_raw[];
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (kTcStages + s); };
   auto accf_bar = [&](int b) { return bars + 8u * (2 * kTcStages + b); };
-  auto acce_bar = [&](int b) { return bars + 8u * (2 * kTcStages + 2 + b); };
-  const uint32_t done_bar = bars + 8u * (2 * kTcStages + 4);
+  auto acce_bar = [&](int b) { return bars + 8u * (2 * kTcStages + kTcAccBufs + b); };
+  const uint32_t done_bar = bars + 8u * (2 * kTcStages + 2 * kTcAccBufs);
   uint32_t* tmem_slot = (uint32_t*)(tc_smem_raw + (bars - raw) + 8u * kTcBarriers);
 
   // tile of this CTA
@@ -239,9 +243,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kTcAccBufs; ++b) {
       mbar_init(accf_bar(b), 1);
-      mbar_init(acce_bar(b), 4);  // one arrival per epilogue warp
+      mbar_init(acce_bar(b), kTcDrainWarps);  // one arrival per drain warp
     }
     mbar_init(done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -306,14 +310,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- MMA issuer
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t use[2] = {0u, 0u};
+    uint32_t use = 0u;  // bit b: parity of accumulator b's next use
     int buf = 0;
     bool ok = true;
     bool any = false;
     for (int grp = 0; grp < 2 && ok; ++grp)
     for (int c = 0; c < nchunks && ok; ++c) {
       for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1] && ok; ++pi) {
-        if (!mbar_wait(acce_bar(buf), use[buf] ^ 1u)) {
+        if (!mbar_wait(acce_bar(buf), ((use >> buf) & 1u) ^ 1u)) {
           record_timeout(G.err);
           ok = false;
           break;
@@ -343,8 +347,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (!ok) break;
         umma_commit(accf_bar(buf));
-        use[buf] ^= 1u;
-        buf ^= 1;
+        use ^= 1u << buf;
+        buf = (buf + 1) % kTcAccBufs;
       }
     }
     // every MMA issued by this thread has completed before the TMEM goes
@@ -353,14 +357,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!mbar_wait(done_bar, 0)) record_timeout(G.err);
     }
   } else if (warp >= 2) {
-    // ---- drain: one row of the tile per thread
+    // ---- drain: 4 warps per TMEM lane quarter (32 rows), each owning 32
+    // of the tile's 128 columns (two pieces of 16), one row per thread
     const int quarter = warp & 3;
-    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int cslice = (warp - 2) >> 2;
+    const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cslice * 32);
     const int64_t row = m0 + quarter * 32 + lane;
     const bool row_ok = row < G.M;
     const int ea = row_ok ? G.ea[row] : 0;
     double* Cbase = G.C + ks * G.c_slice + (row_ok ? row : 0);
-    uint32_t fph[2] = {0u, 0u};
+    const int col0 = n0 + cslice * 32;
+    uint32_t fph = 0u;  // bit b: parity of accumulator b's next completion
     int buf = 0;
     bool ok = true;
     for (int grp = 0; grp < 2 && ok; ++grp)
@@ -369,58 +376,61 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1]; ++pi) {
         int s = 2;
         while ((s - 1) * s / 2 <= pi) ++s;
-        if (!mbar_wait(accf_bar(buf), fph[buf])) {
+        if (!mbar_wait(accf_bar(buf), (fph >> buf) & 1u)) {
           record_timeout(G.err);
           ok = false;
           break;
         }
-        fph[buf] ^= 1u;
+        fph ^= 1u << buf;
         tc_fence_after();
         const bool fresh = c == 0 && pi == kTcGroupFirst[grp];
         const bool emit = c == nchunks - 1 && pi == kTcGroupFirst[grp + 1] - 1;
-        const long long weight = 1ll << (7 * (s_g - s));
+        const int weight = 1 << (7 * (s_g - s));
 #pragma unroll 1
-        for (int piece = 0; piece < kTcBN / 32; ++piece) {
-          uint32_t fa[32], lo[32], hi[32];
-          tmem_ld32(lane_addr + (uint32_t)(buf * kTcBN + piece * 32), fa);
+        for (int h = 0; h < 2; ++h) {
+          uint32_t fa[16], lo[16], hi[16];
+          tmem_ld16(lane_addr + (uint32_t)(buf * kTcBN + h * 16), fa);
           if (!fresh) {
-            tmem_ld32(lane_addr + kTcGroupLo + (uint32_t)(piece * 32), lo);
-            tmem_ld32(lane_addr + kTcGroupHi + (uint32_t)(piece * 32), hi);
+            tmem_ld16(lane_addr + kTcGroupLo + (uint32_t)(h * 16), lo);
+            tmem_ld16(lane_addr + kTcGroupHi + (uint32_t)(h * 16), hi);
           }
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < 16; ++i) {
             long long g = fresh ? 0ll
                                 : (long long)(((unsigned long long)hi[i] << 32) |
                                               (unsigned long long)lo[i]);
-            g += (long long)__float2int_rn(__uint_as_float(fa[i])) * weight;  // exact, < 2^58
+            // exact: |chunk| < 2^24, |g| < 2^58
+            g += (long long)__float2int_rn(__uint_as_float(fa[i])) * weight;
             lo[i] = (uint32_t)((unsigned long long)g & 0xFFFFFFFFull);
             hi[i] = (uint32_t)((unsigned long long)g >> 32);
           }
           if (emit) {
             // the group is complete: one FP64 rounding, scale, store
+            if (row_ok) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int col = n0 + piece * 32 + i;
-              if (!row_ok || col >= G.N) continue;
-              const long long g =
-                  (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
-              const double v = ldexp(__ll2double_rn(g), ea + G.eb[col] - 7 * s_g);
-              double* cp = Cbase + (int64_t)col * G.ldc;
-              if (G.mode == kOzSub) *cp = __dsub_rn(*cp, v);
-              else if (grp == 0) *cp = v;
-              else *cp = __dadd_rn(*cp, v);
+              for (int i = 0; i < 16; ++i) {
+                const int col = col0 + h * 16 + i;
+                if (col >= G.N) continue;
+                const long long g =
+                    (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
+                const double v = scale2(__ll2double_rn(g), ea + G.eb[col] - 7 * s_g);
+                double* cp = Cbase + (int64_t)col * G.ldc;
+                if (G.mode == kOzSub) *cp = __dsub_rn(*cp, v);
+                else if (grp == 0) *cp = v;
+                else *cp = __dadd_rn(*cp, v);
+              }
             }
           } else {
-            tmem_st32(lane_addr + kTcGroupLo + (uint32_t)(piece * 32), lo);
-            tmem_st32(lane_addr + kTcGroupHi + (uint32_t)(piece * 32), hi);
+            tmem_st16(lane_addr + kTcGroupLo + (uint32_t)(h * 16), lo);
+            tmem_st16(lane_addr + kTcGroupHi + (uint32_t)(h * 16), hi);
           }
         }
         if (!emit) tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acce_bar(buf));
-        buf ^= 1;
+        buf = (buf + 1) % kTcAccBufs;
       }
     }
   }

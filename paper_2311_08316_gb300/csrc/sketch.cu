@@ -5,10 +5,13 @@
 //                  that block regrouped by target row i: for each i the rows
 //                  r of the block with S[i,r] != 0 in ascending r, with their
 //                  signs (a CSR of the block of S by target row).
-//   sketch_partial per (row block b, group of kSkCols columns): stages the
-//                  block of M in shared memory (coalesced), then one thread
-//                  per target row i walks its list and accumulates +-M[r, c]
-//                  in ascending r from +0.0, giving P_b[i, c].
+//   sketch_partial per (row block b, pair of columns): stages the block of
+//                  M in shared memory (coalesced, one double2 per row; 64 KB,
+//                  so that three CTAs share an SM and one stages while the
+//                  others add), then one thread per target row i walks its
+//                  list and accumulates +-M[r, c] in ascending r from +0.0,
+//                  giving P_b[i, c].  The kernel is bound by the FP64 add
+//                  pipe (m s n additions).
 //   sketch_combine M^sk[i, c] = scale * (P_0 + P_1 + ...) in ascending block
 //                  order from +0.0; flags non-finite results.
 // The arithmetic (FP64 additions in that order, one final scale) is fixed by
@@ -83,41 +86,42 @@ __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, 
   }
 }
 
+// tile: the block's rows of the kSkCols (= 2) columns, one double2 per row.
 __device__ __forceinline__ void sketch_partial_body(int64_t b, int64_t cg, const SketchDesc& D,
-                                                    double* tile /* [kRowBlock][kSkCols] */) {
+                                                    double2* tile /* [kRowBlock] */) {
+  static_assert(kSkCols == 2, "two columns per CTA, staged as double2");
   const int d = D.d;
   const int64_t n = D.n;
   const int64_t c0 = cg * kSkCols;
   const int64_t r0 = b * kRowBlock;
   const int rows = (int)min64(kRowBlock, D.m - r0);
-  const int ncols = (int)min64(kSkCols, n - c0);
-  for (int cc = 0; cc < kSkCols; ++cc) {
-    if (cc < ncols) {
-      const double* col = D.M + (c0 + cc) * D.ldm + r0;
-      for (int rl = threadIdx.x; rl < rows; rl += blockDim.x) tile[rl * kSkCols + cc] = col[rl];
-    }
+  const bool two = c0 + 1 < n;
+  {
+    const double* col0 = D.M + c0 * D.ldm + r0;
+    const double* col1 = D.M + (two ? c0 + 1 : c0) * D.ldm + r0;
+    for (int rl = threadIdx.x; rl < rows; rl += blockDim.x)
+      tile[rl] = make_double2(col0[rl], two ? col1[rl] : 0.0);
   }
   __syncthreads();
   const int* st = D.seg_start + b * (int64_t)(d + 1);
   const uint32_t* ent = D.entries + b * (int64_t)kRowBlock * D.s;
   double* P = D.partial + b * n * (int64_t)d;  // P_b: d x n, ld d
   for (int i = threadIdx.x; i < d; i += blockDim.x) {
-    double acc[kSkCols];
-#pragma unroll
-    for (int cc = 0; cc < kSkCols; ++cc) acc[cc] = 0.0;
+    double a0 = 0.0, a1 = 0.0;
     const int e1 = st[i + 1];
     for (int e = st[i]; e < e1; ++e) {
       const uint32_t w = ent[e];
-      const double* row = tile + (w >> 1) * kSkCols;
+      const double2 v = tile[w >> 1];
       if (w & 1u) {
-#pragma unroll
-        for (int cc = 0; cc < kSkCols; ++cc) acc[cc] = __dsub_rn(acc[cc], row[cc]);
+        a0 = __dsub_rn(a0, v.x);
+        a1 = __dsub_rn(a1, v.y);
       } else {
-#pragma unroll
-        for (int cc = 0; cc < kSkCols; ++cc) acc[cc] = __dadd_rn(acc[cc], row[cc]);
+        a0 = __dadd_rn(a0, v.x);
+        a1 = __dadd_rn(a1, v.y);
       }
     }
-    for (int cc = 0; cc < ncols; ++cc) P[(c0 + cc) * d + i] = acc[cc];
+    P[c0 * d + i] = a0;
+    if (two) P[(c0 + 1) * d + i] = a1;
   }
 }
 
@@ -145,7 +149,7 @@ __global__ void saso_lists_kernel(SketchDesc D) {
 }
 
 __global__ void __launch_bounds__(kSkThreads) sketch_partial_kernel(SketchDesc D, int64_t ncg) {
-  extern __shared__ double tile[];
+  extern __shared__ double2 tile[];
   sketch_partial_body(blockIdx.x / ncg, blockIdx.x % ncg, D, tile);
 }
 
@@ -164,7 +168,7 @@ __global__ void saso_lists_batched_kernel(const SketchDesc* D, const int64_t* ba
 __global__ void __launch_bounds__(kSkThreads) sketch_partial_batched_kernel(const SketchDesc* D,
                                                                             const int64_t* base,
                                                                             int np) {
-  extern __shared__ double tile[];
+  extern __shared__ double2 tile[];
   int64_t t;
   const int p = find_problem(base, np, blockIdx.x, &t);
   const int64_t ncg = (D[p].n + kSkCols - 1) / kSkCols;
@@ -180,6 +184,15 @@ __global__ void __launch_bounds__(kCombineThreads) sketch_combine_batched_kernel
 
 // ---- host side --------------------------------------------------------------
 static int64_t nblocks_of(int64_t m) { return (m + kRowBlock - 1) / kRowBlock; }
+
+// Threads of a partial-sum CTA: the d target rows spread evenly over at most
+// kSkThreads threads (every thread the same number of rows, up to the last
+// warp), a whole number of warps.
+static int sketch_threads(int d) {
+  const int passes = (d + kSkThreads - 1) / kSkThreads;
+  const int per = (d + passes - 1) / passes;
+  return (per + 31) / 32 * 32;
+}
 
 int64_t sketch_workspace_bytes(int64_t m, int64_t n, int d, int s) {
   const int64_t nb = nblocks_of(m);
@@ -218,7 +231,7 @@ static cudaError_t set_smem_attrs(size_t lists_bytes) {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists_bytes);
     if (e != cudaSuccess) return e;
   }
-  const int tile_bytes = kRowBlock * kSkCols * (int)sizeof(double);
+  const int tile_bytes = kRowBlock * (int)sizeof(double2);
   e = cudaFuncSetAttribute(sketch_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            tile_bytes);
   if (e == cudaSuccess)
@@ -239,8 +252,8 @@ cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, in
   if (e != cudaSuccess) return e;
   saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), 256, sh_lists, stream>>>(D);
   const int64_t ncg = (n + kSkCols - 1) / kSkCols;
-  sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), kSkThreads,
-                          kRowBlock * kSkCols * sizeof(double), stream>>>(D, ncg);
+  sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), sketch_threads(d),
+                          kRowBlock * sizeof(double2), stream>>>(D, ncg);
   sketch_combine_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(D);
   count_launches(3);
   return cudaGetLastError();
@@ -259,8 +272,8 @@ cudaError_t launch_sketch_batched(int phase, const SketchDesc* D, const int64_t*
   if (phase == 0)
     saso_lists_batched_kernel<<<(unsigned)total_tiles, 256, sh_lists, stream>>>(D, base, np);
   else if (phase == 1)
-    sketch_partial_batched_kernel<<<(unsigned)total_tiles, kSkThreads,
-                                    kRowBlock * kSkCols * sizeof(double), stream>>>(D, base, np);
+    sketch_partial_batched_kernel<<<(unsigned)total_tiles, sketch_threads(max_d),
+                                    kRowBlock * sizeof(double2), stream>>>(D, base, np);
   else
     sketch_combine_batched_kernel<<<(unsigned)total_tiles, kCombineThreads, 0, stream>>>(D, base,
                                                                                         np);

@@ -78,13 +78,14 @@ __global__ void oz_colexp_kernel(const double* __restrict__ X, int64_t ldx, int6
   }
 }
 
-// e[r] for every row r over columns [0, cols) of X.
-__global__ void oz_rowexp_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int cols,
-                                 int* __restrict__ e) {
+// e[r] for every row r over columns [0, cols) of X (column c of X is
+// column map[c] of the array when map is given).
+__global__ void oz_rowexp_kernel(const double* __restrict__ X, int64_t ldx, const int64_t* map,
+                                 int64_t rows, int cols, int* __restrict__ e) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= rows) return;
   double mx = 0.0;
-  for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(X[(int64_t)c * ldx + r]));
+  for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(X[(map ? map[c] : (int64_t)c) * ldx + r]));
   e[r] = frexp_exp(mx);
 }
 
@@ -103,11 +104,13 @@ __global__ void oz_split_cols_kernel(const double* __restrict__ X, int64_t ldx, 
 }
 
 // Row operand: digit planes D[p][r][k] of X[r, k] for k in [0, cols) (K =
-// columns, padded to kpad), scale e[r].  32 x 32 tiles transposed through
-// shared memory so that both the reads of X and the writes of D coalesce.
-__global__ void oz_split_rows_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows,
-                                     int cols, int64_t kpad, const int* __restrict__ e,
-                                     __nv_bfloat16* __restrict__ D, int64_t plane) {
+// columns, padded to kpad; column k is column map[k] of the array when map
+// is given), scale e[r].  32 x 32 tiles transposed through shared memory so
+// that both the reads of X and the writes of D coalesce.
+__global__ void oz_split_rows_kernel(const double* __restrict__ X, int64_t ldx, const int64_t* map,
+                                     int64_t rows, int cols, int64_t kpad,
+                                     const int* __restrict__ e, __nv_bfloat16* __restrict__ D,
+                                     int64_t plane) {
   __shared__ double tile[32][33];
   const int64_t r0 = blockIdx.x * 32;
   const int k0 = blockIdx.y * 32;
@@ -115,7 +118,7 @@ __global__ void oz_split_rows_kernel(const double* __restrict__ X, int64_t ldx, 
   for (int j = ty; j < 32; j += 8) {
     const int64_t r = r0 + tx;
     const int k = k0 + j;
-    tile[j][tx] = (r < rows && k < cols) ? X[(int64_t)k * ldx + r] : 0.0;
+    tile[j][tx] = (r < rows && k < cols) ? X[(map ? map[k] : (int64_t)k) * ldx + r] : 0.0;
   }
   __syncthreads();
   for (int j = ty; j < 32; j += 8) {
@@ -308,13 +311,15 @@ void carve_trsm(TrsmCtx& c, int64_t m, int k, void* work) {
   c.status = (int*)w;
 }
 
-// C[:, 0:n] (m x n, ld ldc) op= Xs[:, 0:kk] * Ts (kk x n); mode store/sub.
-cudaError_t oz_mul(const TrsmCtx& c, const double* Xs, int64_t ldxs, int kk, const double* Ts,
-                   int64_t ldts, int n, double* C, int64_t ldc, int mode, cudaStream_t s) {
+// C[:, 0:n] (m x n, ld ldc) op= Xs[:, map[0:kk]] * Ts (kk x n) (identity map
+// when map is null); mode store/sub.
+cudaError_t oz_mul(const TrsmCtx& c, const double* Xs, int64_t ldxs, const int64_t* map, int kk,
+                   const double* Ts, int64_t ldts, int n, double* C, int64_t ldc, int mode,
+                   cudaStream_t s) {
   const int64_t kpad = round_up(kk, kOzKAlign);
-  oz_rowexp_kernel<<<(unsigned)((c.m + 255) / 256), 256, 0, s>>>(Xs, ldxs, c.m, kk, c.ea);
+  oz_rowexp_kernel<<<(unsigned)((c.m + 255) / 256), 256, 0, s>>>(Xs, ldxs, map, c.m, kk, c.ea);
   dim3 gr((unsigned)((c.m + 31) / 32), (unsigned)((kpad + 31) / 32));
-  oz_split_rows_kernel<<<gr, 256, 0, s>>>(Xs, ldxs, c.m, kk, kpad, c.ea, c.DA, c.m * kpad);
+  oz_split_rows_kernel<<<gr, 256, 0, s>>>(Xs, ldxs, map, c.m, kk, kpad, c.ea, c.DA, c.m * kpad);
   oz_colexp_kernel<<<n, 128, 0, s>>>(Ts, ldts, kk, c.eb);
   dim3 gc((unsigned)((kpad + 255) / 256), (unsigned)n);
   oz_split_cols_kernel<<<gc, 256, 0, s>>>(Ts, ldts, kk, n, kpad, c.eb, c.DB, (int64_t)n * kpad);
@@ -341,8 +346,9 @@ cudaError_t solve(const TrsmCtx& c, int a, int b, cudaStream_t s) {
   if (h >= b) h = b - kOzTrsmNB;
   if ((e = solve(c, a, h, s)) != cudaSuccess) return e;
   // X[:, h:b] -= X[:, a:h] T[a:h, h:b]
-  if ((e = oz_mul(c, c.X + (int64_t)a * c.ldx, c.ldx, h - a, c.T + (int64_t)h * c.ldt + a, c.ldt,
-                  b - h, c.X + (int64_t)h * c.ldx, c.ldx, kOzSub, s)) != cudaSuccess)
+  if ((e = oz_mul(c, c.X + (int64_t)a * c.ldx, c.ldx, nullptr, h - a,
+                  c.T + (int64_t)h * c.ldt + a, c.ldt, b - h, c.X + (int64_t)h * c.ldx, c.ldx,
+                  kOzSub, s)) != cudaSuccess)
     return e;
   return solve(c, h, b, s);
 }
@@ -385,11 +391,6 @@ cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const in
   carve_trsm(c, m, k, work);
   c.err = status;
   double* W = (double*)((char*)work + oz_trsm_workspace(m, k));
-  if (B != X || cols) {
-    dim3 g((unsigned)min64((m + 255) / 256, 256), (unsigned)k);
-    oz_gather_kernel<<<g, 256, 0, s>>>(B, ldb, cols, m, X, ldx);
-    count_launches(1);
-  }
   // one row of W per warp in shared memory: as many warps as fit 200 KB
   int warps = (int)(200 * 1024 / ((int64_t)k * (int64_t)sizeof(double)));
   warps = warps < 1 ? 1 : (warps > kTrinvWarps ? kTrinvWarps : warps);
@@ -404,8 +405,9 @@ cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const in
   count_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // the split reads X before the product overwrites it (separate planes)
-  return oz_mul(c, X, ldx, k, W, k, k, X, ldx, kOzStore, s);
+  // the split reads B[:, cols] (the gather is fused into it) before the
+  // product writes X (separate planes, so X may be B)
+  return oz_mul(c, B, ldb, cols, k, W, k, k, X, ldx, kOzStore, s);
 }
 
 }  // namespace cqrrpt

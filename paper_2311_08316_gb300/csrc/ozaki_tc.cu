@@ -15,8 +15,10 @@
 //   warp 1      allocates the 512 tensor-memory columns, and one thread
 //               issues the MMAs (M = 128, N = 128, K = 16; four per stage)
 //               into one of two FP32 accumulators (columns 0-127, 128-255):
-//               one accumulator per chunk, so chunk c + 1 runs while chunk c
-//               is drained;
+//               one accumulator per chunk (at most 1024 K terms of one
+//               level: one pair's K range, or several same-level pairs when
+//               a pair's K is at most 512), so chunk c + 1 runs while chunk
+//               c is drained;
 //   warps 2-17  drain each finished chunk: four warps per TMEM lane quarter
 //               (32 rows of C), each owning 32 columns in two pieces of 16,
 //               one row per thread.  FP32 -> exact int32 -> times
@@ -236,6 +238,9 @@ __global__ void __maxnreg__(96)
   if (G.err && *(volatile const int*)G.err != kOk) return;
   const int nk = (int)((kend - kbeg + kTcBK - 1) / kTcBK);  // K stages per pair
   const int nchunks = (nk + kTcChunkStages - 1) / kTcChunkStages;
+  // pairs of one level that share an FP32 accumulator: up to 1024 terms in
+  // all (when one pair's K fits a chunk several same-level pairs do)
+  const int run = nchunks == 1 ? max(1, kTcChunkStages / nk) : 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -316,7 +321,10 @@ __global__ void __maxnreg__(96)
     bool any = false;
     for (int grp = 0; grp < 2 && ok; ++grp)
     for (int c = 0; c < nchunks && ok; ++c) {
-      for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1] && ok; ++pi) {
+      for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1] && ok;) {
+        int s = 2;
+        while ((s - 1) * s / 2 <= pi) ++s;
+        const int run_end = min(pi + run, (s - 1) * s / 2);  // same level only
         if (!mbar_wait(acce_bar(buf), ((use >> buf) & 1u) ^ 1u)) {
           record_timeout(G.err);
           ok = false;
@@ -325,30 +333,33 @@ __global__ void __maxnreg__(96)
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * kTcBN);
         const int st_n = min(kTcChunkStages, nk - c * kTcChunkStages);
-        for (int j = 0; j < st_n; ++j) {
-          if (!mbar_wait(full_bar(stage), phase)) {
-            record_timeout(G.err);
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t ad = sw128_desc(a_tiles + stage * kTcTileBytes);
-          const uint64_t bd = sw128_desc(b_tiles + stage * kTcTileBytes);
+        for (int pr = pi; pr < run_end && ok; ++pr) {
+          for (int j = 0; j < st_n; ++j) {
+            if (!mbar_wait(full_bar(stage), phase)) {
+              record_timeout(G.err);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(a_tiles + stage * kTcTileBytes);
+            const uint64_t bd = sw128_desc(b_tiles + stage * kTcTileBytes);
 #pragma unroll
-          for (int kk = 0; kk < kTcBK / 16; ++kk)  // K = 16 per MMA: +32 bytes
-            umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                      (j > 0 || kk > 0) ? 1u : 0u);
-          umma_commit(empty_bar(stage));
-          any = true;
-          if (++stage == kTcStages) {
-            stage = 0;
-            phase ^= 1u;
+            for (int kk = 0; kk < kTcBK / 16; ++kk)  // K = 16 per MMA: +32 bytes
+              umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                        (pr > pi || j > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(empty_bar(stage));
+            any = true;
+            if (++stage == kTcStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
         }
         if (!ok) break;
         umma_commit(accf_bar(buf));
         use ^= 1u << buf;
         buf = (buf + 1) % kTcAccBufs;
+        pi = run_end;
       }
     }
     // every MMA issued by this thread has completed before the TMEM goes
@@ -373,9 +384,10 @@ __global__ void __maxnreg__(96)
     for (int grp = 0; grp < 2 && ok; ++grp)
     for (int c = 0; c < nchunks && ok; ++c) {
       const int s_g = grp == 0 ? 5 : 9;  // last level of the group
-      for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1]; ++pi) {
+      for (int pi = kTcGroupFirst[grp]; pi < kTcGroupFirst[grp + 1];) {
         int s = 2;
         while ((s - 1) * s / 2 <= pi) ++s;
+        const int run_end = min(pi + run, (s - 1) * s / 2);  // same level only
         if (!mbar_wait(accf_bar(buf), (fph >> buf) & 1u)) {
           record_timeout(G.err);
           ok = false;
@@ -384,7 +396,7 @@ __global__ void __maxnreg__(96)
         fph ^= 1u << buf;
         tc_fence_after();
         const bool fresh = c == 0 && pi == kTcGroupFirst[grp];
-        const bool emit = c == nchunks - 1 && pi == kTcGroupFirst[grp + 1] - 1;
+        const bool emit = c == nchunks - 1 && run_end == kTcGroupFirst[grp + 1];
         const int weight = 1 << (7 * (s_g - s));
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -431,6 +443,7 @@ __global__ void __maxnreg__(96)
         __syncwarp();
         if (lane == 0) mbar_arrive(acce_bar(buf));
         buf = (buf + 1) % kTcAccBufs;
+        pi = run_end;
       }
     }
   }

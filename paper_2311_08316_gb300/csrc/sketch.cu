@@ -112,13 +112,10 @@ __device__ __forceinline__ void sketch_partial_body(int64_t b, int64_t cg, const
     for (int e = st[i]; e < e1; ++e) {
       const uint32_t w = ent[e];
       const double2 v = tile[w >> 1];
-      if (w & 1u) {
-        a0 = __dsub_rn(a0, v.x);
-        a1 = __dsub_rn(a1, v.y);
-      } else {
-        a0 = __dadd_rn(a0, v.x);
-        a1 = __dadd_rn(a1, v.y);
-      }
+      // a - x == a + (-x) exactly; the sign flip runs on the integer pipe
+      const unsigned long long neg = (unsigned long long)(w & 1u) << 63;
+      a0 = __dadd_rn(a0, __longlong_as_double(__double_as_longlong(v.x) ^ neg));
+      a1 = __dadd_rn(a1, __longlong_as_double(__double_as_longlong(v.y) ^ neg));
     }
     P[c0 * d + i] = a0;
     if (two) P[(c0 + 1) * d + i] = a1;

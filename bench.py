@@ -35,10 +35,12 @@ import workloads as W  # noqa: E402
 # FP64 peak of GB300 for an ALU-bound FP64 kernel: 152 SMs x 2 DFMA/clk x
 # 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s at the maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# DRAM bytes per row of M for one trsm_rut_kernel launch at n = 1024, k = 800
-# (ncu capture of the m = 32768 case, scaled by rows; see profiles/); None
-# until a capture of the current kernel exists.
-TRSM_DRAM_BYTES_PER_ROW = None
+# DRAM bytes per row of M for one trsm_rut_kernel launch at n = 1024, k = 800:
+# dram__bytes_read.sum + dram__bytes_write.sum = 2.013637 GB + 0.206175 GB
+# from an ncu capture of the m = 32768 case (one launch of line 4), divided
+# by its 32768 rows (the kernel's traffic grows in proportion to the rows:
+# one thread per row, T staged per CTA).  Set to None when the kernel changes.
+TRSM_DRAM_BYTES_PER_ROW = (2.013637e9 + 0.206175e9) / 32768
 
 
 def parse():
@@ -272,6 +274,47 @@ def run_batched(args, world, rank, local, C):
                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None},
             "gpu_launches": int(launches), "clocks": clk}
+    # ---- the same batch in the split-BF16 mode (lines 4, 5, 7 as batched
+    # tensor-core products): time, and J / k / accuracy against FP64
+    split = None
+    try:
+        outs_s = [(C.colmajor_empty(w.m, w.n), C.colmajor_empty(w.n, w.n),
+                   torch.empty(w.n, dtype=torch.int64, device="cuda")) for w in ws]
+        for _ in range(2):
+            res_s, _, _ = C.cqrrpt_batched(mats, 1.25, 4, tols, seeds, precision=C.SPLITBF16,
+                                           outs=outs_s, handle=h, stream=stream)
+        ms_s = []
+        for _ in range(max(1, args.steps)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res_s, _, _ = C.cqrrpt_batched(mats, 1.25, 4, tols, seeds, precision=C.SPLITBF16,
+                                           outs=outs_s, handle=h, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_s.append(e0.elapsed_time(e1))
+        same_jk = all(a.k == b.k and torch.equal(a.J, b.J) for a, b in zip(res, res_s))
+        worst_recon, worst_orth = 0.0, 0.0
+        for i in list(range(0, len(ws), max(1, len(ws) // 8)))[:8]:
+            r = res_s[i]
+            if r.k:
+                AJ = mats[i][:, r.J]
+                worst_recon = max(worst_recon, (torch.linalg.norm(AJ - r.Q @ r.R)
+                                                / torch.linalg.norm(mats[i])).item())
+                worst_orth = max(worst_orth, torch.linalg.matrix_norm(
+                    r.Q.t() @ r.Q - torch.eye(r.k, dtype=torch.float64, device="cuda"),
+                    ord=2).item())
+        split = {"ms_per_batch": statistics.median(ms_s),
+                 "factorizations_per_s": len(ws) / (statistics.median(ms_s) / 1e3),
+                 "speedup_vs_fp64": ms_per_step / statistics.median(ms_s),
+                 "J_and_k_equal_fp64": bool(same_jk),
+                 "worst_recon_rel_F_sampled": worst_recon, "worst_orth_2_sampled": worst_orth,
+                 "note": "wall time of the call: includes its two host waits for k"}
+        del outs_s, res_s
+    except Exception as ex:  # reported, not hidden
+        split = {"error": str(ex)}
+    line["splitbf16_same_batch"] = split
+
     if rank == 0 and world == 1:
         import oracle
         # parity and CPU baseline on a sample of 8 problems
@@ -635,6 +678,37 @@ def main():
     alg_flops += float(m) * w.nnz * n
     phase_share = {p: statistics.mean(v) / (ms_per_step) for p, v in phases.items()}
 
+    # ---- the same input in the split-BF16 mode (lines 4, 5, 7 on the
+    # tensor cores): time and accuracy next to the FP64 result
+    split = None
+    try:
+        Qs = C.colmajor_empty(m, n)
+        Rs = C.colmajor_empty(n, n)
+        Js = torch.empty(n, dtype=torch.int64, device="cuda")
+        rs = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, precision=C.SPLITBF16,
+                      out=(Qs, Rs, Js), handle=h, stream=stream)
+        ms_s = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, precision=C.SPLITBF16,
+                          out=(Qs, Rs, Js), handle=h, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_s.append(e0.elapsed_time(e1))
+        ks = rs.k
+        recon = (torch.linalg.norm(A[:, Js] - Qs[:, :ks] @ Rs[:ks]) / torch.linalg.norm(A)).item()
+        orth = torch.linalg.matrix_norm(Qs[:, :ks].t() @ Qs[:, :ks]
+                                        - torch.eye(ks, dtype=torch.float64, device="cuda"),
+                                        ord=2).item()
+        split = {"ms": statistics.median(ms_s), "factorizations_per_s": 1e3 / statistics.median(ms_s),
+                 "speedup_vs_fp64": ms_per_step / statistics.median(ms_s), "k": ks,
+                 "J_equal_fp64": bool(torch.equal(Js, J)), "recon_rel_F": recon, "orth_2": orth}
+        del Qs, Rs, Js
+    except Exception as ex:  # reported, not hidden
+        split = {"error": str(ex)}
+
     # ---- e2e through the public API with host buffers
     A_host = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
     A_host.copy_(A)
@@ -673,7 +747,8 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_step},
             "gpu_launches": int(launches),
-            "clocks": clk}
+            "clocks": clk,
+            "splitbf16_same_input": split}
 
     # ---- CPU baseline: the oracle on the full workload (rank 0, N = 1 only)
     if rank == 0 and world == 1:

@@ -136,12 +136,22 @@ int cqrrpt_batched_workspace_size(int batch, const int64_t* m, const int64_t* n,
  *   m, n, lda, tol, seed, ldq, ldr      HOST arrays of `batch` entries.
  *   A, Q, R, J                  HOST arrays of `batch` DEVICE pointers with
  *                               the meaning and sizes of cqrrpt_d.
- *   gamma, nnz_per_col, precision      shared by all problems.
+ *   gamma, nnz_per_col, precision      shared by all problems; precision
+ *                               CQRRPT_FP64 or CQRRPT_SPLITBF16.  In
+ *                               CQRRPT_SPLITBF16 the sketch, QRCP, rank rule,
+ *                               Cholesky and TRMM run as batched FP64
+ *                               kernels and lines 4, 5 and 7 as batched
+ *                               split-BF16 products; the call then waits for
+ *                               the stream twice (the products are sized by
+ *                               each problem's k) and grows a second,
+ *                               handle-owned workspace for the digit planes
+ *                               (about 16 m k bytes per problem).
  *   k_dev, status_dev           DEVICE arrays of `batch` entries (or NULL):
  *                               each problem's k and final status.
  * Every problem's J, k, Q and R are bit-identical to cqrrpt_d on the same
- * inputs.  The call returns after enqueueing (argument errors: -i for
- * argument i, counting the handle as 1). */
+ * inputs in the same precision.  In CQRRPT_FP64 the call returns after
+ * enqueueing (argument errors: -i for argument i, counting the handle as
+ * 1). */
 int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
                      const double* const* A, const int64_t* lda, double gamma, int nnz_per_col,
                      const double* tol, const uint64_t* seed, int precision, double* const* Q,
@@ -165,7 +175,8 @@ int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable);
  * cqrrpt_batched_d.  The shapes change the blocking only, never the order
  * of any sum, so outputs are bit-identical whatever is chosen.  Waits for
  * the stream.
- *   arguments 1-18      as cqrrpt_batched_d.
+ *   arguments 1-18      as cqrrpt_batched_d (precision CQRRPT_FP64 only:
+ *                       the tuned shapes are those of the FP64 kernels).
  *   times_us_host       HOST array of 64 doubles or NULL: for bucket b,
  *                       [4b + 0, 4b + 1] = TRSM time with 16 / 32 columns,
  *                       [4b + 2, 4b + 3] = Gram time with 16 / 32 tiles

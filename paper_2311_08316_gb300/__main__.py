@@ -1,0 +1,52 @@
+"""Run factorisations of the synthetic workloads from the command line (a
+driver for profilers and quick checks).
+
+    python -m paper_2311_08316_gb300 [--workload single|mixed] [--rows M]
+                                     [--reps R] [--precision fp64|splitbf16|cholqr2]
+
+`single` is the rank-800 workload (n = 1024, planted rank 800, tol 1e-9),
+`mixed` the cond-1e10 workload (n = 512); --rows sets m.  Each repetition
+factors the same matrix on one handle; the last k, status and the library's
+kernel-launch count are printed.
+"""
+import argparse
+import os
+import sys
+
+import torch
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import workloads as W  # noqa: E402
+
+import paper_2311_08316_gb300 as C  # noqa: E402
+from paper_2311_08316_gb300 import build  # noqa: E402
+
+PRECISIONS = {"fp64": C.FP64, "splitbf16": C.SPLITBF16, "cholqr2": C.SPLITBF16_CHOLQR2}
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(prog="python -m paper_2311_08316_gb300")
+    p.add_argument("--workload", default="single", choices=["single", "mixed"])
+    p.add_argument("--rows", type=int, default=None)
+    p.add_argument("--reps", type=int, default=2)
+    p.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    a = p.parse_args(argv)
+    build.build()
+    if a.workload == "single":
+        w = W.single_large(m=a.rows or 131072)
+    else:
+        w = W.mixed_tall(m=a.rows or (1 << 20))
+    A = w.matrix("cuda")
+    h = C.Handle()
+    r = None
+    for _ in range(a.reps):
+        r = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, precision=PRECISIONS[a.precision],
+                     handle=h)
+    torch.cuda.synchronize()
+    print("workload %s m=%d n=%d precision %s: k=%d status=%d launches=%d"
+          % (w.name, w.m, w.n, a.precision, r.k, r.status, C.kernel_launches()))
+
+
+if __name__ == "__main__":
+    main()

@@ -38,6 +38,12 @@ struct cqrrpt_ctx {
   int graph_kernels = 0;
   int use_graphs = 1;
   BatchTuning tune = default_tuning();  // tile shapes of the batched kernels
+  // batched split-BF16 path: its own device workspace, pinned read-back of
+  // every problem's device scalars
+  void* split_ws = nullptr;
+  size_t split_ws_bytes = 0;
+  DeviceScalars* pinned_sc = nullptr;
+  int pinned_sc_count = 0;
 };
 
 static std::atomic<long long> g_launches{0};
@@ -275,6 +281,8 @@ int cqrrpt_destroy(cqrrpt_handle h) {
   if (h->capture) cudaStreamDestroy(h->capture);
   if (h->stage_ev) cudaEventDestroy(h->stage_ev);
   if (h->stage) cudaFreeHost(h->stage);
+  if (h->split_ws) cudaFree(h->split_ws);
+  if (h->pinned_sc) cudaFreeHost(h->pinned_sc);
   delete h;
   return kOk;
 }
@@ -384,7 +392,7 @@ static int batch_check(int batch, const int64_t* m, const int64_t* n, const doub
   if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -7;
   if (!tol) return -9;
   if (!seed) return -10;
-  if (precision != CQRRPT_FP64) return -11;
+  if (precision != CQRRPT_FP64 && precision != CQRRPT_SPLITBF16) return -11;
   if (!Q) return -12;
   if (!ldq) return -13;
   if (!R) return -14;
@@ -487,6 +495,295 @@ int stage_tables(cqrrpt_handle h, const BatchPlan& P, cudaStream_t stream) {
   if (cudaMemcpyAsync(P.tables, h->stage, img, cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return kCudaError;
   if (cudaEventRecord(h->stage_ev, stream) != cudaSuccess) return kCudaError;
+  return kOk;
+}
+
+// Copies n bytes of a host image to device memory through the pinned
+// staging buffer (after the previous copy out of it has finished).
+int stage_bytes(cqrrpt_handle h, const void* host, size_t n, void* dev, cudaStream_t stream) {
+  if (!h->stage_ev && cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess)
+    return kCudaError;
+  if (cudaEventSynchronize(h->stage_ev) != cudaSuccess) return kCudaError;
+  if (n > h->stage_bytes) {
+    if (h->stage) cudaFreeHost(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    if (cudaMallocHost(&h->stage, n) != cudaSuccess) return kNoMemory;
+    h->stage_bytes = n;
+  }
+  memcpy(h->stage, host, n);
+  if (cudaMemcpyAsync(dev, h->stage, n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return kCudaError;
+  if (cudaEventRecord(h->stage_ev, stream) != cudaSuccess) return kCudaError;
+  return kOk;
+}
+
+// Host image of job tables: each table 256-byte aligned.
+struct Image {
+  std::vector<char> b;
+  size_t raw(const void* p, size_t n) {
+    const size_t off = (b.size() + 255) & ~size_t(255);
+    b.resize(off + n);
+    if (n) memcpy(b.data() + off, p, n);
+    return off;
+  }
+  template <class T>
+  size_t push(const std::vector<T>& v) {
+    return raw(v.data(), v.size() * sizeof(T));
+  }
+};
+
+// Prefix table of per-job CTA counts.
+template <class F>
+std::vector<int64_t> prefix(size_t n, F tiles) {
+  std::vector<int64_t> b(n + 1, 0);
+  for (size_t i = 0; i < n; ++i) b[i + 1] = b[i] + tiles(i);
+  return b;
+}
+
+int read_scalars(cqrrpt_handle h, const DeviceScalars* sc, int batch, cudaStream_t stream) {
+  if (batch > h->pinned_sc_count) {
+    if (h->pinned_sc) cudaFreeHost(h->pinned_sc);
+    h->pinned_sc = nullptr;
+    h->pinned_sc_count = 0;
+    if (cudaMallocHost((void**)&h->pinned_sc, (size_t)batch * sizeof(DeviceScalars)) != cudaSuccess)
+      return kNoMemory;
+    h->pinned_sc_count = batch;
+  }
+  if (cudaMemcpyAsync(h->pinned_sc, sc, (size_t)batch * sizeof(DeviceScalars),
+                      cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int ensure_split_ws(cqrrpt_handle h, size_t bytes) {
+  if (bytes <= h->split_ws_bytes) return kOk;
+  if (h->split_ws) {
+    cudaDeviceSynchronize();
+    cudaFree(h->split_ws);
+    h->split_ws = nullptr;
+    h->split_ws_bytes = 0;
+  }
+  if (cudaMalloc(&h->split_ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->split_ws = nullptr;
+    return kNoMemory;
+  }
+  h->split_ws_bytes = bytes;
+  return kOk;
+}
+
+// Device memory of one problem's split steps (rank k): row planes (lines 4
+// and 7) aliased with the Gram's planes (line 5), column planes of W,
+// exponents, W, the Gram's K-slice partials.
+struct SplitWs {
+  __nv_bfloat16 *DA, *DB;
+  int *ea, *eb;
+  double *W, *P;
+};
+int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+size_t split_ws_one(int64_t m, int64_t k, SplitWs* out, char* base) {
+  const int64_t kpad = rup(k, 32), kpadm = rup(m, kOzChunk);
+  const int64_t ns = oz_gram_slices(m, (int)k);
+  const int64_t da = std::max<int64_t>(kOzDigits * m * kpad * 2, kOzDigits * k * kpadm * 2);
+  size_t off = 0;
+  auto take = [&](int64_t bytes) {
+    const size_t o = off;
+    off += (size_t)align256(bytes);
+    return base + o;
+  };
+  char* DA = take(da);
+  char* DB = take(kOzDigits * k * kpad * 2);
+  char* ea = take(std::max<int64_t>(m, k) * 4);
+  char* eb = take(k * 4);
+  char* W = take(k * k * 8);
+  char* P = take(ns * k * k * 8);
+  if (out) *out = SplitWs{(__nv_bfloat16*)DA, (__nv_bfloat16*)DB, (int*)ea, (int*)eb, (double*)W,
+                          (double*)P};
+  return off;
+}
+
+// One of lines 4 and 7 for every listed problem: X = B[:, cols] T^{-1} as
+// row-wise FP64 inverse + one split product (as oz_trsm_inv, job by job).
+int split_trsm_step(cqrrpt_handle h, const std::vector<int>& ids,
+                    const std::vector<BatchProblem>& probs, const std::vector<int64_t>& k,
+                    const std::vector<SplitWs>& ws, const std::vector<double*>& T, bool line4,
+                    DeviceScalars* sc, char* tables, cudaStream_t stream) {
+  const size_t nj = ids.size();
+  if (nj == 0) return kOk;
+  std::vector<OzTrinv> ti(nj);
+  std::vector<OzRowSplit> rs(nj);
+  std::vector<OzColSplit> cs(nj);
+  std::vector<OzGemm> gm(nj);
+  std::vector<char> maps(nj * 2 * kOzMapBytes);
+  int kmax = 1;
+  for (size_t j = 0; j < nj; ++j) {
+    const int p = ids[j];
+    const BatchProblem& q = probs[(size_t)p];
+    const int kk = (int)k[(size_t)p];
+    const int64_t kpad = rup(kk, 32);
+    const SplitWs& w = ws[(size_t)p];
+    kmax = std::max(kmax, kk);
+    ti[j] = OzTrinv{T[(size_t)p], q.n, kk, w.W, kk};
+    if (line4)
+      rs[j] = OzRowSplit{q.A, q.lda, q.J, q.m, kk, kpad, w.ea, w.DA, q.m * kpad};
+    else
+      rs[j] = OzRowSplit{q.Q, q.ldq, nullptr, q.m, kk, kpad, w.ea, w.DA, q.m * kpad};
+    cs[j] = OzColSplit{w.W, kk, kk, kk, kpad, w.eb, w.DB, (int64_t)kk * kpad};
+    OzGemm G{};
+    G.M = q.m; G.N = kk; G.Kpad = kpad; G.kslice = kpad;
+    G.A = w.DA; G.a_plane = q.m * kpad; G.B = w.DB; G.b_plane = (int64_t)kk * kpad;
+    G.ea = w.ea; G.eb = w.eb; G.C = q.Q; G.ldc = q.ldq; G.c_slice = 0;
+    G.mode = kOzStore; G.upper_only = 0; G.err = &sc[p].status;
+    if (!oz_gemm_valid(G) || !oz_gemm_encode_maps(G, maps.data() + j * 2 * kOzMapBytes))
+      return kCudaError;
+    gm[j] = G;
+  }
+  const int warps = oz_trinv_warps(kmax);
+  const auto b_ti = prefix(nj, [&](size_t j) { return oz_trinv_tiles(ti[j], warps); });
+  const auto b_re = prefix(nj, [&](size_t j) { return oz_rowexp_tiles(rs[j]); });
+  const auto b_rs = prefix(nj, [&](size_t j) { return oz_splitrows_tiles(rs[j]); });
+  const auto b_ce = prefix(nj, [&](size_t j) { return oz_colexp_tiles(cs[j]); });
+  const auto b_cs = prefix(nj, [&](size_t j) { return oz_splitcols_tiles(cs[j]); });
+  const auto b_gm = prefix(nj, [&](size_t j) { return oz_gemm_tiles(gm[j]); });
+  Image im;
+  const size_t o_maps = im.raw(maps.data(), maps.size());
+  const size_t o_ti = im.push(ti), o_rs = im.push(rs), o_cs = im.push(cs), o_gm = im.push(gm);
+  const size_t o_bti = im.push(b_ti), o_bre = im.push(b_re), o_brs = im.push(b_rs),
+               o_bce = im.push(b_ce), o_bcs = im.push(b_cs), o_bgm = im.push(b_gm);
+  int st = stage_bytes(h, im.b.data(), im.b.size(), tables, stream);
+  if (st != kOk) return st;
+  const int n = (int)nj;
+  cudaError_t e = oz_trinv_batched((const OzTrinv*)(tables + o_ti), (const int64_t*)(tables + o_bti),
+                                   b_ti[nj], n, warps, kmax, stream);
+  if (e == cudaSuccess)
+    e = oz_rowsplit_batched((const OzRowSplit*)(tables + o_rs), (const int64_t*)(tables + o_bre),
+                            b_re[nj], (const int64_t*)(tables + o_brs), b_rs[nj], n, stream);
+  if (e == cudaSuccess)
+    e = oz_colsplit_batched((const OzColSplit*)(tables + o_cs), (const int64_t*)(tables + o_bce),
+                            b_ce[nj], (const int64_t*)(tables + o_bcs), b_cs[nj], n, stream);
+  if (e == cudaSuccess)
+    e = oz_gemm_tc_batched_launch((const OzGemm*)(tables + o_gm), tables + o_maps,
+                                  (const int64_t*)(tables + o_bgm), n, b_gm[nj], stream);
+  return e == cudaSuccess ? kOk : kCudaError;
+}
+
+// Line 5 for every listed problem: G = Q^T Q as split products over K
+// slices (as oz_gram, job by job).
+int split_gram_step(cqrrpt_handle h, const std::vector<int>& ids,
+                    const std::vector<BatchProblem>& probs, const std::vector<int64_t>& k,
+                    const std::vector<SplitWs>& ws, const std::vector<double*>& Gout,
+                    DeviceScalars* sc, char* tables, cudaStream_t stream) {
+  const size_t nj = ids.size();
+  if (nj == 0) return kOk;
+  std::vector<OzColSplit> cs(nj);
+  std::vector<OzGemm> gm(nj);
+  std::vector<OzCombine> cb(nj);
+  std::vector<char> maps(nj * 2 * kOzMapBytes);
+  for (size_t j = 0; j < nj; ++j) {
+    const int p = ids[j];
+    const BatchProblem& q = probs[(size_t)p];
+    const int kk = (int)k[(size_t)p];
+    const SplitWs& w = ws[(size_t)p];
+    const int64_t kpadm = rup(q.m, kOzChunk);
+    const int64_t ns = oz_gram_slices(q.m, kk);
+    cs[j] = OzColSplit{q.Q, q.ldq, q.m, kk, kpadm, w.ea, w.DA, (int64_t)kk * kpadm};
+    OzGemm G{};
+    G.M = kk; G.N = kk; G.Kpad = kpadm;
+    G.kslice = ((kpadm / kOzChunk + ns - 1) / ns) * kOzChunk;
+    G.A = w.DA; G.a_plane = (int64_t)kk * kpadm; G.B = w.DA; G.b_plane = (int64_t)kk * kpadm;
+    G.ea = w.ea; G.eb = w.ea; G.C = w.P; G.ldc = kk; G.c_slice = (int64_t)kk * kk;
+    G.mode = kOzStore; G.upper_only = 1; G.err = &sc[p].status;
+    if (!oz_gemm_valid(G) || !oz_gemm_encode_maps(G, maps.data() + j * 2 * kOzMapBytes))
+      return kCudaError;
+    gm[j] = G;
+    const int nsr = (int)((kpadm + G.kslice - 1) / G.kslice);
+    cb[j] = OzCombine{w.P, G.c_slice, nsr, kk, Gout[(size_t)p], q.n};
+  }
+  const auto b_ce = prefix(nj, [&](size_t j) { return oz_colexp_tiles(cs[j]); });
+  const auto b_cs = prefix(nj, [&](size_t j) { return oz_splitcols_tiles(cs[j]); });
+  const auto b_gm = prefix(nj, [&](size_t j) { return oz_gemm_tiles(gm[j]); });
+  const auto b_cb = prefix(nj, [&](size_t j) { return oz_combine_tiles(cb[j]); });
+  Image im;
+  const size_t o_maps = im.raw(maps.data(), maps.size());
+  const size_t o_cs = im.push(cs), o_gm = im.push(gm), o_cb = im.push(cb);
+  const size_t o_bce = im.push(b_ce), o_bcs = im.push(b_cs), o_bgm = im.push(b_gm),
+               o_bcb = im.push(b_cb);
+  int st = stage_bytes(h, im.b.data(), im.b.size(), tables, stream);
+  if (st != kOk) return st;
+  const int n = (int)nj;
+  cudaError_t e =
+      oz_colsplit_batched((const OzColSplit*)(tables + o_cs), (const int64_t*)(tables + o_bce),
+                          b_ce[nj], (const int64_t*)(tables + o_bcs), b_cs[nj], n, stream);
+  if (e == cudaSuccess)
+    e = oz_gemm_tc_batched_launch((const OzGemm*)(tables + o_gm), tables + o_maps,
+                                  (const int64_t*)(tables + o_bgm), n, b_gm[nj], stream);
+  if (e == cudaSuccess)
+    e = oz_combine_batched((const OzCombine*)(tables + o_cb), (const int64_t*)(tables + o_bcb),
+                           b_cb[nj], n, stream);
+  return e == cudaSuccess ? kOk : kCudaError;
+}
+
+// Batched CQRRPT in the split-BF16 mode: the FP64 front (sketch, QRCP, rank
+// rule) and back (Cholesky, stage 2, TRMM, finalize) as batched kernels,
+// lines 4, 5 and 7 as batched split products -- every problem's job exactly
+// the single-problem split path's, so results are bit-identical to
+// cqrrpt_d in CQRRPT_SPLITBF16.  Waits for the stream twice (the products
+// are sized by each problem's k).
+int batched_split_run(cqrrpt_handle h, std::vector<BatchProblem>& probs, cudaStream_t stream) {
+  const int batch = (int)probs.size();
+  const BatchWs W = batch_ws(h, batch);
+  BatchPlan P;
+  P.scalars = W.scalars;
+  P.tables = W.tables;
+  batch_plan(P, batch, probs.data(), W.per_problem, nullptr, &h->tune);
+  int st = stage_tables(h, P, stream);
+  if (st != kOk) return st;
+  if (sketch_set_attributes(P.max_d) != cudaSuccess) return kCudaError;
+  if (batch_launch_front(P, stream) != cudaSuccess) return kCudaError;
+  if ((st = read_scalars(h, P.scalars, batch, stream)) != kOk) return st;
+  std::vector<int64_t> k((size_t)batch, 0);
+  std::vector<int> ids;
+  for (int p = 0; p < batch; ++p) {
+    k[(size_t)p] = h->pinned_sc[p].k;
+    if (h->pinned_sc[p].status == kOk && k[(size_t)p] > 0) ids.push_back(p);
+  }
+  // split workspace: per problem at its k, then the job tables
+  std::vector<SplitWs> ws((size_t)batch);
+  std::vector<size_t> offs((size_t)batch, 0);
+  size_t total = 0;
+  for (int p : ids) {
+    offs[(size_t)p] = total;
+    total += split_ws_one(probs[(size_t)p].m, k[(size_t)p], nullptr, nullptr);
+  }
+  const size_t table_bytes = (size_t)align256((int64_t)batch * 2048 + 65536);
+  if ((st = ensure_split_ws(h, total + table_bytes)) != kOk) return st;
+  char* base = (char*)h->split_ws;
+  char* tables = base + total;
+  for (int p : ids) split_ws_one(probs[(size_t)p].m, k[(size_t)p], &ws[(size_t)p], base + offs[(size_t)p]);
+
+  // line 4, line 5, then the FP64 Cholesky and stage 2
+  if ((st = split_trsm_step(h, ids, probs, k, ws, P.rsk, true, P.scalars, tables, stream)) != kOk)
+    return st;
+  if ((st = split_gram_step(h, ids, probs, k, ws, P.g, P.scalars, tables, stream)) != kOk)
+    return st;
+  if (launch_potrf_batched(P.po, batch, stream) != cudaSuccess ||
+      launch_rank_stage2_batched(P.s2, batch, stream) != cudaSuccess)
+    return kCudaError;
+  // line 7 at the rank after the Cholesky (Remark 3, stage 2)
+  if ((st = read_scalars(h, P.scalars, batch, stream)) != kOk) return st;
+  std::vector<int> ids7;
+  for (int p : ids) {
+    k[(size_t)p] = h->pinned_sc[p].k;
+    if (h->pinned_sc[p].status == kOk && k[(size_t)p] > 0) ids7.push_back(p);
+  }
+  if ((st = split_trsm_step(h, ids7, probs, k, ws, P.rpre, false, P.scalars, tables, stream)) !=
+      kOk)
+    return st;
+  if (launch_trmm_batched(P.tm, P.base_tm, batch, P.tiles_tm, stream) != cudaSuccess ||
+      launch_finalize_batched(P.fi, batch, stream) != cudaSuccess)
+    return kCudaError;
   return kOk;
 }
 
@@ -607,6 +904,7 @@ int cqrrpt_batched_d(cqrrpt_handle h, int batch, const int64_t* m, const int64_t
   if (st != kOk) return st;
   std::vector<BatchProblem> probs = batch_problems(batch, m, n, A, lda, gamma, nnz, tol, seed, Q,
                                                    ldq, R, ldr, J, k_dev, status_dev);
+  if (precision == CQRRPT_SPLITBF16) return batched_split_run(h, probs, stream);
   return batched_run(h, probs, stream);
 }
 
@@ -619,6 +917,7 @@ int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const 
   if (!h) return -1;
   int st = batch_check(batch, m, n, A, lda, gamma, nnz, tol, seed, precision, Q, ldq, R, ldr, J);
   if (st != kOk) return st;
+  if (precision != CQRRPT_FP64) return -11;  // the tuned shapes are the FP64 kernels'
   DevGuard g(h->device);
   size_t need = 0;
   st = cqrrpt_batched_workspace_size(batch, m, n, gamma, nnz, &need);

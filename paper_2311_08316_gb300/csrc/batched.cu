@@ -70,6 +70,9 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
   P.scalars = scalars;
   P.tables = tables;
   P.nprob = batch;
+  P.rsk.assign((size_t)batch, nullptr);
+  P.g.assign((size_t)batch, nullptr);
+  P.rpre.assign((size_t)batch, nullptr);
   // per-problem workspace
   char* w = ws_base;
   std::vector<SketchDesc> sk(batch);
@@ -101,6 +104,9 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     double* G = (double*)w; w += align256(n * n * 8);
     double* Rpre = (double*)w; w += align256(n * n * 8);
     double* f2 = (double*)w; w += align256((n + 1) * 8);
+    P.rsk[(size_t)p] = Rsk;
+    P.g[(size_t)p] = G;
+    P.rpre[(size_t)p] = Rpre;
     DeviceScalars* s = sc + (scalar_index ? scalar_index[p] : p);
     const int bucket = tune_bucket(n);
     const int jb = TU.trsm_jb[bucket] == 16 ? 16 : 32;
@@ -171,7 +177,7 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
   return 0;
 }
 
-cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s) {
+cudaError_t batch_launch_front(const BatchPlan& P, cudaStream_t s) {
   const int np = P.nprob;
   cudaError_t e = launch_init_scalars_batched(P.scalars, np, s);
   if (e == cudaSuccess) e = launch_sketch_batched(0, P.sk, P.base_list, np, P.tiles_list, P.max_d, s);
@@ -179,6 +185,12 @@ cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s) {
   if (e == cudaSuccess) e = launch_sketch_batched(2, P.sk, P.base_comb, np, P.tiles_comb, P.max_d, s);
   if (e == cudaSuccess) e = launch_qrcp_batched(P.qr, np, P.base_gath, P.tiles_gath, s);
   if (e == cudaSuccess) e = launch_rank_batched(P.rk, np, s);
+  return e;
+}
+
+cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s) {
+  const int np = P.nprob;
+  cudaError_t e = batch_launch_front(P, s);
   if (e == cudaSuccess) e = launch_trsm_rut_batched(P.t1, P.base_trsm, np, P.tiles_trsm, s);
   if (e == cudaSuccess) e = launch_gram_batched(0, P.gr, P.base_gp, np, P.tiles_gp, s);
   if (e == cudaSuccess) e = launch_gram_batched(1, P.gr, P.base_gc, np, P.tiles_gc, s);

@@ -44,6 +44,8 @@ struct BatchPlan {
   const int64_t *base_list = nullptr, *base_part = nullptr, *base_comb = nullptr,
                 *base_gath = nullptr, *base_trsm = nullptr, *base_gp = nullptr,
                 *base_gc = nullptr, *base_tm = nullptr;
+  // each problem's R^sk, G and R^pre inside its workspace (ld n)
+  std::vector<double*> rsk, g, rpre;
 };
 
 // Tile shapes of the batched O(m n^2) kernels, per problem width bucket
@@ -84,6 +86,8 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
                const int* scalar_index = nullptr);
 // Enqueues the 14 batched launches.
 cudaError_t batch_launch(const BatchPlan& P, cudaStream_t s);
+// The first six of them: scalars, sketch (3), QRCP, rank rule.
+cudaError_t batch_launch_front(const BatchPlan& P, cudaStream_t s);
 cudaError_t sketch_set_attributes(int max_d);
 
 }  // namespace cqrrpt

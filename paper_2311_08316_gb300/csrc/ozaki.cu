@@ -60,72 +60,144 @@ __device__ __forceinline__ void digits8(double x, int e, __nv_bfloat16* out, int
   }
 }
 
-// e[c] for every column c of X (rows x cols, column-major): scale over the
-// column.  One CTA per column.
-__global__ void oz_colexp_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows,
-                                 int* __restrict__ e) {
+// Every helper step below has one body over a job and a tile index; the
+// single-problem kernel runs tiles blockIdx.x of one job, the batched
+// kernel maps CTA b to (job, tile) through a prefix table.
+
+// e[c] for every column c of the column operand: scale over the column.  One
+// CTA (256 threads) per column.
+__device__ __forceinline__ void colexp_body(const OzColSplit& J, int64_t tile) {
   __shared__ double red[32];
-  const int c = blockIdx.x;
-  const double* col = X + (int64_t)c * ldx;
+  const int c = (int)tile;
+  const double* col = J.X + (int64_t)c * J.ldx;
   double mx = 0.0;
-  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) mx = fmax(mx, fabs(col[r]));
+  for (int64_t r = threadIdx.x; r < J.rows; r += blockDim.x) mx = fmax(mx, fabs(col[r]));
   for (int off = 16; off >= 1; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmax(mx, red[i]);
-    e[c] = frexp_exp(mx);
+    J.e[c] = frexp_exp(mx);
   }
 }
 
-// e[r] for every row r over columns [0, cols) of X (column c of X is
-// column map[c] of the array when map is given).
-__global__ void oz_rowexp_kernel(const double* __restrict__ X, int64_t ldx, const int64_t* map,
-                                 int64_t rows, int cols, int* __restrict__ e) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= rows) return;
+// e[r] for every row r of the row operand over its K columns (column k is
+// column map[k] of X when map is given).  256 rows per CTA.
+__device__ __forceinline__ void rowexp_body(const OzRowSplit& J, int64_t tile) {
+  const int64_t r = tile * 256 + threadIdx.x;
+  if (r >= J.rows) return;
   double mx = 0.0;
-  for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(X[(map ? map[c] : (int64_t)c) * ldx + r]));
-  e[r] = frexp_exp(mx);
+  for (int c = 0; c < J.cols; ++c)
+    mx = fmax(mx, fabs(J.X[(J.map ? J.map[c] : (int64_t)c) * J.ldx + r]));
+  J.e[r] = frexp_exp(mx);
 }
 
-// Column operand: digit planes D[p][c][k] of X[k, c] (K = rows, padded to
-// kpad with zeros), scale e[c].
-__global__ void oz_split_cols_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows,
-                                     int cols, int64_t kpad, const int* __restrict__ e,
-                                     __nv_bfloat16* __restrict__ D, int64_t plane) {
-  const int c = blockIdx.y;
-  const int ec = e[c];
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < kpad;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const double x = k < rows ? X[(int64_t)c * ldx + k] : 0.0;
-    digits8(x, ec, D + (int64_t)c * kpad + k, plane);
+// Column operand planes D[p][c][k] of X[k, c] (K = rows, zero past rows up
+// to kpad), scale e[c].  CTA: one column, 2048 consecutive k.
+constexpr int kOzColChunk = 2048;
+__device__ __forceinline__ void splitcols_body(const OzColSplit& J, int64_t tile) {
+  const int64_t chunks = (J.kpad + kOzColChunk - 1) / kOzColChunk;
+  const int c = (int)(tile / chunks);
+  const int64_t k0 = (tile % chunks) * kOzColChunk;
+  const int ec = J.e[c];
+  const int64_t k1 = min64(k0 + kOzColChunk, J.kpad);
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const double x = k < J.rows ? J.X[(int64_t)c * J.ldx + k] : 0.0;
+    digits8(x, ec, J.D + (int64_t)c * J.kpad + k, J.plane);
   }
 }
 
-// Row operand: digit planes D[p][r][k] of X[r, k] for k in [0, cols) (K =
-// columns, padded to kpad; column k is column map[k] of the array when map
-// is given), scale e[r].  32 x 32 tiles transposed through shared memory so
-// that both the reads of X and the writes of D coalesce.
-__global__ void oz_split_rows_kernel(const double* __restrict__ X, int64_t ldx, const int64_t* map,
-                                     int64_t rows, int cols, int64_t kpad,
-                                     const int* __restrict__ e, __nv_bfloat16* __restrict__ D,
-                                     int64_t plane) {
-  __shared__ double tile[32][33];
-  const int64_t r0 = blockIdx.x * 32;
-  const int k0 = blockIdx.y * 32;
+// Row operand planes D[p][r][k] of X[r, map[k]] (K = cols, zero past cols up
+// to kpad), scale e[r].  32 x 32 tiles transposed through shared memory so
+// that both the reads of X and the writes of D coalesce (256 threads).
+__device__ __forceinline__ void splitrows_body(const OzRowSplit& J, int64_t tile) {
+  __shared__ double tl[32][33];
+  const int64_t tiles_r = (J.rows + 31) / 32;
+  const int64_t r0 = (tile % tiles_r) * 32;
+  const int k0 = (int)(tile / tiles_r) * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
   for (int j = ty; j < 32; j += 8) {
     const int64_t r = r0 + tx;
     const int k = k0 + j;
-    tile[j][tx] = (r < rows && k < cols) ? X[(map ? map[k] : (int64_t)k) * ldx + r] : 0.0;
+    tl[j][tx] = (r < J.rows && k < J.cols) ? J.X[(J.map ? J.map[k] : (int64_t)k) * J.ldx + r] : 0.0;
   }
   __syncthreads();
   for (int j = ty; j < 32; j += 8) {
     const int64_t r = r0 + j;
     const int k = k0 + tx;
-    if (r < rows && k < kpad) digits8(tile[tx][j], e[r], D + r * kpad + k, plane);
+    if (r < J.rows && k < J.kpad) digits8(tl[tx][j], J.e[r], J.D + r * J.kpad + k, J.plane);
   }
+}
+
+__global__ void __launch_bounds__(256) oz_colexp_kernel(OzColSplit J) { colexp_body(J, blockIdx.x); }
+__global__ void __launch_bounds__(256) oz_rowexp_kernel(OzRowSplit J) { rowexp_body(J, blockIdx.x); }
+__global__ void __launch_bounds__(256) oz_split_cols_kernel(OzColSplit J) {
+  splitcols_body(J, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(OzRowSplit J) {
+  splitrows_body(J, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) oz_colexp_batched_kernel(const OzColSplit* J,
+                                                                const int64_t* base, int n) {
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  colexp_body(J[j], t);
+}
+__global__ void __launch_bounds__(256) oz_rowexp_batched_kernel(const OzRowSplit* J,
+                                                                const int64_t* base, int n) {
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  rowexp_body(J[j], t);
+}
+__global__ void __launch_bounds__(256) oz_split_cols_batched_kernel(const OzColSplit* J,
+                                                                    const int64_t* base, int n) {
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  splitcols_body(J[j], t);
+}
+__global__ void __launch_bounds__(256) oz_split_rows_batched_kernel(const OzRowSplit* J,
+                                                                    const int64_t* base, int n) {
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  splitrows_body(J[j], t);
+}
+
+int64_t oz_rowexp_tiles(const OzRowSplit& J) { return (J.rows + 255) / 256; }
+int64_t oz_splitrows_tiles(const OzRowSplit& J) { return (J.rows + 31) / 32 * (J.kpad / 32); }
+int64_t oz_colexp_tiles(const OzColSplit& J) { return J.cols; }
+int64_t oz_splitcols_tiles(const OzColSplit& J) {
+  return (int64_t)J.cols * ((J.kpad + kOzColChunk - 1) / kOzColChunk);
+}
+
+cudaError_t oz_rowsplit(const OzRowSplit& J, cudaStream_t s) {
+  oz_rowexp_kernel<<<(unsigned)oz_rowexp_tiles(J), 256, 0, s>>>(J);
+  oz_split_rows_kernel<<<(unsigned)oz_splitrows_tiles(J), 256, 0, s>>>(J);
+  count_launches(2);
+  return cudaGetLastError();
+}
+cudaError_t oz_colsplit(const OzColSplit& J, cudaStream_t s) {
+  oz_colexp_kernel<<<(unsigned)oz_colexp_tiles(J), 256, 0, s>>>(J);
+  oz_split_cols_kernel<<<(unsigned)oz_splitcols_tiles(J), 256, 0, s>>>(J);
+  count_launches(2);
+  return cudaGetLastError();
+}
+cudaError_t oz_rowsplit_batched(const OzRowSplit* jobs, const int64_t* base_exp,
+                                int64_t tiles_exp, const int64_t* base_split,
+                                int64_t tiles_split, int njobs, cudaStream_t s) {
+  if (njobs <= 0 || tiles_exp <= 0) return cudaSuccess;
+  oz_rowexp_batched_kernel<<<(unsigned)tiles_exp, 256, 0, s>>>(jobs, base_exp, njobs);
+  oz_split_rows_batched_kernel<<<(unsigned)tiles_split, 256, 0, s>>>(jobs, base_split, njobs);
+  count_launches(2);
+  return cudaGetLastError();
+}
+cudaError_t oz_colsplit_batched(const OzColSplit* jobs, const int64_t* base_exp,
+                                int64_t tiles_exp, const int64_t* base_split,
+                                int64_t tiles_split, int njobs, cudaStream_t s) {
+  if (njobs <= 0 || tiles_exp <= 0) return cudaSuccess;
+  oz_colexp_batched_kernel<<<(unsigned)tiles_exp, 256, 0, s>>>(jobs, base_exp, njobs);
+  oz_split_cols_batched_kernel<<<(unsigned)tiles_split, 256, 0, s>>>(jobs, base_split, njobs);
+  count_launches(2);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -134,17 +206,35 @@ __global__ void oz_split_rows_kernel(const double* __restrict__ X, int64_t ldx, 
 constexpr int kOzKAlign = 32;  // K of every product padded to a multiple of this
 
 // G[a, c] = sum over K slices s of P_s[a, c] (ascending s), upper triangle
-// mirrored to the lower one.
-__global__ void oz_combine_sym_kernel(const double* __restrict__ P, int64_t slice, int nslices,
-                                      int n, double* __restrict__ G, int64_t ldg) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// mirrored to the lower one.  256 entries per CTA.
+__device__ __forceinline__ void combine_body(const OzCombine& J, int64_t tile) {
+  const int64_t idx = tile * 256 + threadIdx.x;
+  const int n = J.n;
   if (idx >= (int64_t)n * n) return;
   const int c = (int)(idx / n), a = (int)(idx - (int64_t)c * n);
   if (a > c) return;
   double s = 0.0;
-  for (int k = 0; k < nslices; ++k) s = __dadd_rn(s, P[(int64_t)k * slice + (int64_t)c * n + a]);
-  G[(int64_t)c * ldg + a] = s;
-  G[(int64_t)a * ldg + c] = s;
+  for (int k = 0; k < J.nslices; ++k)
+    s = __dadd_rn(s, J.P[(int64_t)k * J.slice + (int64_t)c * n + a]);
+  J.G[(int64_t)c * J.ldg + a] = s;
+  J.G[(int64_t)a * J.ldg + c] = s;
+}
+__global__ void __launch_bounds__(256) oz_combine_sym_kernel(OzCombine J) {
+  combine_body(J, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) oz_combine_sym_batched_kernel(const OzCombine* J,
+                                                                     const int64_t* base, int n) {
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  combine_body(J[j], t);
+}
+int64_t oz_combine_tiles(const OzCombine& J) { return ((int64_t)J.n * J.n + 255) / 256; }
+cudaError_t oz_combine_batched(const OzCombine* jobs, const int64_t* base, int64_t tiles,
+                               int njobs, cudaStream_t s) {
+  if (njobs <= 0 || tiles <= 0) return cudaSuccess;
+  oz_combine_sym_batched_kernel<<<(unsigned)tiles, 256, 0, s>>>(jobs, base, njobs);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // Gather: X[:, j] = B[:, cols[j]] for j < k (FP64 copy, column-major).
@@ -166,16 +256,14 @@ __global__ void oz_gather_kernel(const double* __restrict__ B, int64_t ldb,
 // lanes (T's column j is contiguous: coalesced) and reduced by a fixed
 // shuffle tree; the row being built lives in shared memory.
 constexpr int kTrinvWarps = 8;  // at most; fewer when k rows do not fit
-__global__ void __launch_bounds__(kTrinvWarps * 32)
-    oz_trinv_rows_kernel(const double* __restrict__ T, int64_t ldt, int k, double* __restrict__ W,
-                         int64_t ldw) {
-  extern __shared__ double trinv_rows[];  // [warps][k]
+__device__ __forceinline__ void trinv_body(const OzTrinv& J, int64_t tile, double* rows) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (int)(blockDim.x >> 5) + warp;
+  const int k = J.k;
+  const int i = (int)(tile * (int64_t)(blockDim.x >> 5)) + warp;
   if (i >= k) return;
-  double* w = trinv_rows + (int64_t)warp * k;
+  double* w = rows + (int64_t)warp * k;
   for (int j = i; j < k; ++j) {
-    const double* tc = T + (int64_t)j * ldt;
+    const double* tc = J.T + (int64_t)j * J.ldt;
     double part = 0.0;
     for (int t = i + lane; t < j; t += 32) part = __fma_rn(w[t], tc[t], part);
 #pragma unroll
@@ -183,7 +271,47 @@ __global__ void __launch_bounds__(kTrinvWarps * 32)
     if (lane == 0) w[j] = __ddiv_rn(((i == j) ? 1.0 : 0.0) - part, tc[j]);
     __syncwarp();
   }
-  for (int j = lane; j < k; j += 32) W[(int64_t)j * ldw + i] = j < i ? 0.0 : w[j];
+  for (int j = lane; j < k; j += 32) J.W[(int64_t)j * J.ldw + i] = j < i ? 0.0 : w[j];
+}
+__global__ void __launch_bounds__(kTrinvWarps * 32) oz_trinv_rows_kernel(OzTrinv J) {
+  extern __shared__ double trinv_rows[];  // [warps][k]
+  trinv_body(J, blockIdx.x, trinv_rows);
+}
+__global__ void __launch_bounds__(kTrinvWarps * 32)
+    oz_trinv_rows_batched_kernel(const OzTrinv* J, const int64_t* base, int n) {
+  extern __shared__ double trinv_rows[];  // [warps][max k]
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  trinv_body(J[j], t, trinv_rows);
+}
+// one row of W per warp in shared memory: as many warps as fit 200 KB
+int oz_trinv_warps(int kmax) {
+  int warps = (int)(200 * 1024 / ((int64_t)kmax * (int64_t)sizeof(double)));
+  return warps < 1 ? 1 : (warps > kTrinvWarps ? kTrinvWarps : warps);
+}
+int64_t oz_trinv_tiles(const OzTrinv& J, int warps) { return (J.k + warps - 1) / warps; }
+static cudaError_t trinv_smem_attr(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+cudaError_t oz_trinv(const OzTrinv& J, cudaStream_t s) {
+  const int warps = oz_trinv_warps(J.k);
+  const size_t smem = (size_t)warps * J.k * sizeof(double);
+  cudaError_t e = trinv_smem_attr((const void*)oz_trinv_rows_kernel, smem);
+  if (e != cudaSuccess) return e;
+  oz_trinv_rows_kernel<<<(unsigned)oz_trinv_tiles(J, warps), warps * 32, smem, s>>>(J);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t oz_trinv_batched(const OzTrinv* jobs, const int64_t* base, int64_t tiles, int njobs,
+                             int warps, int kmax, cudaStream_t s) {
+  if (njobs <= 0 || tiles <= 0) return cudaSuccess;
+  const size_t smem = (size_t)warps * kmax * sizeof(double);
+  cudaError_t e = trinv_smem_attr((const void*)oz_trinv_rows_batched_kernel, smem);
+  if (e != cudaSuccess) return e;
+  oz_trinv_rows_batched_kernel<<<(unsigned)tiles, warps * 32, smem, s>>>(jobs, base, njobs);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -228,6 +356,12 @@ int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out) {
          align256(nslices * (int64_t)k * k * 8);
 }
 
+int64_t oz_gram_slices(int64_t m, int k) {
+  int64_t ns = 1;
+  oz_gram_workspace(m, k, &ns);
+  return ns;
+}
+
 cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, int64_t ldg,
                     void* work, cudaStream_t s, int* status) {
   int64_t nslices = 1;
@@ -240,9 +374,9 @@ cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, 
   int* e = (int*)w;
   w += align256((int64_t)k * 4);
   double* P = (double*)w;
-  oz_colexp_kernel<<<k, 256, 0, s>>>(X, ldx, m, e);
-  dim3 sg((unsigned)min64((kpad + 255) / 256, 1024), (unsigned)k);
-  oz_split_cols_kernel<<<sg, 256, 0, s>>>(X, ldx, m, k, kpad, e, D, plane);
+  const OzColSplit cs{X, ldx, m, k, kpad, e, D, plane};
+  cudaError_t err0 = oz_colsplit(cs, s);
+  if (err0 != cudaSuccess) return err0;
   OzGemm G{};
   G.M = k; G.N = k; G.Kpad = kpad;
   G.kslice = ((kpad / kOzChunk + nslices - 1) / nslices) * kOzChunk;
@@ -254,9 +388,9 @@ cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, 
   cudaError_t err = oz_gemm_launch(G, s);
   if (err != cudaSuccess) return err;
   const int64_t ns = (kpad + G.kslice - 1) / G.kslice;
-  oz_combine_sym_kernel<<<(unsigned)(((int64_t)k * k + 255) / 256), 256, 0, s>>>(P, G.c_slice, (int)ns,
-                                                                                k, Gm, ldg);
-  count_launches(3);
+  const OzCombine cb{P, G.c_slice, (int)ns, k, Gm, ldg};
+  oz_combine_sym_kernel<<<(unsigned)oz_combine_tiles(cb), 256, 0, s>>>(cb);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -317,13 +451,11 @@ cudaError_t oz_mul(const TrsmCtx& c, const double* Xs, int64_t ldxs, const int64
                    const double* Ts, int64_t ldts, int n, double* C, int64_t ldc, int mode,
                    cudaStream_t s) {
   const int64_t kpad = round_up(kk, kOzKAlign);
-  oz_rowexp_kernel<<<(unsigned)((c.m + 255) / 256), 256, 0, s>>>(Xs, ldxs, map, c.m, kk, c.ea);
-  dim3 gr((unsigned)((c.m + 31) / 32), (unsigned)((kpad + 31) / 32));
-  oz_split_rows_kernel<<<gr, 256, 0, s>>>(Xs, ldxs, map, c.m, kk, kpad, c.ea, c.DA, c.m * kpad);
-  oz_colexp_kernel<<<n, 128, 0, s>>>(Ts, ldts, kk, c.eb);
-  dim3 gc((unsigned)((kpad + 255) / 256), (unsigned)n);
-  oz_split_cols_kernel<<<gc, 256, 0, s>>>(Ts, ldts, kk, n, kpad, c.eb, c.DB, (int64_t)n * kpad);
-  count_launches(4);
+  const OzRowSplit rs{Xs, ldxs, map, c.m, kk, kpad, c.ea, c.DA, c.m * kpad};
+  const OzColSplit cs{Ts, ldts, kk, n, kpad, c.eb, c.DB, (int64_t)n * kpad};
+  cudaError_t e0 = oz_rowsplit(rs, s);
+  if (e0 == cudaSuccess) e0 = oz_colsplit(cs, s);
+  if (e0 != cudaSuccess) return e0;
   OzGemm G{};
   G.M = c.m; G.N = n; G.Kpad = kpad; G.kslice = kpad;
   G.A = c.DA; G.a_plane = c.m * kpad; G.B = c.DB; G.b_plane = (int64_t)n * kpad;
@@ -391,19 +523,8 @@ cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const in
   carve_trsm(c, m, k, work);
   c.err = status;
   double* W = (double*)((char*)work + oz_trsm_workspace(m, k));
-  // one row of W per warp in shared memory: as many warps as fit 200 KB
-  int warps = (int)(200 * 1024 / ((int64_t)k * (int64_t)sizeof(double)));
-  warps = warps < 1 ? 1 : (warps > kTrinvWarps ? kTrinvWarps : warps);
-  const size_t trinv_smem = (size_t)warps * k * sizeof(double);
-  if (trinv_smem > 48 * 1024) {
-    cudaError_t ea = cudaFuncSetAttribute(oz_trinv_rows_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)trinv_smem);
-    if (ea != cudaSuccess) return ea;
-  }
-  oz_trinv_rows_kernel<<<(k + warps - 1) / warps, warps * 32, trinv_smem, s>>>(T, ldt, k, W, k);
-  count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  const OzTrinv ti{T, ldt, k, W, k};
+  cudaError_t e = oz_trinv(ti, s);
   if (e != cudaSuccess) return e;
   // the split reads B[:, cols] (the gather is fused into it) before the
   // product writes X (separate planes, so X may be B)

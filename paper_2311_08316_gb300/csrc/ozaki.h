@@ -38,6 +38,73 @@ struct OzGemm {
 // tcgen05 engine (ozaki_tc.cu)
 cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s);
 cudaError_t oz_gemm_launch(const OzGemm& G, cudaStream_t s);
+// many products in one launch: jobs, their two TMA maps each (A, B; 64-byte
+// aligned CUtensorMap objects in device memory) and the CTA prefix table
+// (job j owns CTAs [base[j], base[j + 1])).
+int64_t oz_gemm_tiles(const OzGemm& G);
+bool oz_gemm_valid(const OzGemm& G);
+bool oz_gemm_encode_maps(const OzGemm& G, void* maps_host /* 2 CUtensorMap */);
+constexpr size_t kOzMapBytes = 128;  // sizeof(CUtensorMap)
+cudaError_t oz_gemm_tc_batched_launch(const OzGemm* jobs, const void* maps, const int64_t* base,
+                                      int njobs, int64_t total_tiles, cudaStream_t s);
+
+// Operand splits and the small helper steps, as jobs so that one body serves
+// a single launch and a batched launch over many problems.
+struct OzRowSplit {   // row operand: digit planes of X[r, map[k]], K = cols
+  const double* X;
+  int64_t ldx;
+  const int64_t* map;  // column map or null (identity)
+  int64_t rows;
+  int cols;
+  int64_t kpad;
+  int* e;              // rows exponents (written)
+  __nv_bfloat16* D;    // planes [8][rows][kpad]
+  int64_t plane;
+};
+struct OzColSplit {   // column operand: digit planes of X[k, c], K = rows
+  const double* X;
+  int64_t ldx;
+  int64_t rows;
+  int cols;
+  int64_t kpad;
+  int* e;              // cols exponents (written)
+  __nv_bfloat16* D;    // planes [8][cols][kpad]
+  int64_t plane;
+};
+struct OzTrinv {      // W = T^{-1}, row by row
+  const double* T;
+  int64_t ldt;
+  int k;
+  double* W;
+  int64_t ldw;
+};
+struct OzCombine {    // G = sum of the K-slice partials, mirrored
+  const double* P;
+  int64_t slice;
+  int nslices;
+  int n;
+  double* G;
+  int64_t ldg;
+};
+int64_t oz_rowexp_tiles(const OzRowSplit& J);
+int64_t oz_splitrows_tiles(const OzRowSplit& J);
+int64_t oz_colexp_tiles(const OzColSplit& J);
+int64_t oz_splitcols_tiles(const OzColSplit& J);
+int oz_trinv_warps(int kmax);
+int64_t oz_trinv_tiles(const OzTrinv& J, int warps);
+int64_t oz_combine_tiles(const OzCombine& J);
+cudaError_t oz_rowsplit_batched(const OzRowSplit* jobs, const int64_t* base_exp,
+                                int64_t tiles_exp, const int64_t* base_split,
+                                int64_t tiles_split, int njobs, cudaStream_t s);
+cudaError_t oz_colsplit_batched(const OzColSplit* jobs, const int64_t* base_exp,
+                                int64_t tiles_exp, const int64_t* base_split,
+                                int64_t tiles_split, int njobs, cudaStream_t s);
+cudaError_t oz_trinv_batched(const OzTrinv* jobs, const int64_t* base, int64_t tiles, int njobs,
+                             int warps, int kmax, cudaStream_t s);
+cudaError_t oz_combine_batched(const OzCombine* jobs, const int64_t* base, int64_t tiles,
+                               int njobs, cudaStream_t s);
+// number of K slices the Gram of an m x k matrix uses (as oz_gram)
+int64_t oz_gram_slices(int64_t m, int k);
 int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out);
 cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* G, int64_t ldg,
                     void* work, cudaStream_t s, int* status = nullptr);

@@ -206,10 +206,11 @@ __device__ __forceinline__ void record_timeout(int* err) {
   if (err) atomicExch(err, kTimeout);
 }
 
-__global__ void __maxnreg__(96)
-    oz_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 OzGemm G) {
-  extern __shared__ unsigned char tc_smem_raw[];
+// One CTA's tile of one product.  tmA, tmB: the product's TMA maps (kernel
+// parameters of a single launch, or device memory for a batched launch).
+__device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                           const OzGemm& G, int64_t tile,
+                                           unsigned char* tc_smem_raw) {
   const uint32_t raw = smem_u32(tc_smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle tiles: 1024-aligned
   const uint32_t a_tiles = base;
@@ -225,7 +226,6 @@ __global__ void __maxnreg__(96)
   // tile of this CTA
   const int64_t tiles_m = (G.M + kTcBM - 1) / kTcBM;
   const int64_t tiles_n = (G.N + kTcBN - 1) / kTcBN;
-  const int64_t tile = blockIdx.x;
   const int64_t tn = tile % tiles_n, tm = (tile / tiles_n) % tiles_m;
   const int64_t ks = tile / (tiles_m * tiles_n);
   const int64_t m0 = tm * kTcBM;
@@ -289,8 +289,8 @@ __global__ void __maxnreg__(96)
         }
         mbar_expect_tx(full_bar(stage), kTcStageBytes);
         const int kx = (int)(kbeg + (int64_t)kst * kTcBK);
-        tma_load_3d(a_tiles + stage * kTcTileBytes, &tmA, full_bar(stage), kx, (int)m0, p - 1);
-        tma_load_3d(b_tiles + stage * kTcTileBytes, &tmB, full_bar(stage), kx, n0, q - 1);
+        tma_load_3d(a_tiles + stage * kTcTileBytes, tmA, full_bar(stage), kx, (int)m0, p - 1);
+        tma_load_3d(b_tiles + stage * kTcTileBytes, tmB, full_bar(stage), kx, n0, q - 1);
         ++issued;
         if (++stage == kTcStages) {
           stage = 0;
@@ -459,6 +459,24 @@ __global__ void __maxnreg__(96)
   }
 }
 
+__global__ void __maxnreg__(96)
+    oz_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 OzGemm G) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  oz_tc_body(&tmA, &tmB, G, blockIdx.x, tc_smem_raw);
+}
+
+// CTA b -> (job, tile) through the prefix table; maps[2 j], maps[2 j + 1]
+// are job j's A and B maps.
+__global__ void __maxnreg__(96)
+    oz_tc_batched_kernel(const OzGemm* __restrict__ jobs, const CUtensorMap* __restrict__ maps,
+                         const int64_t* __restrict__ base, int njobs) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  int64_t t;
+  const int j = find_problem(base, njobs, blockIdx.x, &t);
+  oz_tc_body(maps + 2 * j, maps + 2 * j + 1, jobs[j], t, tc_smem_raw);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -489,30 +507,62 @@ bool plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_
 
 }  // namespace
 
-cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s) {
+static cudaError_t tc_attributes() {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTcSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(oz_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kTcSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // TMA: 16-byte aligned bases, row strides and plane strides
-  // (several K slices: slice boundaries on stage boundaries; one slice may
-  // end mid-stage, TMA fills zeros past Kpad)
+  return cudaSuccess;
+}
+
+// TMA: 16-byte aligned bases, row strides and plane strides (several K
+// slices: slice boundaries on stage boundaries; one slice may end
+// mid-stage, TMA fills zeros past Kpad).
+bool oz_gemm_valid(const OzGemm& G) {
   const bool sliced = G.kslice < G.Kpad;
-  if (((uintptr_t)G.A & 15) || ((uintptr_t)G.B & 15) || (G.Kpad % 8) || (G.a_plane % 8) ||
-      (G.b_plane % 8) || G.kslice <= 0 || (sliced && (G.kslice % kTcBK)))
-    return cudaErrorInvalidValue;
-  alignas(64) CUtensorMap ma;
-  alignas(64) CUtensorMap mb;
-  if (!plane_map(&ma, G.A, G.M, G.Kpad, G.a_plane) ||
-      !plane_map(&mb, G.B, G.N, G.Kpad, G.b_plane))
-    return cudaErrorInvalidValue;
+  return !(((uintptr_t)G.A & 15) || ((uintptr_t)G.B & 15) || (G.Kpad % 8) || (G.a_plane % 8) ||
+           (G.b_plane % 8) || G.kslice <= 0 || (sliced && (G.kslice % kTcBK)));
+}
+
+int64_t oz_gemm_tiles(const OzGemm& G) {
   const int64_t tiles_m = (G.M + kTcBM - 1) / kTcBM;
   const int64_t tiles_n = (G.N + kTcBN - 1) / kTcBN;
   const int64_t nks = (G.Kpad + G.kslice - 1) / G.kslice;
-  oz_tc_kernel<<<(unsigned)(tiles_m * tiles_n * nks), kTcThreads, kTcSmem, s>>>(ma, mb, G);
+  return tiles_m * tiles_n * nks;
+}
+
+bool oz_gemm_encode_maps(const OzGemm& G, void* maps_host) {
+  static_assert(sizeof(CUtensorMap) == kOzMapBytes, "tensor map size");
+  CUtensorMap* m = (CUtensorMap*)maps_host;
+  return plane_map(&m[0], G.A, G.M, G.Kpad, G.a_plane) &&
+         plane_map(&m[1], G.B, G.N, G.Kpad, G.b_plane);
+}
+
+cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s) {
+  cudaError_t e = tc_attributes();
+  if (e != cudaSuccess) return e;
+  if (!oz_gemm_valid(G)) return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap mp[2];
+  if (!oz_gemm_encode_maps(G, mp)) return cudaErrorInvalidValue;
+  oz_tc_kernel<<<(unsigned)oz_gemm_tiles(G), kTcThreads, kTcSmem, s>>>(mp[0], mp[1], G);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_gemm_tc_batched_launch(const OzGemm* jobs, const void* maps, const int64_t* base,
+                                      int njobs, int64_t total_tiles, cudaStream_t s) {
+  if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+  cudaError_t e = tc_attributes();
+  if (e != cudaSuccess) return e;
+  if ((uintptr_t)maps & 63) return cudaErrorInvalidValue;
+  oz_tc_batched_kernel<<<(unsigned)total_tiles, kTcThreads, kTcSmem, s>>>(
+      jobs, (const CUtensorMap*)maps, base, njobs);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -149,3 +149,30 @@ def test_batched_autotune_picks_shapes_and_keeps_results(C):
         for x in (r, r2):
             assert bits_equal(host(x.J), ref.J)
             assert bits_equal(host(x.Q), ref.Q) and bits_equal(host(x.R), ref.R)
+
+
+def test_batched_split_bf16_matches_single_split_and_oracle(C):
+    # lines 4, 5, 7 as batched split products: every problem bit-identical to
+    # cqrrpt_d in CQRRPT_SPLITBF16 (same jobs), J and k equal to the oracle's,
+    # residuals at FP64 level
+    mats, tols = make_batch(10, 8)
+    mats.append(np.asfortranarray(W.planted(3000, 140, W.logspaced(140, -9.0), 77).numpy()))
+    tols.append(1e-12)
+    seeds = [600 + i for i in range(len(mats))]
+    As = [gpu(A) for A in mats]
+    res, _, _ = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, precision=C.SPLITBF16)
+    for i, (A, r) in enumerate(zip(mats, res)):
+        ref = oracle.cqrrpt(A, 1.25, 4, tols[i], seeds[i])
+        assert r.status == ref.status and r.k == ref.k, (i, r.status, r.k, ref.k)
+        assert bits_equal(host(r.J), ref.J), i
+        one = C.cqrrpt(As[i], 1.25, 4, tols[i], seeds[i], precision=C.SPLITBF16)
+        assert one.k == r.k
+        assert torch.equal(one.Q[:, :r.k], r.Q[:, :r.k]) and torch.equal(one.R[:r.k], r.R[:r.k]), i
+        if r.k:
+            Q, R = host(r.Q)[:, :r.k], host(r.R)[:r.k]
+            AJ = A[:, ref.J]
+            # planted rank: the dropped 1e-15 noise tail bounds the residual
+            m, n = A.shape
+            bound = 1e-12 if r.k == n else max(1e-12, 10e-15 * np.sqrt(m * n) / np.linalg.norm(A))
+            assert np.linalg.norm(AJ - Q @ R) / np.linalg.norm(A) <= bound, i
+            assert np.linalg.norm(Q.T @ Q - np.eye(r.k), 2) <= 1e-12, i

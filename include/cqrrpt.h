@@ -227,17 +227,19 @@ typedef struct cqrrpt_server_s* cqrrpt_server;
 
 /* A server that factors submitted requests with continuous batching: a
  * scheduler thread admits requests in arrival order while their device
- * footprint (A, Q, R, J and, for requests of the batched route, the batched
+ * footprint (A, Q, R, J and, for requests of a batched route, the batched
  * workspace) fits hbm_budget_bytes (one allocation made here) and at most
  * max_inflight are in flight, and copies their inputs in while earlier work
  * runs.  Whenever the GPU is free it starts the next unit of work, chosen by
- * the oldest request whose input has arrived: either one batched pass over
- * every arrived FP64 request with n <= 256 (requests that arrived while the
- * previous pass ran join the next one), or a single-problem run (cqrrpt_d on
- * the whole GPU) of a split-BF16 request or of an FP64 request with n > 256.
- * Results are bit-identical to standalone calls of the same precision.  The
- * server owns `h` until cqrrpt_server_destroy (single-problem runs use its
- * workspace, outside the budget).  The current device is used. */
+ * the oldest request whose input has arrived: one batched pass over every
+ * arrived request of the same precision with n <= 256 (CQRRPT_FP64 or
+ * CQRRPT_SPLITBF16; requests that arrived while the previous pass ran join
+ * the next one), or a single-problem run (cqrrpt_d on the whole GPU) of a
+ * request with n > 256 or in CQRRPT_SPLITBF16_CHOLQR2.  Results are
+ * bit-identical to standalone calls of the same precision.  The server owns
+ * `h` until cqrrpt_server_destroy (single-problem runs and the split-BF16
+ * digit planes use its workspaces, outside the budget).  The current device
+ * is used. */
 int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight, double gamma,
                          int nnz_per_col, cqrrpt_server* server);
 

@@ -731,15 +731,16 @@ int split_gram_step(cqrrpt_handle h, const std::vector<int>& ids,
 // the single-problem split path's, so results are bit-identical to
 // cqrrpt_d in CQRRPT_SPLITBF16.  Waits for the stream twice (the products
 // are sized by each problem's k).
-int batched_split_run(cqrrpt_handle h, std::vector<BatchProblem>& probs, cudaStream_t stream) {
+}  // namespace
+
+namespace cqrrpt {
+
+// The batched split-BF16 steps of a planned batch whose tables are already
+// on the device (in stream order): everything from the FP64 front on.
+int batched_split_exec(cqrrpt_handle h, BatchPlan& P, const std::vector<BatchProblem>& probs,
+                       cudaStream_t stream) {
   const int batch = (int)probs.size();
-  const BatchWs W = batch_ws(h, batch);
-  BatchPlan P;
-  P.scalars = W.scalars;
-  P.tables = W.tables;
-  batch_plan(P, batch, probs.data(), W.per_problem, nullptr, &h->tune);
-  int st = stage_tables(h, P, stream);
-  if (st != kOk) return st;
+  int st = kOk;
   if (sketch_set_attributes(P.max_d) != cudaSuccess) return kCudaError;
   if (batch_launch_front(P, stream) != cudaSuccess) return kCudaError;
   if ((st = read_scalars(h, P.scalars, batch, stream)) != kOk) return st;
@@ -785,6 +786,22 @@ int batched_split_run(cqrrpt_handle h, std::vector<BatchProblem>& probs, cudaStr
       launch_finalize_batched(P.fi, batch, stream) != cudaSuccess)
     return kCudaError;
   return kOk;
+}
+
+}  // namespace cqrrpt
+
+namespace {
+
+int batched_split_run(cqrrpt_handle h, std::vector<BatchProblem>& probs, cudaStream_t stream) {
+  const int batch = (int)probs.size();
+  const BatchWs W = batch_ws(h, batch);
+  BatchPlan P;
+  P.scalars = W.scalars;
+  P.tables = W.tables;
+  batch_plan(P, batch, probs.data(), W.per_problem, nullptr, &h->tune);
+  int st = stage_tables(h, P, stream);
+  if (st != kOk) return st;
+  return batched_split_exec(h, P, probs, stream);
 }
 
 int batched_run(cqrrpt_handle h, std::vector<BatchProblem>& probs, cudaStream_t stream) {

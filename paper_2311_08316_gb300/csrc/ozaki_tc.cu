@@ -9,11 +9,12 @@
 //
 // CTA tile 128 x 128 of C for one K slice; 18 warps (at most 96 registers a
 // thread, so that five warps fit one SM sub-partition's register file):
-//   warp 0      TMA producer: for every digit pair (p, q) and every 64-wide
-//               K stage, loads the 128 x 64 tiles of A_p and B_q (128-byte
-//               swizzle) into a 6-deep shared-memory ring;
+//   warp 0      TMA producer: for every digit pair (p, q) and every 128-wide
+//               K stage, loads the 128 x 128 tiles of A_p and B_q (two
+//               128-byte-swizzle atoms of 64 K each) into a 3-deep
+//               shared-memory ring;
 //   warp 1      allocates the 512 tensor-memory columns, and one thread
-//               issues the MMAs (M = 128, N = 128, K = 16; four per stage)
+//               issues the MMAs (M = 128, N = 128, K = 16; eight per stage)
 //               into one of two FP32 accumulators (columns 0-127, 128-255):
 //               one accumulator per chunk (at most 1024 K terms of one
 //               level: one pair's K range, or several same-level pairs when
@@ -34,7 +35,7 @@
 //               once to FP64, scaled by 2^(ea + eb - 7 s_g) and stored into C
 //               (group 1: C = v, or C - v; group 2: C + v, or C - v).
 // Work order inside a CTA: group, then 1024-term K chunk, then the group's
-// pairs (level order), then the chunk's 64-wide K stages, so that the digit
+// pairs (level order), then the chunk's 128-wide K stages, so that the digit
 // planes of one chunk are reused by every pair of the group while they are
 // hot in L2.  CTA order: the column tiles of one row block are consecutive
 // (they share the row block's A planes), K slices outermost.
@@ -56,10 +57,12 @@ namespace cqrrpt {
 
 namespace {
 
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64, kTcStages = 6;
-constexpr int kTcTileBytes = kTcBM * kTcBK * 2;            // 16 KB, one operand tile
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 3;
+constexpr int kTcAtomK = 64;                                // K of one 128-byte swizzle atom
+constexpr int kTcAtomBytes = kTcBM * kTcAtomK * 2;          // 16 KB: 128 rows x 64 K
+constexpr int kTcTileBytes = kTcBM * kTcBK * 2;             // 32 KB, one operand tile
 constexpr int kTcStageBytes = 2 * kTcTileBytes;             // A + B
-constexpr int kTcChunkStages = kOzChunk / kTcBK;            // 16 stages = 1024 K terms
+constexpr int kTcChunkStages = kOzChunk / kTcBK;            // 8 stages = 1024 K terms
 constexpr int kTcDrainWarps = 16;                          // 4 per TMEM lane quarter
 constexpr int kTcThreads = 32 * (2 + kTcDrainWarps);        // 18 warps: <= 96 registers
 constexpr int kTcAccBufs = 2;                               // FP32 accumulators in TMEM
@@ -289,8 +292,13 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
         }
         mbar_expect_tx(full_bar(stage), kTcStageBytes);
         const int kx = (int)(kbeg + (int64_t)kst * kTcBK);
-        tma_load_3d(a_tiles + stage * kTcTileBytes, tmA, full_bar(stage), kx, (int)m0, p - 1);
-        tma_load_3d(b_tiles + stage * kTcTileBytes, tmB, full_bar(stage), kx, n0, q - 1);
+#pragma unroll
+        for (int at = 0; at < kTcBK / kTcAtomK; ++at) {  // one swizzle atom per copy
+          tma_load_3d(a_tiles + stage * kTcTileBytes + at * kTcAtomBytes, tmA, full_bar(stage),
+                      kx + at * kTcAtomK, (int)m0, p - 1);
+          tma_load_3d(b_tiles + stage * kTcTileBytes + at * kTcAtomBytes, tmB, full_bar(stage),
+                      kx + at * kTcAtomK, n0, q - 1);
+        }
         ++issued;
         if (++stage == kTcStages) {
           stage = 0;
@@ -341,12 +349,15 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
               break;
             }
             tc_fence_after();
-            const uint64_t ad = sw128_desc(a_tiles + stage * kTcTileBytes);
-            const uint64_t bd = sw128_desc(b_tiles + stage * kTcTileBytes);
 #pragma unroll
-            for (int kk = 0; kk < kTcBK / 16; ++kk)  // K = 16 per MMA: +32 bytes
-              umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                        (pr > pi || j > 0 || kk > 0) ? 1u : 0u);
+            for (int at = 0; at < kTcBK / kTcAtomK; ++at) {
+              const uint64_t ad = sw128_desc(a_tiles + stage * kTcTileBytes + at * kTcAtomBytes);
+              const uint64_t bd = sw128_desc(b_tiles + stage * kTcTileBytes + at * kTcAtomBytes);
+#pragma unroll
+              for (int kk = 0; kk < kTcAtomK / 16; ++kk)  // K = 16 per MMA: +32 bytes
+                umma_bf16(d, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                          (pr > pi || j > 0 || at > 0 || kk > 0) ? 1u : 0u);
+            }
             umma_commit(empty_bar(stage));
             any = true;
             if (++stage == kTcStages) {
@@ -498,7 +509,7 @@ bool plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_
   if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)kOzDigits};
   const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)plane * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)kTcAtomK, (cuuint32_t)kTcBM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

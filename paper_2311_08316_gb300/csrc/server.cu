@@ -7,14 +7,15 @@
 //     arena over one allocation made at creation -- and at most max_inflight
 //     are in flight; the host -> device copy of an admitted request's A is
 //     issued at once on a copy stream, overlapping the running wave;
-//   * whenever no wave is running, either launches one batched pass (the
-//     batched kernels of batched.cu) over every admitted small FP64 request
-//     whose input has arrived -- requests that arrived while the previous
-//     wave ran join the next one -- or, when the oldest arrived request is
-//     routed to the single-problem path (split-BF16 precision, or n above
-//     kBatchMaxN, where the one-CTA-per-problem QRCP and Cholesky of the
-//     batched kernels would serialise), runs that request alone on the whole
-//     GPU;
+//   * whenever no wave is running, starts the next unit of work, chosen by
+//     the oldest request whose input has arrived: one batched pass over
+//     every arrived request of its kind (FP64 waves run the batched kernels
+//     of batched.cu, split-BF16 waves the batched split path) -- requests
+//     that arrived while the previous wave ran join the next one -- or, for
+//     a request routed to the single-problem path (n above kBatchMaxN, where
+//     the one-CTA-per-problem QRCP and Cholesky of the batched kernels would
+//     serialise, or the mode with a second Cholesky-QR pass), that request
+//     alone on the whole GPU;
 //   * when a wave completes, copies each result (Q, R, J, k, status) back on
 //     the copy stream, frees the request's arena block when the copy is done
 //     and records the completion time.
@@ -41,6 +42,8 @@ namespace cqrrpt {
 
 int handle_finalize(cqrrpt_handle h, int64_t* k_out, int* status_out, cudaStream_t s);
 const BatchTuning* handle_tuning(cqrrpt_handle h);
+int batched_split_exec(cqrrpt_handle h, BatchPlan& P, const std::vector<BatchProblem>& probs,
+                       cudaStream_t stream);
 
 namespace {
 
@@ -111,12 +114,13 @@ struct Req {
   cqrrpt_result res{};
 };
 
-// Widest problem a batched wave takes; wider ones (and every split-BF16
-// request) run alone through cqrrpt_d with the multi-CTA QRCP and Cholesky.
+// Widest problem a batched wave takes; wider ones (and the split-BF16 mode
+// with a second Cholesky-QR pass) run alone through cqrrpt_d with the
+// multi-CTA QRCP and Cholesky.
 constexpr int64_t kBatchMaxN = 256;
 
 bool single_route(const cqrrpt_request& r) {
-  return r.precision != CQRRPT_FP64 || r.n > kBatchMaxN;
+  return r.precision == CQRRPT_SPLITBF16_CHOLQR2 || r.n > kBatchMaxN;
 }
 
 // Device bytes a request holds while in flight.  Requests on the single
@@ -254,22 +258,26 @@ bool Server::step() {
   // launch the next unit of work: the oldest arrived request decides
   // between a batched wave and a single-path run
   if (!wave_running) {
+    // arrived requests: single route, or one of the two batched routes
+    // (FP64 waves and split-BF16 waves); the oldest decides what runs
     std::vector<Req*> ready;
     Req* solo = nullptr;
-    double ready_first = 0.0;
+    Req* oldest = nullptr;
     {
       std::lock_guard<std::mutex> lock(mu);
       for (Req* q : inflight) {
         if (q->state != kStaging || cudaEventQuery(q->h2d) != cudaSuccess) continue;
-        if (single_route(q->r)) {
-          if (!solo || q->t_submit < solo->t_submit) solo = q;
-        } else {
-          if (ready.empty() || q->t_submit < ready_first) ready_first = q->t_submit;
-          ready.push_back(q);
-        }
+        if (!oldest || q->t_submit < oldest->t_submit) oldest = q;
+        if (single_route(q->r) && (!solo || q->t_submit < solo->t_submit)) solo = q;
       }
+      if (oldest && !single_route(oldest->r))
+        for (Req* q : inflight)
+          if (q->state == kStaging && !single_route(q->r) &&
+              q->r.precision == oldest->r.precision && cudaEventQuery(q->h2d) == cudaSuccess)
+            ready.push_back(q);
     }
-    if (!ready.empty() && !(solo && solo->t_submit < ready_first)) {
+    const bool split_wave = !ready.empty() && oldest->r.precision != CQRRPT_FP64;
+    if (!ready.empty()) {
       std::vector<BatchProblem> probs(ready.size());
       std::vector<char*> wss(ready.size());
       for (size_t i = 0; i < ready.size(); ++i) {
@@ -296,12 +304,18 @@ bool Server::step() {
       memcpy(stage, P.image.data(), img);
       cudaMemcpyAsync(P.tables, stage, img, cudaMemcpyHostToDevice, compute);
       cudaEventRecord(stage_ev, compute);
-      sketch_set_attributes(P.max_d);
-      if (batch_launch(P, compute) != cudaSuccess) { error = kCudaError; return false; }
       {
         std::lock_guard<std::mutex> lock(mu);
         for (Req* q : ready) q->state = kRunning;
         wave = ready;
+      }
+      if (split_wave) {
+        // the split products are sized by each problem's k: this waits for
+        // the compute stream twice
+        if (batched_split_exec(h, P, probs, compute) != kOk) { error = kCudaError; return false; }
+      } else {
+        sketch_set_attributes(P.max_d);
+        if (batch_launch(P, compute) != cudaSuccess) { error = kCudaError; return false; }
       }
       cudaEventRecord(wave_done, compute);
       wave_running = true;

@@ -45,8 +45,11 @@
  *   - All other sums (substitution, Cholesky, triangular product) run in
  *     ascending index order, one fma per term.
  *   - QRCP pivots on the largest partial column norm, lowest position on
- *     exact ties; the LAPACK dlaqp2 downdate with the Drmac-Bujanovic
- *     recompute safeguard (threshold sqrt(u)); after the n steps every row
+ *     exact ties; reflectors as LAPACK's dlarfg: beta = -sign(alpha) ||x||,
+ *     tau = (beta - alpha) / beta, v = x * (1 / (alpha - beta)) (one
+ *     division, then a scaling); the LAPACK dlaqp2 downdate with the
+ *     Drmac-Bujanovic recompute safeguard (threshold sqrt(u)); after the
+ *     n steps every row
  *     of R^sk with a negative diagonal is negated, so diag(R^sk) >= 0 and
  *     the returned R has a positive diagonal.
  *   - Plain a*b+c is never contracted: build with -ffp-contract=off; every
@@ -274,8 +277,10 @@ void oracle_qrcp(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J, doubl
             double nrm = sqrt(fma(alpha, alpha, sumsq));
             double beta = (alpha >= 0.0) ? -nrm : nrm;
             tau = (beta - alpha) / beta;
-            double denom = alpha - beta;
-            for (int64_t r = j + 1; r < d; ++r) colj[r] = colj[r] / denom;
+            /* v = x (1 / (alpha - beta)): one division, then a scaling, as
+             * LAPACK's reflector generator (dlarfg) does in GEQP3 */
+            double rden = 1.0 / (alpha - beta);
+            for (int64_t r = j + 1; r < d; ++r) colj[r] = colj[r] * rden;
             colj[j] = beta;
         }
         if (tau_out) tau_out[j] = tau;

@@ -10,8 +10,10 @@
 // pivot exchange moves no data.  Each of the n steps is:
 //   1. every CTA reduces the per-CTA candidates (largest partial norm,
 //      lowest position on exact ties) to the same pivot column P;
-//   2. the owner of P forms the reflector H = I - tau v v^T (v written over
-//      the column below the diagonal, beta on it); CTA 0 records the swap;
+//   2. the owner of P forms the reflector H = I - tau v v^T as LAPACK's
+//      dlarfg: beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta,
+//      v = x * (1 / (alpha - beta)) (v written over the column below the
+//      diagonal, beta on it); CTA 0 records the swap;
 //      -- barrier --
 //   3. every CTA applies H to its unpivoted columns (w = v^T x by dot32,
 //      x += v (-tau w) with one fma per element) and downdates their norms
@@ -69,7 +71,7 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
   const int nwarps = blockDim.x >> 5;
   int* status = &sc->status;
   __shared__ int sh_P, sh_p;
-  __shared__ double sh_tau, sh_beta, sh_denom;
+  __shared__ double sh_tau, sh_beta, sh_denom;  // sh_denom: 1 / (alpha - beta)
   __shared__ int sh_nz;
   __shared__ double red_val[32];
   __shared__ int red_pos[32];
@@ -161,16 +163,16 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
             const double beta = (alpha >= 0.0) ? -nrm : nrm;
             sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
             sh_beta = beta;
-            sh_denom = __dsub_rn(alpha, beta);
+            sh_denom = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
             sh_nz = 1;
           }
         }
       }
       __syncthreads();
       if (sh_nz) {
-        const double denom = sh_denom;
+        const double rden = sh_denom;
         for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x)
-          colP[r] = __ddiv_rn(__ldcg(colP + r), denom);
+          colP[r] = __dmul_rn(__ldcg(colP + r), rden);
         if (threadIdx.x == 0) colP[j] = sh_beta;
       }
       if (threadIdx.x == 0) w.tau[j] = sh_tau;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   const int nown = bid < n ? (n - bid + G - 1) / G : 0;
   double* vbuf = cache + (int64_t)nown * d;
   __shared__ int sh_P, sh_p;
-  __shared__ double sh_tau, sh_beta, sh_denom;
+  __shared__ double sh_tau, sh_beta, sh_denom;  // sh_denom: 1 / (alpha - beta)
   __shared__ int sh_nz;
   __shared__ double red_val[32];
   __shared__ int red_pos[32];
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
             const double beta = (alpha >= 0.0) ? -nrm : nrm;
             sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
             sh_beta = beta;
-            sh_denom = __dsub_rn(alpha, beta);
+            sh_denom = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
             sh_nz = 1;
           }
         }
@@ -366,9 +368,9 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
       __syncthreads();
       double* gP = X + (int64_t)P * ldx;
       if (sh_nz) {
-        const double denom = sh_denom;
+        const double rden = sh_denom;
         for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x) {
-          const double v = __ddiv_rn(colP[r], denom);
+          const double v = __dmul_rn(colP[r], rden);
           colP[r] = v;
           gP[r] = v;
         }

@@ -249,12 +249,18 @@ __device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len)
   return warp_tree_sum32(acc);
 }
 
-// Same steps and arithmetic as qrcp_body, with every CTA's owned columns
-// held in shared memory for the whole factorisation (cache[q * d + r] is
-// row r of physical column bid + G q) and the reflector vector of each step
-// staged once per CTA in shared memory; the pivot column's reflector is also
-// written to global memory for the other CTAs, and all owned columns are
-// written back at the end.  Used when the owned columns fit.
+// Same arithmetic as qrcp_body, one grid barrier per step instead of two.
+// Every CTA keeps its owned columns (cache[q * d + r] is row r of physical
+// column bid + G q), their partial norms and its own copy of the
+// position <-> column maps in shared memory for the whole factorisation.
+// At the end of a step a CTA publishes its best candidate and writes that
+// column's current rows j+1.. to X (global); after the barrier every CTA
+// picks the same pivot P, reads P's column from X and forms the same
+// reflector itself (same dot32, same operations: identical bits on every
+// CTA), updates its maps with the same swap and applies the reflector to its
+// columns -- so no second barrier is needed to broadcast the reflector.  The
+// owner of P also stores beta and v into its cached column.  All owned
+// columns are written back at the end; CTA 0 writes the maps and tau.
 __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, double tol3z) {
   extern __shared__ double cache[];
   const int G = gridDim.x, bid = blockIdx.x;
@@ -267,9 +273,13 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   const int nwarps = blockDim.x >> 5;
   int* status = &sc->status;
   const int nown = bid < n ? (n - bid + G - 1) / G : 0;
-  double* vbuf = cache + (int64_t)nown * d;
+  double* vbuf = cache + (int64_t)nown * d;          // d
+  double* vn1 = vbuf + d;                             // nown
+  double* vn2 = vn1 + nown;                           // nown
+  int* phys = (int*)(vn2 + nown);                     // n
+  int* posof = phys + n;                              // n
   __shared__ int sh_P, sh_p;
-  __shared__ double sh_tau, sh_beta, sh_denom;  // sh_denom: 1 / (alpha - beta)
+  __shared__ double sh_tau, sh_beta, sh_rden;
   __shared__ int sh_nz;
   __shared__ double red_val[32];
   __shared__ int red_pos[32];
@@ -281,45 +291,56 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     const double* src = X + (int64_t)(bid + G * q) * ldx;
     for (int r = threadIdx.x; r < d; r += blockDim.x) cache[(int64_t)q * d + r] = src[r];
   }
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    phys[c] = c;
+    posof[c] = c;
+  }
   __syncthreads();
   for (int q = warp; q < nown; q += nwarps) {
-    const int c = bid + G * q;
     const double s = warp_dot32_self_smem(cache + (int64_t)q * d, d);
     if (lane == 0) {
       const double v = __dsqrt_rn(s);
-      w.vn1[c] = v;
-      w.vn2[c] = v;
-      w.phys[c] = c;
-      w.posof[c] = c;
+      vn1[q] = v;
+      vn2[q] = v;
     }
   }
+  __syncthreads();
 
+  // local best unpivoted column (largest partial norm, lowest position on
+  // exact ties); its rows j_done+1.. go to X for the other CTAs
   auto publish_candidate = [&](int j_done) {
     double bv = -1.0;
-    int bp = 0x7fffffff, bc = -1;
+    int bp = 0x7fffffff, bq = -1;
     for (int q = warp; q < nown; q += nwarps) {
       const int c = bid + G * q;
-      const int pc = __ldcg(w.posof + c);
+      const int pc = posof[c];
       if (pc <= j_done) continue;
-      const double v = __ldcg(w.vn1 + c);
-      if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bc = c; }
+      const double v = vn1[q];
+      if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bq = q; }
     }
-    if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bc; }
+    if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bq; }
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int i = 1; i < nwarps; ++i)
-        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bc = red_col[i]; }
+        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bq = red_col[i]; }
       w.cand_val[bid] = bv;
       w.cand_pos[bid] = bp;
-      w.cand_col[bid] = bc;
+      w.cand_col[bid] = bq >= 0 ? bid + G * bq : -1;
+      red_col[0] = bq;
+    }
+    __syncthreads();
+    const int q = red_col[0];
+    if (q >= 0) {
+      double* dst = X + (int64_t)(bid + G * q) * ldx;
+      const double* src = cache + (int64_t)q * d;
+      for (int r = j_done + 1 + threadIdx.x; r < d; r += blockDim.x) dst[r] = src[r];
     }
   };
-  __syncthreads();
   publish_candidate(-1);
   bool ok = grid_sync(&sc->bar, G, status);
 
   for (int j = 0; ok && j < n; ++j) {
-    // 1. global pivot
+    // 1. global pivot (every CTA alike)
     if (warp == 0) {
       double bv = -1.0;
       int bp = 0x7fffffff, bc = -1;
@@ -345,59 +366,56 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
       ok = false;
       break;
     }
-    // 2. reflector by the owner of P (from its cache); swap record by CTA 0
-    if (P % G == bid) {
-      double* colP = cache + (int64_t)((P - bid) / G) * d;
-      if (warp == 0) {
-        const double alpha = colP[j];
-        const double sumsq = (j + 1 < d) ? warp_dot32_self_smem(colP + j + 1, d - j - 1) : 0.0;
-        if (lane == 0) {
-          if (sumsq == 0.0) {
-            sh_tau = 0.0;
-            sh_nz = 0;
-          } else {
-            const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
-            const double beta = (alpha >= 0.0) ? -nrm : nrm;
-            sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
-            sh_beta = beta;
-            sh_denom = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
-            sh_nz = 1;
-          }
+    // 2. the reflector of column P (published rows j.. in X), by every CTA
+    const double* gP = X + (int64_t)P * ldx;
+    if (warp == 0) {
+      const double alpha = __ldcg(gP + j);
+      const double sumsq = (j + 1 < d) ? warp_dot32_self(gP + j + 1, d - j - 1) : 0.0;
+      if (lane == 0) {
+        if (sumsq == 0.0) {
+          sh_tau = 0.0;
+          sh_nz = 0;
+        } else {
+          const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
+          const double beta = (alpha >= 0.0) ? -nrm : nrm;
+          sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
+          sh_beta = beta;
+          sh_rden = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
+          sh_nz = 1;
         }
       }
-      __syncthreads();
-      double* gP = X + (int64_t)P * ldx;
-      if (sh_nz) {
-        const double rden = sh_denom;
-        for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x) {
-          const double v = __dmul_rn(colP[r], rden);
-          colP[r] = v;
-          gP[r] = v;
-        }
-        if (threadIdx.x == 0) { colP[j] = sh_beta; gP[j] = sh_beta; }
-      } else {
-        for (int r = j + 1 + threadIdx.x; r < d; r += blockDim.x) gP[r] = colP[r];
-      }
-      if (threadIdx.x == 0) w.tau[j] = sh_tau;
     }
-    if (bid == 0 && threadIdx.x == 0) {
-      const int Pj = __ldcg(w.phys + j);
-      w.phys[p] = Pj;
-      w.posof[Pj] = p;
-      w.phys[j] = P;
-      w.posof[P] = j;
-    }
-    if (!grid_sync(&sc->bar, G, status)) { ok = false; break; }
-
-    // 3. stage v, apply H to owned unpivoted columns, downdate norms
-    const double tau = __ldcg(w.tau + j);
-    const int len = d - j;
-    const double* gP = X + (int64_t)P * ldx + j;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = (i == 0) ? 1.0 : __ldcg(gP + i);
     __syncthreads();
+    const int len = d - j;
+    const double tau = sh_tau;
+    const bool nz = sh_nz != 0;
+    const double rden = sh_rden;
+    const bool owner = (P % G == bid);
+    double* cP = owner ? cache + (int64_t)((P - bid) / G) * d : nullptr;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      double v = 1.0;
+      if (i > 0) {
+        const double x = __ldcg(gP + j + i);
+        v = nz ? __dmul_rn(x, rden) : x;
+        if (owner) cP[j + i] = v;
+      }
+      vbuf[i] = v;
+    }
+    if (threadIdx.x == 0) {
+      if (owner && nz) cP[j] = sh_beta;
+      const int Pj = phys[j];
+      phys[p] = Pj;
+      posof[Pj] = p;
+      phys[j] = P;
+      posof[P] = j;
+      if (bid == 0) w.tau[j] = tau;
+    }
+    __syncthreads();
+
+    // 3. apply H to owned unpivoted columns, downdate norms
     for (int q = warp; q < nown; q += nwarps) {
       const int c = bid + G * q;
-      if (__ldcg(w.posof + c) <= j) continue;
+      if (posof[c] <= j) continue;
       double* colc = cache + (int64_t)q * d + j;
       double acc = 0.0;
       for (int i = lane; i < len; i += 32) acc = __fma_rn(vbuf[i], colc[i], acc);
@@ -405,23 +423,23 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
       const double t = __dmul_rn(-tau, wsum);
       for (int i = lane; i < len; i += 32) colc[i] = __fma_rn(vbuf[i], t, colc[i]);
       __syncwarp();
-      const double v1 = __ldcg(w.vn1 + c);
+      const double v1 = vn1[q];
       if (v1 != 0.0) {
-        const double v2 = __ldcg(w.vn2 + c);
+        const double v2 = vn2[q];
         double temp = __ddiv_rn(fabs(colc[0]), v1);
         temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
         temp = temp > 0.0 ? temp : 0.0;
         const double ratio = __ddiv_rn(v1, v2);
         const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
         if (temp2 <= tol3z) {
-          const double s = (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1) : 0.0;
+          const double s2 = (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1) : 0.0;
           if (lane == 0) {
-            const double nv = (j + 1 < d) ? __dsqrt_rn(s) : 0.0;
-            w.vn1[c] = nv;
-            w.vn2[c] = nv;
+            const double nv = (j + 1 < d) ? __dsqrt_rn(s2) : 0.0;
+            vn1[q] = nv;
+            vn2[q] = nv;
           }
         } else if (lane == 0) {
-          w.vn1[c] = __dmul_rn(v1, __dsqrt_rn(temp));
+          vn1[q] = __dmul_rn(v1, __dsqrt_rn(temp));
         }
       }
       __syncwarp();
@@ -431,12 +449,17 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     if (!grid_sync(&sc->bar, G, status)) { ok = false; break; }
   }
   // write the owned columns back (also after an early exit, so that global
-  // memory holds this CTA's last state)
+  // memory holds this CTA's last state) and, from CTA 0, the maps
   __syncthreads();
   for (int q = 0; q < nown; ++q) {
     double* dst = X + (int64_t)(bid + G * q) * ldx;
     for (int r = threadIdx.x; r < d; r += blockDim.x) dst[r] = cache[(int64_t)q * d + r];
   }
+  if (bid == 0)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      w.phys[c] = phys[c];
+      w.posof[c] = posof[c];
+    }
 }
 
 // R^sk[i, q] = s_i X[i, phys[q]] for i <= q < n (0 below), s_i = -1 when the
@@ -482,9 +505,10 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   if (G < 1) G = 1;
   const double tol3z = tol3z_value();
   void* args[] = {&D, (void*)&tol3z};
-  // owned columns resident in shared memory when they fit
+  // owned columns, their norms and the maps resident in shared memory when
+  // they fit
   const int64_t nown = (n + G - 1) / G;
-  const size_t smem = (size_t)(nown * d + d) * sizeof(double);
+  const size_t smem = (size_t)(nown * d + d + 2 * nown) * sizeof(double) + (size_t)2 * n * sizeof(int);
   bool cached = smem <= 200 * 1024;
   if (cached) {
     e = cudaFuncSetAttribute(qrcp_cached_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

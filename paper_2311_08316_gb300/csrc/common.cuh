@@ -79,7 +79,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks
             ok = 0;
             break;
           }
-          __nanosleep(64);
+          if (spins > 256) __nanosleep(64);  // poll tightly first, then back off
         }
       }
       __threadfence();

@@ -366,11 +366,16 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
       ok = false;
       break;
     }
-    // 2. the reflector of column P (published rows j.. in X), by every CTA
+    // 2. the reflector of column P (published rows j.. in X), by every CTA:
+    // the column is staged in shared memory by all threads, then one warp
+    // takes its norm (dot32) and the column is scaled in place
     const double* gP = X + (int64_t)P * ldx;
+    const int len = d - j;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = __ldcg(gP + j + i);
+    __syncthreads();
     if (warp == 0) {
-      const double alpha = __ldcg(gP + j);
-      const double sumsq = (j + 1 < d) ? warp_dot32_self(gP + j + 1, d - j - 1) : 0.0;
+      const double alpha = vbuf[0];
+      const double sumsq = (j + 1 < d) ? warp_dot32_self_smem(vbuf + 1, d - j - 1) : 0.0;
       if (lane == 0) {
         if (sumsq == 0.0) {
           sh_tau = 0.0;
@@ -386,7 +391,6 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
       }
     }
     __syncthreads();
-    const int len = d - j;
     const double tau = sh_tau;
     const bool nz = sh_nz != 0;
     const double rden = sh_rden;
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
       double v = 1.0;
       if (i > 0) {
-        const double x = __ldcg(gP + j + i);
+        const double x = vbuf[i];
         v = nz ? __dmul_rn(x, rden) : x;
         if (owner) cP[j + i] = v;
       }

@@ -688,11 +688,12 @@ int split_gram_step(cqrrpt_handle h, const std::vector<int>& ids,
     const SplitWs& w = ws[(size_t)p];
     const int64_t kpadm = rup(q.m, kOzChunk);
     const int64_t ns = oz_gram_slices(q.m, kk);
-    cs[j] = OzColSplit{q.Q, q.ldq, q.m, kk, kpadm, w.ea, w.DA, (int64_t)kk * kpadm};
+    cs[j] = OzColSplit{q.Q, q.ldq, q.m, kk, kpadm, w.ea, w.DA, (int64_t)kk * kpadm, kOzChunk};
     OzGemm G{};
     G.M = kk; G.N = kk; G.Kpad = kpadm;
     G.kslice = ((kpadm / kOzChunk + ns - 1) / ns) * kOzChunk;
     G.A = w.DA; G.a_plane = (int64_t)kk * kpadm; G.B = w.DA; G.b_plane = (int64_t)kk * kpadm;
+    G.a_kblk = kOzChunk; G.b_kblk = kOzChunk;
     G.ea = w.ea; G.eb = w.ea; G.C = w.P; G.ldc = kk; G.c_slice = (int64_t)kk * kk;
     G.mode = kOzStore; G.upper_only = 1; G.err = &sc[p].status;
     if (!oz_gemm_valid(G) || !oz_gemm_encode_maps(G, maps.data() + j * 2 * kOzMapBytes))

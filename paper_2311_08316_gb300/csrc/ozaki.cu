@@ -92,8 +92,13 @@ __device__ __forceinline__ void rowexp_body(const OzRowSplit& J, int64_t tile) {
   J.e[r] = frexp_exp(mx);
 }
 
-// Column operand planes D[p][c][k] of X[k, c] (K = rows, zero past rows up
-// to kpad), scale e[c].  CTA: one column, 2048 consecutive k.
+// Column operand planes of X[k, c] (K = rows, zero past rows up to kpad),
+// scale e[c].  Unblocked (kblk = 0): D[p][c][k].  Blocked (kblk = kOzChunk):
+// D[p][k / 1024][c][k % 1024], so that a 128-column tile of one 1024-term
+// K chunk is one contiguous 256 KB range; the Gram's planes have K = m
+// (rows of the unblocked layout are 2m bytes long, and a tile would touch
+// 128 rows that far apart: one DRAM page and one TLB entry per 128 bytes).
+// CTA: one column, 2048 consecutive k.
 constexpr int kOzColChunk = 2048;
 __device__ __forceinline__ void splitcols_body(const OzColSplit& J, int64_t tile) {
   const int64_t chunks = (J.kpad + kOzColChunk - 1) / kOzColChunk;
@@ -101,9 +106,15 @@ __device__ __forceinline__ void splitcols_body(const OzColSplit& J, int64_t tile
   const int64_t k0 = (tile % chunks) * kOzColChunk;
   const int ec = J.e[c];
   const int64_t k1 = min64(k0 + kOzColChunk, J.kpad);
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const double x = k < J.rows ? J.X[(int64_t)c * J.ldx + k] : 0.0;
-    digits8(x, ec, J.D + (int64_t)c * J.kpad + k, J.plane);
+  const double* col = J.X + (int64_t)c * J.ldx;
+  if (J.kblk == 0) {
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+      digits8(k < J.rows ? col[k] : 0.0, ec, J.D + (int64_t)c * J.kpad + k, J.plane);
+  } else {
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int64_t off = (k / kOzChunk) * J.cols * kOzChunk + (int64_t)c * kOzChunk + k % kOzChunk;
+      digits8(k < J.rows ? col[k] : 0.0, ec, J.D + off, J.plane);
+    }
   }
 }
 
@@ -374,13 +385,14 @@ cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, 
   int* e = (int*)w;
   w += align256((int64_t)k * 4);
   double* P = (double*)w;
-  const OzColSplit cs{X, ldx, m, k, kpad, e, D, plane};
+  const OzColSplit cs{X, ldx, m, k, kpad, e, D, plane, kOzChunk};
   cudaError_t err0 = oz_colsplit(cs, s);
   if (err0 != cudaSuccess) return err0;
   OzGemm G{};
   G.M = k; G.N = k; G.Kpad = kpad;
   G.kslice = ((kpad / kOzChunk + nslices - 1) / nslices) * kOzChunk;
   G.A = D; G.a_plane = plane; G.B = D; G.b_plane = plane;
+  G.a_kblk = kOzChunk; G.b_kblk = kOzChunk;
   G.ea = e; G.eb = e;
   G.C = P; G.ldc = k; G.c_slice = (int64_t)k * k;
   G.mode = kOzStore; G.upper_only = 1;

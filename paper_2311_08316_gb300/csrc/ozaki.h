@@ -20,9 +20,9 @@ struct OzGemm {
   int N;
   int64_t Kpad;       // multiple of 32, digits beyond the true K are zero
   int64_t kslice;     // K range per CTA (multiple of 32); partial results per slice
-  const __nv_bfloat16* A;  // planes [8][M][Kpad]
+  const __nv_bfloat16* A;  // planes [8][Kpad/a_kblk][M][a_kblk] ([8][M][Kpad] unblocked)
   int64_t a_plane;
-  const __nv_bfloat16* B;  // planes [8][N][Kpad]
+  const __nv_bfloat16* B;  // planes [8][Kpad/b_kblk][N][b_kblk]
   int64_t b_plane;
   const int* ea;
   const int* eb;
@@ -33,6 +33,8 @@ struct OzGemm {
   int upper_only;     // skip tiles strictly below the diagonal
   int* err;           // device status word (or null): set to CQRRPT_TIMEOUT
                       // when a bounded wait of the engine expires
+  int64_t a_kblk;     // K extent of one plane block of A (0: Kpad, unblocked)
+  int64_t b_kblk;     // the same for B
 };
 
 // tcgen05 engine (ozaki_tc.cu)
@@ -68,8 +70,9 @@ struct OzColSplit {   // column operand: digit planes of X[k, c], K = rows
   int cols;
   int64_t kpad;
   int* e;              // cols exponents (written)
-  __nv_bfloat16* D;    // planes [8][cols][kpad]
+  __nv_bfloat16* D;    // planes [8][kpad/kblk][cols][kblk]
   int64_t plane;
+  int64_t kblk;        // 0 (= kpad: planes [8][cols][kpad]) or kOzChunk
 };
 struct OzTrinv {      // W = T^{-1}, row by row
   const double* T;

@@ -124,12 +124,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int x, int y, int z) {
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z, int w) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
       : "memory");
 }
 
@@ -272,6 +272,10 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
 
   if (warp == 0 && lane == 0) {
     // ---- producer
+    // blocked operands: power-of-two block extents (shift, mask); an
+    // unblocked operand is one block (shift 62: block 0, x = kx)
+    const int ash = G.a_kblk > 0 && G.a_kblk < G.Kpad ? __ffsll(G.a_kblk) - 1 : 62;
+    const int bsh = G.b_kblk > 0 && G.b_kblk < G.Kpad ? __ffsll(G.b_kblk) - 1 : 62;
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
@@ -291,13 +295,17 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
           break;
         }
         mbar_expect_tx(full_bar(stage), kTcStageBytes);
-        const int kx = (int)(kbeg + (int64_t)kst * kTcBK);
+        const int64_t kx = kbeg + (int64_t)kst * kTcBK;
+        // (K within the block, block) of each operand: a stage never
+        // straddles a block (block extents are multiples of kTcBK)
+        const int xa = (int)(kx & ((1ll << ash) - 1)), ba = (int)(kx >> ash);
+        const int xb = (int)(kx & ((1ll << bsh) - 1)), bb = (int)(kx >> bsh);
 #pragma unroll
         for (int at = 0; at < kTcBK / kTcAtomK; ++at) {  // one swizzle atom per copy
-          tma_load_3d(a_tiles + stage * kTcTileBytes + at * kTcAtomBytes, tmA, full_bar(stage),
-                      kx + at * kTcAtomK, (int)m0, p - 1);
-          tma_load_3d(b_tiles + stage * kTcTileBytes + at * kTcAtomBytes, tmB, full_bar(stage),
-                      kx + at * kTcAtomK, n0, q - 1);
+          tma_load_4d(a_tiles + stage * kTcTileBytes + at * kTcAtomBytes, tmA, full_bar(stage),
+                      xa + at * kTcAtomK, (int)m0, ba, p - 1);
+          tma_load_4d(b_tiles + stage * kTcTileBytes + at * kTcAtomBytes, tmB, full_bar(stage),
+                      xb + at * kTcAtomK, n0, bb, q - 1);
         }
         ++issued;
         if (++stage == kTcStages) {
@@ -501,17 +509,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D map over digit planes [8][rows][kpad] (BF16), box 64 (K) x 128 rows x
-// 1 plane, 128-byte swizzle, zero fill outside.
+// 4-D map over digit planes [8][kpad / kblk][rows][kblk] (BF16): K within
+// the block, row, block, plane; box 64 (K) x 128 rows x 1 x 1, 128-byte
+// swizzle, zero fill outside.  Unblocked planes [8][rows][kpad] are the
+// case kblk = kpad (one block).
 bool plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t kpad,
-               int64_t plane) {
+               int64_t kblk, int64_t plane) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)kOzDigits};
-  const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)plane * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)kTcAtomK, (cuuint32_t)kTcBM, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, estr,
+  if (kblk <= 0) kblk = kpad;
+  const cuuint64_t dims[4] = {(cuuint64_t)kblk, (cuuint64_t)rows, (cuuint64_t)(kpad / kblk),
+                              (cuuint64_t)kOzDigits};
+  const cuuint64_t strides[3] = {(cuuint64_t)kblk * 2, (cuuint64_t)(rows * kblk) * 2,
+                                 (cuuint64_t)plane * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)kTcAtomK, (cuuint32_t)kTcBM, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -534,11 +547,18 @@ static cudaError_t tc_attributes() {
 
 // TMA: 16-byte aligned bases, row strides and plane strides (several K
 // slices: slice boundaries on stage boundaries; one slice may end
-// mid-stage, TMA fills zeros past Kpad).
+// mid-stage, TMA fills zeros past Kpad).  Blocked planes: power-of-two
+// blocks of a whole number of stages that tile Kpad, slices on block
+// boundaries.
+static bool kblk_valid(int64_t kb, const OzGemm& G) {
+  if (kb <= 0 || kb >= G.Kpad) return kb <= G.Kpad;
+  return (kb & (kb - 1)) == 0 && kb % kTcBK == 0 && G.Kpad % kb == 0 && G.kslice % kb == 0;
+}
 bool oz_gemm_valid(const OzGemm& G) {
   const bool sliced = G.kslice < G.Kpad;
   return !(((uintptr_t)G.A & 15) || ((uintptr_t)G.B & 15) || (G.Kpad % 8) || (G.a_plane % 8) ||
-           (G.b_plane % 8) || G.kslice <= 0 || (sliced && (G.kslice % kTcBK)));
+           (G.b_plane % 8) || G.kslice <= 0 || (sliced && (G.kslice % kTcBK)) ||
+           !kblk_valid(G.a_kblk, G) || !kblk_valid(G.b_kblk, G));
 }
 
 int64_t oz_gemm_tiles(const OzGemm& G) {
@@ -551,8 +571,8 @@ int64_t oz_gemm_tiles(const OzGemm& G) {
 bool oz_gemm_encode_maps(const OzGemm& G, void* maps_host) {
   static_assert(sizeof(CUtensorMap) == kOzMapBytes, "tensor map size");
   CUtensorMap* m = (CUtensorMap*)maps_host;
-  return plane_map(&m[0], G.A, G.M, G.Kpad, G.a_plane) &&
-         plane_map(&m[1], G.B, G.N, G.Kpad, G.b_plane);
+  return plane_map(&m[0], G.A, G.M, G.Kpad, G.a_kblk, G.a_plane) &&
+         plane_map(&m[1], G.B, G.N, G.Kpad, G.b_kblk, G.b_plane);
 }
 
 cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s) {

@@ -348,8 +348,8 @@ int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R
 
 /* Line 5 in the CQRRPT_SPLITBF16 arithmetic: G = X^T X (k x k) as 36 BF16
  * tensor-core products of 7-bit digit planes: exact FP32 chunk sums of 1024
- * terms, combined exactly in 64-bit integers (two groups of four levels),
- * each group rounded once to FP64.  A bounded device wait that expires is
+ * terms, combined exactly in integers (two 64-bit groups of four levels,
+ * then one 128-bit sum) and rounded once to FP64.  A bounded device wait that expires is
  * reported as CQRRPT_TIMEOUT by cqrrpt_last_status. */
 int cqrrpt_gram_split_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_t ldx,
                         double* G, int64_t ldg, cudaStream_t stream);

@@ -19,7 +19,8 @@
 // dropped levels are below 9 * 2^-56 relative to the scales.  Each digit
 // product is an integer of magnitude < 2^14, so an FP32 tensor-core
 // accumulation of up to 1024 such terms is exact; chunk sums are combined
-// exactly in 64-bit integers and rounded to FP64 twice per entry.  The
+// exactly in integers and rounded to FP64 once per entry (twice when the
+// product is subtracted from C).  The
 // engine (tcgen05 + TMA + tensor memory) is in ozaki_tc.cu.  All operands
 // are "K-contiguous" digit planes: A is stored as M rows of K digits per
 // plane, B as N rows of K digits per plane.

@@ -31,9 +31,12 @@
 //                 2^(7 (s_g - s)) * chunk sum.
 //               Integer addition is exact, so the order of pairs and chunks
 //               is free; with L_s <= (s - 1) K 127^2 both groups stay below
-//               2^58 for any K <= 2^20.  At the end of a group G is rounded
-//               once to FP64, scaled by 2^(ea + eb - 7 s_g) and stored into C
-//               (group 1: C = v, or C - v; group 2: C + v, or C - v).
+//               2^58 for any K <= 2^20.  Store mode: group 1 leaves its raw
+//               sum G1 in C, group 2 forms the exact 128-bit G1 2^28 + G2
+//               and rounds it once to FP64 with the scale 2^(ea + eb - 63)
+//               (C = v).  Subtract mode: each group is rounded once, scaled
+//               by 2^(ea + eb - 7 s_g) and subtracted (C = C - v).  The
+//               rounding is done on the integer pipe (rne_f64).
 // Work order inside a CTA: group, then 1024-term K chunk, then the group's
 // pairs (level order), then the chunk's 128-wide K stages, so that the digit
 // planes of one chunk are reused by every pair of the group while they are
@@ -66,12 +69,13 @@ constexpr int kTcChunkStages = kOzChunk / kTcBK;            // 8 stages = 1024 K
 constexpr int kTcDrainWarps = 16;                          // 4 per TMEM lane quarter
 constexpr int kTcThreads = 32 * (2 + kTcDrainWarps);        // 18 warps: <= 96 registers
 constexpr int kTcAccBufs = 2;                               // FP32 accumulators in TMEM
+constexpr int kTcEmitCols = 8;                              // columns per batch of C loads
 constexpr uint32_t kTcTmemCols = 512;
 constexpr uint32_t kTcGroupLo = kTcAccBufs * kTcBN;         // 256: low words of the sums
 constexpr uint32_t kTcGroupHi = kTcGroupLo + kTcBN;         // 384: high words
 constexpr int kTcBarriers = 2 * kTcStages + 2 * kTcAccBufs + 1;  // full, empty, acc full/empty, done
 constexpr size_t kTcSmem = 1024 /* alignment slack */ + (size_t)kTcStages * kTcStageBytes +
-                           kTcBarriers * 8 + 16;
+                           kTcBarriers * 8 + 16 + kTcBN * 4 /* column exponents */;
 
 // first pair index of each group of levels (2..5, 6..9), and the end
 __constant__ int kTcGroupFirst[3] = {0, 10, 36};
@@ -198,11 +202,50 @@ __device__ __forceinline__ void tmem_wait_st() {
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// x * 2^e, rounded once (as ldexp): one multiplication by the exact power
-// of two when 2^e is a normal double, ldexp otherwise.
-__device__ __forceinline__ double scale2(double x, int e) {
-  if (e >= -1022 && e <= 1023) return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
-  return ldexp(x, e);
+// S * 2^e rounded to the nearest double (ties to even), S = hi:lo a signed
+// 128-bit integer, by integer operations on the IEEE 754 binary64 encoding:
+// normalise |S| so that its leading one is bit 127, keep 53 bits, round on
+// the next bit and the sticky rest, and write the exponent field directly
+// (the scale 2^e costs nothing).  Results outside the normal range go
+// through ldexp of the rounded 53-bit value.
+__device__ __forceinline__ double rne_f64(long long hi, unsigned long long lo, int e) {
+  const bool neg = hi < 0;
+  unsigned long long mh = (unsigned long long)hi, ml = lo;
+  if (neg) {  // two's complement negation of the 128-bit value
+    ml = ~ml + 1ull;
+    mh = ~mh + (ml == 0ull ? 1ull : 0ull);
+  }
+  if ((mh | ml) == 0ull) return 0.0;
+  const int nb = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);  // bits of |S|
+  const int L = 128 - nb;  // left shift that puts the leading one at bit 127
+  unsigned long long nh, nl;
+  if (L >= 64) {
+    nh = ml << (L - 64);
+    nl = 0ull;
+  } else if (L > 0) {
+    nh = (mh << L) | (ml >> (64 - L));
+    nl = ml << L;
+  } else {
+    nh = mh;
+    nl = ml;
+  }
+  unsigned long long mant = nh >> 11;  // 53 bits, leading one at bit 52
+  const bool rb = (nh >> 10) & 1ull;
+  const bool sticky = (nh & 0x3FFull) != 0ull || nl != 0ull;
+  if (rb && (sticky || (mant & 1ull))) ++mant;
+  int E = nb - 1 + e;  // exponent of the leading bit
+  if (mant >> 53) {
+    mant >>= 1;
+    ++E;
+  }
+  if (E >= -1022 && E <= 1023) {
+    const unsigned long long bits = ((unsigned long long)neg << 63) |
+                                    ((unsigned long long)(E + 1023) << 52) |
+                                    (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+  }
+  const double m = ldexp((double)mant, E - 52);
+  return neg ? -m : m;
 }
 
 __device__ __forceinline__ void record_timeout(int* err) {
@@ -225,6 +268,7 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
   auto acce_bar = [&](int b) { return bars + 8u * (2 * kTcStages + kTcAccBufs + b); };
   const uint32_t done_bar = bars + 8u * (2 * kTcStages + 2 * kTcAccBufs);
   uint32_t* tmem_slot = (uint32_t*)(tc_smem_raw + (bars - raw) + 8u * kTcBarriers);
+  int* eb_s = (int*)(tc_smem_raw + (bars - raw) + 8u * kTcBarriers + 16u);  // eb of the tile
 
   // tile of this CTA
   const int64_t tiles_m = (G.M + kTcBM - 1) / kTcBM;
@@ -264,6 +308,10 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
                  "r"(kTcTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x >= 64 && threadIdx.x < 64 + kTcBN) {
+    const int col = n0 + (int)threadIdx.x - 64;
+    eb_s[threadIdx.x - 64] = col < G.N ? G.eb[col] : 0;
   }
   tc_fence_before();
   __syncthreads();
@@ -437,19 +485,43 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
             hi[i] = (uint32_t)((unsigned long long)g >> 32);
           }
           if (emit) {
-            // the group is complete: one FP64 rounding, scale, store
+            // the group is complete.  Store mode: group 1 leaves its raw
+            // 64-bit sum in C; group 2 reads it back and rounds the exact
+            // 128-bit G1 2^28 + G2 once.  Subtract mode: each group is
+            // rounded once and subtracted from C.  Integer pipe only, except
+            // the subtraction (FP64 is scarce on this part).
             if (row_ok) {
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int col = col0 + h * 16 + i;
-                if (col >= G.N) continue;
-                const long long g =
-                    (long long)(((unsigned long long)hi[i] << 32) | (unsigned long long)lo[i]);
-                const double v = scale2(__ll2double_rn(g), ea + G.eb[col] - 7 * s_g);
-                double* cp = Cbase + (int64_t)col * G.ldc;
-                if (G.mode == kOzSub) *cp = __dsub_rn(*cp, v);
-                else if (grp == 0) *cp = v;
-                else *cp = __dadd_rn(*cp, v);
+              for (int e8 = 0; e8 < 16; e8 += kTcEmitCols) {
+                const int c0 = cslice * 32 + h * 16 + e8;  // column within the tile
+                double old[kTcEmitCols];
+                const bool stash = G.mode == kOzStore && grp == 0;
+                if (!stash) {
+#pragma unroll
+                  for (int i = 0; i < kTcEmitCols; ++i)
+                    old[i] = n0 + c0 + i < G.N ? Cbase[(int64_t)(n0 + c0 + i) * G.ldc] : 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < kTcEmitCols; ++i) {
+                  if (n0 + c0 + i >= G.N) continue;
+                  const long long g = (long long)(((unsigned long long)hi[e8 + i] << 32) |
+                                                  (unsigned long long)lo[e8 + i]);
+                  const int e = ea + eb_s[c0 + i] - 7 * s_g;
+                  double r;
+                  if (stash) {
+                    r = __longlong_as_double(g);
+                  } else if (G.mode == kOzStore) {
+                    // S = G1 2^(7 (9 - 5)) + G2 as a 128-bit integer
+                    const long long g1 = __double_as_longlong(old[i]);
+                    const unsigned long long l1 = (unsigned long long)g1 << 28;
+                    const unsigned long long l = l1 + (unsigned long long)g;
+                    const long long hh = (g1 >> 36) + (g >> 63) + (l < l1 ? 1 : 0);
+                    r = rne_f64(hh, l, e);
+                  } else {
+                    r = __dsub_rn(old[i], rne_f64(g >> 63, (unsigned long long)g, e));
+                  }
+                  Cbase[(int64_t)(n0 + c0 + i) * G.ldc] = r;
+                }
               }
             }
           } else {

@@ -121,6 +121,35 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
              double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
              cudaStream_t stream);
 
+/* ---- many factorisations from host memory -------------------------------- */
+
+/* `count` factorisations of m x n host-resident matrices (the same
+ * `[Q,R,J] = cqrrpt(M, gamma, F)` as cqrrpt_d, one per matrix) in a
+ * copy/compute pipeline: while matrix i is factored on `stream`, matrix i+1
+ * is copied in on a second stream and the result of matrix i-1 is copied
+ * out on a third (double-buffered device copies of A, Q, R and J owned by
+ * the handle).  The call returns when every result is in host memory.
+ *   count             number of matrices >= 1.
+ *   A_host[i], lda    host pointers (column-major, lda >= m); pinned host
+ *                     memory lets the copies run as asynchronous DMA.  The
+ *                     same pointer may appear more than once.
+ *   seeds[i]          host array: seed of S for matrix i.
+ *   Q_host[i], ldq    host, m x n capacity; columns 0..k_i-1 receive Q.
+ *   R_host[i], ldr    host, n x n capacity; rows 0..k_i-1 receive R.
+ *   J_host[i]         host, n int64 entries.
+ *   k_host, status_host  host arrays of count entries: k and the final
+ *                     status of each factorisation (as cqrrpt_last_status).
+ * Output buffers of different i may alias (results are copied out in
+ * order).  gamma, nnz_per_col, tol and precision as in cqrrpt_d.  Returns
+ * the first argument or launch error (negative or CQRRPT_CUDA_ERROR /
+ * CQRRPT_NO_MEMORY); per-matrix device conditions are in status_host. */
+int cqrrpt_host_pipeline_d(cqrrpt_handle h, int count, int64_t m, int64_t n,
+                           const double* const* A_host, int64_t lda, double gamma,
+                           int nnz_per_col, double tol, const uint64_t* seeds, int precision,
+                           double* const* Q_host, int64_t ldq, double* const* R_host, int64_t ldr,
+                           int64_t* const* J_host, int64_t* k_host, int* status_host,
+                           cudaStream_t stream);
+
 /* ---- batched CQRRPT ------------------------------------------------------ */
 
 /* Workspace bytes cqrrpt_batched_d needs for `batch` problems (m, n: host

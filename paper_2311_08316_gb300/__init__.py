@@ -75,6 +75,8 @@ def lib():
     L.cqrrpt_batched_set_tuning.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
     L.cqrrpt_gram_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
     L.cqrrpt_trsm_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_host_pipeline_d.argtypes = [_p, _int, _i64, _i64, _p, _i64, _d, _int, _d, _p, _int,
+                                         _p, _i64, _p, _i64, _p, _p, _p, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
     L.cqrrpt_sketch_dim.restype = _i64
     L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -93,7 +95,7 @@ def exported_symbols():
             "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches",
             "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs",
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
-            "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d"]
+            "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -124,6 +126,14 @@ def _ld(x, rows_needed=None):
         raise CqrrptError("expected a 2-D float64 CUDA tensor")
     if x.stride(0) != 1:
         raise CqrrptError("expected a column-major tensor (stride(0) == 1); use colmajor()")
+    return max(x.stride(1), x.shape[0], 1)
+
+
+def _ld_host(x):
+    if x.dim() != 2 or x.dtype != torch.float64 or x.device.type != "cpu":
+        raise CqrrptError("expected a 2-D float64 host tensor")
+    if x.stride(0) != 1:
+        raise CqrrptError("expected a column-major host tensor (stride(0) == 1)")
     return max(x.stride(1), x.shape[0], 1)
 
 
@@ -354,6 +364,39 @@ def cqrrpt_from_host(A_host, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64
         Jh.copy_(J, non_blocking=True)
     s.synchronize()
     return Factorization(Qh, Rh, Jh, k, res.status)
+
+
+def cqrrpt_host_pipeline(A_hosts, gamma=1.25, nnz=4, tol=-1.0, seeds=None, precision=FP64,
+                         outs_host=None, handle=None, stream=None):
+    """CQRRPT of several host-resident column-major float64 matrices of one
+    shape through cqrrpt_host_pipeline_d: copies in, factorisations and
+    copies out overlap.  outs_host: one (Q, R, J) host tuple per matrix
+    (tuples may repeat; pinned buffers make the copies asynchronous DMA), or
+    None to allocate pinned ones.  Returns a list of Factorization whose
+    Qbuf/Rbuf/J are the host buffers."""
+    h = handle or default_handle()
+    count = len(A_hosts)
+    m, n = A_hosts[0].shape
+    lda = _ld_host(A_hosts[0])
+    for A in A_hosts:
+        if A.shape != (m, n) or _ld_host(A) != lda:
+            raise CqrrptError("cqrrpt_host_pipeline: host matrices of one shape and leading dimension")
+    if outs_host is None:
+        outs_host = [(torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
+                      torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
+                      torch.empty(n, dtype=torch.int64, pin_memory=True)) for _ in range(count)]
+    seeds = list(range(count)) if seeds is None else [int(x) for x in seeds]
+    k = (_i64 * count)()
+    st = (_int * count)()
+    P = ctypes.c_void_p
+    rc = lib().cqrrpt_host_pipeline_d(
+        h.h, count, m, n, _arr(P, [A.data_ptr() for A in A_hosts]), lda, gamma, nnz, tol,
+        _arr(_u64, seeds), precision, _arr(P, [o[0].data_ptr() for o in outs_host]),
+        _ld_host(outs_host[0][0]), _arr(P, [o[1].data_ptr() for o in outs_host]),
+        _ld_host(outs_host[0][1]),
+        _arr(P, [o[2].data_ptr() for o in outs_host]), k, st, _stream(stream))
+    _check(rc, "cqrrpt_host_pipeline_d")
+    return [Factorization(o[0], o[1], o[2], int(k[i]), int(st[i])) for i, o in enumerate(outs_host)]
 
 
 def _arr(ctype, values):

@@ -44,6 +44,18 @@ struct cqrrpt_ctx {
   size_t split_ws_bytes = 0;
   DeviceScalars* pinned_sc = nullptr;
   int pinned_sc_count = 0;
+  // host pipeline: double-buffered device copies of A, Q, R, J for an
+  // m x n shape, copy-in and copy-out streams, events (in, compute, out per
+  // buffer), device and pinned slots for k and status
+  double* pipe_a[2] = {};
+  double* pipe_q[2] = {};
+  double* pipe_r[2] = {};
+  int64_t* pipe_j[2] = {};
+  int64_t pipe_m = 0, pipe_n = 0;
+  int64_t* pipe_slots = nullptr;  // device: k[2], then status[2] as int
+  int64_t* pipe_pin = nullptr;    // pinned copy of the same 32 bytes
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev[6] = {};
 };
 
 static std::atomic<long long> g_launches{0};
@@ -283,6 +295,18 @@ int cqrrpt_destroy(cqrrpt_handle h) {
   if (h->stage) cudaFreeHost(h->stage);
   if (h->split_ws) cudaFree(h->split_ws);
   if (h->pinned_sc) cudaFreeHost(h->pinned_sc);
+  for (int b = 0; b < 2; ++b) {
+    if (h->pipe_a[b]) cudaFree(h->pipe_a[b]);
+    if (h->pipe_q[b]) cudaFree(h->pipe_q[b]);
+    if (h->pipe_r[b]) cudaFree(h->pipe_r[b]);
+    if (h->pipe_j[b]) cudaFree(h->pipe_j[b]);
+  }
+  if (h->pipe_slots) cudaFree(h->pipe_slots);
+  if (h->pipe_pin) cudaFreeHost(h->pipe_pin);
+  if (h->pipe_in) cudaStreamDestroy(h->pipe_in);
+  if (h->pipe_out) cudaStreamDestroy(h->pipe_out);
+  for (int i = 0; i < 6; ++i)
+    if (h->pipe_ev[i]) cudaEventDestroy(h->pipe_ev[i]);
   delete h;
   return kOk;
 }
@@ -378,6 +402,171 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
     return st2;
   }
   return kOk;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Streams, events, slots and the two device buffer sets of the host
+// pipeline for an m x n shape (grown, never shrunk).
+int pipe_ensure(cqrrpt_handle h, int64_t m, int64_t n) {
+  if (!h->pipe_in) {
+    if (cudaStreamCreateWithFlags(&h->pipe_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->pipe_out, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return kCudaError;
+    }
+    for (int i = 0; i < 6; ++i)
+      if (cudaEventCreateWithFlags(&h->pipe_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return kCudaError;
+      }
+    if (cudaMalloc(&h->pipe_slots, 32) != cudaSuccess ||
+        cudaMallocHost(&h->pipe_pin, 32) != cudaSuccess) {
+      cudaGetLastError();
+      return kNoMemory;
+    }
+  }
+  if (m <= h->pipe_m && n <= h->pipe_n && m * n <= h->pipe_m * h->pipe_n) return kOk;
+  cudaDeviceSynchronize();
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(h->pipe_a[b]);
+    cudaFree(h->pipe_q[b]);
+    cudaFree(h->pipe_r[b]);
+    cudaFree(h->pipe_j[b]);
+    h->pipe_a[b] = h->pipe_q[b] = h->pipe_r[b] = nullptr;
+    h->pipe_j[b] = nullptr;
+  }
+  h->pipe_m = h->pipe_n = 0;
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMalloc(&h->pipe_a[b], (size_t)(m * n * 8)) != cudaSuccess ||
+        cudaMalloc(&h->pipe_q[b], (size_t)(m * n * 8)) != cudaSuccess ||
+        cudaMalloc(&h->pipe_r[b], (size_t)(n * n * 8)) != cudaSuccess ||
+        cudaMalloc(&h->pipe_j[b], (size_t)(n * 8)) != cudaSuccess) {
+      cudaGetLastError();
+      return kNoMemory;
+    }
+  }
+  h->pipe_m = m;
+  h->pipe_n = n;
+  return kOk;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cqrrpt_host_pipeline_d(cqrrpt_handle h, int count, int64_t m, int64_t n,
+                           const double* const* A_host, int64_t lda, double gamma, int nnz,
+                           double tol, const uint64_t* seeds, int precision,
+                           double* const* Q_host, int64_t ldq, double* const* R_host, int64_t ldr,
+                           int64_t* const* J_host, int64_t* k_host, int* status_host,
+                           cudaStream_t stream) {
+  if (!h) return -1;
+  if (count < 1) return -2;
+  if (m < 1) return -3;
+  if (n < 1 || n > 16384) return -4;
+  if (!A_host) return -5;
+  if (lda < m) return -6;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -7;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -7;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -8;
+  if (std::isnan(tol)) return -9;
+  if (!seeds) return -10;
+  if (!precision_ok(precision)) return -11;
+  if (!Q_host) return -12;
+  if (ldq < m) return -13;
+  if (!R_host) return -14;
+  if (ldr < n) return -15;
+  if (!J_host) return -16;
+  if (!k_host) return -17;
+  if (!status_host) return -18;
+  for (int i = 0; i < count; ++i) {
+    if (!A_host[i]) return -5;
+    if (!Q_host[i]) return -12;
+    if (!R_host[i]) return -14;
+    if (!J_host[i]) return -16;
+  }
+  DevGuard g(h->device);
+  int st = pipe_ensure(h, m, n);
+  if (st != kOk) return st;
+  cudaEvent_t* ev_in = h->pipe_ev;
+  cudaEvent_t* ev_comp = h->pipe_ev + 2;
+  cudaEvent_t* ev_out = h->pipe_ev + 4;
+  int64_t* ks_dev = h->pipe_slots;           // k[2]
+  int* st_dev = (int*)(h->pipe_slots + 2);   // status[2]
+  const int64_t* ks_pin = h->pipe_pin;
+  const int* st_pin = (const int*)(h->pipe_pin + 2);
+  cudaError_t e = cudaSuccess;
+
+  // copy in matrix i (after the factorisation of i - 2 has read its buffer)
+  auto copy_in = [&](int i) {
+    const int b = i & 1;
+    if (i >= 2 && e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_in, ev_comp[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(h->pipe_a[b], (size_t)m * 8, A_host[i], (size_t)lda * 8,
+                            (size_t)m * 8, (size_t)n, cudaMemcpyHostToDevice, h->pipe_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[b], h->pipe_in);
+  };
+  // factor matrix i on the caller's stream (after its copy-in, and after
+  // the results of i - 2 have left its output buffers); k and status go to
+  // the pinned slots
+  int first_error = kOk;
+  auto factor = [&](int i) {
+    const int b = i & 1;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_in[b], 0);
+    if (i >= 2 && e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_out[b], 0);
+    if (e != cudaSuccess) return;
+    const int r = cqrrpt_d(h, m, n, h->pipe_a[b], m, gamma, nnz, tol, seeds[i], precision,
+                           h->pipe_q[b], m, h->pipe_r[b], n, h->pipe_j[b], nullptr, nullptr, stream);
+    if (r != kOk && first_error == kOk) first_error = r;
+    if (e == cudaSuccess && handle_finalize(h, ks_dev + b, st_dev + b, stream) != kOk)
+      e = cudaErrorUnknown;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->pipe_pin + b, ks_dev + b, 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((int*)(h->pipe_pin + 2) + b, st_dev + b, 4, cudaMemcpyDeviceToHost,
+                          stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_comp[b], stream);
+  };
+
+  copy_in(0);
+  factor(0);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    const int b = i & 1;
+    if (i + 1 < count) {  // queue the next matrix before waiting for this one
+      copy_in(i + 1);
+      factor(i + 1);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev_comp[b]);
+    if (e != cudaSuccess) break;
+    const int64_t k = ks_pin[b];
+    k_host[i] = k;
+    status_host[i] = st_pin[b];
+    // copy out the result of matrix i: Q[:, :k], R[:k, :], J
+    e = cudaStreamWaitEvent(h->pipe_out, ev_comp[b], 0);
+    if (e == cudaSuccess && k > 0)
+      e = cudaMemcpy2DAsync(Q_host[i], (size_t)ldq * 8, h->pipe_q[b], (size_t)m * 8,
+                            (size_t)m * 8, (size_t)k, cudaMemcpyDeviceToHost, h->pipe_out);
+    if (e == cudaSuccess && k > 0)
+      e = cudaMemcpy2DAsync(R_host[i], (size_t)ldr * 8, h->pipe_r[b], (size_t)n * 8,
+                            (size_t)k * 8, (size_t)n, cudaMemcpyDeviceToHost, h->pipe_out);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(J_host[i], h->pipe_j[b], (size_t)n * 8, cudaMemcpyDeviceToHost,
+                          h->pipe_out);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], h->pipe_out);
+  }
+  const cudaError_t e1 = cudaStreamSynchronize(h->pipe_out);
+  const cudaError_t e2 = cudaStreamSynchronize(h->pipe_in);
+  const cudaError_t e3 = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return kCudaError;
+  }
+  return first_error;
 }
 
 static int batch_check(int batch, const int64_t* m, const int64_t* n, const double* const* A,

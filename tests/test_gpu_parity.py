@@ -270,3 +270,66 @@ def test_cqrrpt_async_status(C):
     st, k = h.last_status()
     assert st == 0 and k == 12
     h.close()
+
+
+def _host_colmajor(A, ld=None, pinned=True):
+    """Column-major host tensor holding A (leading dimension ld >= m)."""
+    m, n = A.shape
+    ld = ld or m
+    t = torch.zeros((n, ld), dtype=torch.float64, pin_memory=pinned)
+    t[:, :m] = torch.from_numpy(np.ascontiguousarray(A.T))
+    return t.t()[:m, :]
+
+
+def test_host_pipeline_matches_oracle(C):
+    """cqrrpt_host_pipeline_d: five host matrices (full rank, planted rank,
+    zero, ragged m, padded lda) through the copy/compute pipeline, each
+    result bit-identical to the oracle; then the same inputs with two
+    alternating output buffers (results copied out in order)."""
+    m, n = 4096 + 777, 40
+    mats = []
+    for i in range(5):
+        sv = np.zeros(n)
+        rank = [40, 25, 0, 40, 33][i]
+        if rank:
+            sv[:rank] = W.logspaced(rank, -6.0).numpy()
+            mats.append(np.asfortranarray(W.planted(m, n, sv, 50 + i,
+                                                    noise=(1e-15 if rank < n else 0.0)).numpy()))
+        else:
+            mats.append(np.zeros((m, n), order="F"))
+    seeds = [11, 12, 13, 14, 2**40 + 15]
+    A_h = [_host_colmajor(A, ld=m + 3) for A in mats]
+    res = C.cqrrpt_host_pipeline(A_h, 1.25, 4, 1e-9, seeds)
+    for i, A in enumerate(mats):
+        ref = oracle.cqrrpt(A, 1.25, 4, 1e-9, seeds[i])
+        assert res[i].status == ref.status and res[i].k == ref.k, i
+        assert_bits(res[i].J.numpy(), ref.J, "J[%d]" % i)
+        if ref.k:
+            assert_bits(np.asfortranarray(res[i].Q.numpy()), ref.Q, "Q[%d]" % i)
+            assert_bits(np.asfortranarray(res[i].R.numpy()), ref.R, "R[%d]" % i)
+    assert res[2].status == 1 and res[2].k == 0
+    # two output buffers, reused in turn: the last two results are the
+    # pipeline's, and equal the first run's
+    outs = [(torch.empty((n, m), dtype=torch.float64, pin_memory=True).t(),
+             torch.empty((n, n), dtype=torch.float64, pin_memory=True).t(),
+             torch.empty(n, dtype=torch.int64, pin_memory=True)) for _ in range(2)]
+    res2 = C.cqrrpt_host_pipeline(A_h, 1.25, 4, 1e-9, seeds, outs_host=[outs[i % 2] for i in range(5)])
+    assert [r.k for r in res2] == [r.k for r in res]
+    for i in (3, 4):
+        assert torch.equal(res2[i].J, res[i].J)
+        assert torch.equal(res2[i].Q, res[i].Q) and torch.equal(res2[i].R, res[i].R)
+
+
+def test_host_pipeline_splitbf16_matches_single_calls(C):
+    """The split-BF16 precision through the pipeline equals the one-matrix
+    call bit for bit (same kernels, same inputs)."""
+    w = W.single_large(m=8192 + 300, n=96, rank=70)
+    A = np.asfortranarray(w.matrix().numpy())
+    A_h = [_host_colmajor(A), _host_colmajor(A)]
+    res = C.cqrrpt_host_pipeline(A_h, w.gamma, w.nnz, w.tol, [w.sketch_seed] * 2,
+                                 precision=C.SPLITBF16)
+    one = C.cqrrpt(gpu(A), w.gamma, w.nnz, w.tol, w.sketch_seed, precision=C.SPLITBF16)
+    for r in res:
+        assert r.status == 0 and r.k == one.k == 70
+        assert torch.equal(r.J, one.J.cpu())
+        assert torch.equal(r.Q, one.Q.cpu()) and torch.equal(r.R, one.R.cpu())

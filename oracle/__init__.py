@@ -47,6 +47,8 @@ def lib():
         L.oracle_potrf_upper.argtypes = [_i64, _p, _i64, _p, _i64]
         L.oracle_potrf_upper.restype = _i64
         L.oracle_trmm_upper.argtypes = [_i64, _i64, _p, _i64, _p, _i64, _p, _i64]
+        L.oracle_apply_q.argtypes = [ctypes.c_int, _i64, _i64, _p, _i64, _p, _i64, _i64, _p,
+                                     _i64, _p, _i64]
         L.oracle_sketch_dim.argtypes = [_i64, _d]
         L.oracle_sketch_dim.restype = _i64
         L.oracle_cqrrpt.argtypes = [_i64, _i64, _p, _i64, _d, ctypes.c_int, _d, _u64,
@@ -179,6 +181,33 @@ def trmm_upper(Rpre, Rsk_k):
     R = np.zeros((k, n), dtype=np.float64, order="F")
     lib().oracle_trmm_upper(k, n, _ptr(Rpre), k, _ptr(Rsk_k), k, _ptr(R), k)
     return R
+
+
+def apply_q(Apre, Rpre, X, trans=False):
+    """Q X (trans False; X k x r) or Q^T X (trans True; X m x r) for the
+    implicit Q = Apre Rpre^{-1} (Apre m x k, Rpre k x k upper)."""
+    Apre = _fortran(Apre)
+    Rpre = _fortran(Rpre)
+    X = _fortran(X if X.ndim == 2 else X.reshape(-1, 1))
+    m, k = Apre.shape
+    r = X.shape[1]
+    Y = np.zeros((k if trans else m, r), dtype=np.float64, order="F")
+    lib().oracle_apply_q(1 if trans else 0, m, k, _ptr(Apre), m, _ptr(Rpre), k, r, _ptr(X),
+                         X.shape[0], _ptr(Y), Y.shape[0])
+    return Y
+
+
+def cqrrpt_implicit(M, gamma=1.25, nnz=4, tol=-1.0, seed=0):
+    """Alg. 1 without line 7: J, k, R as cqrrpt, plus M^pre[:, :k] (the
+    preconditioned matrix, line 4) and R^pre[:k, :k] (line 6), which
+    represent Q_k = M^pre (R^pre)^{-1}."""
+    res = cqrrpt(M, gamma, nnz, tol, seed)
+    k = res.k
+    if k:
+        res.Apre = trsm_rut(_fortran(M), res.Rsk[:k, :k], res.J[:k])
+    else:
+        res.Apre = np.zeros((_fortran(M).shape[0], 0), order="F")
+    return res
 
 
 class Result:

@@ -19,6 +19,8 @@
  *   Alg. 2 line 6          -> oracle_potrf_upper     R^pre = chol(G), Remark 3
  *   Alg. 2 line 7          -> oracle_trsm_rut        Q_k = M^pre (R^pre)^-1
  *   Alg. 2 line 8          -> oracle_trmm_upper      R_k = R^pre R^sk_k
+ *   Q_k = M^pre (R^pre)^-1 -> oracle_apply_q         Q X and Q^T Y without forming Q
+ *   (implicit Q: Sec. 3.2 notes that M^pre and R^pre represent Q_k)
  * The SASO operator is the one of Sec. 3.3.1 (each column of S has exactly s
  * nonzeros at uniformly random rows with values +-1/sqrt(s)).
  *
@@ -525,4 +527,56 @@ int oracle_cqrrpt(int64_t m, int64_t n, const double* M, int64_t ldm, double gam
                                          Rsk_out, Rpre_out, pivnorm, second);
     free(Msk);
     return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Implicit Q (Sec. 3.2: Q_k = M^pre (R^pre)^{-1}, Alg. 2 line 7 not formed): */
+/* trans == 0: Y (m x r) = Q X with X k x r:                                  */
+/*     W = (R^pre)^{-1} X by back substitution (row j: terms t = k-1 down to  */
+/*     j+1, one fma each, then one division), Y = M^pre W in ascending t     */
+/*     from +0.0, one fma per term;                                           */
+/* trans == 1: Y (k x r) = Q^T X with X m x r:                                */
+/*     Z = (M^pre)^T X as a blocked sum over the rows (ROW_BLOCK blocks,     */
+/*     ascending rows inside from +0.0, blocks added in ascending order from */
+/*     +0.0), then Y = (R^pre)^{-T} Z by forward substitution (row j: terms   */
+/*     t = 0 up to j-1, one fma each, then one division).                     */
+/* ------------------------------------------------------------------------ */
+void oracle_apply_q(int trans, int64_t m, int64_t k, const double* Apre, int64_t lda,
+                    const double* Rpre, int64_t ldr, int64_t nrhs, const double* X, int64_t ldx,
+                    double* Y, int64_t ldy) {
+    double* W = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    for (int64_t c = 0; c < nrhs; ++c) {
+        const double* x = X + c * ldx;
+        double* y = Y + c * ldy;
+        if (trans == 0) {
+            for (int64_t j = k - 1; j >= 0; --j) {
+                double s = x[j];
+                for (int64_t t = k - 1; t > j; --t) s = fma(-Rpre[j + t * ldr], W[t], s);
+                W[j] = s / Rpre[j + j * ldr];
+            }
+            for (int64_t i = 0; i < m; ++i) {
+                double s = 0.0;
+                for (int64_t t = 0; t < k; ++t) s = fma(Apre[i + t * lda], W[t], s);
+                y[i] = s;
+            }
+        } else {
+            for (int64_t t = 0; t < k; ++t) {
+                const double* a = Apre + t * lda;
+                double total = 0.0;
+                for (int64_t r0 = 0; r0 < m; r0 += ROW_BLOCK) {
+                    int64_t r1 = r0 + ROW_BLOCK < m ? r0 + ROW_BLOCK : m;
+                    double part = 0.0;
+                    for (int64_t r = r0; r < r1; ++r) part = fma(a[r], x[r], part);
+                    total = total + part;
+                }
+                W[t] = total;
+            }
+            for (int64_t j = 0; j < k; ++j) {
+                double s = W[j];
+                for (int64_t t = 0; t < j; ++t) s = fma(-Rpre[t + j * ldr], y[t], s);
+                y[j] = s / Rpre[j + j * ldr];
+            }
+        }
+    }
+    free(W);
 }

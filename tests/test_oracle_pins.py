@@ -377,3 +377,62 @@ def test_default_rank_rule_and_degenerate_cases():
     # non-finite input
     A[3, 2] = np.inf
     assert oracle.cqrrpt(A, 1.0, 2, -1.0, 4).status == 2
+
+
+# --------------------------------------------------------------------------
+# Implicit Q (Sec. 3.2: Q_k = M^pre (R^pre)^{-1}): apply Q and Q^T
+# --------------------------------------------------------------------------
+def test_apply_q_exact_on_integer_factors():
+    """With an integer M^pre and an upper R^pre whose diagonal holds powers
+    of two and whose solves stay integral, every step is exact: Q X and
+    Q^T Y equal exact rational arithmetic (pins the substitution direction,
+    the transposes and the indexing)."""
+    rng = _rng(41)
+    m, k, r = 2 * 4096 + 19, 5, 3
+    Apre = np.asfortranarray(rng.integers(-8, 9, (m, k)).astype(np.float64))
+    Rpre = np.triu(rng.integers(-3, 4, (k, k)).astype(np.float64), 1) + np.diag([1.0, 2.0, 1.0, 4.0, 1.0])
+    # X such that W = Rpre^{-1} X is integral: X = Rpre @ Wi
+    Wi = rng.integers(-5, 6, (k, r)).astype(np.float64)
+    X = Rpre @ Wi
+    Y = oracle.apply_q(Apre, Rpre, X)
+    assert np.array_equal(Y, Apre @ Wi)
+    # Q^T Y0: Z = Apre^T Y0 in exact integers, then the forward substitution
+    # with R^T in exact rationals (the divisors are powers of two)
+    Y0 = np.asfortranarray(rng.integers(-4, 5, (m, r)).astype(np.float64))
+    Z = [[sum(Fraction(int(a)) * Fraction(int(b)) for a, b in zip(Apre[:, t], Y0[:, c]))
+          for c in range(r)] for t in range(k)]
+    # exact forward substitution with R^T
+    Vx = [[None] * r for _ in range(k)]
+    for c in range(r):
+        for j in range(k):
+            s = Z[j][c] - sum(Fraction(Rpre[t, j]) * Vx[t][c] for t in range(j))
+            Vx[j][c] = s / Fraction(Rpre[j, j])
+    V = oracle.apply_q(Apre, Rpre, Y0, trans=True)
+    for j in range(k):
+        for c in range(r):
+            assert V[j, c] == float(Vx[j][c]), (j, c)
+
+
+def test_apply_q_matches_explicit_q_and_adjoint():
+    """On a cond-1e8 factorisation: the implicit Q X and Q^T Y match the
+    explicit Q of Alg. 2 line 7 to a few u, <Qx, y> = <x, Q^T y>, and
+    Q^T Q x = x (orthonormal columns, Theorem 2)."""
+    w = W.single_small()
+    M = np.asfortranarray(w.matrix().numpy())
+    res = oracle.cqrrpt_implicit(M, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    k = res.k
+    assert k == 64 and res.Apre.shape == (M.shape[0], k)
+    rng = _rng(42)
+    X = rng.standard_normal((k, 4))
+    Yq = oracle.apply_q(res.Apre, res.Rpre, X)
+    assert np.abs(Yq - res.Q @ X).max() <= 1e-12 * np.abs(X).max()
+    Y = rng.standard_normal((M.shape[0], 4))
+    Z = oracle.apply_q(res.Apre, res.Rpre, Y, trans=True)
+    assert np.abs(Z - res.Q.T @ Y).max() <= 1e-12 * np.linalg.norm(Y, axis=0).max()
+    lhs = np.sum(Yq * Y, axis=0)
+    rhs = np.sum(X * Z, axis=0)
+    assert np.abs(lhs - rhs).max() <= 1e-11 * np.abs(lhs).max()
+    back = oracle.apply_q(res.Apre, res.Rpre, Yq, trans=True)
+    assert np.abs(back - X).max() <= 1e-12 * np.abs(X).max()
+    # the implicit pieces are the explicit run's intermediates
+    assert np.array_equal(oracle.trsm_rut(res.Apre, res.Rpre), res.Q)

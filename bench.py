@@ -710,6 +710,45 @@ def main():
     except Exception as ex:  # reported, not hidden
         split = {"error": str(ex)}
 
+    # ---- the implicit Q (Alg. 2 without line 7): the factorisation returns
+    # M^pre and R^pre; Q X and Q^T Y are applied to 16 right-hand sides
+    implicit = None
+    try:
+        Ap = C.colmajor_empty(m, n)
+        Rp = C.colmajor_empty(n, n)
+        Ri = C.colmajor_empty(n, n)
+        Ji = torch.empty(n, dtype=torch.int64, device="cuda")
+        imp = C.cqrrpt_implicit(A, w.gamma, w.nnz, w.tol, w.sketch_seed, out=(Ap, Rp, Ri, Ji),
+                                handle=h, stream=stream)
+        Xr = torch.randn(16, imp.k, dtype=torch.float64, device="cuda").t()
+        Yr = torch.randn(16, m, dtype=torch.float64, device="cuda").t()
+        ms_i, ms_q, ms_qt = [], [], []
+        for _ in range(3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            imp = C.cqrrpt_implicit(A, w.gamma, w.nnz, w.tol, w.sketch_seed, out=(Ap, Rp, Ri, Ji),
+                                    handle=h, stream=stream)
+            ev[1].record(stream)
+            yq = imp.apply_q(Xr, stream=stream)
+            ev[2].record(stream)
+            zq = imp.apply_qt(Yr, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            ms_i.append(ev[0].elapsed_time(ev[1]))
+            ms_q.append(ev[1].elapsed_time(ev[2]))
+            ms_qt.append(ev[2].elapsed_time(ev[3]))
+        implicit = {"ms": statistics.median(ms_i),
+                    "factorizations_per_s": 1e3 / statistics.median(ms_i),
+                    "speedup_vs_explicit_q": ms_per_step / statistics.median(ms_i),
+                    "k": imp.k, "R_and_J_equal_explicit": bool(torch.equal(Ri[:k], R[:k])
+                                                               and torch.equal(Ji, J)),
+                    "apply_q_16rhs_ms": statistics.median(ms_q),
+                    "apply_qt_16rhs_ms": statistics.median(ms_qt),
+                    "apply_q_vs_explicit_max_abs": (yq - Q[:, :k] @ Xr).abs().max().item()}
+        del Ap, Rp, Ri, Ji, Xr, Yr, yq, zq
+    except Exception as ex:  # reported, not hidden
+        implicit = {"error": str(ex)}
+
     # ---- e2e through the public API with host buffers
     A_host = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
     A_host.copy_(A)
@@ -770,7 +809,8 @@ def main():
                     "one_call_per_matrix_ms_per_step": one_call_step},
             "gpu_launches": int(launches),
             "clocks": clk,
-            "splitbf16_same_input": split}
+            "splitbf16_same_input": split,
+            "implicit_q": implicit}
 
     # ---- CPU baseline: the oracle on the full workload (rank 0, N = 1 only)
     if rank == 0 and world == 1:

@@ -121,6 +121,37 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
              double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
              cudaStream_t stream);
 
+/* ---- implicit Q --------------------------------------------------------- */
+
+/* Alg. 1 in FP64 stopped before Alg. 2 line 7: M^pre = M[:, J[:k]]
+ * (R^sk_11)^{-1} (line 4) and R^pre = chol(M^pre^T M^pre) (line 6) are
+ * returned instead of Q_k; together they represent Q_k = M^pre (R^pre)^{-1}
+ * (Sec. 3.2), which cqrrpt_apply_q_d applies.  A client that only applies Q
+ * skips the line-7 solve, one of the two O(m k^2) triangular solves.
+ * J, k and R (= R^pre R^sk_k, line 8) are those of cqrrpt_d, bit for bit;
+ * Apre holds column j of cqrrpt_d's M^pre.  Arguments as cqrrpt_d, plus:
+ *   Apre, ldp     m x n capacity, ldp >= m; columns 0..k-1 receive M^pre.
+ *   Rpre, ldrp    n x n capacity, ldrp >= n; the leading k x k upper
+ *                 triangle receives R^pre. */
+int cqrrpt_implicit_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                      double gamma, int nnz_per_col, double tol, uint64_t seed, double* Apre,
+                      int64_t ldp, double* Rpre, int64_t ldrp, double* R, int64_t ldr, int64_t* J,
+                      int64_t* k_dev, int64_t* k_host, cudaStream_t stream);
+
+/* Y = Q X (trans 0) or Y = Q^T X (trans 1) for Q = Apre Rpre^{-1} (m x k,
+ * from cqrrpt_implicit_d; k is the host value it returned):
+ *   trans 0: X k x nrhs (ldx >= k), Y m x nrhs (ldy >= m):
+ *            W = Rpre^{-1} X by back substitution, then Y = Apre W;
+ *   trans 1: X m x nrhs (ldx >= m), Y k x nrhs (ldy >= k):
+ *            Z = Apre^T X as a sum over 4096-row blocks in ascending order,
+ *            then Y = Rpre^{-T} Z by forward substitution.
+ * Every sum has a fixed order (documented in applyq.cu), so results repeat
+ * bit for bit.  k = 0 gives Y = 0 (trans 0) or nothing (trans 1).  Device
+ * pointers; uses the handle's workspace; no host wait. */
+int cqrrpt_apply_q_d(cqrrpt_handle h, int trans, int64_t m, int64_t k, const double* Apre,
+                     int64_t ldp, const double* Rpre, int64_t ldrp, int64_t nrhs, const double* X,
+                     int64_t ldx, double* Y, int64_t ldy, cudaStream_t stream);
+
 /* ---- many factorisations from host memory -------------------------------- */
 
 /* `count` factorisations of m x n host-resident matrices (the same

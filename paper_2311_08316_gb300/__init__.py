@@ -75,6 +75,10 @@ def lib():
     L.cqrrpt_batched_set_tuning.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
     L.cqrrpt_gram_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
     L.cqrrpt_trsm_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_implicit_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _p, _i64, _p,
+                                    _i64, _p, _i64, _p, _p, _p, _p]
+    L.cqrrpt_apply_q_d.argtypes = [_p, _int, _i64, _i64, _p, _i64, _p, _i64, _i64, _p, _i64, _p,
+                                   _i64, _p]
     L.cqrrpt_host_pipeline_d.argtypes = [_p, _int, _i64, _i64, _p, _i64, _d, _int, _d, _p, _int,
                                          _p, _i64, _p, _i64, _p, _p, _p, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
@@ -95,7 +99,8 @@ def exported_symbols():
             "cqrrpt_set_profiling", "cqrrpt_phase_times", "cqrrpt_kernel_launches",
             "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs",
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
-            "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d"]
+            "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
+            "cqrrpt_implicit_d", "cqrrpt_apply_q_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -245,6 +250,76 @@ def cqrrpt(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64, out=None, han
     if not sync:
         return Factorization(Q, R, J, None, None)
     return Factorization(Q, R, J, k.value, rc)
+
+
+class ImplicitFactorization:
+    """Output of cqrrpt_implicit: M^pre (m x k), R^pre (k x k), R (k x n),
+    J, k, status; Q = M^pre (R^pre)^{-1} is applied with apply_q/apply_qt."""
+
+    def __init__(self, Abuf, Rprebuf, Rbuf, J, k, status, handle):
+        self.Abuf, self.Rprebuf, self.Rbuf, self.J = Abuf, Rprebuf, Rbuf, J
+        self.k, self.status, self.handle = k, status, handle
+
+    @property
+    def Apre(self):
+        return self.Abuf[:, : self.k]
+
+    @property
+    def Rpre(self):
+        return self.Rprebuf[: self.k, : self.k]
+
+    @property
+    def R(self):
+        return self.Rbuf[: self.k, :]
+
+    def apply_q(self, X, out=None, stream=None):
+        """Q X for X k x r (column-major CUDA float64)."""
+        return apply_q(self.Abuf, self.Rprebuf, self.k, X, False, out, self.handle, stream)
+
+    def apply_qt(self, Y, out=None, stream=None):
+        """Q^T Y for Y m x r."""
+        return apply_q(self.Abuf, self.Rprebuf, self.k, Y, True, out, self.handle, stream)
+
+
+def cqrrpt_implicit(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, out=None, handle=None, stream=None):
+    """Alg. 1 in FP64 without line 7 (cqrrpt_implicit_d): returns an
+    ImplicitFactorization (waits for k)."""
+    h = handle or default_handle()
+    m, n = A.shape
+    if out is None:
+        Ap = colmajor_empty(m, n, A.device)
+        Rp = colmajor_empty(n, n, A.device)
+        R = colmajor_empty(n, n, A.device)
+        J = torch.empty(n, dtype=torch.int64, device=A.device)
+    else:
+        Ap, Rp, R, J = out
+    k = _i64()
+    rc = lib().cqrrpt_implicit_d(h.h, m, n, A.data_ptr(), _ld(A), gamma, nnz, tol, seed,
+                                 Ap.data_ptr(), _ld(Ap), Rp.data_ptr(), _ld(Rp), R.data_ptr(),
+                                 _ld(R), J.data_ptr(), None, ctypes.byref(k), _stream(stream))
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_implicit_d")
+    return ImplicitFactorization(Ap, Rp, R, J, k.value, rc, h)
+
+
+def apply_q(Apre, Rpre, k, X, trans=False, out=None, handle=None, stream=None):
+    """Y = Q X (trans False, X k x r) or Q^T X (trans True, X m x r) for
+    Q = Apre[:, :k] Rpre[:k, :k]^{-1} through cqrrpt_apply_q_d."""
+    h = handle or default_handle()
+    m = Apre.shape[0]
+    if X.dim() == 1:
+        X = X.reshape(-1, 1)
+    if X.shape[0] and X.stride(0) != 1:
+        X = colmajor(X)
+    r = X.shape[1]
+    if out is None:
+        out = colmajor_empty(k if trans else m, r, X.device)
+    rc = lib().cqrrpt_apply_q_d(h.h, 1 if trans else 0, m, k, Apre.data_ptr(), _ld(Apre),
+                                Rpre.data_ptr(), _ld(Rpre), r, X.data_ptr(),
+                                _ld(X) if X.shape[0] else 1, out.data_ptr(),
+                                _ld(out) if out.shape[0] else 1, _stream(stream))
+    _check(rc, "cqrrpt_apply_q_d")
+    return out
 
 
 def sketch(A, d, nnz, seed, handle=None, stream=None):

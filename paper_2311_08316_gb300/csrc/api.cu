@@ -257,6 +257,69 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
 
 }  // namespace
 
+// Alg. 2 in FP64, one stream-ordered launch sequence (no host wait unless
+// k_host is given).  form_q = false stops before line 7: Q then holds
+// M^pre (the implicit Q with R^pre); Rpre_out (ld ld_rpre) receives R^pre,
+// else it stays in the workspace.
+static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                    int64_t d, int nnz, double tol, uint64_t seed, double* Q, int64_t ldq,
+                    double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
+                    cudaStream_t stream, bool form_q, double* Rpre_out, int64_t ld_rpre) {
+  const Plan p = plan_fp64(m, n, d, nnz);
+  int st = ensure_ws(h, p.total);
+  if (st != kOk) return st;
+  char* w = (char*)h->ws;
+  void* region = w; w += p.region;
+  double* X = (double*)w; w += p.x;
+  void* qw = w; w += p.qrcp;
+  double* Rsk = (double*)w; w += p.rsk;
+  double* G = (double*)w; w += p.g;
+  double* Rpre = (double*)w; w += p.rpre;
+  int64_t ldp = n;
+  if (Rpre_out) {  // R^pre straight into the caller's buffer
+    Rpre = Rpre_out;
+    ldp = ld_rpre;
+  }
+  double* f2 = (double*)w;
+  DeviceScalars* sc = h->sc;
+  int* status = &sc->status;
+  const int ni = (int)n, di = (int)d;
+  const double scale = 1.0 / std::sqrt((double)nnz);
+
+  cudaError_t e = launch_init_scalars(sc, 0, stream);
+  mark(h, 0, stream);
+  if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
+  mark(h, 1, stream);
+  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
+  mark(h, 2, stream);
+  if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
+  mark(h, 3, stream);
+  if (e == cudaSuccess)
+    e = launch_trsm_rut(m, ni, &sc->k, A, lda, J, Rsk, n, Q, ldq, status, stream);
+  mark(h, 4, stream);
+  if (e == cudaSuccess) e = launch_gram(m, ni, &sc->k, Q, ldq, G, n, region, status, stream);
+  mark(h, 5, stream);
+  if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, ldp, sc, stream);
+  if (e == cudaSuccess) e = launch_rank_stage2(Rpre, ldp, !(tol > 0.0), sc, stream);
+  mark(h, 6, stream);
+  if (e == cudaSuccess && form_q)
+    e = launch_trsm_rut(m, ni, &sc->k, Q, ldq, nullptr, Rpre, ldp, Q, ldq, status, stream);
+  mark(h, 7, stream);
+  if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, ldp, Rsk, n, R, ldr, status, stream);
+  mark(h, 8, stream);
+  if (e == cudaSuccess) e = launch_finalize(sc, k_dev, nullptr, stream);
+  if (e != cudaSuccess) return kCudaError;
+  if (k_host) {
+    int st2 = kOk;
+    int64_t kk = 0;
+    int r = cqrrpt_last_status(h, stream, &st2, &kk);
+    if (r != kOk) return r;
+    *k_host = kk;
+    return st2;
+  }
+  return kOk;
+}
+
 extern "C" {
 
 int cqrrpt_create(cqrrpt_handle* h, int device) {
@@ -354,54 +417,66 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
   if (precision != CQRRPT_FP64)
     return run_split(h, m, n, A, lda, d, nnz, tol, seed, precision, Q, ldq, R, ldr, J, k_dev,
                      k_host, stream);
-  const Plan p = plan_fp64(m, n, d, nnz);
-  int st = ensure_ws(h, p.total);
-  if (st != kOk) return st;
-  char* w = (char*)h->ws;
-  void* region = w; w += p.region;
-  double* X = (double*)w; w += p.x;
-  void* qw = w; w += p.qrcp;
-  double* Rsk = (double*)w; w += p.rsk;
-  double* G = (double*)w; w += p.g;
-  double* Rpre = (double*)w; w += p.rpre;
-  double* f2 = (double*)w;
-  DeviceScalars* sc = h->sc;
-  int* status = &sc->status;
-  const int ni = (int)n, di = (int)d;
-  const double scale = 1.0 / std::sqrt((double)nnz);
+  return run_fp64(h, m, n, A, lda, d, nnz, tol, seed, Q, ldq, R, ldr, J, k_dev, k_host, stream,
+                  true, nullptr, 0);
+}
 
-  cudaError_t e = launch_init_scalars(sc, 0, stream);
-  mark(h, 0, stream);
-  if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
-  mark(h, 1, stream);
-  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
-  mark(h, 2, stream);
-  if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
-  mark(h, 3, stream);
-  if (e == cudaSuccess)
-    e = launch_trsm_rut(m, ni, &sc->k, A, lda, J, Rsk, n, Q, ldq, status, stream);
-  mark(h, 4, stream);
-  if (e == cudaSuccess) e = launch_gram(m, ni, &sc->k, Q, ldq, G, n, region, status, stream);
-  mark(h, 5, stream);
-  if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, n, sc, stream);
-  if (e == cudaSuccess) e = launch_rank_stage2(Rpre, n, !(tol > 0.0), sc, stream);
-  mark(h, 6, stream);
-  if (e == cudaSuccess)
-    e = launch_trsm_rut(m, ni, &sc->k, Q, ldq, nullptr, Rpre, n, Q, ldq, status, stream);
-  mark(h, 7, stream);
-  if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, Rsk, n, R, ldr, status, stream);
-  mark(h, 8, stream);
-  if (e == cudaSuccess) e = launch_finalize(sc, k_dev, nullptr, stream);
-  if (e != cudaSuccess) return kCudaError;
-  if (k_host) {
-    int st2 = kOk;
-    int64_t kk = 0;
-    int r = cqrrpt_last_status(h, stream, &st2, &kk);
-    if (r != kOk) return r;
-    *k_host = kk;
-    return st2;
+int cqrrpt_implicit_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                      double gamma, int nnz, double tol, uint64_t seed, double* Apre, int64_t ldp,
+                      double* Rpre, int64_t ldrp, double* R, int64_t ldr, int64_t* J,
+                      int64_t* k_dev, int64_t* k_host, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 16384) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -6;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -6;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
+  if (std::isnan(tol)) return -8;
+  if (!Apre) return -10;
+  if (ldp < m) return -11;
+  if (!Rpre) return -12;
+  if (ldrp < n) return -13;
+  if (!R) return -14;
+  if (ldr < n) return -15;
+  if (!J) return -16;
+  DevGuard g(h->device);
+  return run_fp64(h, m, n, A, lda, d, nnz, tol, seed, Apre, ldp, R, ldr, J, k_dev, k_host, stream,
+                  false, Rpre, ldrp);
+}
+
+int cqrrpt_apply_q_d(cqrrpt_handle h, int trans, int64_t m, int64_t k, const double* Apre,
+                     int64_t ldp, const double* Rpre, int64_t ldrp, int64_t nrhs, const double* X,
+                     int64_t ldx, double* Y, int64_t ldy, cudaStream_t stream) {
+  if (!h) return -1;
+  if (trans != 0 && trans != 1) return -2;
+  if (m < 1) return -3;
+  if (k < 0 || k > m || k > 16384) return -4;
+  if (!Apre && k > 0) return -5;
+  if (ldp < m) return -6;
+  if (!Rpre && k > 0) return -7;
+  if (ldrp < (k > 0 ? k : 1)) return -8;
+  if (nrhs < 1 || nrhs > 65535) return -9;
+  if (!X && k > 0) return -10;
+  const int64_t xrows = trans ? m : k, yrows = trans ? k : m;
+  if (ldx < (xrows > 0 ? xrows : 1)) return -11;
+  if (!Y) return -12;
+  if (ldy < (yrows > 0 ? yrows : 1)) return -13;
+  DevGuard g(h->device);
+  if (k == 0) {  // Q has no columns: Q X = 0 (m x r); Q^T X is empty
+    if (!trans &&
+        cudaMemset2DAsync(Y, (size_t)ldy * 8, 0, (size_t)m * 8, (size_t)nrhs, stream) != cudaSuccess)
+      return kCudaError;
+    return kOk;
   }
-  return kOk;
+  int st = ensure_ws(h, (size_t)apply_q_workspace_bytes(trans, m, k, nrhs));
+  if (st != kOk) return st;
+  return launch_apply_q(trans, m, (int)k, Apre, ldp, Rpre, ldrp, (int)nrhs, X, ldx, Y, ldy, h->ws,
+                        stream) == cudaSuccess
+             ? kOk
+             : kCudaError;
 }
 
 }  // extern "C"

@@ -89,6 +89,13 @@ cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* bas
 // ---- Alg. 2 line 6 -------------------------------------------------------
 // Factors G (overwritten as working storage) into R (upper); on a
 // non-positive pivot at column j records sc->fail = j (Remark 3).
+// Implicit Q = M^pre (R^pre)^{-1} (applyq.cu): Y = Q X (trans 0, X k x r,
+// Y m x r) or Y = Q^T X (trans 1, X m x r, Y k x r); host k and r.
+int64_t apply_q_workspace_bytes(int trans, int64_t m, int64_t k, int64_t r);
+cudaError_t launch_apply_q(int trans, int64_t m, int k, const double* Apre, int64_t ldp,
+                           const double* Rpre, int64_t ldrp, int r, const double* X, int64_t ldx,
+                           double* Y, int64_t ldy, void* work, cudaStream_t s);
+
 cudaError_t launch_potrf(int kmax, double* G, int64_t ldg, double* R, int64_t ldr,
                          DeviceScalars* sc, cudaStream_t stream);
 // one CTA per problem runs every panel

@@ -333,3 +333,64 @@ def test_host_pipeline_splitbf16_matches_single_calls(C):
         assert r.status == 0 and r.k == one.k == 70
         assert torch.equal(r.J, one.J.cpu())
         assert torch.equal(r.Q, one.Q.cpu()) and torch.equal(r.R, one.R.cpu())
+
+
+# ---------------------------------------------------------------- implicit Q
+@pytest.mark.parametrize("m,n,rank,gamma,nnz,tol", [
+    (4096 * 2 + 77, 60, 60, 1.25, 4, -1.0),
+    (16384 + 5, 96, 70, 1.25, 8, 1e-9),
+])
+def test_implicit_matches_oracle(C, m, n, rank, gamma, nnz, tol):
+    """cqrrpt_implicit_d: M^pre, R^pre, R, J and k bit-identical to the
+    oracle's lines 1-6 and 8 (line 7 not formed)."""
+    sv = np.zeros(n)
+    sv[:rank] = W.logspaced(rank, -7.0).numpy()
+    A = np.asfortranarray(W.planted(m, n, sv, 77 + m, noise=(1e-15 if rank < n else 0.0)).numpy())
+    ref = oracle.cqrrpt_implicit(A, gamma, nnz, tol, 5 + n)
+    res = C.cqrrpt_implicit(gpu(A), gamma, nnz, tol, 5 + n)
+    assert res.status == ref.status and res.k == ref.k
+    if tol > 0:
+        assert res.k == rank
+    assert_bits(host(res.J), ref.J, "J")
+    assert_bits(host(res.Apre), ref.Apre, "Apre")
+    assert_bits(np.triu(host(res.Rpre)), np.triu(ref.Rpre), "Rpre")
+    assert_bits(host(res.R), ref.R, "R")
+
+
+@pytest.mark.parametrize("r", [1, 5, 17, 40])
+def test_apply_q_matches_oracle(C, r):
+    """Q X and Q^T Y through cqrrpt_apply_q_d, bit for bit against the
+    oracle's apply_q on the oracle's own M^pre and R^pre (ragged row blocks,
+    right-hand-side counts across the kernels' 16- and 32-column tiles)."""
+    w = W.single_large(m=3 * 4096 + 501, n=72, rank=50)
+    A = np.asfortranarray(w.matrix().numpy())
+    ref = oracle.cqrrpt_implicit(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    k = ref.k
+    assert k == 50
+    rng = _rng(100 + r)
+    X = np.asfortranarray(rng.standard_normal((k, r)))
+    Y = np.asfortranarray(rng.standard_normal((A.shape[0], r)))
+    Ap, Rp = gpu(ref.Apre), gpu(ref.Rpre)
+    got_q = C.apply_q(Ap, Rp, k, gpu(X))
+    got_qt = C.apply_q(Ap, Rp, k, gpu(Y), trans=True)
+    assert_bits(host(got_q), oracle.apply_q(ref.Apre, ref.Rpre, X), "QX")
+    assert_bits(host(got_qt), oracle.apply_q(ref.Apre, ref.Rpre, Y, trans=True), "QtY")
+
+
+def test_apply_q_through_the_factorisation_and_k_zero(C):
+    """The implicit factorisation's own apply_q equals the explicit Q of
+    cqrrpt_d applied with torch to a few u; k = 0 gives Q X = 0."""
+    w = W.single_small()
+    A = gpu(np.asfortranarray(w.matrix().numpy()))
+    imp = C.cqrrpt_implicit(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    exp = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    assert imp.k == exp.k == 64
+    assert torch.equal(imp.R, exp.R) and torch.equal(imp.J, exp.J)
+    X = torch.randn(64, 3, dtype=torch.float64, device="cuda")
+    assert (imp.apply_q(X) - exp.Q @ X).abs().max().item() <= 1e-12 * X.abs().max().item()
+    Y = torch.randn(A.shape[0], 3, dtype=torch.float64, device="cuda")
+    assert (imp.apply_qt(Y) - exp.Q.t() @ Y).abs().max().item() <= 1e-12 * Y.norm(dim=0).max().item()
+    zero = C.cqrrpt_implicit(gpu(np.zeros((300, 6))), 1.25, 2, -1.0, 1)
+    assert zero.k == 0 and zero.status == 1
+    out = C.apply_q(zero.Abuf, zero.Rprebuf, 0, torch.zeros(0, 2, dtype=torch.float64, device="cuda"))
+    assert out.shape == (300, 2) and torch.count_nonzero(out).item() == 0

@@ -29,7 +29,7 @@ constexpr int kTrsvThreads = 256;
 constexpr int kQaRows = 128;    // Q X: rows (threads) per CTA
 constexpr int kQaCols = 16;     // Q X: right-hand sides per CTA (register accumulators)
 constexpr int kQaChunk = 128;   // Q X: rows of W staged per chunk
-constexpr int kQtTile = 32;     // Q^T Y: output tile edge (t x c)
+constexpr int kQtTile = 32;     // Q^T Y: output tile edge in t
 constexpr int kQtRows = 32;     // Q^T Y: rows staged per chunk
 
 // Solve T w = b for every column of B (T upper k x k: back substitution),
@@ -123,27 +123,29 @@ __global__ void __launch_bounds__(kQaRows)
 }
 
 // Partial P_b[t, c] = sum_{rows of block b} A[row, t] X[row, c] (ascending
-// rows, one fma per term from +0.0): one CTA per (block, 32 x 32 tile), 64
-// threads with 4 x 4 register tiles.
+// rows, one fma per term from +0.0): one CTA per (block, 32 x TC tile), 64
+// threads in an 8 x 8 grid with 4 x (TC / 8) register tiles (TC = 16 when
+// there are at most 16 right-hand sides).
+template <int TC>
 __global__ void __launch_bounds__(64)
     qt_partial_kernel(int64_t m, int k, int r, const double* __restrict__ A, int64_t lda,
                       const double* __restrict__ X, int64_t ldx, double* __restrict__ P) {
   __shared__ double As[kQtTile][kQtRows + 1];
-  __shared__ double Xs[kQtTile][kQtRows + 1];
-  constexpr int R = kQtTile / 8;
+  __shared__ double Xs[TC][kQtRows + 1];
+  constexpr int RT = kQtTile / 8, RC = TC / 8;
   const int tiles_t = (k + kQtTile - 1) / kQtTile;
-  const int tiles_c = (r + kQtTile - 1) / kQtTile;
+  const int tiles_c = (r + TC - 1) / TC;
   const int64_t b = blockIdx.x / ((int64_t)tiles_t * tiles_c);
   const int rem = (int)(blockIdx.x - b * (int64_t)tiles_t * tiles_c);
-  const int t0 = (rem / tiles_c) * kQtTile, c0 = (rem % tiles_c) * kQtTile;
+  const int t0 = (rem / tiles_c) * kQtTile, c0 = (rem % tiles_c) * TC;
   const int64_t r0 = b * kRowBlock;
   const int rows = (int)min64(kRowBlock, m - r0);
   const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
-  double acc[R][R];
+  double acc[RT][RC];
 #pragma unroll
-  for (int u = 0; u < R; ++u)
+  for (int u = 0; u < RT; ++u)
 #pragma unroll
-    for (int v = 0; v < R; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < RC; ++v) acc[u][v] = 0.0;
   for (int rr0 = 0; rr0 < rows; rr0 += kQtRows) {
     const int nr = min(kQtRows, rows - rr0);
     __syncthreads();
@@ -152,27 +154,27 @@ __global__ void __launch_bounds__(64)
       const int64_t rr = r0 + rr0 + row;
       const bool rok = row < nr;
       As[col][row] = (rok && t0 + col < k) ? A[(int64_t)(t0 + col) * lda + rr] : 0.0;
-      Xs[col][row] = (rok && c0 + col < r) ? X[(int64_t)(c0 + col) * ldx + rr] : 0.0;
+      if (col < TC) Xs[col][row] = (rok && c0 + col < r) ? X[(int64_t)(c0 + col) * ldx + rr] : 0.0;
     }
     __syncthreads();
     for (int row = 0; row < nr; ++row) {
-      double va[R], vx[R];
+      double va[RT], vx[RC];
 #pragma unroll
-      for (int u = 0; u < R; ++u) va[u] = As[ty * R + u][row];
+      for (int u = 0; u < RT; ++u) va[u] = As[ty * RT + u][row];
 #pragma unroll
-      for (int v = 0; v < R; ++v) vx[v] = Xs[tx * R + v][row];
+      for (int v = 0; v < RC; ++v) vx[v] = Xs[tx * RC + v][row];
 #pragma unroll
-      for (int u = 0; u < R; ++u)
+      for (int u = 0; u < RT; ++u)
 #pragma unroll
-        for (int v = 0; v < R; ++v) acc[u][v] = __fma_rn(va[u], vx[v], acc[u][v]);
+        for (int v = 0; v < RC; ++v) acc[u][v] = __fma_rn(va[u], vx[v], acc[u][v]);
     }
   }
   double* Pb = P + b * (int64_t)k * r;
 #pragma unroll
-  for (int u = 0; u < R; ++u)
+  for (int u = 0; u < RT; ++u)
 #pragma unroll
-    for (int v = 0; v < R; ++v) {
-      const int t = t0 + ty * R + u, c = c0 + tx * R + v;
+    for (int v = 0; v < RC; ++v) {
+      const int t = t0 + ty * RT + u, c = c0 + tx * RC + v;
       if (t < k && c < r) Pb[(int64_t)c * k + t] = acc[u][v];
     }
 }
@@ -230,8 +232,12 @@ cudaError_t launch_apply_q(int trans, int64_t m, int k, const double* Apre, int6
   double* Tt = (double*)w;
   const dim3 tg((unsigned)((k + 31) / 32), (unsigned)((k + 31) / 32));
   transpose_kernel<<<tg, 256, 0, s>>>(k, Rpre, ldrp, Tt);
-  const int64_t tiles = nb * ((k + kQtTile - 1) / kQtTile) * ((r + kQtTile - 1) / kQtTile);
-  qt_partial_kernel<<<(unsigned)tiles, 64, 0, s>>>(m, k, r, Apre, ldp, X, ldx, P);
+  const int tc = r <= 16 ? 16 : 32;
+  const int64_t tiles = nb * ((k + kQtTile - 1) / kQtTile) * ((r + tc - 1) / tc);
+  if (tc == 16)
+    qt_partial_kernel<16><<<(unsigned)tiles, 64, 0, s>>>(m, k, r, Apre, ldp, X, ldx, P);
+  else
+    qt_partial_kernel<32><<<(unsigned)tiles, 64, 0, s>>>(m, k, r, Apre, ldp, X, ldx, P);
   qt_combine_kernel<<<(unsigned)(((int64_t)k * r + kCombineThreads - 1) / kCombineThreads),
                       kCombineThreads, 0, s>>>(nb, k, r, P, Z);
   count_launches(3);

@@ -21,6 +21,9 @@
 //      then publishes its candidate;  -- barrier --
 // All reads of data written by other CTAs bypass L1 (ld.global.cg).  Grid
 // barriers spin a bounded number of times (status kTimeout on expiry).
+#include <algorithm>
+#include <cstdlib>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -241,18 +244,34 @@ __global__ void __launch_bounds__(1024) qrcp_batched_kernel(const QrcpDesc* D, d
   qrcp_body(1, 0, D[blockIdx.x], tol3z);
 }
 
-// dot32 of x[0..len) with itself from shared memory, by one warp.
-__device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len) {
+// dot32 of x[0..len) with itself (shared memory, or an owned column in
+// global memory: eight loads in flight per lane), by one warp.
+__device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len,
+                                                       bool global = false) {
   const int lane = threadIdx.x & 31;
   double acc = 0.0;
-  for (int i = lane; i < len; i += 32) acc = __fma_rn(x[i], x[i], acc);
+  int i = lane;
+  if (global)
+    for (; i + 32 * 7 < len; i += 32 * 8) {
+    double xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = x[i + 32 * u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = __fma_rn(xv[u], xv[u], acc);
+  }
+  for (; i < len; i += 32) acc = __fma_rn(x[i], x[i], acc);
   return warp_tree_sum32(acc);
 }
 
 // Same arithmetic as qrcp_body, one grid barrier per step instead of two.
-// Every CTA keeps its owned columns (cache[q * d + r] is row r of physical
-// column bid + G q), their partial norms and its own copy of the
-// position <-> column maps in shared memory for the whole factorisation.
+// Every CTA keeps its first qc owned columns (cache[q * d + r] is row r of
+// physical column bid + G q), the partial norms of all of them and its own
+// copy of the position <-> column maps in shared memory for the whole
+// factorisation; owned columns q >= qc (when the sketch is too large for
+// the SMs' shared memory) stay in X, which only their owner writes.  For a
+// pivot column in X the owner writes beta into X after the next barrier
+// (the other CTAs read the column during the step) and leaves the rows
+// below it as they were (only R^sk is read afterwards).
 // At the end of a step a CTA publishes its best candidate and writes that
 // column's current rows j+1.. to X (global); after the barrier every CTA
 // picks the same pivot P, reads P's column from X and forms the same
@@ -261,7 +280,8 @@ __device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len)
 // columns -- so no second barrier is needed to broadcast the reflector.  The
 // owner of P also stores beta and v into its cached column.  All owned
 // columns are written back at the end; CTA 0 writes the maps and tau.
-__global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, double tol3z) {
+__global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, double tol3z,
+                                                                   int qc) {
   extern __shared__ double cache[];
   const int G = gridDim.x, bid = blockIdx.x;
   const int d = D.d, n = D.n;
@@ -273,7 +293,8 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   const int nwarps = blockDim.x >> 5;
   int* status = &sc->status;
   const int nown = bid < n ? (n - bid + G - 1) / G : 0;
-  double* vbuf = cache + (int64_t)nown * d;          // d
+  const int ncached = nown < qc ? nown : qc;
+  double* vbuf = cache + (int64_t)ncached * d;       // d
   double* vn1 = vbuf + d;                             // nown
   double* vn2 = vn1 + nown;                           // nown
   int* phys = (int*)(vn2 + nown);                     // n
@@ -281,13 +302,19 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   __shared__ int sh_P, sh_p;
   __shared__ double sh_tau, sh_beta, sh_rden;
   __shared__ int sh_nz;
+  __shared__ double* sh_pend;  // beta of a pivot column in X, written after the barrier
+  __shared__ double sh_pend_val;
   __shared__ double red_val[32];
   __shared__ int red_pos[32];
   __shared__ int red_col[32];
 
   if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
 
-  for (int q = 0; q < nown; ++q) {
+  // owned column q: shared memory for q < ncached, else its column of X
+  auto colptr = [&](int q) -> double* {
+    return q < ncached ? cache + (int64_t)q * d : X + (int64_t)(bid + G * q) * ldx;
+  };
+  for (int q = 0; q < ncached; ++q) {
     const double* src = X + (int64_t)(bid + G * q) * ldx;
     for (int r = threadIdx.x; r < d; r += blockDim.x) cache[(int64_t)q * d + r] = src[r];
   }
@@ -295,9 +322,10 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     phys[c] = c;
     posof[c] = c;
   }
+  if (threadIdx.x == 0) sh_pend = nullptr;
   __syncthreads();
   for (int q = warp; q < nown; q += nwarps) {
-    const double s = warp_dot32_self_smem(cache + (int64_t)q * d, d);
+    const double s = warp_dot32_self_smem(colptr(q), d, q >= ncached);
     if (lane == 0) {
       const double v = __dsqrt_rn(s);
       vn1[q] = v;
@@ -330,7 +358,7 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     }
     __syncthreads();
     const int q = red_col[0];
-    if (q >= 0) {
+    if (q >= 0 && q < ncached) {  // a column in X is already there
       double* dst = X + (int64_t)(bid + G * q) * ldx;
       const double* src = cache + (int64_t)q * d;
       for (int r = j_done + 1 + threadIdx.x; r < d; r += blockDim.x) dst[r] = src[r];
@@ -340,6 +368,12 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   bool ok = grid_sync(&sc->bar, G, status);
 
   for (int j = 0; ok && j < n; ++j) {
+    // beta of the previous pivot, if its column lives in X: every CTA has
+    // read that column by now
+    if (threadIdx.x == 0 && sh_pend) {
+      *sh_pend = sh_pend_val;
+      sh_pend = nullptr;
+    }
     // 1. global pivot (every CTA alike)
     if (warp == 0) {
       double bv = -1.0;
@@ -395,18 +429,24 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     const bool nz = sh_nz != 0;
     const double rden = sh_rden;
     const bool owner = (P % G == bid);
-    double* cP = owner ? cache + (int64_t)((P - bid) / G) * d : nullptr;
+    const int qP = (P - bid) / G;
+    const bool owner_cached = owner && qP < ncached;
+    double* cP = owner_cached ? cache + (int64_t)qP * d : nullptr;
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
       double v = 1.0;
       if (i > 0) {
         const double x = vbuf[i];
         v = nz ? __dmul_rn(x, rden) : x;
-        if (owner) cP[j + i] = v;
+        if (owner_cached) cP[j + i] = v;
       }
       vbuf[i] = v;
     }
     if (threadIdx.x == 0) {
-      if (owner && nz) cP[j] = sh_beta;
+      if (owner_cached && nz) cP[j] = sh_beta;
+      if (owner && !owner_cached && nz) {
+        sh_pend = X + (int64_t)P * ldx + j;
+        sh_pend_val = sh_beta;
+      }
       const int Pj = phys[j];
       phys[p] = Pj;
       posof[Pj] = p;
@@ -420,12 +460,24 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     for (int q = warp; q < nown; q += nwarps) {
       const int c = bid + G * q;
       if (posof[c] <= j) continue;
-      double* colc = cache + (int64_t)q * d + j;
+      double* colc = colptr(q) + j;
+      // eight loads in flight per lane (a column in X sits in L2), the fmas
+      // still in ascending order
       double acc = 0.0;
-      for (int i = lane; i < len; i += 32) acc = __fma_rn(vbuf[i], colc[i], acc);
+      int i = lane;
+      if (q >= ncached)
+        for (; i + 32 * 7 < len; i += 32 * 8) {
+          double xv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) xv[u] = colc[i + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) acc = __fma_rn(vbuf[i + 32 * u], xv[u], acc);
+        }
+      for (; i < len; i += 32) acc = __fma_rn(vbuf[i], colc[i], acc);
       const double wsum = warp_tree_sum32(acc);
       const double t = __dmul_rn(-tau, wsum);
-      for (int i = lane; i < len; i += 32) colc[i] = __fma_rn(vbuf[i], t, colc[i]);
+#pragma unroll 8
+      for (int i2 = lane; i2 < len; i2 += 32) colc[i2] = __fma_rn(vbuf[i2], t, colc[i2]);
       __syncwarp();
       const double v1 = vn1[q];
       if (v1 != 0.0) {
@@ -436,7 +488,8 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
         const double ratio = __ddiv_rn(v1, v2);
         const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
         if (temp2 <= tol3z) {
-          const double s2 = (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1) : 0.0;
+          const double s2 =
+              (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1, q >= ncached) : 0.0;
           if (lane == 0) {
             const double nv = (j + 1 < d) ? __dsqrt_rn(s2) : 0.0;
             vn1[q] = nv;
@@ -455,7 +508,8 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   // write the owned columns back (also after an early exit, so that global
   // memory holds this CTA's last state) and, from CTA 0, the maps
   __syncthreads();
-  for (int q = 0; q < nown; ++q) {
+  if (threadIdx.x == 0 && sh_pend) *sh_pend = sh_pend_val;  // after the last barrier
+  for (int q = 0; q < ncached; ++q) {
     double* dst = X + (int64_t)(bid + G * q) * ldx;
     for (int r = threadIdx.x; r < d; r += blockDim.x) dst[r] = cache[(int64_t)q * d + r];
   }
@@ -509,11 +563,23 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   if (G < 1) G = 1;
   const double tol3z = tol3z_value();
   void* args[] = {&D, (void*)&tol3z};
-  // owned columns, their norms and the maps resident in shared memory when
-  // they fit
+  // the maps, norms and reflector buffer in shared memory, and as many
+  // owned columns as fit beside them (all of them for most sketches)
   const int64_t nown = (n + G - 1) / G;
-  const size_t smem = (size_t)(nown * d + d + 2 * nown) * sizeof(double) + (size_t)2 * n * sizeof(int);
-  bool cached = smem <= 200 * 1024;
+  const int64_t kSmemCap = 200 * 1024;
+  const int64_t fixed = (int64_t)(d + 2 * nown) * 8 + (int64_t)2 * n * 4;
+  int64_t qc = fixed < kSmemCap ? std::min<int64_t>(nown, (kSmemCap - fixed) / ((int64_t)d * 8)) : 0;
+  // CQRRPT_QRCP_CACHED_COLUMNS caps the columns kept in shared memory per
+  // CTA (tests of the mixed storage on small sketches); the result is the
+  // same whatever the cap
+  if (const char* cap = std::getenv("CQRRPT_QRCP_CACHED_COLUMNS")) {
+    const long v = std::strtol(cap, nullptr, 10);
+    if (v >= 0 && v < qc) qc = v;
+  }
+  const size_t smem = (size_t)(fixed + qc * d * 8);
+  bool cached = fixed < kSmemCap;
+  int qci = (int)qc;
+  void* args_c[] = {&D, (void*)&tol3z, &qci};
   if (cached) {
     e = cudaFuncSetAttribute(qrcp_cached_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
@@ -526,7 +592,7 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   }
   if (cached)
     e = cudaLaunchCooperativeKernel((const void*)qrcp_cached_kernel, dim3(G), dim3(kQrcpThreads),
-                                    args, smem, stream);
+                                    args_c, smem, stream);
   else
     e = cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(G), dim3(kQrcpThreads), args, 0,
                                     stream);

@@ -394,3 +394,25 @@ def test_apply_q_through_the_factorisation_and_k_zero(C):
     assert zero.k == 0 and zero.status == 1
     out = C.apply_q(zero.Abuf, zero.Rprebuf, 0, torch.zeros(0, 2, dtype=torch.float64, device="cuda"))
     assert out.shape == (300, 2) and torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("cap", ["0", "1", "3"])
+def test_qrcp_mixed_storage(C, cap, monkeypatch):
+    """Sketches too large for the SMs' shared memory keep some owned columns
+    in global memory; forcing that on a small sketch (at most `cap` columns
+    per CTA in shared memory) leaves J and R^sk bit-identical to the
+    oracle, including exact ties and a zero column."""
+    monkeypatch.setenv("CQRRPT_QRCP_CACHED_COLUMNS", cap)
+    rng = _rng(90 + int(cap))
+    d, n = 700, 600
+    X = rng.standard_normal((d, 300)) @ rng.standard_normal((300, n))
+    X[:, 7] = X[:, 2]
+    X[:, 500] = 0.0
+    R_ref, J_ref, *_ = oracle.qrcp(X)
+    Rsk, J = C.qrcp(gpu(X))
+    torch.cuda.synchronize()
+    assert_bits(host(J), J_ref, "J")
+    assert_bits(host(Rsk), R_ref, "R^sk")
+    w = W.single_large(m=8192 + 300, n=96, rank=70)
+    A = np.asfortranarray(w.matrix().numpy())
+    _compare_full(C, A, w.gamma, w.nnz, w.tol, w.sketch_seed)

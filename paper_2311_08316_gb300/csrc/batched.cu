@@ -13,6 +13,7 @@
 // pinned host staging buffer and copied to the workspace with one
 // cudaMemcpyAsync per call; the copy is ordered before the launches on the
 // caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -89,6 +90,7 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
   DeviceScalars* sc = P.scalars;
   b_list[0] = b_part[0] = b_comb[0] = b_gath[0] = b_trsm[0] = b_gp[0] = b_gc[0] = b_tm[0] = 0;
   int max_d = 1;
+  int64_t qrcp_smem = 0;
   for (int p = 0; p < batch; ++p) {
     const BatchProblem& q = probs[p];
     const int64_t m = q.m, n = q.n, d = q.d;
@@ -118,6 +120,10 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     S.M = q.A; S.ldm = q.lda; S.Msk = X; S.ldsk = d; S.status = &s->status;
     sketch_carve(S, region);
     qr[p] = QrcpDesc{(int)d, (int)n, X, d, qrcp_carve(qw, (int)n), q.J, Rsk, n, s};
+    {  // shared memory the batched QRCP would like for this problem
+      const int64_t want = (d + 2 * n) * 8 + 2 * n * 4 + n * d * 8;
+      if (want > qrcp_smem) qrcp_smem = want;
+    }
     rk[p] = RankDesc{(int)n, Rsk, n, q.tol, f2, s};
     t1[p] = TrsmDesc{m, &s->k, q.A, q.lda, q.J, Rsk, n, q.Q, q.ldq, &s->status, jb};
     gr[p] = GramDesc{m, (int)n, &s->k, q.Q, q.ldq, (double*)region, G, n, &s->status, gt};
@@ -129,13 +135,32 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     b_list[p + 1] = b_list[p] + sketch_list_tiles(S);
     b_part[p + 1] = b_part[p] + sketch_partial_tiles(S);
     b_comb[p + 1] = b_comb[p] + sketch_combine_tiles(S);
-    b_gath[p + 1] = b_gath[p] + n;
+
     b_trsm[p + 1] = b_trsm[p] + trsm_tiles(m);
     b_gp[p + 1] = b_gp[p] + gram_partial_tiles(m, (int)n, gt);
     b_gc[p + 1] = b_gc[p] + gram_combine_tiles((int)n);
     b_tm[p + 1] = b_tm[p] + trmm_tiles((int)n);
   }
   P.max_d = max_d;
+  P.qrcp_smem = qrcp_smem < kQrcpSmemCap ? qrcp_smem : kQrcpSmemCap;
+  // the QRCP takes one CTA per problem: largest work (n^2 d) first, so that
+  // the long factorisations do not start last; the gather follows the same
+  // order
+  {
+    std::vector<int> order((size_t)batch);
+    for (int p = 0; p < batch; ++p) order[(size_t)p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      const double wa = (double)probs[a].n * probs[a].n * probs[a].d;
+      const double wb = (double)probs[b].n * probs[b].n * probs[b].d;
+      return wa > wb;
+    });
+    std::vector<QrcpDesc> sorted((size_t)batch);
+    for (int i = 0; i < batch; ++i) {
+      sorted[(size_t)i] = qr[(size_t)order[(size_t)i]];
+      b_gath[i + 1] = b_gath[i] + sorted[(size_t)i].n;
+    }
+    qr.swap(sorted);
+  }
   P.tiles_list = b_list[batch];
   P.tiles_part = b_part[batch];
   P.tiles_comb = b_comb[batch];
@@ -183,7 +208,8 @@ cudaError_t batch_launch_front(const BatchPlan& P, cudaStream_t s) {
   if (e == cudaSuccess) e = launch_sketch_batched(0, P.sk, P.base_list, np, P.tiles_list, P.max_d, s);
   if (e == cudaSuccess) e = launch_sketch_batched(1, P.sk, P.base_part, np, P.tiles_part, P.max_d, s);
   if (e == cudaSuccess) e = launch_sketch_batched(2, P.sk, P.base_comb, np, P.tiles_comb, P.max_d, s);
-  if (e == cudaSuccess) e = launch_qrcp_batched(P.qr, np, P.base_gath, P.tiles_gath, s);
+  if (e == cudaSuccess)
+    e = launch_qrcp_batched(P.qr, np, P.base_gath, P.tiles_gath, P.qrcp_smem, s);
   if (e == cudaSuccess) e = launch_rank_batched(P.rk, np, s);
   return e;
 }

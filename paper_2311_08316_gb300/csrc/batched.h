@@ -26,6 +26,7 @@ struct BatchProblem {
 
 struct BatchPlan {
   int nprob = 0, max_d = 1;
+  int64_t qrcp_smem = 0;  // dynamic shared memory of the batched QRCP
   int64_t tiles_list = 0, tiles_part = 0, tiles_comb = 0, tiles_gath = 0, tiles_trsm = 0,
           tiles_gp = 0, tiles_gc = 0, tiles_tm = 0;
   DeviceScalars* scalars = nullptr;  // device, nprob entries

@@ -15,6 +15,7 @@ namespace cqrrpt {
 constexpr int kSkCols = 2;        // sketch: columns per CTA
 constexpr int kSkThreads = 1024;  // sketch: threads per CTA, at most
 constexpr int kQrcpThreads = 256;
+constexpr int64_t kQrcpSmemCap = 200 * 1024;  // QRCP: dynamic shared memory per CTA, at most
 constexpr int kTrsmThreads = 128;
 constexpr int kTrsmJB = 32;       // TRSM: columns solved per register block
 constexpr int kTrsmTB = 64;       // TRSM: rows of T staged per chunk
@@ -51,8 +52,11 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
                         cudaStream_t stream);
 // one CTA per problem (no grid barrier), then the gather
+// qrcp_smem_bytes > 0: one CTA per problem in shared memory (sketch columns
+// that do not fit stay in global memory); 0: the global-memory kernel.
 cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gather_base,
-                                int64_t gather_tiles, cudaStream_t stream);
+                                int64_t gather_tiles, int64_t qrcp_smem_bytes,
+                                cudaStream_t stream);
 
 // ---- Alg. 2 line 3 -------------------------------------------------------
 // tol > 0: leading count of R_jj > tol R_00; tol <= 0: stage 1.

@@ -280,10 +280,12 @@ __device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len,
 // columns -- so no second barrier is needed to broadcast the reflector.  The
 // owner of P also stores beta and v into its cached column.  All owned
 // columns are written back at the end; CTA 0 writes the maps and tau.
-__global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, double tol3z,
-                                                                   int qc) {
-  extern __shared__ double cache[];
-  const int G = gridDim.x, bid = blockIdx.x;
+// G CTAs (bid = this CTA's index) on one problem, qc owned columns of each
+// cached; G = 1 (one CTA per problem, the batched form) keeps the candidate
+// and reads the pivot column in shared memory when it is cached: no global
+// memory round trip per step.
+__device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z, int qc, int G,
+                                                 int bid, double* cache) {
   const int d = D.d, n = D.n;
   double* X = D.X;
   const int64_t ldx = D.ldx;
@@ -351,14 +353,17 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     if (threadIdx.x == 0) {
       for (int i = 1; i < nwarps; ++i)
         if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bq = red_col[i]; }
-      w.cand_val[bid] = bv;
-      w.cand_pos[bid] = bp;
-      w.cand_col[bid] = bq >= 0 ? bid + G * bq : -1;
+      if (G > 1) {
+        w.cand_val[bid] = bv;
+        w.cand_pos[bid] = bp;
+        w.cand_col[bid] = bq >= 0 ? bid + G * bq : -1;
+      }
       red_col[0] = bq;
+      red_pos[0] = bp;
     }
     __syncthreads();
     const int q = red_col[0];
-    if (q >= 0 && q < ncached) {  // a column in X is already there
+    if (G > 1 && q >= 0 && q < ncached) {  // a column in X is already there
       double* dst = X + (int64_t)(bid + G * q) * ldx;
       const double* src = cache + (int64_t)q * d;
       for (int r = j_done + 1 + threadIdx.x; r < d; r += blockDim.x) dst[r] = src[r];
@@ -375,7 +380,12 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
       sh_pend = nullptr;
     }
     // 1. global pivot (every CTA alike)
-    if (warp == 0) {
+    if (G == 1) {
+      if (threadIdx.x == 0) {
+        sh_P = red_col[0] >= 0 ? red_col[0] : -1;  // G = 1: column q is physical column q
+        sh_p = red_pos[0];
+      }
+    } else if (warp == 0) {
       double bv = -1.0;
       int bp = 0x7fffffff, bc = -1;
       for (int i = lane; i < G; i += 32) {
@@ -405,7 +415,12 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     // takes its norm (dot32) and the column is scaled in place
     const double* gP = X + (int64_t)P * ldx;
     const int len = d - j;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = __ldcg(gP + j + i);
+    if (G == 1 && P < ncached) {  // the pivot column is in this CTA's shared memory
+      const double* cPs = cache + (int64_t)P * d + j;
+      for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = cPs[i];
+    } else {
+      for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = __ldcg(gP + j + i);
+    }
     __syncthreads();
     if (warp == 0) {
       const double alpha = vbuf[0];
@@ -520,6 +535,29 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
     }
 }
 
+__global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, double tol3z,
+                                                                   int qc) {
+  extern __shared__ double cache[];
+  qrcp_cached_body(D, tol3z, qc, gridDim.x, blockIdx.x, cache);
+}
+
+// One CTA per problem (G = 1), the problems in the table's order (the batch
+// planner puts the largest first); smem_bytes of dynamic shared memory hold
+// the maps, norms and reflector buffer and as many columns as fit.
+constexpr int kQrcpBatchThreads = 512;
+__global__ void __launch_bounds__(kQrcpBatchThreads)
+    qrcp_cached_batched_kernel(const QrcpDesc* Ds, double tol3z, int64_t smem_bytes) {
+  extern __shared__ double cache[];
+  const QrcpDesc& D = Ds[blockIdx.x];
+  const int64_t fixed = (int64_t)(D.d + 2 * D.n) * 8 + (int64_t)2 * D.n * 4;  // vbuf, norms, maps
+  if (fixed > smem_bytes) {  // the maps alone do not fit: the global-memory body
+    qrcp_body(1, 0, D, tol3z);
+    return;
+  }
+  const int64_t qc = (smem_bytes - fixed) / ((int64_t)D.d * 8);
+  qrcp_cached_body(D, tol3z, (int)(qc < D.n ? qc : D.n), 1, 0, cache);
+}
+
 // R^sk[i, q] = s_i X[i, phys[q]] for i <= q < n (0 below), s_i = -1 when the
 // diagonal X[i, phys[i]] is negative; J[q] = phys[q].
 __device__ __forceinline__ void qrcp_gather_body(int q, const QrcpDesc& D) {
@@ -566,7 +604,7 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   // the maps, norms and reflector buffer in shared memory, and as many
   // owned columns as fit beside them (all of them for most sketches)
   const int64_t nown = (n + G - 1) / G;
-  const int64_t kSmemCap = 200 * 1024;
+  const int64_t kSmemCap = kQrcpSmemCap;
   const int64_t fixed = (int64_t)(d + 2 * nown) * 8 + (int64_t)2 * n * 4;
   int64_t qc = fixed < kSmemCap ? std::min<int64_t>(nown, (kSmemCap - fixed) / ((int64_t)d * 8)) : 0;
   // CQRRPT_QRCP_CACHED_COLUMNS caps the columns kept in shared memory per
@@ -603,9 +641,19 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
 }
 
 cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gather_base,
-                                int64_t gather_tiles, cudaStream_t stream) {
+                                int64_t gather_tiles, int64_t qrcp_smem_bytes,
+                                cudaStream_t stream) {
   if (nprob <= 0) return cudaSuccess;
-  qrcp_batched_kernel<<<nprob, 512, 0, stream>>>(D, tol3z_value());
+  if (qrcp_smem_bytes > 0) {
+    cudaError_t e = cudaFuncSetAttribute(qrcp_cached_batched_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)qrcp_smem_bytes);
+    if (e != cudaSuccess) return e;
+    qrcp_cached_batched_kernel<<<nprob, kQrcpBatchThreads, (size_t)qrcp_smem_bytes, stream>>>(
+        D, tol3z_value(), qrcp_smem_bytes);
+  } else {
+    qrcp_batched_kernel<<<nprob, 512, 0, stream>>>(D, tol3z_value());
+  }
   qrcp_gather_batched_kernel<<<(unsigned)gather_tiles, 128, 0, stream>>>(D, gather_base, nprob);
   count_launches(2);
   return cudaGetLastError();

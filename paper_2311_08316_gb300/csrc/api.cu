@@ -56,6 +56,9 @@ struct cqrrpt_ctx {
   int64_t* pipe_pin = nullptr;    // pinned copy of the same 32 bytes
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev[6] = {};
+  // split path: side stream and fork/join events (inverses beside splits)
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_ev[2] = {};
 };
 
 static std::atomic<long long> g_launches{0};
@@ -197,10 +200,25 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
   int64_t k = 0;
   int dst = kOk;
   if ((st = read_k(h, sc, stream, &k, &dst)) != kOk) return st;
+  // the inverses of lines 4 and 7 run on a side stream beside the splits
+  const OzSide* side = nullptr;
+  OzSide side_v{};
+  if (!h->side && cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) == cudaSuccess) {
+    if (cudaEventCreateWithFlags(&h->side_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->side_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return kCudaError;
+    }
+  }
+  cudaGetLastError();
+  if (h->side && h->side_ev[0] && h->side_ev[1]) {
+    side_v = OzSide{h->side, h->side_ev[0], h->side_ev[1]};
+    side = &side_v;
+  }
   if (dst == kOk && k > 0) {
     // line 4: M^pre = M[:, J[:k]] (R^sk_11)^{-1} into Q
     // (row-wise FP64 inverse of the row-graded R^sk_11, then one product)
-    e = oz_trsm_inv(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream, status);
+    e = oz_trsm_inv(m, (int)k, A, lda, J, Rsk, n, Q, ldq, region, stream, status, side);
     mark(h, 4, stream);
     // line 5: G = M^pre^T M^pre
     if (e == cudaSuccess) e = oz_gram(m, (int)k, Q, ldq, G, n, region, stream, status);
@@ -214,7 +232,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
     if (dst == kOk && k > 0) {
       // line 7: Q_k = M^pre (R^pre)^{-1}, in place; R^pre is well conditioned
       // (Theorem 2), so one product with its FP64 inverse
-      e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream, status);
+      e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream, status, side);
       mark(h, 7, stream);
       // line 8: R_k = R^pre R^sk_k
       double* Rout = (precision == CQRRPT_SPLITBF16_CHOLQR2) ? R1 : R;
@@ -366,6 +384,9 @@ int cqrrpt_destroy(cqrrpt_handle h) {
   }
   if (h->pipe_slots) cudaFree(h->pipe_slots);
   if (h->pipe_pin) cudaFreeHost(h->pipe_pin);
+  if (h->side) cudaStreamDestroy(h->side);
+  for (int i = 0; i < 2; ++i)
+    if (h->side_ev[i]) cudaEventDestroy(h->side_ev[i]);
   if (h->pipe_in) cudaStreamDestroy(h->pipe_in);
   if (h->pipe_out) cudaStreamDestroy(h->pipe_out);
   for (int i = 0; i < 6; ++i)

@@ -460,13 +460,16 @@ void carve_trsm(TrsmCtx& c, int64_t m, int k, void* work) {
 
 // C[:, 0:n] (m x n, ld ldc) op= Xs[:, map[0:kk]] * Ts (kk x n) (identity map
 // when map is null); mode store/sub.
+// ts_ready (or null): an event the column operand Ts waits for (it may be
+// produced on another stream while the row operand is split).
 cudaError_t oz_mul(const TrsmCtx& c, const double* Xs, int64_t ldxs, const int64_t* map, int kk,
                    const double* Ts, int64_t ldts, int n, double* C, int64_t ldc, int mode,
-                   cudaStream_t s) {
+                   cudaStream_t s, cudaEvent_t ts_ready = nullptr) {
   const int64_t kpad = round_up(kk, kOzKAlign);
   const OzRowSplit rs{Xs, ldxs, map, c.m, kk, kpad, c.ea, c.DA, c.m * kpad};
   const OzColSplit cs{Ts, ldts, kk, n, kpad, c.eb, c.DB, (int64_t)n * kpad};
   cudaError_t e0 = oz_rowsplit(rs, s);
+  if (e0 == cudaSuccess && ts_ready) e0 = cudaStreamWaitEvent(s, ts_ready, 0);
   if (e0 == cudaSuccess) e0 = oz_colsplit(cs, s);
   if (e0 != cudaSuccess) return e0;
   OzGemm G{};
@@ -530,18 +533,30 @@ int64_t oz_trsm_inv_workspace(int64_t m, int k) {
 // |U_ij| <= 1 above a unit diagonal), where |W||T| = |U^{-1}||U|.
 cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                         const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
-                        cudaStream_t s, int* status) {
+                        cudaStream_t s, int* status, const OzSide* side) {
   TrsmCtx c{};
   c.m = m; c.k = k; c.X = X; c.ldx = ldx; c.T = T; c.ldt = ldt;
   carve_trsm(c, m, k, work);
   c.err = status;
   double* W = (double*)((char*)work + oz_trsm_workspace(m, k));
   const OzTrinv ti{T, ldt, k, W, k};
-  cudaError_t e = oz_trinv(ti, s);
+  cudaError_t e;
+  cudaEvent_t w_ready = nullptr;
+  if (side) {
+    // W = T^{-1} (latency-bound, a few CTAs) on the side stream while the
+    // row operand is split on s (HBM-bound): disjoint buffers
+    e = cudaEventRecord(side->fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side->stream, side->fork, 0);
+    if (e == cudaSuccess) e = oz_trinv(ti, side->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(side->join, side->stream);
+    w_ready = side->join;
+  } else {
+    e = oz_trinv(ti, s);
+  }
   if (e != cudaSuccess) return e;
   // the split reads B[:, cols] (the gather is fused into it) before the
   // product writes X (separate planes, so X may be B)
-  return oz_mul(c, B, ldb, cols, k, W, k, k, X, ldx, kOzStore, s);
+  return oz_mul(c, B, ldb, cols, k, W, k, k, X, ldx, kOzStore, s, w_ready);
 }
 
 }  // namespace cqrrpt

@@ -112,11 +112,17 @@ int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out);
 cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* G, int64_t ldg,
                     void* work, cudaStream_t s, int* status = nullptr);
 int64_t oz_trsm_workspace(int64_t m, int k);
-// X := B[:, cols] T^{-1} through the FP64 (row-wise) inverse of T
+// X := B[:, cols] T^{-1} through the FP64 (row-wise) inverse of T.  side
+// (or null): a second stream and two events on which T^{-1} is formed while
+// B[:, cols] is split on s (joined before the product).
+struct OzSide {
+  cudaStream_t stream;
+  cudaEvent_t fork, join;
+};
 int64_t oz_trsm_inv_workspace(int64_t m, int k);
 cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                         const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
-                        cudaStream_t s, int* status = nullptr);
+                        cudaStream_t s, int* status = nullptr, const OzSide* side = nullptr);
 cudaError_t oz_trsm(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                     const double* T, int64_t ldt, double* X, int64_t ldx, void* work,
                     cudaStream_t s, int* status = nullptr);

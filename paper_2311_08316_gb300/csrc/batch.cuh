@@ -89,7 +89,7 @@ struct GramDesc {
   double* G;
   int64_t ldg;
   const int* status;
-  int tile;  // output tile edge: 16 or 32 (0 = 32)
+  int tile;  // output tile edge: 8, 16 or 32 (0 = 32)
 };
 
 struct PotrfDesc {

@@ -8,8 +8,10 @@
 // upper triangle.  One CTA computes one output tile of one row block
 // (kGramTile x kGramTile, or 16 x 16 where a batched problem's descriptor
 // asks for it: less padding when k is small; the batched autotuner picks the
-// edge per problem size); its 64 threads own 4 x 4 (2 x 2) register tiles,
-// and rows are staged kGramRows at a time in shared memory.  Each entry is
+// edge per problem size; a small single problem uses 16 x 16 or 8 x 8 tiles
+// so that enough CTAs share the work); its 64 threads own 4 x 4 (2 x 2,
+// 1 x 1) register tiles, and rows are staged kGramRows at a time in shared
+// memory.  Each entry is
 // the same ascending-r fma chain whatever the tile, so the tile does not
 // change the result.  The kernel is bound by the FP64 pipe.  Single-problem
 // and batched launches share the bodies.
@@ -21,7 +23,9 @@ namespace cqrrpt {
 static __host__ __device__ int64_t gram_nblocks(int64_t m) {
   return (m + kRowBlock - 1) / kRowBlock;
 }
-static __host__ __device__ int gram_tile_edge(int tile) { return tile == 16 ? 16 : kGramTile; }
+static __host__ __device__ int gram_tile_edge(int tile) {
+  return tile == 8 ? 8 : tile == 16 ? 16 : kGramTile;
+}
 static __host__ __device__ int64_t gram_ntri(int kmax, int tile) {
   const int e = gram_tile_edge(tile);
   const int64_t t1 = (kmax + e - 1) / e;
@@ -104,7 +108,9 @@ __device__ __forceinline__ void gram_partial_tile(int64_t tile, const GramDesc& 
 __device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& D) {
   __shared__ GramStage Xa, Xc;
   if (*D.status != kOk) return;
-  if (D.tile == 16)
+  if (D.tile == 8)
+    gram_partial_tile<8>(tile, D, Xa, Xc);
+  else if (D.tile == 16)
     gram_partial_tile<16>(tile, D, Xa, Xc);
   else
     gram_partial_tile<kGramTile>(tile, D, Xa, Xc);
@@ -127,8 +133,13 @@ __device__ __forceinline__ void gram_combine_body(int64_t tile, const GramDesc& 
   D.G[(int64_t)a * D.ldg + c] = tsum;
 }
 
-__global__ void __launch_bounds__(64) gram_partial_kernel(GramDesc D) {
-  gram_partial_body(blockIdx.x, D);
+// single problem: one instantiation per tile edge (each with its own
+// register budget; 14 CTAs per SM for the 16 x 16 and 32 x 32 tiles)
+template <int TILE>
+__global__ void __launch_bounds__(64, TILE == 8 ? 1 : 14) gram_partial_kernel(GramDesc D) {
+  __shared__ GramStage Xa, Xc;
+  if (*D.status != kOk) return;
+  gram_partial_tile<TILE>(blockIdx.x, D, Xa, Xc);
 }
 __global__ void __launch_bounds__(kCombineThreads) gram_combine_kernel(GramDesc D) {
   gram_combine_body(blockIdx.x, D);
@@ -147,11 +158,27 @@ __global__ void __launch_bounds__(kCombineThreads) gram_combine_batched_kernel(c
   gram_combine_body(t, D[p]);
 }
 
+// Output tile edge of a single-problem Gram: the largest of 32, 16, 8 that
+// still gives two waves of CTAs (a small problem has few 4096-row blocks, and
+// the FP64 pipe of a few SMs would otherwise carry it alone).
+static int gram_single_tile(int64_t m, int kmax) {
+  for (int t : {kGramTile, 16})
+    if (gram_partial_tiles(m, kmax, t) >= 2 * 152) return t;
+  return 8;
+}
+
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
                         cudaStream_t stream) {
-  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status, kGramTile};
-  gram_partial_kernel<<<(unsigned)gram_partial_tiles(m, kmax, kGramTile), 64, 0, stream>>>(D);
+  const int tile = gram_single_tile(m, kmax);
+  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status, tile};
+  const unsigned grid = (unsigned)gram_partial_tiles(m, kmax, tile);
+  if (tile == 8)
+    gram_partial_kernel<8><<<grid, 64, 0, stream>>>(D);
+  else if (tile == 16)
+    gram_partial_kernel<16><<<grid, 64, 0, stream>>>(D);
+  else
+    gram_partial_kernel<kGramTile><<<grid, 64, 0, stream>>>(D);
   gram_combine_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
   count_launches(2);
   return cudaGetLastError();

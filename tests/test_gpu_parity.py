@@ -132,8 +132,11 @@ def test_trsm_bitexact(C, m, n, k):
 
 
 # ---------------------------------------------------------------- line 5
-@pytest.mark.parametrize("m,k", [(4096, 64), (3 * 4096 + 77, 45), (100, 1), (9000, 130)])
+@pytest.mark.parametrize("m,k", [(4096, 64), (3 * 4096 + 77, 45), (100, 1), (9000, 130),
+                                 (10 * 4096, 200), (32 * 4096 + 5, 100)])
 def test_gram_bitexact(C, m, k):
+    # the launch picks 8 x 8 tiles for the small cases, 16 x 16 for
+    # (10 * 4096, 200) and 32 x 32 for (32 * 4096 + 5, 100): same bits
     X = _rng(m).standard_normal((m, k))
     ref = oracle.gram(X)
     got = C.gram(gpu(X))

@@ -120,24 +120,36 @@ __device__ __forceinline__ void splitcols_body(const OzColSplit& J, int64_t tile
 }
 
 // Row operand planes D[p][r][k] of X[r, map[k]] (K = cols, zero past cols up
-// to kpad), scale e[r].  32 x 32 tiles transposed through shared memory so
-// that both the reads of X and the writes of D coalesce (256 threads).
+// to kpad), scale e[r].  One CTA per 32 rows walks the whole K range in
+// 32 x 32 tiles transposed through shared memory, so that the reads of X
+// coalesce and every plane row is written whole by one CTA (256 threads).
 __device__ __forceinline__ void splitrows_body(const OzRowSplit& J, int64_t tile) {
   __shared__ double tl[32][33];
-  const int64_t tiles_r = (J.rows + 31) / 32;
-  const int64_t r0 = (tile % tiles_r) * 32;
-  const int k0 = (int)(tile / tiles_r) * 32;
+  const int64_t r0 = tile * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int j = ty; j < 32; j += 8) {
-    const int64_t r = r0 + tx;
-    const int k = k0 + j;
-    tl[j][tx] = (r < J.rows && k < J.cols) ? J.X[(J.map ? J.map[k] : (int64_t)k) * J.ldx + r] : 0.0;
+  int er[4];  // exponents of this thread's output rows r0 + ty + 8 i
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + ty + 8 * i;
+    er[i] = r < J.rows ? J.e[r] : 0;
   }
-  __syncthreads();
-  for (int j = ty; j < 32; j += 8) {
-    const int64_t r = r0 + j;
-    const int k = k0 + tx;
-    if (r < J.rows && k < J.kpad) digits8(tl[tx][j], J.e[r], J.D + r * J.kpad + k, J.plane);
+  for (int k0 = 0; k0 < J.kpad; k0 += 32) {
+    __syncthreads();  // the previous tile's reads of tl are done
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = ty + 8 * i;
+      const int64_t r = r0 + tx;
+      const int k = k0 + j;
+      tl[j][tx] = (r < J.rows && k < J.cols) ? J.X[(J.map ? J.map[k] : (int64_t)k) * J.ldx + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = ty + 8 * i;
+      const int64_t r = r0 + j;
+      const int k = k0 + tx;
+      if (r < J.rows && k < J.kpad) digits8(tl[tx][j], er[i], J.D + r * J.kpad + k, J.plane);
+    }
   }
 }
 
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(256) oz_split_rows_batched_kernel(const OzRowS
 }
 
 int64_t oz_rowexp_tiles(const OzRowSplit& J) { return (J.rows + 255) / 256; }
-int64_t oz_splitrows_tiles(const OzRowSplit& J) { return (J.rows + 31) / 32 * (J.kpad / 32); }
+int64_t oz_splitrows_tiles(const OzRowSplit& J) { return (J.rows + 31) / 32; }
 int64_t oz_colexp_tiles(const OzColSplit& J) { return J.cols; }
 int64_t oz_splitcols_tiles(const OzColSplit& J) {
   return (int64_t)J.cols * ((J.kpad + kOzColChunk - 1) / kOzColChunk);

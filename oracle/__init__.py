@@ -47,6 +47,10 @@ def lib():
         L.oracle_potrf_upper.argtypes = [_i64, _p, _i64, _p, _i64]
         L.oracle_potrf_upper.restype = _i64
         L.oracle_trmm_upper.argtypes = [_i64, _i64, _p, _i64, _p, _i64, _p, _i64]
+        L.oracle_qr_nopivot.argtypes = [_i64, _i64, _p, _i64, _p, _p]
+        L.oracle_rcholqr.argtypes = [_i64, _i64, _p, _i64, _d, ctypes.c_int, _u64, _p, _i64, _p,
+                                     _i64, _p, _p, _p, _p]
+        L.oracle_rcholqr.restype = ctypes.c_int
         L.oracle_apply_q.argtypes = [ctypes.c_int, _i64, _i64, _p, _i64, _p, _i64, _i64, _p,
                                      _i64, _p, _i64]
         L.oracle_sketch_dim.argtypes = [_i64, _d]
@@ -195,6 +199,36 @@ def apply_q(Apre, Rpre, X, trans=False):
     lib().oracle_apply_q(1 if trans else 0, m, k, _ptr(Apre), m, _ptr(Rpre), k, r, _ptr(X),
                          X.shape[0], _ptr(Y), Y.shape[0])
     return Y
+
+
+def qr_nopivot(X):
+    """Householder QR of X (d x n) without pivoting, with the QRCP's
+    reflectors and sign convention: returns (R n x n upper, positive
+    diagonal)."""
+    X = _fortran(X).copy(order="F")
+    d, n = X.shape
+    J = np.zeros(n, dtype=np.int64)
+    tau = np.zeros(n)
+    lib().oracle_qr_nopivot(d, n, _ptr(X), d, _ptr(J), _ptr(tau))
+    return np.triu(X[:n, :]).copy(order="F")
+
+
+def rcholqr(M, gamma=1.25, nnz=4, seed=0):
+    """Sec. 2.3's randomized CholeskyQR (no pivoting; M of full column
+    rank): Result with Q, R, J (identity), k, status, Rsk, Rpre."""
+    M = _fortran(M)
+    m, n = M.shape
+    Q = np.zeros((m, n), dtype=np.float64, order="F")
+    R = np.zeros((n, n), dtype=np.float64, order="F")
+    J = np.zeros(n, dtype=np.int64)
+    k = np.zeros(1, dtype=np.int64)
+    Rsk = np.zeros((n, n), dtype=np.float64, order="F")
+    Rpre = np.zeros((n, n), dtype=np.float64, order="F")
+    st = lib().oracle_rcholqr(m, n, _ptr(M), m, gamma, nnz, seed, _ptr(Q), m, _ptr(R), n,
+                              _ptr(J), _ptr(k), _ptr(Rsk), _ptr(Rpre))
+    kk = int(k[0])
+    return Result(Q=Q[:, :kk], R=R[:kk, :], J=J, k=kk, status=int(st), Rsk=Rsk,
+                  Rpre=Rpre[:kk, :kk], Qfull=Q, Rfull=R)
 
 
 def cqrrpt_implicit(M, gamma=1.25, nnz=4, tol=-1.0, seed=0):

@@ -20,6 +20,7 @@
  *   Alg. 2 line 7          -> oracle_trsm_rut        Q_k = M^pre (R^pre)^-1
  *   Alg. 2 line 8          -> oracle_trmm_upper      R_k = R^pre R^sk_k
  *   Q_k = M^pre (R^pre)^-1 -> oracle_apply_q         Q X and Q^T Y without forming Q
+ *   Sec. 2.3 (rCholQR)     -> oracle_rcholqr         unpivoted randomized CholeskyQR
  *   (implicit Q: Sec. 3.2 notes that M^pre and R^pre represent Q_k)
  * The SASO operator is the one of Sec. 3.3.1 (each column of S has exactly s
  * nonzeros at uniformly random rows with values +-1/sqrt(s)).
@@ -66,6 +67,7 @@
  * = 0), Theorem 2 (singular values of M^pre are the inverses of those of
  * S U), and planted-rank recovery.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -234,8 +236,23 @@ double oracle_dot32(const double* x, const double* y, int64_t len) {
  * rows with negative diagonal negated; below the diagonal: Householder data).
  * J: n pivots (position -> original column).  vn_out (optional): vn1 at the
  * moment each column was chosen (the pivot norm), for near-tie analysis. */
+/* pivoting == 0: plain Householder QR (the column at position j is step j's
+ * pivot; Sec. 2.3's randomized CholeskyQR), same reflectors and updates. */
+static void qrcp_ex(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J, double* tau_out,
+                    double* pivnorm_out, double* second_out, int pivoting);
+
 void oracle_qrcp(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J, double* tau_out,
                  double* pivnorm_out, double* second_out) {
+    qrcp_ex(d, n, X, ldx, J, tau_out, pivnorm_out, second_out, 1);
+}
+
+void oracle_qr_nopivot(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J,
+                       double* tau_out) {
+    qrcp_ex(d, n, X, ldx, J, tau_out, NULL, NULL, 0);
+}
+
+static void qrcp_ex(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J, double* tau_out,
+                    double* pivnorm_out, double* second_out, int pivoting) {
     const double u = ldexp(1.0, -53);
     const double tol3z = sqrt(u);
     double* vn1 = (double*)malloc(sizeof(double) * (size_t)n);
@@ -249,8 +266,9 @@ void oracle_qrcp(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J, doubl
     for (int64_t j = 0; j < n; ++j) {
         /* pivot: largest vn1 over positions j..n-1, lowest position on ties */
         int64_t p = j;
-        for (int64_t c = j + 1; c < n; ++c)
-            if (vn1[c] > vn1[p]) p = c;
+        if (pivoting)
+            for (int64_t c = j + 1; c < n; ++c)
+                if (vn1[c] > vn1[p]) p = c;
         if (pivnorm_out) pivnorm_out[j] = vn1[p];
         if (second_out) {
             double sec = -1.0;
@@ -459,13 +477,26 @@ int64_t oracle_sketch_dim(int64_t n, double gamma) { return (int64_t)ceil(gamma 
  * written); R: n x n capacity (first k rows written); J: n pivots; *k_out:
  * rank.  Optional diagnostics (may be NULL): Rsk_out (n x n, ld n) R^sk;
  * Rpre_out (n x n, ld n) R^pre; pivnorm/second (n). */
+static int core_ex(int64_t m, int64_t n, const double* M, int64_t ldm, double* Msk, int64_t d,
+                   double tol, double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* J,
+                   int64_t* k_out, double* Rsk_out, double* Rpre_out, double* pivnorm,
+                   double* second, int pivoting);
+
 int oracle_cqrrpt_core_sketched(int64_t m, int64_t n, const double* M, int64_t ldm, double* Msk,
                                 int64_t d, double tol, double* Q, int64_t ldq, double* R,
                                 int64_t ldr, int64_t* J, int64_t* k_out, double* Rsk_out,
                                 double* Rpre_out, double* pivnorm, double* second) {
+    return core_ex(m, n, M, ldm, Msk, d, tol, Q, ldq, R, ldr, J, k_out, Rsk_out, Rpre_out,
+                   pivnorm, second, 1);
+}
+
+static int core_ex(int64_t m, int64_t n, const double* M, int64_t ldm, double* Msk, int64_t d,
+                   double tol, double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* J,
+                   int64_t* k_out, double* Rsk_out, double* Rpre_out, double* pivnorm,
+                   double* second, int pivoting) {
     *k_out = 0;
     double* tau = (double*)malloc(sizeof(double) * (size_t)n);
-    oracle_qrcp(d, n, Msk, d, J, tau, pivnorm, second);
+    qrcp_ex(d, n, Msk, d, J, tau, pivnorm, second, pivoting);
     /* R^sk: upper n x n */
     double* Rsk = (double*)calloc((size_t)(n * n), sizeof(double));
     for (int64_t c = 0; c < n; ++c)
@@ -579,4 +610,35 @@ void oracle_apply_q(int trans, int64_t m, int64_t k, const double* Apre, int64_t
         }
     }
     free(W);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3: randomized CholeskyQR (the method CQRRPT extends) -- sketch,    */
+/* unpivoted QR of the sketch, M^pre = M (R^sk)^{-1}, G, R^pre = chol(G),   */
+/* Q = M^pre (R^pre)^{-1}, R = R^pre R^sk.  M must have full column rank:  */
+/* k = n, except that an exactly zero diagonal of R^sk (below DBL_MIN times */
+/* R^sk[0,0]) ends k there and a Cholesky breakdown lowers k (Remark 3).    */
+/* J is the identity.  Returns as oracle_cqrrpt.                            */
+/* ------------------------------------------------------------------------ */
+int oracle_rcholqr(int64_t m, int64_t n, const double* M, int64_t ldm, double gamma, int nnz,
+                   uint64_t seed, double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* J,
+                   int64_t* k_out, double* Rsk_out, double* Rpre_out) {
+    *k_out = 0;
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (ldm < m) return -4;
+    if (!(gamma >= 1.0)) return -5;
+    int64_t d = oracle_sketch_dim(n, gamma);
+    if (d > m) return -5;
+    if (nnz < 1 || nnz > d) return -6;
+    if (ldq < m) return -10;
+    if (ldr < n) return -12;
+    double scale = 1.0 / sqrt((double)nnz);
+    double* Msk = (double*)malloc(sizeof(double) * (size_t)(d * n));
+    int st = oracle_sketch(m, n, M, ldm, d, nnz, seed, scale, Msk, d);
+    if (st == 0)
+        st = core_ex(m, n, M, ldm, Msk, d, DBL_MIN, Q, ldq, R, ldr, J, k_out, Rsk_out, Rpre_out,
+                     NULL, NULL, 0);
+    free(Msk);
+    return st;
 }

@@ -436,3 +436,49 @@ def test_apply_q_matches_explicit_q_and_adjoint():
     assert np.abs(back - X).max() <= 1e-12 * np.abs(X).max()
     # the implicit pieces are the explicit run's intermediates
     assert np.array_equal(oracle.trsm_rut(res.Apre, res.Rpre), res.Q)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3: randomized CholeskyQR (unpivoted)
+# --------------------------------------------------------------------------
+def test_qr_nopivot_matches_lapack_qr():
+    """The unpivoted Householder QR (same reflectors, diagonal made
+    non-negative) equals LAPACK's R up to row signs."""
+    rng = _rng(51)
+    X = rng.standard_normal((60, 40)) * np.logspace(0, -4, 40)
+    R = oracle.qr_nopivot(X)
+    Rl = np.linalg.qr(X, mode="r")
+    Rl = Rl * np.where(np.diag(Rl) < 0, -1.0, 1.0)[:, None]
+    assert (np.diag(R) >= 0).all()
+    assert np.abs(R - Rl).max() <= 1e-13 * np.abs(Rl).max()
+
+
+def test_rcholqr_factorises_a_full_rank_matrix():
+    """Sec. 2.3 on a cond-1e6 matrix: J is the identity, k = n, M = Q R,
+    Q^T Q = I, and R equals LAPACK's R of M (unique with a positive
+    diagonal) to the conditioning."""
+    m, n = 3000, 30
+    M = np.asfortranarray(W.planted(m, n, W.logspaced(n, -6.0), 52).numpy())
+    res = oracle.rcholqr(M, 1.25, 4, 17)
+    assert res.status == 0 and res.k == n
+    assert np.array_equal(res.J, np.arange(n))
+    assert np.linalg.norm(M - res.Q @ res.R) / np.linalg.norm(M) <= 1e-14
+    assert np.linalg.norm(res.Q.T @ res.Q - np.eye(n), 2) <= 1e-13
+    Rl = np.linalg.qr(M, mode="r")
+    Rl = Rl * np.where(np.diag(Rl) < 0, -1.0, 1.0)[:, None]
+    assert np.abs(res.R - Rl).max() <= 1e-9 * np.abs(Rl).max()
+
+
+def test_rcholqr_equals_cqrrpt_when_the_pivots_are_the_identity():
+    """Columns whose norms fall by 10x each: the QRCP of the sketch picks
+    them in order, so CQRRPT (with the same near-zero rank tolerance) and
+    the unpivoted method run the same arithmetic: identical bits."""
+    m, n = 2500, 12
+    rng = _rng(53)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    M = np.asfortranarray(U * np.logspace(0, -11, n))
+    a = oracle.rcholqr(M, 1.25, 4, 9)
+    b = oracle.cqrrpt(M, 1.25, 4, 1e-300, 9)
+    assert np.array_equal(b.J, np.arange(n)) and a.k == b.k == n
+    assert np.array_equal(a.Q.view(np.uint64), b.Q.view(np.uint64))
+    assert np.array_equal(a.R.view(np.uint64), b.R.view(np.uint64))

@@ -388,6 +388,28 @@ def run_mixed(args, world, rank, local, C):
         results[name] = (Q, R, J, k)
         out[name] = {"ms": statistics.median(ms), "factorizations_per_s": 1e3 / statistics.median(ms),
                      "k": k, "recon_rel_F": recon, "orth_2": orth}
+    # Sec. 2.3's randomized CholeskyQR (no pivoting) on the same full-rank
+    # matrix, in FP64: time and accuracy beside CQRRPT's
+    try:
+        Qr, Rr, Jr = C.colmajor_empty(m, n), C.colmajor_empty(n, n), torch.empty(
+            n, dtype=torch.int64, device="cuda")
+        rr = C.rcholqr(A, w.gamma, w.nnz, w.sketch_seed, out=(Qr, Rr, Jr), handle=h, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rr = C.rcholqr(A, w.gamma, w.nnz, w.sketch_seed, out=(Qr, Rr, Jr), handle=h, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kr = rr.k
+        out["fp64_rcholqr"] = {
+            "ms": e0.elapsed_time(e1), "k": kr,
+            "recon_rel_F": (torch.linalg.norm(A - Qr[:, :kr] @ Rr[:kr]) / torch.linalg.norm(A)).item(),
+            "orth_2": torch.linalg.matrix_norm(Qr[:, :kr].t() @ Qr[:, :kr] - torch.eye(
+                kr, dtype=torch.float64, device="cuda"), ord=2).item(),
+            "note": "unpivoted (Sec. 2.3): J is the identity"}
+        del Qr, Rr, Jr
+    except Exception as ex:  # reported, not hidden
+        out["fp64_rcholqr"] = {"error": str(ex)}
     Rf = results["fp64"][1][: results["fp64"][3]]
     for name in ("splitbf16", "splitbf16_cholqr2"):
         Rs = results[name][1][: results[name][3]]

@@ -121,6 +121,20 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
              double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
              cudaStream_t stream);
 
+/* ---- randomized CholeskyQR (Sec. 2.3) ------------------------------------ */
+
+/* The method CQRRPT extends, in FP64: M^sk = S M (the same SASO S),
+ * [Q^sk, R^sk] = qr(M^sk) WITHOUT pivoting (the QRCP's reflectors, every
+ * pivot the next column), M^pre = M (R^sk)^{-1}, G = M^pre^T M^pre,
+ * R^pre = chol(G), Q = M^pre (R^pre)^{-1}, R = R^pre R^sk.  M must have full
+ * column rank: k = n, except that an exactly zero diagonal of R^sk ends k
+ * there and a Cholesky breakdown lowers k (Remark 3).  J receives the
+ * identity.  Arguments and errors as cqrrpt_d (no tol, no precision). */
+int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                     double gamma, int nnz_per_col, uint64_t seed, double* Q, int64_t ldq,
+                     double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
+                     cudaStream_t stream);
+
 /* ---- implicit Q --------------------------------------------------------- */
 
 /* Alg. 1 in FP64 stopped before Alg. 2 line 7: M^pre = M[:, J[:k]]

@@ -75,6 +75,8 @@ def lib():
     L.cqrrpt_batched_set_tuning.argtypes = [_p, ctypes.POINTER(_int), ctypes.POINTER(_int)]
     L.cqrrpt_gram_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _i64, _p]
     L.cqrrpt_trsm_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_rcholqr_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _u64, _p, _i64, _p, _i64,
+                                   _p, _p, _p, _p]
     L.cqrrpt_implicit_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _p, _i64, _p,
                                     _i64, _p, _i64, _p, _p, _p, _p]
     L.cqrrpt_apply_q_d.argtypes = [_p, _int, _i64, _i64, _p, _i64, _p, _i64, _i64, _p, _i64, _p,
@@ -100,7 +102,7 @@ def exported_symbols():
             "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs",
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
-            "cqrrpt_implicit_d", "cqrrpt_apply_q_d"]
+            "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -249,6 +251,27 @@ def cqrrpt(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64, out=None, han
         _check(rc, "cqrrpt_d")
     if not sync:
         return Factorization(Q, R, J, None, None)
+    return Factorization(Q, R, J, k.value, rc)
+
+
+def rcholqr(A, gamma=1.25, nnz=4, seed=0, out=None, handle=None, stream=None):
+    """Sec. 2.3's randomized CholeskyQR (no pivoting; A of full column
+    rank) through cqrrpt_rcholqr_d; waits for k.  Returns a Factorization
+    (J is the identity)."""
+    h = handle or default_handle()
+    m, n = A.shape
+    if out is None:
+        Q = colmajor_empty(m, n, A.device)
+        R = colmajor_empty(n, n, A.device)
+        J = torch.empty(n, dtype=torch.int64, device=A.device)
+    else:
+        Q, R, J = out
+    k = _i64()
+    rc = lib().cqrrpt_rcholqr_d(h.h, m, n, A.data_ptr(), _ld(A), gamma, nnz, seed, Q.data_ptr(),
+                                _ld(Q), R.data_ptr(), _ld(R), J.data_ptr(), None,
+                                ctypes.byref(k), _stream(stream))
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_rcholqr_d")
     return Factorization(Q, R, J, k.value, rc)
 
 

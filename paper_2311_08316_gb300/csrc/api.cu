@@ -1,6 +1,7 @@
 // C ABI of the CQRRPT library (declared in include/cqrrpt.h): argument
 // checking, workspace planning and the stream-ordered pipeline of Alg. 2.
 // No entry point synchronises unless it is given a host output pointer.
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -282,7 +283,8 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
 static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
                     int64_t d, int nnz, double tol, uint64_t seed, double* Q, int64_t ldq,
                     double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
-                    cudaStream_t stream, bool form_q, double* Rpre_out, int64_t ld_rpre) {
+                    cudaStream_t stream, bool form_q, double* Rpre_out, int64_t ld_rpre,
+                    bool pivoting = true) {
   const Plan p = plan_fp64(m, n, d, nnz);
   int st = ensure_ws(h, p.total);
   if (st != kOk) return st;
@@ -308,7 +310,7 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
   mark(h, 0, stream);
   if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
   mark(h, 1, stream);
-  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
+  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream, !pivoting);
   mark(h, 2, stream);
   if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
   mark(h, 3, stream);
@@ -466,6 +468,31 @@ int cqrrpt_implicit_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, in
   DevGuard g(h->device);
   return run_fp64(h, m, n, A, lda, d, nnz, tol, seed, Apre, ldp, R, ldr, J, k_dev, k_host, stream,
                   false, Rpre, ldrp);
+}
+
+int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                     double gamma, int nnz, uint64_t seed, double* Q, int64_t ldq, double* R,
+                     int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
+                     cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 16384) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -6;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -6;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
+  if (!Q) return -9;
+  if (ldq < m) return -10;
+  if (!R) return -11;
+  if (ldr < n) return -12;
+  if (!J) return -13;
+  DevGuard g(h->device);
+  // k = n up to an exactly zero diagonal of R^sk: the rank rule with the
+  // smallest normal tolerance
+  return run_fp64(h, m, n, A, lda, d, nnz, DBL_MIN, seed, Q, ldq, R, ldr, J, k_dev, k_host,
+                  stream, true, nullptr, 0, false);
 }
 
 int cqrrpt_apply_q_d(cqrrpt_handle h, int trans, int64_t m, int64_t k, const double* Apre,

@@ -54,6 +54,7 @@ struct QrcpDesc {
   double* Rsk;
   int64_t ldr;
   DeviceScalars* sc;
+  int nopivot;  // 1: plain Householder QR (the column at position j is step j's pivot)
 };
 
 struct RankDesc {

@@ -50,7 +50,7 @@ QrcpWork qrcp_carve(void* work, int n);
 // Rsk (n x n, ld ldr) receives the sign-normalised upper triangle.
 cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double* Rsk,
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
-                        cudaStream_t stream);
+                        cudaStream_t stream, bool nopivot = false);
 // one CTA per problem (no grid barrier), then the gather
 // qrcp_smem_bytes > 0: one CTA per problem in shared memory (sketch columns
 // that do not fit stay in global memory); 0: the global-memory kernel.

@@ -106,7 +106,8 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
       if (c >= n) break;
       const int pc = __ldcg(w.posof + c);
       if (pc <= j_done) continue;
-      const double v = __ldcg(w.vn1 + c);
+      // without pivoting the key is n - position: the lowest position wins
+      const double v = D.nopivot ? (double)(n - pc) : __ldcg(w.vn1 + c);
       if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bc = c; }
     }
     if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bc; }
@@ -345,7 +346,8 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
       const int c = bid + G * q;
       const int pc = posof[c];
       if (pc <= j_done) continue;
-      const double v = vn1[q];
+      // without pivoting the key is n - position: the lowest position wins
+      const double v = D.nopivot ? (double)(n - pc) : vn1[q];
       if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bq = q; }
     }
     if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bq; }
@@ -589,8 +591,8 @@ static double tol3z_value() { return sqrt(ldexp(1.0, -53)); }
 
 cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double* Rsk,
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
-                        cudaStream_t stream) {
-  QrcpDesc D{d, n, X, ldx, qrcp_carve(work, n), J, Rsk, ldr, sc};
+                        cudaStream_t stream, bool nopivot) {
+  QrcpDesc D{d, n, X, ldx, qrcp_carve(work, n), J, Rsk, ldr, sc, nopivot ? 1 : 0};
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, kQrcpThreads, 0);
   if (e != cudaSuccess) return e;

@@ -419,3 +419,19 @@ def test_qrcp_mixed_storage(C, cap, monkeypatch):
     w = W.single_large(m=8192 + 300, n=96, rank=70)
     A = np.asfortranarray(w.matrix().numpy())
     _compare_full(C, A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+
+
+# ---------------------------------------------------------- Sec. 2.3 rCholQR
+@pytest.mark.parametrize("m,n,seed", [(4096 + 33, 64, 1), (3 * 4096 + 5, 150, 2), (5000, 8, 3),
+                                      (9000, 300, 4)])
+def test_rcholqr_matches_oracle(C, m, n, seed):
+    """The unpivoted randomized CholeskyQR through cqrrpt_rcholqr_d: Q and R
+    bit-identical to the oracle's, J the identity, k = n (one CTA and
+    several CTAs in the QR of the sketch)."""
+    M = np.asfortranarray(W.planted(m, n, W.logspaced(n, -6.0), 300 + seed).numpy())
+    ref = oracle.rcholqr(M, 1.25, 4, 40 + seed)
+    res = C.rcholqr(gpu(M), 1.25, 4, 40 + seed)
+    assert res.status == ref.status == 0 and res.k == ref.k == n
+    assert np.array_equal(host(res.J), np.arange(n))
+    assert_bits(host(res.Q), ref.Q, "Q")
+    assert_bits(host(res.R), ref.R, "R")

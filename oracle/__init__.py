@@ -61,6 +61,11 @@ def lib():
         L.oracle_cqrrpt_core_sketched.argtypes = [_i64, _i64, _p, _i64, _p, _i64, _d,
                                                   _p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]
         L.oracle_cqrrpt_core_sketched.restype = ctypes.c_int
+        L.oracle_sketch_dense.argtypes = [_i64, _i64, _i64, _p, _i64, _p, _i64, _p, _i64]
+        L.oracle_sketch_dense.restype = ctypes.c_int
+        L.oracle_cqrrpt_dense.argtypes = [_i64, _i64, _p, _i64, _i64, _p, _i64, _d,
+                                          _p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]
+        L.oracle_cqrrpt_dense.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -111,6 +116,19 @@ def sketch(M, d, s, seed):
     m, n = M.shape
     Msk = np.zeros((d, n), dtype=np.float64, order="F")
     st = lib().oracle_sketch(m, n, _ptr(M), m, d, s, seed, saso_scale(s), _ptr(Msk), d)
+    return Msk, st
+
+
+def sketch_dense(S, M):
+    """M^sk = S M for a dense operator S (d x m), the blocked order of every
+    tall sum, no final scaling.  Returns (Msk, status)."""
+    S = _fortran(S)
+    M = _fortran(M)
+    d, m = S.shape
+    n = M.shape[1]
+    assert M.shape[0] == m
+    Msk = np.zeros((d, n), dtype=np.float64, order="F")
+    st = lib().oracle_sketch_dense(m, n, d, _ptr(S), d, _ptr(M), m, _ptr(Msk), d)
     return Msk, st
 
 
@@ -288,6 +306,29 @@ def cqrrpt_core_sketched(M, Msk, tol=-1.0):
     st = lib().oracle_cqrrpt_core_sketched(m, n, _ptr(M), m, _ptr(W), d, tol, _ptr(Q), m,
                                            _ptr(R), n, _ptr(J), _ptr(k), _ptr(Rsk), _ptr(Rpre),
                                            _ptr(piv), _ptr(sec))
+    kk = int(k[0])
+    return Result(Q=Q[:, :kk], R=R[:kk, :], J=J, k=kk, status=int(st), Rsk=Rsk,
+                  Rpre=Rpre[:kk, :kk], pivnorm=piv, second=sec, Qfull=Q, Rfull=R)
+
+
+def cqrrpt_dense(M, S, tol=-1.0):
+    """Alg. 2 with the dense sketching operator S (d x m) given, e.g. a
+    Gaussian operator (Sec. 3.3.1)."""
+    M = _fortran(M)
+    S = _fortran(S)
+    m, n = M.shape
+    d = S.shape[0]
+    assert S.shape[1] == m
+    Q = np.zeros((m, n), dtype=np.float64, order="F")
+    R = np.zeros((n, n), dtype=np.float64, order="F")
+    J = np.zeros(n, dtype=np.int64)
+    k = np.zeros(1, dtype=np.int64)
+    Rsk = np.zeros((n, n), dtype=np.float64, order="F")
+    Rpre = np.zeros((n, n), dtype=np.float64, order="F")
+    piv = np.zeros(n)
+    sec = np.zeros(n)
+    st = lib().oracle_cqrrpt_dense(m, n, _ptr(M), m, d, _ptr(S), d, tol, _ptr(Q), m, _ptr(R), n,
+                                   _ptr(J), _ptr(k), _ptr(Rsk), _ptr(Rpre), _ptr(piv), _ptr(sec))
     kk = int(k[0])
     return Result(Q=Q[:, :kk], R=R[:kk, :], J=J, k=kk, status=int(st), Rsk=Rsk,
                   Rpre=Rpre[:kk, :kk], pivnorm=piv, second=sec, Qfull=Q, Rfull=R)

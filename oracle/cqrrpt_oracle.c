@@ -10,6 +10,9 @@
  * paper's notation:
  *   Alg. 1 (cqrrpt)        -> oracle_cqrrpt          d = ceil(gamma n)
  *   Alg. 2 line 1 (sketch) -> oracle_sketch          M^sk = S M
+ *                             oracle_sketch_dense    the same for a dense S
+ *                             (Sec. 3.3.1's Gaussian operators), with
+ *                             oracle_cqrrpt_dense for the whole method
  *   Alg. 2 line 2 (qrcp)   -> oracle_qrcp            GEQP3-style QRCP
  *   Alg. 2 line 3 (rank)   -> oracle_rank_tol / oracle_rank_stage1 / _stage2
  *                             (Sec. 4.3, eqs. initial_numerical_rank and
@@ -215,6 +218,41 @@ int oracle_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, int64_t d,
     }
     free(rows);
     free(neg);
+    return bad ? 2 : 0;
+}
+
+/* Alg. 2 line 1 with a dense operator S (d x m, column-major, ld lds) that
+ * the caller drew, e.g. from the Gaussian family of Sec. 3.3.1 (iid entries
+ * of mean 0 and variance 1/d).  M^sk[i, c] = sum_r S[i, r] M[r, c], blocked
+ * over the rows like every tall sum: one fma per term in ascending r from
+ * +0.0 inside a block, block sums added in ascending block order from +0.0.
+ * There is no final scaling: S carries its own.  Returns 0, or 2 if the
+ * sketch holds a non-finite value. */
+int oracle_sketch_dense(int64_t m, int64_t n, int64_t d, const double* S, int64_t lds,
+                        const double* M, int64_t ldm, double* Msk, int64_t ldsk) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic) reduction(| : bad)
+    for (int64_t c = 0; c < n; ++c) {
+        double* total = (double*)malloc(sizeof(double) * (size_t)d);
+        double* part = (double*)malloc(sizeof(double) * (size_t)d);
+        for (int64_t i = 0; i < d; ++i) total[i] = 0.0;
+        for (int64_t r0 = 0; r0 < m; r0 += ROW_BLOCK) {
+            int64_t r1 = r0 + ROW_BLOCK < m ? r0 + ROW_BLOCK : m;
+            for (int64_t i = 0; i < d; ++i) part[i] = 0.0;
+            for (int64_t r = r0; r < r1; ++r) {
+                double a = M[r + c * ldm];
+                const double* Sr = S + r * lds;
+                for (int64_t i = 0; i < d; ++i) part[i] = fma(Sr[i], a, part[i]);
+            }
+            for (int64_t i = 0; i < d; ++i) total[i] = total[i] + part[i];
+        }
+        for (int64_t i = 0; i < d; ++i) {
+            Msk[i + c * ldsk] = total[i];
+            if (!isfinite(total[i])) bad = 1;
+        }
+        free(total);
+        free(part);
+    }
     return bad ? 2 : 0;
 }
 
@@ -553,6 +591,32 @@ int oracle_cqrrpt(int64_t m, int64_t n, const double* M, int64_t ldm, double gam
     double scale = 1.0 / sqrt((double)nnz);
     double* Msk = (double*)malloc(sizeof(double) * (size_t)(d * n));
     int st = oracle_sketch(m, n, M, ldm, d, nnz, seed, scale, Msk, d);
+    if (st == 0)
+        st = oracle_cqrrpt_core_sketched(m, n, M, ldm, Msk, d, tol, Q, ldq, R, ldr, J, k_out,
+                                         Rsk_out, Rpre_out, pivnorm, second);
+    free(Msk);
+    return st;
+}
+
+/* Alg. 2 with a dense sketching operator S (d x m, ld lds) given by the
+ * caller (Sec. 3.3.1's Gaussian family, or any operator of the family F that
+ * Alg. 1 takes as a parameter): line 1 by oracle_sketch_dense, then lines 2-8
+ * as oracle_cqrrpt.  Returns 0, -i for invalid argument i, 1 when k == 0, 2
+ * for a non-finite sketch. */
+int oracle_cqrrpt_dense(int64_t m, int64_t n, const double* M, int64_t ldm, int64_t d,
+                        const double* S, int64_t lds, double tol, double* Q, int64_t ldq,
+                        double* R, int64_t ldr, int64_t* J, int64_t* k_out, double* Rsk_out,
+                        double* Rpre_out, double* pivnorm, double* second) {
+    *k_out = 0;
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (ldm < m) return -4;
+    if (d < n || d > m) return -5;
+    if (lds < d) return -7;
+    if (ldq < m) return -10;
+    if (ldr < n) return -12;
+    double* Msk = (double*)malloc(sizeof(double) * (size_t)(d * n));
+    int st = oracle_sketch_dense(m, n, d, S, lds, M, ldm, Msk, d);
     if (st == 0)
         st = oracle_cqrrpt_core_sketched(m, n, M, ldm, Msk, d, tol, Q, ldq, R, ldr, J, k_out,
                                          Rsk_out, Rpre_out, pivnorm, second);

@@ -482,3 +482,125 @@ def test_rcholqr_equals_cqrrpt_when_the_pivots_are_the_identity():
     assert np.array_equal(b.J, np.arange(n)) and a.k == b.k == n
     assert np.array_equal(a.Q.view(np.uint64), b.Q.view(np.uint64))
     assert np.array_equal(a.R.view(np.uint64), b.R.view(np.uint64))
+
+
+# --------------------------------------------------------------------------
+# Dense sketching operators (Sec. 3.3.1's Gaussian family)
+# --------------------------------------------------------------------------
+def test_sketch_dense_exact_on_integer_operands():
+    """Integer S (|S| <= 3) and M (|M| <= 2^20): every product and partial
+    sum is exact, so the dense sketch equals the exact product S M (int64)
+    bit for bit; m spans two 4096-row blocks and a ragged tail."""
+    rng = _rng(41)
+    m, n, d = 2 * 4096 + 77, 5, 24
+    S = np.asfortranarray(rng.integers(-3, 4, size=(d, m)).astype(np.float64))
+    M = np.asfortranarray(rng.integers(-(2 ** 20), 2 ** 20, size=(m, n)).astype(np.float64))
+    Msk, st = oracle.sketch_dense(S, M)
+    assert st == 0
+    exact = S.astype(np.int64) @ M.astype(np.int64)
+    assert np.array_equal(Msk, exact.astype(np.float64))
+
+
+def test_sketch_dense_of_the_saso_pattern_is_the_saso_sketch():
+    """With S = the SASO's +-1 pattern, fma(+-1, a, p) rounds exactly like
+    p +- a, zero entries change nothing, and the blocks are summed in the same
+    order, so scale * (S_pattern M) equals the SASO sketch bit for bit."""
+    rng = _rng(42)
+    m, n, d, s = 3 * 4096 + 123, 6, 40, 4
+    M = np.asfortranarray(rng.standard_normal((m, n)))
+    scale = oracle.saso_scale(s)
+    pattern = np.asfortranarray(oracle.saso_dense(9, d, m, s) / scale)
+    assert set(np.unique(pattern).tolist()) <= {-1.0, 0.0, 1.0}
+    Md, st = oracle.sketch_dense(pattern, M)
+    assert st == 0
+    Ms, st2 = oracle.sketch(M, d, s, seed=9)
+    assert st2 == 0
+    assert np.array_equal(Md * scale, Ms)
+
+
+def test_sketch_dense_within_the_dot_product_bound():
+    """Gaussian S: against the exact sum of the exact products (rationals),
+    every entry lies within (4096 + blocks) u sum |S_ir M_rc|."""
+    rng = _rng(43)
+    m, n, d = 4096 + 50, 2, 3
+    S = np.asfortranarray(W.gaussian_operator(d, m, 5).numpy())
+    M = np.asfortranarray(rng.standard_normal((m, n)))
+    Msk, st = oracle.sketch_dense(S, M)
+    assert st == 0
+    absprod = np.abs(S) @ np.abs(M)
+    for i in range(d):
+        for c in range(n):
+            exact = sum((Fraction(float(S[i, r])) * Fraction(float(M[r, c])) for r in range(m)),
+                        Fraction(0))
+            err = abs(Fraction(float(Msk[i, c])) - exact)
+            assert err <= Fraction((4096 + 2) * U * absprod[i, c])
+
+
+def test_sketch_dense_nonfinite_status():
+    S = np.asfortranarray(np.ones((4, 10)))
+    M = np.asfortranarray(np.ones((10, 2)))
+    M[3, 1] = np.inf
+    _, st = oracle.sketch_dense(S, M)
+    assert st == 2
+    assert oracle.cqrrpt_dense(M, S, 1e-12).status == 2
+
+
+def test_cqrrpt_dense_identity_operator_is_geqp3():
+    """S = I_m (d = m): the sketch is M exactly, and CQRRPT is QRCP of M:
+    J equals LAPACK GEQP3's pivots and |R| its |R|."""
+    X = np.asfortranarray(_graded(90, 17, 13))
+    I = np.asfortranarray(np.eye(90))
+    Msk, st = oracle.sketch_dense(I, X)
+    assert st == 0 and np.array_equal(Msk, X)
+    res = oracle.cqrrpt_dense(X, I, 1e-14)
+    _, Rl, Jl = sl.qr(X, mode="economic", pivoting=True)
+    assert res.k == 17
+    assert np.array_equal(res.J, Jl)
+    assert np.abs(np.abs(res.R) - np.abs(Rl)).max() <= 1e-12 * np.abs(Rl).max()
+
+
+def test_cqrrpt_dense_with_one_nonzero_saso_equals_cqrrpt():
+    """s = 1: the SASO's entries are +-1 and its scale is exactly 1, so CQRRPT
+    with that dense S is CQRRPT with the SASO, bit for bit."""
+    m, n, gamma, seed = 5000, 24, 1.25, 31
+    A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -5.0), 8).numpy())
+    d = oracle.sketch_dim(n, gamma)
+    S = oracle.saso_dense(seed, d, m, 1)
+    ref = oracle.cqrrpt(A, gamma, 1, 1e-12, seed)
+    res = oracle.cqrrpt_dense(A, S, 1e-12)
+    assert ref.status == 0 and res.status == 0 and res.k == ref.k == n
+    assert np.array_equal(res.J, ref.J)
+    assert np.array_equal(res.Q, ref.Q) and np.array_equal(res.R, ref.R)
+
+
+def test_cqrrpt_dense_gaussian_theorem2_and_invariants():
+    """Gaussian S (Sec. 3.3.1): sigma_i(M^pre) = 1 / sigma_{k-i+1}(S U)
+    (Thm. 2, with M^pre = Q R^pre), and the factorisation invariants."""
+    m, n = 4096 + 300, 20
+    d = oracle.sketch_dim(n, 1.25)
+    U_ = W.haar(m, n, 51).numpy()
+    V_ = W.haar(n, n, 52).numpy()
+    A = np.asfortranarray((U_ * W.logspaced(n, -4.0).numpy()) @ V_.T)
+    S = np.asfortranarray(W.gaussian_operator(d, m, 53).numpy())
+    res = oracle.cqrrpt_dense(A, S, 1e-12)
+    assert res.status == 0 and res.k == n
+    Mpre = res.Q @ res.Rpre
+    sv_pre = np.linalg.svd(Mpre, compute_uv=False)
+    sv_su = np.linalg.svd(S @ U_, compute_uv=False)
+    assert np.abs(sv_pre - 1.0 / sv_su[::-1]).max() <= 1e-9 * sv_pre.max()
+    assert np.array_equal(np.triu(res.R), res.R) and (np.diag(res.R) > 0).all()
+    assert np.linalg.norm(A[:, res.J] - res.Q @ res.R) / np.linalg.norm(A) <= 1e-13
+    assert np.linalg.norm(res.Q.T @ res.Q - np.eye(n), 2) <= 1e-13
+
+
+def test_cqrrpt_dense_planted_rank_and_argument_errors():
+    sv = np.zeros(40)
+    sv[:25] = W.logspaced(25, -6.0).numpy()
+    m = 6000
+    A = np.asfortranarray(W.planted(m, 40, sv, 61, noise=1e-15).numpy())
+    S = np.asfortranarray(W.gaussian_operator(50, m, 62).numpy())
+    res = oracle.cqrrpt_dense(A, S, 1e-9)
+    assert res.k == 25
+    assert np.linalg.norm(res.Q.T @ res.Q - np.eye(25), 2) <= 1e-13
+    Sbad = np.asfortranarray(W.gaussian_operator(30, m, 63).numpy())   # d < n
+    assert oracle.cqrrpt_dense(A, Sbad, 1e-9).status == -5

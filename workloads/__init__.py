@@ -64,6 +64,12 @@ def gaussian(m, n, seed, device="cpu"):
     return to_colmajor(_gaussian(m, n, seed, device))
 
 
+def gaussian_operator(d, m, seed, device="cpu"):
+    """d x m Gaussian sketching operator of Sec. 3.3.1: iid entries of mean 0
+    and variance 1/d (column-major)."""
+    return to_colmajor(_gaussian(d, m, seed, device) * (1.0 / math.sqrt(d)))
+
+
 def high_coherence(m, n, seed, device="cpu", big=1e10):
     """Sec. 5.2: stacked identities, n random rows scaled by `big`, then a
     random right rotation."""

@@ -135,6 +135,35 @@ int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int
                      double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
                      cudaStream_t stream);
 
+/* ---- dense sketching operators -------------------------------------------- */
+
+/* Alg. 2 with a dense sketching operator S that the caller drew: the
+ * Gaussian family of Sec. 3.3.1 (iid entries of mean 0 and variance 1/d), or
+ * any other d x m operator (Alg. 1 takes the distribution F as a parameter).
+ * Line 1 is M^sk = S M in FP64: for each 4096-row block one fma per term in
+ * ascending row order from +0.0, the blocks then added in ascending order,
+ * no scaling (S carries its own); 2 d m n flops against the m n s additions
+ * of a SASO.  Lines 2-8 are those of cqrrpt_d in the chosen precision.
+ *   d          sketch rows, n <= d <= m and d <= 28000 (else -6).
+ *   S, lds     d x m column-major device matrix, lds >= d; read only,
+ *              owned by the caller (arguments 7, 8).
+ *   tol        rank rule as cqrrpt_d (argument 9).
+ *   precision  as cqrrpt_d (argument 10).
+ *   Q ... k_host as cqrrpt_d (arguments 11-17).
+ * Errors and statuses as cqrrpt_d. */
+int cqrrpt_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,
+                   const double* S, int64_t lds, double tol, int precision, double* Q,
+                   int64_t ldq, double* R, int64_t ldr, int64_t* J, int64_t* k_dev,
+                   int64_t* k_host, cudaStream_t stream);
+
+/* Line 1 alone with a dense operator: Ask (d x n, ldsk >= d) = S A in the
+ * sum order of cqrrpt_dense_d; S d x m (lds >= d).  A non-finite result
+ * sets the handle's status (CQRRPT_NONFINITE, read by cqrrpt_last_status).
+ * Uses the handle's workspace ((m/4096 + 1) n d 8 bytes); no host wait. */
+int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                          int64_t d, const double* S, int64_t lds, double* Ask, int64_t ldsk,
+                          cudaStream_t stream);
+
 /* ---- implicit Q --------------------------------------------------------- */
 
 /* Alg. 1 in FP64 stopped before Alg. 2 line 7: M^pre = M[:, J[:k]]

@@ -83,6 +83,9 @@ def lib():
                                    _i64, _p]
     L.cqrrpt_host_pipeline_d.argtypes = [_p, _int, _i64, _i64, _p, _i64, _d, _int, _d, _p, _int,
                                          _p, _i64, _p, _i64, _p, _p, _p, _p]
+    L.cqrrpt_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _d, _int, _p, _i64,
+                                 _p, _i64, _p, _p, _p, _p]
+    L.cqrrpt_sketch_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
     L.cqrrpt_sketch_dim.restype = _i64
     L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -102,7 +105,8 @@ def exported_symbols():
             "cqrrpt_batched_d", "cqrrpt_batched_workspace_size", "cqrrpt_set_batch_graphs",
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
-            "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d"]
+            "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d", "cqrrpt_dense_d",
+            "cqrrpt_sketch_dense_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -275,6 +279,33 @@ def rcholqr(A, gamma=1.25, nnz=4, seed=0, out=None, handle=None, stream=None):
     return Factorization(Q, R, J, k.value, rc)
 
 
+def cqrrpt_dense(A, S, tol=-1.0, precision=FP64, out=None, handle=None, stream=None, sync=True):
+    """Alg. 2 with the dense sketching operator S (d x m column-major
+    float64 CUDA tensor, e.g. a Gaussian operator of Sec. 3.3.1) through
+    cqrrpt_dense_d; line 1 in FP64, lines 2-8 in `precision`.  Returns a
+    Factorization (k and status None when sync=False)."""
+    h = handle or default_handle()
+    m, n = A.shape
+    d = S.shape[0]
+    if S.shape[1] != m:
+        raise ValueError("S must be d x m")
+    if out is None:
+        Q = colmajor_empty(m, n, A.device)
+        R = colmajor_empty(n, n, A.device)
+        J = torch.empty(n, dtype=torch.int64, device=A.device)
+    else:
+        Q, R, J = out
+    k = _i64()
+    rc = lib().cqrrpt_dense_d(h.h, m, n, A.data_ptr(), _ld(A), d, S.data_ptr(), _ld(S), tol,
+                              precision, Q.data_ptr(), _ld(Q), R.data_ptr(), _ld(R), J.data_ptr(), None,
+                              ctypes.byref(k) if sync else None, _stream(stream))
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_dense_d")
+    if not sync:
+        return Factorization(Q, R, J, None, None)
+    return Factorization(Q, R, J, k.value, rc)
+
+
 class ImplicitFactorization:
     """Output of cqrrpt_implicit: M^pre (m x k), R^pre (k x k), R (k x n),
     J, k, status; Q = M^pre (R^pre)^{-1} is applied with apply_q/apply_qt."""
@@ -351,6 +382,20 @@ def sketch(A, d, nnz, seed, handle=None, stream=None):
     out = colmajor_empty(d, n, A.device)
     _check(lib().cqrrpt_sketch_d(h.h, m, n, A.data_ptr(), _ld(A), d, nnz, seed, out.data_ptr(),
                                  _ld(out), _stream(stream)), "cqrrpt_sketch_d")
+    return out
+
+
+def sketch_dense(A, S, handle=None, stream=None):
+    """Line 1 with a dense operator: S A (d x n) through cqrrpt_sketch_dense_d."""
+    h = handle or default_handle()
+    m, n = A.shape
+    d = S.shape[0]
+    if S.shape[1] != m:
+        raise ValueError("S must be d x m")
+    out = colmajor_empty(d, n, A.device)
+    _check(lib().cqrrpt_sketch_dense_d(h.h, m, n, A.data_ptr(), _ld(A), d, S.data_ptr(), _ld(S),
+                                       out.data_ptr(), _ld(out), _stream(stream)),
+           "cqrrpt_sketch_dense_d")
     return out
 
 

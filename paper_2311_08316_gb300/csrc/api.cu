@@ -170,7 +170,8 @@ int read_k(cqrrpt_handle h, DeviceScalars* sc, cudaStream_t s, int64_t* k, int* 
 // rule and after the Cholesky).
 int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,
               int nnz, double tol, uint64_t seed, int precision, double* Q, int64_t ldq, double* R,
-              int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host, cudaStream_t stream) {
+              int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host, cudaStream_t stream,
+              const double* S_dense = nullptr, int64_t lds = 0) {
   const Plan p = plan_for(m, n, d, nnz, precision);
   int st = ensure_ws(h, p.total);
   if (st != kOk) return st;
@@ -191,7 +192,9 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
 
   cudaError_t e = launch_init_scalars(sc, 0, stream);
   mark(h, 0, stream);
-  if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
+  if (e == cudaSuccess)
+    e = S_dense ? launch_sketch_dense(m, n, S_dense, lds, A, lda, di, X, d, region, status, stream)
+                : launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
   mark(h, 1, stream);
   if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
   mark(h, 2, stream);
@@ -284,7 +287,7 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
                     int64_t d, int nnz, double tol, uint64_t seed, double* Q, int64_t ldq,
                     double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
                     cudaStream_t stream, bool form_q, double* Rpre_out, int64_t ld_rpre,
-                    bool pivoting = true) {
+                    bool pivoting = true, const double* S_dense = nullptr, int64_t lds = 0) {
   const Plan p = plan_fp64(m, n, d, nnz);
   int st = ensure_ws(h, p.total);
   if (st != kOk) return st;
@@ -308,7 +311,9 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
 
   cudaError_t e = launch_init_scalars(sc, 0, stream);
   mark(h, 0, stream);
-  if (e == cudaSuccess) e = launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
+  if (e == cudaSuccess)
+    e = S_dense ? launch_sketch_dense(m, n, S_dense, lds, A, lda, di, X, d, region, status, stream)
+                : launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
   mark(h, 1, stream);
   if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream, !pivoting);
   mark(h, 2, stream);
@@ -493,6 +498,56 @@ int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int
   // smallest normal tolerance
   return run_fp64(h, m, n, A, lda, d, nnz, DBL_MIN, seed, Q, ldq, R, ldr, J, k_dev, k_host,
                   stream, true, nullptr, 0, false);
+}
+
+int cqrrpt_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,
+                   const double* S, int64_t lds, double tol, int precision, double* Q,
+                   int64_t ldq, double* R, int64_t ldr, int64_t* J, int64_t* k_dev,
+                   int64_t* k_host, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 16384) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (d < n || d > m || d > 28000) return -6;
+  if (!S) return -7;
+  if (lds < d) return -8;
+  if (std::isnan(tol)) return -9;
+  if (!precision_ok(precision)) return -10;
+  if (!Q) return -11;
+  if (ldq < m) return -12;
+  if (!R) return -13;
+  if (ldr < n) return -14;
+  if (!J) return -15;
+  DevGuard g(h->device);
+  if (precision != CQRRPT_FP64)
+    return run_split(h, m, n, A, lda, d, 1, tol, 0, precision, Q, ldq, R, ldr, J, k_dev, k_host,
+                     stream, S, lds);
+  return run_fp64(h, m, n, A, lda, d, 1, tol, 0, Q, ldq, R, ldr, J, k_dev, k_host, stream, true,
+                  nullptr, 0, true, S, lds);
+}
+
+int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                          int64_t d, const double* S, int64_t lds, double* Ask, int64_t ldsk,
+                          cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (d < 1) return -6;
+  if (!S) return -7;
+  if (lds < d) return -8;
+  if (!Ask) return -9;
+  if (ldsk < d) return -10;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)sketch_dense_workspace_bytes(m, n, (int)d));
+  if (st != kOk) return st;
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  if (launch_sketch_dense(m, n, S, lds, A, lda, (int)d, Ask, ldsk, h->ws, &h->sc->status,
+                          stream) != cudaSuccess)
+    return kCudaError;
+  return kOk;
 }
 
 int cqrrpt_apply_q_d(cqrrpt_handle h, int trans, int64_t m, int64_t k, const double* Apre,

@@ -36,6 +36,13 @@ void sketch_carve(SketchDesc& D, void* work);
 cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, int d, int s,
                           uint64_t seed, double scale, double* Msk, int64_t ldsk, void* work,
                           int* status, cudaStream_t stream);
+// Line 1 with a dense operator S (d x m, ld lds): M^sk = S M, one fma per
+// term in ascending row order inside each kRowBlock block, blocks added in
+// ascending order, no scaling.  work: sketch_dense_workspace_bytes.
+int64_t sketch_dense_workspace_bytes(int64_t m, int64_t n, int d);
+cudaError_t launch_sketch_dense(int64_t m, int64_t n, const double* S, int64_t lds,
+                                const double* M, int64_t ldm, int d, double* Msk, int64_t ldsk,
+                                void* work, int* status, cudaStream_t stream);
 int64_t sketch_list_tiles(const SketchDesc& D);
 int64_t sketch_partial_tiles(const SketchDesc& D);
 int64_t sketch_combine_tiles(const SketchDesc& D);

@@ -17,6 +17,11 @@
 // The arithmetic (FP64 additions in that order, one final scale) is fixed by
 // the data, not by the launch shape.  Each kernel exists as a single-problem
 // launch and a batched launch (CTA -> (problem, tile)) over the same body.
+//
+// A dense operator S (d x m, given by the caller: Sec. 3.3.1's Gaussian
+// family) replaces the first two kernels by sketch_dense_partial, which forms
+// P_b[i, c] = sum_{r in b} S[i, r] M[r, c] with one fma per term in ascending
+// r from +0.0; sketch_combine then adds the blocks with scale 1 (exact).
 #include "common.cuh"
 #include "kernels.h"
 #include "saso.cuh"
@@ -179,6 +184,77 @@ __global__ void __launch_bounds__(kCombineThreads) sketch_combine_batched_kernel
   sketch_combine_body(t, D[p]);
 }
 
+// ---- dense operators --------------------------------------------------------
+// One CTA per (row block b, 32 x 32 tile of the d x n output); 64 threads in
+// an 8 x 8 grid, each with a 4 x 4 register tile; rows staged kDsRows at a
+// time in shared memory (S read along i, M along r: both coalesced).  The
+// kernel is bound by the FP64 pipe (2 d m n flops); the CTAs of one row block
+// are adjacent in launch order, so its slices of S and M are read from HBM
+// about once and reused from L2 by the block's tiles.
+constexpr int kDsTile = 32;
+constexpr int kDsRows = 32;
+
+struct DenseSketchDesc {
+  int64_t m, n;
+  int d;
+  const double* S;
+  int64_t lds;
+  const double* M;
+  int64_t ldm;
+  double* partial;  // nblocks x (n x d), ld d
+};
+
+__global__ void __launch_bounds__(64, 14) sketch_dense_partial_kernel(DenseSketchDesc D,
+                                                                      int ti_count, int tiles) {
+  __shared__ double Ss[kDsTile][kDsRows + 1];  // [i][row]
+  __shared__ double Ms[kDsTile][kDsRows + 1];  // [c][row]
+  const int64_t b = blockIdx.x / tiles;
+  const int t = (int)(blockIdx.x - b * tiles);
+  const int i0 = (t % ti_count) * kDsTile, c0 = (t / ti_count) * kDsTile;
+  const int64_t r0 = b * kRowBlock;
+  const int rows = (int)min64(kRowBlock, D.m - r0);
+  const int d = D.d;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+
+  for (int rr0 = 0; rr0 < rows; rr0 += kDsRows) {
+    const int nr = min(kDsRows, rows - rr0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kDsTile * kDsRows; e += 64) {
+      const int i = e % kDsTile, srow = e / kDsTile;
+      Ss[i][srow] = (srow < nr && i0 + i < d)
+                        ? D.S[(r0 + rr0 + srow) * D.lds + (i0 + i)] : 0.0;
+      const int c = e / kDsRows, mrow = e % kDsRows;
+      Ms[c][mrow] = (mrow < nr && c0 + c < D.n)
+                        ? D.M[(int64_t)(c0 + c) * D.ldm + (r0 + rr0 + mrow)] : 0.0;
+    }
+    __syncthreads();
+    for (int row = 0; row < nr; ++row) {
+      double va[4], vc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) va[u] = Ss[ty * 4 + u][row];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) vc[v] = Ms[tx * 4 + v][row];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = __fma_rn(va[u], vc[v], acc[u][v]);
+    }
+  }
+  double* P = D.partial + b * D.n * (int64_t)d;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, c = c0 + tx * 4 + v;
+      if (i < d && c < D.n) P[(int64_t)c * d + i] = acc[u][v];
+    }
+}
+
 // ---- host side --------------------------------------------------------------
 static int64_t nblocks_of(int64_t m) { return (m + kRowBlock - 1) / kRowBlock; }
 
@@ -253,6 +329,26 @@ cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, in
                           kRowBlock * sizeof(double2), stream>>>(D, ncg);
   sketch_combine_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(D);
   count_launches(3);
+  return cudaGetLastError();
+}
+
+int64_t sketch_dense_workspace_bytes(int64_t m, int64_t n, int d) {
+  return align256(nblocks_of(m) * n * (int64_t)d * 8);
+}
+
+cudaError_t launch_sketch_dense(int64_t m, int64_t n, const double* S, int64_t lds,
+                                const double* M, int64_t ldm, int d, double* Msk, int64_t ldsk,
+                                void* work, int* status, cudaStream_t stream) {
+  const int ti_count = (d + kDsTile - 1) / kDsTile;
+  const int tiles = ti_count * (int)((n + kDsTile - 1) / kDsTile);
+  DenseSketchDesc P{m, n, d, S, lds, M, ldm, (double*)work};
+  sketch_dense_partial_kernel<<<(unsigned)(nblocks_of(m) * tiles), 64, 0, stream>>>(P, ti_count,
+                                                                                 tiles);
+  SketchDesc D{};
+  D.m = m; D.n = n; D.d = d; D.scale = 1.0;
+  D.partial = (double*)work; D.Msk = Msk; D.ldsk = ldsk; D.status = status;
+  sketch_combine_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(D);
+  count_launches(2);
   return cudaGetLastError();
 }
 

@@ -435,3 +435,91 @@ def test_rcholqr_matches_oracle(C, m, n, seed):
     assert np.array_equal(host(res.J), np.arange(n))
     assert_bits(host(res.Q), ref.Q, "Q")
     assert_bits(host(res.R), ref.R, "R")
+
+
+# ------------------------------------------- dense (Gaussian) sketching operator
+@pytest.mark.parametrize("m,n,d,seed", [
+    (2 * 4096 + 77, 20, 40, 1),     # two blocks + ragged tail; d, n not multiples of 32
+    (1000, 8, 10, 2),               # less than one row block
+    (3 * 4096, 64, 96, 3),          # whole tiles, whole blocks
+])
+def test_sketch_dense_matches_oracle(C, m, n, d, seed):
+    """Line 1 with a Gaussian operator (Sec. 3.3.1): bit-identical to the
+    oracle's blocked ascending-fma product."""
+    S = np.asfortranarray(W.gaussian_operator(d, m, 500 + seed).numpy())
+    M = np.asfortranarray(_rng(seed).standard_normal((m, n)))
+    ref, st = oracle.sketch_dense(S, M)
+    assert st == 0
+    got = C.sketch_dense(gpu(M), gpu(S))
+    torch.cuda.synchronize()
+    assert_bits(host(got), ref, "S M")
+
+
+@pytest.mark.parametrize("case", ["planted", "full", "identity"])
+def test_cqrrpt_dense_matches_oracle(C, case):
+    """Alg. 2 with a dense operator through cqrrpt_dense_d: Q, R, J and k
+    bit-identical to the oracle (planted rank with noise; full rank; S = I
+    with d = m, where the method is QRCP of M itself)."""
+    if case == "planted":
+        m, n, rank, tol = 3 * 4096 + 5, 48, 30, 1e-9
+        sv = np.zeros(n)
+        sv[:rank] = W.logspaced(rank, -6.0).numpy()
+        A = np.asfortranarray(W.planted(m, n, sv, 601, noise=1e-15).numpy())
+        S = np.asfortranarray(W.gaussian_operator(60, m, 602).numpy())
+    elif case == "full":
+        m, n, rank, tol = 5000, 64, 64, 1e-12
+        A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -8.0), 603).numpy())
+        S = np.asfortranarray(W.gaussian_operator(80, m, 604).numpy())
+    else:
+        m, n, rank, tol = 200, 17, 17, 1e-14
+        A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -3.0), 605).numpy())
+        S = np.asfortranarray(np.eye(m))
+    ref = oracle.cqrrpt_dense(A, S, tol)
+    res = C.cqrrpt_dense(gpu(A), gpu(S), tol)
+    assert res.status == ref.status == 0 and res.k == ref.k == rank
+    assert np.array_equal(host(res.J), ref.J)
+    assert_bits(host(res.Q), ref.Q, "Q")
+    assert_bits(host(res.R), ref.R, "R")
+
+
+def test_cqrrpt_dense_one_nonzero_saso_equals_cqrrpt(C):
+    """s = 1 gives a SASO with entries +-1 and scale exactly 1: the dense
+    path on that operator reproduces cqrrpt_d's outputs bit for bit."""
+    m, n, gamma, seed = 2 * 4096 + 300, 40, 1.25, 71
+    A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -6.0), 606).numpy())
+    d = oracle.sketch_dim(n, gamma)
+    S = oracle.saso_dense(seed, d, m, 1)
+    a = C.cqrrpt(gpu(A), gamma, 1, 1e-12, seed)
+    b = C.cqrrpt_dense(gpu(A), gpu(S), 1e-12)
+    assert a.status == b.status == 0 and a.k == b.k == n
+    assert torch.equal(a.J, b.J)
+    assert_bits(host(b.Q), host(a.Q), "Q")
+    assert_bits(host(b.R), host(a.R), "R")
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_cqrrpt_dense_split_modes(C, precision):
+    """Dense operator with lines 4, 5, 7 in split-BF16 (with and without the
+    second CholeskyQR pass): the FP64 sketch and QRCP give the oracle's J and
+    k; residuals at the FP64 level."""
+    m, n = 2 * 4096 + 11, 64
+    A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -8.0), 607).numpy())
+    S = np.asfortranarray(W.gaussian_operator(80, m, 608).numpy())
+    ref = oracle.cqrrpt_dense(A, S, 1e-12)
+    res = C.cqrrpt_dense(gpu(A), gpu(S), 1e-12, precision=precision)
+    assert res.status == ref.status == 0 and res.k == ref.k == n
+    assert np.array_equal(host(res.J), ref.J)
+    Q, R = host(res.Q), host(res.R)
+    assert np.linalg.norm(A[:, ref.J] - Q @ R) / np.linalg.norm(A) <= 1e-13
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 1e-13
+
+
+def test_cqrrpt_dense_nonfinite_and_arguments(C):
+    m, n = 300, 10
+    A = np.asfortranarray(_rng(9).standard_normal((m, n)))
+    A[17, 3] = np.nan
+    S = np.asfortranarray(W.gaussian_operator(13, m, 609).numpy())
+    res = C.cqrrpt_dense(gpu(A), gpu(S), 1e-12)
+    assert res.status == 2 and res.k == 0
+    with pytest.raises(Exception):
+        C.cqrrpt_dense(gpu(A), gpu(S[:8, :]), 1e-12)          # d < n

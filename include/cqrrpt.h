@@ -135,6 +135,39 @@ int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int
                      double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
                      cudaStream_t stream);
 
+/* ---- row panels of a host-resident matrix --------------------------------- */
+
+/* The row-partitioned form of Alg. 2 (Sec. 3.2 notes that the sketch and the
+ * Gram matrix are sums over row blocks, so rows can be split among
+ * processors with one reduction each) run on one GPU over row panels of a
+ * host-resident M that need not fit in device memory.  Panels of
+ * panel_rows rows are streamed through two device slots (copy-in, compute
+ * and copy-out on three streams):
+ *   pass 1: line 1 per panel; each panel's 4096-row block sums continue the
+ *           sketch's ascending block sum (the reduction); then lines 2-3;
+ *   pass 2: lines 4-5 per panel; M^pre is parked in Q_host's first k
+ *           columns and its Gram blocks continue G's ascending block sum;
+ *           then line 6;
+ *   pass 3: line 7 per panel, in place on the parked M^pre; then line 8.
+ * Because panel_rows is a multiple of 4096, every sum keeps cqrrpt_d's
+ * order: Q, R, J and k equal cqrrpt_d's (FP64) bit for bit.  Device memory:
+ * 4 panel_rows n 8 bytes plus one panel_rows-row workspace.  Host traffic:
+ * M read twice, M^pre written and read once, Q written once.  The host
+ * waits for k after line 3 and after line 6.  Pin A_host and Q_host
+ * (cudaHostRegister) for copies that overlap the kernels.
+ *   A_host, lda   m x n host matrix (lda >= m), read only (arguments 4, 5).
+ *   panel_rows    a positive multiple of 4096 (else -10).
+ *   Q_host, ldq   m x n host capacity, ldq >= m; first k columns receive Q
+ *                 (the first columns hold M^pre in between) (11, 12).
+ *   R_host, ldr   n x n host capacity, ldr >= n; first k rows receive R (13, 14).
+ *   J_host        n host int64 pivots (15); k_host: host int64 rank (16).
+ * Other arguments as cqrrpt_d (FP64 only).  Returns 0 or a status of
+ * cqrrpt_d (the call completes before returning). */
+int cqrrpt_panels_host_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A_host,
+                         int64_t lda, double gamma, int nnz_per_col, double tol, uint64_t seed,
+                         int64_t panel_rows, double* Q_host, int64_t ldq, double* R_host,
+                         int64_t ldr, int64_t* J_host, int64_t* k_host, cudaStream_t stream);
+
 /* ---- dense sketching operators -------------------------------------------- */
 
 /* Alg. 2 with a dense sketching operator S that the caller drew: the

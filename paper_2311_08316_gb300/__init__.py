@@ -86,6 +86,8 @@ def lib():
     L.cqrrpt_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _d, _int, _p, _i64,
                                  _p, _i64, _p, _p, _p, _p]
     L.cqrrpt_sketch_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_panels_host_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _i64, _p,
+                                       _i64, _p, _i64, _p, _p, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
     L.cqrrpt_sketch_dim.restype = _i64
     L.cqrrpt_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
@@ -106,7 +108,7 @@ def exported_symbols():
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
             "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d", "cqrrpt_dense_d",
-            "cqrrpt_sketch_dense_d"]
+            "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -277,6 +279,31 @@ def rcholqr(A, gamma=1.25, nnz=4, seed=0, out=None, handle=None, stream=None):
     if rc < 0 or rc >= 3:
         _check(rc, "cqrrpt_rcholqr_d")
     return Factorization(Q, R, J, k.value, rc)
+
+
+def cqrrpt_panels(A_host, gamma=1.25, nnz=4, tol=-1.0, seed=0, panel_rows=65536, out=None,
+                  handle=None, stream=None):
+    """Alg. 2 over row panels of a host-resident A (m x n column-major
+    float64 CPU tensor; pin it for overlapped copies) through
+    cqrrpt_panels_host_d.  Returns (Q m x k, R k x n, J, k, status) as host
+    tensors (views of the full-capacity outputs)."""
+    h = handle or default_handle()
+    m, n = A_host.shape
+    if out is None:
+        Q = colmajor_empty(m, n, "cpu")
+        R = colmajor_empty(n, n, "cpu")
+        J = torch.empty(n, dtype=torch.int64)
+    else:
+        Q, R, J = out
+    k = _i64()
+    rc = lib().cqrrpt_panels_host_d(h.h, m, n, A_host.data_ptr(), _ld_host(A_host), gamma, nnz,
+                                    tol, seed, panel_rows, Q.data_ptr(), _ld_host(Q),
+                                    R.data_ptr(), _ld_host(R), J.data_ptr(), ctypes.byref(k),
+                                    _stream(stream))
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_panels_host_d")
+    kk = k.value
+    return Q[:, :kk], R[:kk, :], J, kk, rc
 
 
 def cqrrpt_dense(A, S, tol=-1.0, precision=FP64, out=None, handle=None, stream=None, sync=True):

@@ -747,6 +747,160 @@ int cqrrpt_host_pipeline_d(cqrrpt_handle h, int count, int64_t m, int64_t n,
   return first_error;
 }
 
+int cqrrpt_panels_host_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A_host,
+                         int64_t lda, double gamma, int nnz, double tol, uint64_t seed,
+                         int64_t panel_rows, double* Q_host, int64_t ldq, double* R_host,
+                         int64_t ldr, int64_t* J_host, int64_t* k_host, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 16384) return -3;
+  if (!A_host) return -4;
+  if (lda < m) return -5;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -6;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -6;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
+  if (std::isnan(tol)) return -8;
+  if (panel_rows < kRowBlock || panel_rows % kRowBlock != 0) return -10;
+  if (!Q_host) return -11;
+  if (ldq < m) return -12;
+  if (!R_host) return -13;
+  if (ldr < n) return -14;
+  if (!J_host) return -15;
+  if (!k_host) return -16;
+  DevGuard g(h->device);
+  *k_host = 0;
+  const int64_t P = panel_rows < m ? panel_rows : (m + kRowBlock - 1) / kRowBlock * kRowBlock;
+  const int64_t npan = (m + P - 1) / P;
+  // device: two A panels and two M^pre / Q panels (P x n each), R and J,
+  // the workspace of one P-row factorisation, the sketch accumulator
+  int st = pipe_ensure(h, P, n);
+  if (st != kOk) return st;
+  const Plan p = plan_fp64(P, n, d, nnz);
+  const size_t acc_bytes = (size_t)align256(d * n * 8);
+  st = ensure_ws(h, p.total + acc_bytes);
+  if (st != kOk) return st;
+  char* w = (char*)h->ws;
+  void* region = w; w += p.region;
+  double* X = (double*)w; w += p.x;
+  void* qw = w; w += p.qrcp;
+  double* Rsk = (double*)w; w += p.rsk;
+  double* G = (double*)w; w += p.g;
+  double* Rpre = (double*)w; w += p.rpre;
+  double* f2 = (double*)w; w += p.f2;
+  double* acc = (double*)w;
+  int64_t* Jd = h->pipe_j[0];
+  double* Rd = h->pipe_r[0];
+  DeviceScalars* sc = h->sc;
+  int* status = &sc->status;
+  const int ni = (int)n, di = (int)d;
+  cudaEvent_t* ev_in = h->pipe_ev;
+  cudaEvent_t* ev_comp = h->pipe_ev + 2;
+  cudaEvent_t* ev_out = h->pipe_ev + 4;
+  double** abuf = h->pipe_a;
+  double** xbuf = h->pipe_q;
+  cudaError_t e = cudaSuccess;
+  int64_t it = 0;  // panel uses so far; slot it & 1
+  auto rows_of = [&](int64_t q) { return q * P + P <= m ? P : m - q * P; };
+  // rows of panel q (cols columns of a host matrix) into a device buffer of
+  // slot b, after the compute and the copy-out that last used slot b
+  auto copy_in = [&](double* dst, const double* src, int64_t ld, int64_t q, int64_t cols,
+                     int b) {
+    if (it >= 2 && e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_in, ev_comp[b], 0);
+    if (it >= 2 && e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_in, ev_out[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dst, (size_t)P * 8, src + q * P, (size_t)ld * 8,
+                            (size_t)rows_of(q) * 8, (size_t)cols, cudaMemcpyHostToDevice,
+                            h->pipe_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[b], h->pipe_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_in[b], 0);
+  };
+  // the slot's compute is queued: its M^pre / Q panel (cols columns) to the
+  // rows of panel q of Q_host
+  auto copy_out = [&](int64_t q, int64_t cols, int b) {
+    if (e == cudaSuccess) e = cudaEventRecord(ev_comp[b], stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_out, ev_comp[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Q_host + q * P, (size_t)ldq * 8, xbuf[b], (size_t)P * 8,
+                            (size_t)rows_of(q) * 8, (size_t)cols, cudaMemcpyDeviceToHost,
+                            h->pipe_out);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], h->pipe_out);
+  };
+  auto drain = [&]() {
+    const cudaError_t e1 = cudaStreamSynchronize(h->pipe_in);
+    const cudaError_t e2 = cudaStreamSynchronize(h->pipe_out);
+    const cudaError_t e3 = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess;
+  };
+
+  // line 1: each panel's block sums continue the sketch's ascending sum
+  if (e == cudaSuccess) e = launch_init_scalars(sc, 0, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (size_t)d * n * 8, stream);
+  for (int64_t q = 0; q < npan && e == cudaSuccess; ++q, ++it) {
+    const int b = (int)(it & 1);
+    copy_in(abuf[b], A_host, lda, q, n, b);
+    if (e == cudaSuccess)
+      e = launch_sketch_panel(rows_of(q), n, abuf[b], P, di, nnz, seed, q * P, acc, region,
+                              stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_comp[b], stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out[b], stream);
+  }
+  if (e == cudaSuccess)
+    e = launch_sketch_finish(di, n, acc, 1.0 / std::sqrt((double)nnz), X, d, status, stream);
+  // lines 2 and 3
+  if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, Jd, Rsk, n, qw, sc, h->num_sms, stream);
+  if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
+  int st1 = kOk;
+  int64_t k1 = 0;
+  if (e == cudaSuccess && cqrrpt_last_status(h, stream, &st1, &k1) != kOk) e = cudaErrorUnknown;
+  if (e == cudaSuccess && st1 == kOk && k1 > 0) {
+    // lines 4 and 5: M^pre panel by panel (parked in Q_host's first k1
+    // columns), its Gram blocks continuing G's ascending sums
+    e = cudaMemsetAsync(G, 0, (size_t)n * n * 8, stream);
+    for (int64_t q = 0; q < npan && e == cudaSuccess; ++q, ++it) {
+      const int b = (int)(it & 1);
+      copy_in(abuf[b], A_host, lda, q, n, b);
+      if (e == cudaSuccess)
+        e = launch_trsm_rut(rows_of(q), ni, &sc->k, abuf[b], P, Jd, Rsk, n, xbuf[b], P, status,
+                            stream);
+      if (e == cudaSuccess)
+        e = launch_gram(rows_of(q), ni, &sc->k, xbuf[b], P, G, n, region, status, stream, true);
+      copy_out(q, k1, b);
+    }
+    // line 6 (Remark 3, stage 2)
+    if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, n, sc, stream);
+    if (e == cudaSuccess) e = launch_rank_stage2(Rpre, n, !(tol > 0.0), sc, stream);
+    int st2 = kOk;
+    int64_t k2 = 0;
+    if (e == cudaSuccess && cqrrpt_last_status(h, stream, &st2, &k2) != kOk) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->pipe_out);  // M^pre is on the host
+    // line 7: Q panel by panel, in place on the parked M^pre
+    for (int64_t q = 0; q < npan && e == cudaSuccess && k2 > 0; ++q, ++it) {
+      const int b = (int)(it & 1);
+      copy_in(xbuf[b], Q_host, ldq, q, k2, b);
+      if (e == cudaSuccess)
+        e = launch_trsm_rut(rows_of(q), ni, &sc->k, xbuf[b], P, nullptr, Rpre, n, xbuf[b], P,
+                            status, stream);
+      copy_out(q, k2, b);
+    }
+    // line 8
+    if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, Rpre, n, Rsk, n, Rd, n, status, stream);
+    if (e == cudaSuccess && k2 > 0)
+      e = cudaMemcpy2DAsync(R_host, (size_t)ldr * 8, Rd, (size_t)n * 8, (size_t)k2 * 8,
+                            (size_t)n, cudaMemcpyDeviceToHost, stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(J_host, Jd, (size_t)n * 8, cudaMemcpyDeviceToHost, stream);
+  if (!drain()) return kCudaError;
+  int st3 = kOk;
+  int64_t k3 = 0;
+  if (cqrrpt_last_status(h, stream, &st3, &k3) != kOk) return kCudaError;
+  *k_host = k3;
+  return st3;
+}
+
 static int batch_check(int batch, const int64_t* m, const int64_t* n, const double* const* A,
                        const int64_t* lda, double gamma, int nnz, const double* tol,
                        const uint64_t* seed, int precision, double* const* Q, const int64_t* ldq,

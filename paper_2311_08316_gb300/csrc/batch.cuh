@@ -23,6 +23,7 @@ struct SketchDesc {
   int64_t m, n;
   int d, s;
   uint64_t seed;
+  int64_t row0;  // index in the whole matrix of M's first row (column row0 + r of S)
   double scale;
   const double* M;
   int64_t ldm;

@@ -116,7 +116,10 @@ __device__ __forceinline__ void gram_partial_body(int64_t tile, const GramDesc& 
     gram_partial_tile<kGramTile>(tile, D, Xa, Xc);
 }
 
-__device__ __forceinline__ void gram_combine_body(int64_t tile, const GramDesc& D) {
+// accumulate: the sum starts from G's upper entry instead of +0.0 (row
+// panels: G holds the ascending block sum of the panels before this one)
+__device__ __forceinline__ void gram_combine_body(int64_t tile, const GramDesc& D,
+                                                  bool accumulate = false) {
   if (*D.status != kOk) return;
   const int k = (int)*D.k_dev;
   const int n_ld = D.n_ld;
@@ -126,7 +129,7 @@ __device__ __forceinline__ void gram_combine_body(int64_t tile, const GramDesc& 
   const int c = (int)(idx / k), a = (int)(idx - (int64_t)c * k);
   if (a > c) return;
   const int64_t off = (int64_t)c * n_ld + a;
-  double tsum = 0.0;
+  double tsum = accumulate ? D.G[(int64_t)c * D.ldg + a] : 0.0;
   for (int64_t b = 0; b < nblocks; ++b)
     tsum = __dadd_rn(tsum, D.partial[b * (int64_t)n_ld * n_ld + off]);
   D.G[(int64_t)c * D.ldg + a] = tsum;
@@ -143,6 +146,9 @@ __global__ void __launch_bounds__(64, TILE == 8 ? 1 : 14) gram_partial_kernel(Gr
 }
 __global__ void __launch_bounds__(kCombineThreads) gram_combine_kernel(GramDesc D) {
   gram_combine_body(blockIdx.x, D);
+}
+__global__ void __launch_bounds__(kCombineThreads) gram_accumulate_kernel(GramDesc D) {
+  gram_combine_body(blockIdx.x, D, true);
 }
 __global__ void __launch_bounds__(64) gram_partial_batched_kernel(const GramDesc* D,
                                                                   const int64_t* base, int np) {
@@ -169,7 +175,7 @@ static int gram_single_tile(int64_t m, int kmax) {
 
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, bool accumulate) {
   const int tile = gram_single_tile(m, kmax);
   GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status, tile};
   const unsigned grid = (unsigned)gram_partial_tiles(m, kmax, tile);
@@ -179,7 +185,10 @@ cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double*
     gram_partial_kernel<16><<<grid, 64, 0, stream>>>(D);
   else
     gram_partial_kernel<kGramTile><<<grid, 64, 0, stream>>>(D);
-  gram_combine_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
+  if (accumulate)
+    gram_accumulate_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
+  else
+    gram_combine_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -43,6 +43,15 @@ int64_t sketch_dense_workspace_bytes(int64_t m, int64_t n, int d);
 cudaError_t launch_sketch_dense(int64_t m, int64_t n, const double* S, int64_t lds,
                                 const double* M, int64_t ldm, int d, double* Msk, int64_t ldsk,
                                 void* work, int* status, cudaStream_t stream);
+// Row panels of M (rows [row0, row0 + rows), row0 a multiple of kRowBlock):
+// acc (d x n, ld d) += the panel's block sums in ascending block order;
+// acc = +0.0 before the first panel; after the last, sketch_finish writes
+// M^sk = scale * acc, bit-identical to launch_sketch on the whole M.
+cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_t ldm, int d,
+                                int s, uint64_t seed, int64_t row0, double* acc, void* work,
+                                cudaStream_t stream);
+cudaError_t launch_sketch_finish(int d, int64_t n, const double* acc, double scale, double* Msk,
+                                 int64_t ldsk, int* status, cudaStream_t stream);
 int64_t sketch_list_tiles(const SketchDesc& D);
 int64_t sketch_partial_tiles(const SketchDesc& D);
 int64_t sketch_combine_tiles(const SketchDesc& D);
@@ -90,9 +99,11 @@ cudaError_t launch_trsm_rut_batched(const TrsmDesc* D, const int64_t* base, int 
 int64_t gram_workspace_bytes(int64_t m, int64_t n);
 int64_t gram_partial_tiles(int64_t m, int kmax, int tile);
 int64_t gram_combine_tiles(int kmax);
+// accumulate: G (both triangles) += this X's blocks, continuing G's sums
+// in ascending block order (row panels; G = 0 before the first panel).
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
-                        cudaStream_t stream);
+                        cudaStream_t stream, bool accumulate = false);
 // phase 0: partial tiles, 1: combine
 cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* base, int nprob,
                                 int64_t total_tiles, cudaStream_t stream);

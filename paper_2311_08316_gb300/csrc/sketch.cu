@@ -43,7 +43,7 @@ __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, 
   int tr[kMaxNnzInline];
   uint32_t neg;
   for (int rl = threadIdx.x; rl < rows; rl += blockDim.x) {
-    saso_column(D.seed, r0 + rl, d, s, tr, &neg);
+    saso_column(D.seed, D.row0 + r0 + rl, d, s, tr, &neg);
     for (int q = 0; q < s; ++q) atomicAdd(&count[tr[q]], 1);
   }
   __syncthreads();
@@ -69,7 +69,7 @@ __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, 
   for (int i = threadIdx.x; i < d; i += blockDim.x) count[i] = start[i];  // cursors
   __syncthreads();
   for (int rl = threadIdx.x; rl < rows; rl += blockDim.x) {
-    saso_column(D.seed, r0 + rl, d, s, tr, &neg);
+    saso_column(D.seed, D.row0 + r0 + rl, d, s, tr, &neg);
     for (int q = 0; q < s; ++q) {
       const int pos = atomicAdd(&count[tr[q]], 1);
       gent[pos] = ((uint32_t)rl << 1) | ((neg >> q) & 1u);
@@ -142,6 +142,36 @@ __device__ __forceinline__ void sketch_combine_body(int64_t tile, const SketchDe
     bad = !isfinite(v);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(D.status, kNonFinite);
+}
+
+// Row panels: acc[i, c] continues the ascending block sum of the panels
+// before this one (acc = +0.0 before the first panel), so that after the
+// last panel acc equals the combine's sum bit for bit when every panel
+// starts on a kRowBlock boundary; sketch_finish then scales.
+__global__ void __launch_bounds__(kCombineThreads) sketch_accumulate_kernel(SketchDesc D,
+                                                                            double* acc) {
+  const int64_t total = D.n * (int64_t)D.d;
+  const int64_t nblocks = (D.m + kRowBlock - 1) / kRowBlock;
+  const int64_t idx = (int64_t)blockIdx.x * kCombineThreads + threadIdx.x;
+  if (idx >= total) return;
+  double t = acc[idx];
+  for (int64_t b = 0; b < nblocks; ++b) t = __dadd_rn(t, D.partial[b * total + idx]);
+  acc[idx] = t;
+}
+
+__global__ void __launch_bounds__(kCombineThreads) sketch_finish_kernel(const double* acc, int d,
+                                                                        int64_t n, double scale,
+                                                                        double* Msk, int64_t ldsk,
+                                                                        int* status) {
+  const int64_t idx = (int64_t)blockIdx.x * kCombineThreads + threadIdx.x;
+  bool bad = false;
+  if (idx < n * (int64_t)d) {
+    const int64_t c = idx / d, i = idx - c * d;
+    const double v = __dmul_rn(acc[idx], scale);
+    Msk[c * ldsk + i] = v;
+    bad = !isfinite(v);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(status, kNonFinite);
 }
 
 // ---- single-problem kernels -------------------------------------------------
@@ -349,6 +379,34 @@ cudaError_t launch_sketch_dense(int64_t m, int64_t n, const double* S, int64_t l
   D.partial = (double*)work; D.Msk = Msk; D.ldsk = ldsk; D.status = status;
   sketch_combine_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(D);
   count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_t ldm, int d,
+                                int s, uint64_t seed, int64_t row0, double* acc, void* work,
+                                cudaStream_t stream) {
+  SketchDesc D{};
+  D.m = rows; D.n = n; D.d = d; D.s = s; D.seed = seed; D.row0 = row0; D.scale = 1.0;
+  D.M = M; D.ldm = ldm;
+  sketch_carve(D, work);
+  const size_t sh_lists = (size_t)(2 * d + 1) * sizeof(int);
+  cudaError_t e = set_smem_attrs(sh_lists);
+  if (e != cudaSuccess) return e;
+  saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), 256, sh_lists, stream>>>(D);
+  const int64_t ncg = (n + kSkCols - 1) / kSkCols;
+  sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), sketch_threads(d),
+                          kRowBlock * sizeof(double2), stream>>>(D, ncg);
+  sketch_accumulate_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(
+      D, acc);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_finish(int d, int64_t n, const double* acc, double scale, double* Msk,
+                                 int64_t ldsk, int* status, cudaStream_t stream) {
+  const unsigned grid = (unsigned)((n * (int64_t)d + kCombineThreads - 1) / kCombineThreads);
+  sketch_finish_kernel<<<grid, kCombineThreads, 0, stream>>>(acc, d, n, scale, Msk, ldsk, status);
+  count_launches(1);
   return cudaGetLastError();
 }
 

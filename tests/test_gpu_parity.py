@@ -523,3 +523,46 @@ def test_cqrrpt_dense_nonfinite_and_arguments(C):
     assert res.status == 2 and res.k == 0
     with pytest.raises(Exception):
         C.cqrrpt_dense(gpu(A), gpu(S[:8, :]), 1e-12)          # d < n
+
+
+# ------------------------------------------- row panels of a host-resident matrix
+@pytest.mark.parametrize("panel_rows,tol,case", [
+    (4096, 1e-9, "planted"),     # six panels, ragged last one
+    (8192, 1e-9, "planted"),
+    (65536, 1e-9, "planted"),    # one panel larger than m
+    (8192, -1.0, "graded"),      # default rank rule (stage 2 after the Cholesky)
+])
+def test_panels_host_matches_oracle(C, panel_rows, tol, case):
+    """Alg. 2 over row panels streamed from host memory
+    (cqrrpt_panels_host_d): the panels' block sums continue the sketch's and
+    the Gram's ascending sums, so Q, R, J and k equal the oracle's bit for
+    bit whatever the panel height."""
+    m, n = 5 * 4096 + 123, 40
+    if case == "planted":
+        sv = np.zeros(n)
+        sv[:30] = W.logspaced(30, -6.0).numpy()
+        A = np.asfortranarray(W.planted(m, n, sv, 701, noise=1e-15).numpy())
+    else:
+        A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -13.0), 702).numpy())
+    ref = oracle.cqrrpt(A, 1.25, 4, tol, 77)
+    Ah = _host_colmajor(A, ld=m + 3, pinned=panel_rows != 8192)   # padded lda; pageable once
+    Q, R, J, k, st = C.cqrrpt_panels(Ah, 1.25, 4, tol, 77, panel_rows=panel_rows)
+    assert st == ref.status == 0 and k == ref.k > 0
+    assert np.array_equal(J.numpy(), ref.J)
+    assert_bits(np.asfortranarray(Q.numpy()), ref.Q, "Q")
+    assert_bits(np.asfortranarray(R.numpy()), ref.R, "R")
+
+
+def test_panels_host_degenerate_cases(C):
+    m, n = 2 * 4096 + 5, 12
+    Z = _host_colmajor(np.zeros((m, n)))
+    _, _, J, k, st = C.cqrrpt_panels(Z, 1.25, 4, 1e-12, 3, panel_rows=4096)
+    ref = oracle.cqrrpt(np.zeros((m, n), order="F"), 1.25, 4, 1e-12, 3)
+    assert k == 0 and st == ref.status == 1
+    assert np.array_equal(J.numpy(), ref.J)
+    A = _rng(5).standard_normal((m, n))
+    A[4100, 2] = np.inf
+    _, _, _, k, st = C.cqrrpt_panels(_host_colmajor(A), 1.25, 4, 1e-12, 3, panel_rows=4096)
+    assert k == 0 and st == 2
+    with pytest.raises(Exception):
+        C.cqrrpt_panels(_host_colmajor(A), 1.25, 4, 1e-12, 3, panel_rows=5000)

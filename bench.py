@@ -205,7 +205,7 @@ def config_of(w):
 
 
 def cqrrpt_flops(m, n, d, k, s):
-    """Sec. 3.2 count (GEQP3 on the sketch) at the actual k, plus the sketch's
+    """Sec. 2.1 count (GEQP3 on the sketch) at the actual k, plus the sketch's
     m*s*n additions."""
     return (2.0 * m * k * k + m * k * (k + 1) + 4.0 * d * n * k - 2.0 * k * k * (d + n)
             + 5.0 * k ** 3 / 3.0 + float(m) * s * n)
@@ -341,7 +341,7 @@ def run_batched(args, world, rank, local, C):
         line["cpu_baseline"] = {"value": len(ws) / cpu_batch_s, "unit": "factorizations/s",
                                 "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": "%d of the %d problems (%.1f s), extrapolated to the "
-                                          "batch by the Sec. 3.2 flop count" % (len(sample), len(ws), t_cpu)}
+                                          "batch by the Sec. 2.1 flop count" % (len(sample), len(ws), t_cpu)}
         line["parity_vs_oracle"] = ("bit-identical J, k, Q, R on %d sampled problems" % len(sample)
                                     if same else "MISMATCH")
     if rank == 0:
@@ -391,7 +391,7 @@ def run_mixed(args, world, rank, local, C):
         results[name] = (Q, R, J, k)
         out[name] = {"ms": statistics.median(ms), "factorizations_per_s": 1e3 / statistics.median(ms),
                      "k": k, "recon_rel_F": recon, "orth_2": orth}
-    # Sec. 2.3's randomized CholeskyQR (no pivoting) on the same full-rank
+    # Sec. 1.3's randomized CholeskyQR (no pivoting) on the same full-rank
     # matrix, in FP64: time and accuracy beside CQRRPT's
     try:
         Qr, Rr, Jr = C.colmajor_empty(m, n), C.colmajor_empty(n, n), torch.empty(
@@ -409,7 +409,7 @@ def run_mixed(args, world, rank, local, C):
             "recon_rel_F": (torch.linalg.norm(A - Qr[:, :kr] @ Rr[:kr]) / torch.linalg.norm(A)).item(),
             "orth_2": torch.linalg.matrix_norm(Qr[:, :kr].t() @ Qr[:, :kr] - torch.eye(
                 kr, dtype=torch.float64, device="cuda"), ord=2).item(),
-            "note": "unpivoted (Sec. 2.3): J is the identity"}
+            "note": "unpivoted (Sec. 1.3): J is the identity"}
         del Qr, Rr, Jr
     except Exception as ex:  # reported, not hidden
         out["fp64_rcholqr"] = {"error": str(ex)}
@@ -437,7 +437,7 @@ def run_mixed(args, world, rank, local, C):
 
 def run_dense(args, world, rank, local, C):
     """The headline matrix (m = 131072, n = 1024, planted rank 800, tol 1e-9)
-    sketched by a dense Gaussian operator (Sec. 3.3.1: iid N(0, 1/d),
+    sketched by a dense Gaussian operator (Sec. 2.3.1: iid N(0, 1/d),
     d = 1280, drawn once on the device, resident) instead of the SASO; lines
     2-8 in FP64 (bit-identical to the oracle, tests) and in split-BF16.  The
     sketch is 2 d m n FP64 flops; its time and FP64-roofline fraction are
@@ -840,7 +840,7 @@ def main():
             "launch_ms": trsm_ms,
             "peak_note": "FP64 ALU: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, nominal)"}
     alg_flops = (2.0 * m * k * k + m * k * (k + 1) + 4.0 * w.d * n * k - 2.0 * k * k * (w.d + n)
-                 + 5.0 * k ** 3 / 3.0)   # paper's count (Sec. 3.2), plus sketch adds below
+                 + 5.0 * k ** 3 / 3.0)   # paper's count (Sec. 2.1), plus sketch adds below
     alg_flops += float(m) * w.nnz * n
     phase_share = {p: statistics.mean(v) / (ms_per_step) for p, v in phases.items()}
 

@@ -4,7 +4,7 @@
  * CQRRPT ("CholeskyQR with Randomization and Pivoting for Tall matrices",
  * Melnichenko, Balabanov, Murray, Demmel, Mahoney, Luszczek; arXiv
  * 2311.08316) computes a column-pivoted QR decomposition M[:, J] = Q_k R_k
- * of a tall m x n matrix M (Def. 1 of the paper, Sec. 1.4):
+ * of a tall m x n matrix M (Def. 1 of the paper, Sec. 1.6.2):
  *   Alg. 1: d = ceil(gamma n), sample a d x m sketching operator S;
  *   Alg. 2: M^sk = S M; [Q^sk, R^sk, J] = qrcp(M^sk); k = rank(R^sk);
  *           M^pre = M[:, J[:k]] (R^sk[:k,:k])^{-1}; G = M^pre^T M^pre;
@@ -27,7 +27,7 @@
  *     order of every sum is fixed (see the library's design notes), so the
  *     same inputs give bit-identical outputs on every call.
  *
- * The sketching operator is the SASO of Sec. 3.3.1: each of the m columns of
+ * The sketching operator is the SASO of Sec. 2.3.1: each of the m columns of
  * S has exactly nnz_per_col nonzeros at distinct uniformly random rows, each
  * +-1/sqrt(nnz_per_col); S is generated on the fly from `seed` by the
  * counter-based Philox4x32-10 generator and never stored.
@@ -89,19 +89,19 @@ int cqrrpt_workspace_size(int64_t m, int64_t n, double gamma, int nnz_per_col, i
 int cqrrpt_reserve(cqrrpt_handle h, size_t bytes);
 
 /* Full CQRRPT, Alg. 1 + Alg. 2 (the paper's cqrrpt(M, gamma, F) with F the
- * SASO family; defaults gamma = 1.25, nnz_per_col = 4, Sec. 6.1).
+ * SASO family; defaults gamma = 1.25, nnz_per_col = 4, Sec. 5.1).
  *   m, n          M is m x n, n <= ceil(gamma n) = d <= m, n <= 16384.
  *   A, lda        M (read only), lda >= m.
  *   gamma         sampling factor >= 1 (Alg. 1).
  *   nnz_per_col   nonzeros per column of S, 1 <= nnz_per_col <= min(d, 32).
- *   tol           rank rule (Alg. 2 line 3, Sec. 4.3): tol > 0 keeps the
+ *   tol           rank rule (Alg. 2 line 3, Sec. 3.3): tol > 0 keeps the
  *                 leading columns with R^sk[j,j] > tol R^sk[0,0];
  *                 tol <= 0 runs the paper's two-stage estimate (stage 1:
  *                 smallest l with ||R^sk[l:,l:]||_F <= u max|R^sk|; stage 2
  *                 after the Cholesky: largest l with
  *                 cond(diag(R^pre[:l,:l])) <= sqrt(100u/u) = 10).  In both
  *                 cases a Cholesky breakdown at column j sets k = j
- *                 (Remark 3).
+ *                 (Remark 4).
  *   seed          seed of S.
  *   precision     CQRRPT_FP64, CQRRPT_SPLITBF16 or CQRRPT_SPLITBF16_CHOLQR2.
  *   Q, ldq        m x n capacity, ldq >= m; columns 0..k-1 receive Q_k
@@ -121,14 +121,14 @@ int cqrrpt_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda
              double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
              cudaStream_t stream);
 
-/* ---- randomized CholeskyQR (Sec. 2.3) ------------------------------------ */
+/* ---- randomized CholeskyQR (Sec. 1.3) ------------------------------------ */
 
 /* The method CQRRPT extends, in FP64: M^sk = S M (the same SASO S),
  * [Q^sk, R^sk] = qr(M^sk) WITHOUT pivoting (the QRCP's reflectors, every
  * pivot the next column), M^pre = M (R^sk)^{-1}, G = M^pre^T M^pre,
  * R^pre = chol(G), Q = M^pre (R^pre)^{-1}, R = R^pre R^sk.  M must have full
  * column rank: k = n, except that an exactly zero diagonal of R^sk ends k
- * there and a Cholesky breakdown lowers k (Remark 3).  J receives the
+ * there and a Cholesky breakdown lowers k (Remark 4).  J receives the
  * identity.  Arguments and errors as cqrrpt_d (no tol, no precision). */
 int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
                      double gamma, int nnz_per_col, uint64_t seed, double* Q, int64_t ldq,
@@ -137,7 +137,7 @@ int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int
 
 /* ---- row panels of a host-resident matrix --------------------------------- */
 
-/* The row-partitioned form of Alg. 2 (Sec. 3.2 notes that the sketch and the
+/* The row-partitioned form of Alg. 2 (Sec. 2.1 notes that the sketch and the
  * Gram matrix are sums over row blocks, so rows can be split among
  * processors with one reduction each) run on one GPU over row panels of a
  * host-resident M that need not fit in device memory.  Panels of
@@ -171,7 +171,7 @@ int cqrrpt_panels_host_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A_
 /* ---- dense sketching operators -------------------------------------------- */
 
 /* Alg. 2 with a dense sketching operator S that the caller drew: the
- * Gaussian family of Sec. 3.3.1 (iid entries of mean 0 and variance 1/d), or
+ * Gaussian family of Sec. 2.3.1 (iid entries of mean 0 and variance 1/d), or
  * any other d x m operator (Alg. 1 takes the distribution F as a parameter).
  * Line 1 is M^sk = S M in FP64: for each 4096-row block one fma per term in
  * ascending row order from +0.0, the blocks then added in ascending order,
@@ -202,7 +202,7 @@ int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A
 /* Alg. 1 in FP64 stopped before Alg. 2 line 7: M^pre = M[:, J[:k]]
  * (R^sk_11)^{-1} (line 4) and R^pre = chol(M^pre^T M^pre) (line 6) are
  * returned instead of Q_k; together they represent Q_k = M^pre (R^pre)^{-1}
- * (Sec. 3.2), which cqrrpt_apply_q_d applies.  A client that only applies Q
+ * (Sec. 2.1), which cqrrpt_apply_q_d applies.  A client that only applies Q
  * skips the line-7 solve, one of the two O(m k^2) triangular solves.
  * J, k and R (= R^pre R^sk_k, line 8) are those of cqrrpt_d, bit for bit;
  * Apre holds column j of cqrrpt_d's M^pre.  Arguments as cqrrpt_d, plus:
@@ -410,7 +410,7 @@ const char* cqrrpt_status_string(int status);
 /* ---- tracing ------------------------------------------------------------ */
 
 /* enable != 0: cqrrpt_d records a CUDA event between its phases (the
- * per-subroutine runtime breakdown of the paper's Sec. 6.3 profiling). */
+ * per-subroutine runtime breakdown of the paper's Sec. 5.2 profiling). */
 int cqrrpt_set_profiling(cqrrpt_handle h, int enable);
 
 /* Waits for the last profiled cqrrpt_d and writes the device time in ms of
@@ -478,7 +478,7 @@ int cqrrpt_gram_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_
 
 /* Line 6: upper Cholesky of G (k x k, overwritten as working storage) into
  * R (upper triangle written).  *fail_dev (device int64) receives -1 or the
- * first column whose pivot is not positive (Remark 3). */
+ * first column whose pivot is not positive (Remark 4). */
 int cqrrpt_potrf_d(cqrrpt_handle h, int64_t k, double* G, int64_t ldg, double* R, int64_t ldr,
                    int64_t* fail_dev, cudaStream_t stream);
 

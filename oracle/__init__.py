@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` are the only callers.  The CUDA library never
 imports this package.
 
-All matrices are numpy float64 arrays in Fortran (column-major) order, matching
-the LAPACK layout of the paper (Sec. 5: "column-major").  Indices are 0-based.
+All matrices are numpy float64 arrays in Fortran (column-major) order, the
+LAPACK layout (the paper's implementation is built on LAPACK, Sec. 5).
+Indices are 0-based.
 """
 import ctypes
 import math
@@ -232,7 +233,7 @@ def qr_nopivot(X):
 
 
 def rcholqr(M, gamma=1.25, nnz=4, seed=0):
-    """Sec. 2.3's randomized CholeskyQR (no pivoting; M of full column
+    """Sec. 1.3's randomized CholeskyQR (no pivoting; M of full column
     rank): Result with Q, R, J (identity), k, status, Rsk, Rpre."""
     M = _fortran(M)
     m, n = M.shape
@@ -313,7 +314,7 @@ def cqrrpt_core_sketched(M, Msk, tol=-1.0):
 
 def cqrrpt_dense(M, S, tol=-1.0):
     """Alg. 2 with the dense sketching operator S (d x m) given, e.g. a
-    Gaussian operator (Sec. 3.3.1)."""
+    Gaussian operator (Sec. 2.3.1)."""
     M = _fortran(M)
     S = _fortran(S)
     m, n = M.shape

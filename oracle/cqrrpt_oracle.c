@@ -11,21 +11,21 @@
  *   Alg. 1 (cqrrpt)        -> oracle_cqrrpt          d = ceil(gamma n)
  *   Alg. 2 line 1 (sketch) -> oracle_sketch          M^sk = S M
  *                             oracle_sketch_dense    the same for a dense S
- *                             (Sec. 3.3.1's Gaussian operators), with
+ *                             (Sec. 2.3.1's Gaussian operators), with
  *                             oracle_cqrrpt_dense for the whole method
  *   Alg. 2 line 2 (qrcp)   -> oracle_qrcp            GEQP3-style QRCP
  *   Alg. 2 line 3 (rank)   -> oracle_rank_tol / oracle_rank_stage1 / _stage2
- *                             (Sec. 4.3, eqs. initial_numerical_rank and
+ *                             (Sec. 3.3, eqs. initial_numerical_rank and
  *                              updated_numerical_rank)
  *   Alg. 2 line 4          -> oracle_trsm_rut        M^pre = M_k (A^sk_k)^-1
  *   Alg. 2 line 5          -> oracle_gram            G = (M^pre)^T M^pre
- *   Alg. 2 line 6          -> oracle_potrf_upper     R^pre = chol(G), Remark 3
+ *   Alg. 2 line 6          -> oracle_potrf_upper     R^pre = chol(G), Remark 4
  *   Alg. 2 line 7          -> oracle_trsm_rut        Q_k = M^pre (R^pre)^-1
  *   Alg. 2 line 8          -> oracle_trmm_upper      R_k = R^pre R^sk_k
  *   Q_k = M^pre (R^pre)^-1 -> oracle_apply_q         Q X and Q^T Y without forming Q
- *   Sec. 2.3 (rCholQR)     -> oracle_rcholqr         unpivoted randomized CholeskyQR
- *   (implicit Q: Sec. 3.2 notes that M^pre and R^pre represent Q_k)
- * The SASO operator is the one of Sec. 3.3.1 (each column of S has exactly s
+ *   Sec. 1.3 (rCholQR)     -> oracle_rcholqr         unpivoted randomized CholeskyQR
+ *   (implicit Q: Sec. 2.1 notes that M^pre and R^pre represent Q_k)
+ * The SASO operator is the one of Sec. 2.3.1 (each column of S has exactly s
  * nonzeros at uniformly random rows with values +-1/sqrt(s)).
  *
  * Where the paper is silent (random number generator, sampling rule,
@@ -66,8 +66,8 @@
  * Pins (tests/test_oracle_*.py): Philox known-answer vectors, brute-force
  * rational sketch on integer inputs, scipy GEQP3 pivots on the sketch, the
  * S = I special case (CQRRPT reduces to GEQP3 on M), the unique
- * positive-diagonal QR of M[:, J] from numpy, Theorem 1 (S (M_n - Q_k R_k)
- * = 0), Theorem 2 (singular values of M^pre are the inverses of those of
+ * positive-diagonal QR of M[:, J] from numpy, Theorem 2 (S (M_n - Q_k R_k)
+ * = 0), Theorem 3 (singular values of M^pre are the inverses of those of
  * S U), and planted-rank recovery.
  */
 #include <float.h>
@@ -145,7 +145,7 @@ static uint32_t uniform_below(word_stream* ws, uint32_t range) {
     return (uint32_t)(prod >> 32);
 }
 
-/* Column r of the SASO S (Sec. 3.3.1): s distinct rows of [0, d) in draw
+/* Column r of the SASO S (Sec. 2.3.1): s distinct rows of [0, d) in draw
  * order and their signs (1 = negative). */
 void oracle_saso_column(uint64_t seed, int64_t r, int64_t d, int s, int32_t* rows, uint8_t* neg) {
     word_stream rs, ss;
@@ -222,7 +222,7 @@ int oracle_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, int64_t d,
 }
 
 /* Alg. 2 line 1 with a dense operator S (d x m, column-major, ld lds) that
- * the caller drew, e.g. from the Gaussian family of Sec. 3.3.1 (iid entries
+ * the caller drew, e.g. from the Gaussian family of Sec. 2.3.1 (iid entries
  * of mean 0 and variance 1/d).  M^sk[i, c] = sum_r S[i, r] M[r, c], blocked
  * over the rows like every tall sum: one fma per term in ascending r from
  * +0.0 inside a block, block sums added in ascending block order from +0.0.
@@ -258,7 +258,7 @@ int oracle_sketch_dense(int64_t m, int64_t n, int64_t d, const double* S, int64_
 
 /* ------------------------------------------------------------------------ */
 /* Alg. 2 line 2: QRCP of the sketch (Businger-Golub max-norm pivoting as in  */
-/* LAPACK GEQP3, Sec. 2.2 and Sec. 3.2 flop count).                          */
+/* LAPACK GEQP3, Sec. 1 and Sec. 2.1 flop count).                          */
 /* ------------------------------------------------------------------------ */
 /* dot32 of x[0..len) and y[0..len) (the reading stated in the header). */
 double oracle_dot32(const double* x, const double* y, int64_t len) {
@@ -275,7 +275,7 @@ double oracle_dot32(const double* x, const double* y, int64_t len) {
  * J: n pivots (position -> original column).  vn_out (optional): vn1 at the
  * moment each column was chosen (the pivot norm), for near-tie analysis. */
 /* pivoting == 0: plain Householder QR (the column at position j is step j's
- * pivot; Sec. 2.3's randomized CholeskyQR), same reflectors and updates. */
+ * pivot; Sec. 1.3's randomized CholeskyQR), same reflectors and updates. */
 static void qrcp_ex(int64_t d, int64_t n, double* X, int64_t ldx, int64_t* J, double* tau_out,
                     double* pivnorm_out, double* second_out, int pivoting);
 
@@ -471,7 +471,7 @@ void oracle_gram(int64_t m, int64_t k, const double* X, int64_t ldx, double* G, 
 
 /* Alg. 2 line 6: upper Cholesky G = R^T R (unblocked, ascending sums).
  * Returns -1 on success or the first column j whose pivot is not positive
- * (Remark 3: the leading j x j block of R is then valid). */
+ * (Remark 4: the leading j x j block of R is then valid). */
 int64_t oracle_potrf_upper(int64_t k, const double* G, int64_t ldg, double* R, int64_t ldr) {
     for (int64_t c = 0; c < k; ++c)
         for (int64_t i = 0; i < k; ++i) R[i + c * ldr] = 0.0;
@@ -551,7 +551,7 @@ static int core_ex(int64_t m, int64_t n, const double* M, int64_t ldm, double* M
         oracle_gram(m, k, Q, ldq, G, k);
         double* Rpre = (double*)malloc(sizeof(double) * (size_t)(k * k));
         int64_t fail = oracle_potrf_upper(k, G, k, Rpre, k);
-        int64_t kc = fail >= 0 ? fail : k; /* Remark 3 */
+        int64_t kc = fail >= 0 ? fail : k; /* Remark 4 */
         if (stage2 && kc > 0) kc = oracle_rank_stage2(kc, Rpre, k);
         k = kc;
         if (k > 0) {
@@ -599,7 +599,7 @@ int oracle_cqrrpt(int64_t m, int64_t n, const double* M, int64_t ldm, double gam
 }
 
 /* Alg. 2 with a dense sketching operator S (d x m, ld lds) given by the
- * caller (Sec. 3.3.1's Gaussian family, or any operator of the family F that
+ * caller (Sec. 2.3.1's Gaussian family, or any operator of the family F that
  * Alg. 1 takes as a parameter): line 1 by oracle_sketch_dense, then lines 2-8
  * as oracle_cqrrpt.  Returns 0, -i for invalid argument i, 1 when k == 0, 2
  * for a non-finite sketch. */
@@ -625,7 +625,7 @@ int oracle_cqrrpt_dense(int64_t m, int64_t n, const double* M, int64_t ldm, int6
 }
 
 /* ------------------------------------------------------------------------ */
-/* Implicit Q (Sec. 3.2: Q_k = M^pre (R^pre)^{-1}, Alg. 2 line 7 not formed): */
+/* Implicit Q (Sec. 2.1: Q_k = M^pre (R^pre)^{-1}, Alg. 2 line 7 not formed): */
 /* trans == 0: Y (m x r) = Q X with X k x r:                                  */
 /*     W = (R^pre)^{-1} X by back substitution (row j: terms t = k-1 down to  */
 /*     j+1, one fma each, then one division), Y = M^pre W in ascending t     */
@@ -677,11 +677,11 @@ void oracle_apply_q(int trans, int64_t m, int64_t k, const double* Apre, int64_t
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 2.3: randomized CholeskyQR (the method CQRRPT extends) -- sketch,    */
+/* Sec. 1.3: randomized CholeskyQR (the method CQRRPT extends) -- sketch,    */
 /* unpivoted QR of the sketch, M^pre = M (R^sk)^{-1}, G, R^pre = chol(G),   */
 /* Q = M^pre (R^pre)^{-1}, R = R^pre R^sk.  M must have full column rank:  */
 /* k = n, except that an exactly zero diagonal of R^sk (below DBL_MIN times */
-/* R^sk[0,0]) ends k there and a Cholesky breakdown lowers k (Remark 3).    */
+/* R^sk[0,0]) ends k there and a Cholesky breakdown lowers k (Remark 4).    */
 /* J is the identity.  Returns as oracle_cqrrpt.                            */
 /* ------------------------------------------------------------------------ */
 int oracle_rcholqr(int64_t m, int64_t n, const double* M, int64_t ldm, double gamma, int nnz,

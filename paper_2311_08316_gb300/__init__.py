@@ -261,7 +261,7 @@ def cqrrpt(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64, out=None, han
 
 
 def rcholqr(A, gamma=1.25, nnz=4, seed=0, out=None, handle=None, stream=None):
-    """Sec. 2.3's randomized CholeskyQR (no pivoting; A of full column
+    """Sec. 1.3's randomized CholeskyQR (no pivoting; A of full column
     rank) through cqrrpt_rcholqr_d; waits for k.  Returns a Factorization
     (J is the identity)."""
     h = handle or default_handle()
@@ -308,7 +308,7 @@ def cqrrpt_panels(A_host, gamma=1.25, nnz=4, tol=-1.0, seed=0, panel_rows=65536,
 
 def cqrrpt_dense(A, S, tol=-1.0, precision=FP64, out=None, handle=None, stream=None, sync=True):
     """Alg. 2 with the dense sketching operator S (d x m column-major
-    float64 CUDA tensor, e.g. a Gaussian operator of Sec. 3.3.1) through
+    float64 CUDA tensor, e.g. a Gaussian operator of Sec. 2.3.1) through
     cqrrpt_dense_d; line 1 in FP64, lines 2-8 in `precision`.  Returns a
     Factorization (k and status None when sync=False)."""
     h = handle or default_handle()

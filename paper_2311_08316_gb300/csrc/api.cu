@@ -235,7 +235,7 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
     mark(h, 6, stream);
     if (dst == kOk && k > 0) {
       // line 7: Q_k = M^pre (R^pre)^{-1}, in place; R^pre is well conditioned
-      // (Theorem 2), so one product with its FP64 inverse
+      // (Theorem 3), so one product with its FP64 inverse
       e = oz_trsm_inv(m, (int)k, Q, ldq, nullptr, Rpre, n, Q, ldq, region, stream, status, side);
       mark(h, 7, stream);
       // line 8: R_k = R^pre R^sk_k
@@ -869,7 +869,7 @@ int cqrrpt_panels_host_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A_
         e = launch_gram(rows_of(q), ni, &sc->k, xbuf[b], P, G, n, region, status, stream, true);
       copy_out(q, k1, b);
     }
-    // line 6 (Remark 3, stage 2)
+    // line 6 (Remark 4, stage 2)
     if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, n, sc, stream);
     if (e == cudaSuccess) e = launch_rank_stage2(Rpre, n, !(tol > 0.0), sc, stream);
     int st2 = kOk;
@@ -1294,7 +1294,7 @@ int batched_split_exec(cqrrpt_handle h, BatchPlan& P, const std::vector<BatchPro
   if (launch_potrf_batched(P.po, batch, stream) != cudaSuccess ||
       launch_rank_stage2_batched(P.s2, batch, stream) != cudaSuccess)
     return kCudaError;
-  // line 7 at the rank after the Cholesky (Remark 3, stage 2)
+  // line 7 at the rank after the Cholesky (Remark 4, stage 2)
   if ((st = read_scalars(h, P.scalars, batch, stream)) != kOk) return st;
   std::vector<int> ids7;
   for (int p : ids) {

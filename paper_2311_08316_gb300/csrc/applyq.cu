@@ -1,6 +1,6 @@
 // The implicit Q of a factorisation stopped before Alg. 2 line 7: the
 // preconditioned matrix M^pre (m x k, line 4) and R^pre (k x k, line 6)
-// represent Q_k = M^pre (R^pre)^{-1} (Sec. 3.2), and Q X or Q^T Y is applied
+// represent Q_k = M^pre (R^pre)^{-1} (Sec. 2.1), and Q X or Q^T Y is applied
 // without forming Q (a client that only applies Q skips the line-7 TRSM,
 // one of the two O(m k^2) solves).
 //

@@ -12,7 +12,7 @@ namespace cqrrpt {
 
 // Device scalars of one factorisation.
 struct DeviceScalars {
-  int64_t k;         // current rank (rank rule, then Remark 3, then stage 2)
+  int64_t k;         // current rank (rank rule, then Remark 4, then stage 2)
   int64_t fail;      // Cholesky failure column or -1
   int status;        // kOk / kNonFinite / kTimeout ...
   int pad;

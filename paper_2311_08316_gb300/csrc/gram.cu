@@ -1,5 +1,5 @@
 // Alg. 2 line 5: the Gram matrix G = (M^pre)^T M^pre (k x k, the SYRK of
-// the CholeskyQR step, Sec. 2.1).
+// the CholeskyQR step, Sec. 1.2).
 //
 // The sum over the m rows is blocked: for each row block b of kRowBlock rows
 // gram_partial forms P_b[a, c] = sum_{r in b} X[r, a] X[r, c] in ascending r

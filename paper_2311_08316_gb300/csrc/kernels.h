@@ -110,7 +110,7 @@ cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* bas
 
 // ---- Alg. 2 line 6 -------------------------------------------------------
 // Factors G (overwritten as working storage) into R (upper); on a
-// non-positive pivot at column j records sc->fail = j (Remark 3).
+// non-positive pivot at column j records sc->fail = j (Remark 4).
 // Implicit Q = M^pre (R^pre)^{-1} (applyq.cu): Y = Q X (trans 0, X k x r,
 // Y m x r) or Y = Q^T X (trans 1, X m x r, Y k x r); host k and r.
 int64_t apply_q_workspace_bytes(int trans, int64_t m, int64_t k, int64_t r);

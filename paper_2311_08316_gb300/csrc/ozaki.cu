@@ -4,7 +4,7 @@
 // multiplication and its applications", Numer. Algorithms 2012; tensor-core
 // use as in Mukunoki, Ozaki, Ogita & Imamura, ICCS 2020).  Used by the
 // split-BF16 precision modes for Alg. 2 lines 4, 5 and 7, the O(m n^2) steps
-// (the paper's two-roundoff model, Sec. 4.1, lets line 4 run in a
+// (the paper's two-roundoff model, Sec. 3.1, lets line 4 run in a
 // different arithmetic; here all three keep FP64-level accuracy).
 //
 // Splitting.  Every row (or column) v of an operand gets a power-of-two
@@ -541,7 +541,7 @@ int64_t oz_trsm_inv_workspace(int64_t m, int k) {
 // X := B[:, cols] T^{-1} as one split-BF16 product with W = T^{-1} computed
 // row by row in FP64 (small right residual |W T - I|).  Accurate when that
 // residual times the row grading of T is small: for R^pre (condition near 1,
-// Theorem 2) and for the row-graded R^sk of a max-norm QRCP (R = D U with
+// Theorem 3) and for the row-graded R^sk of a max-norm QRCP (R = D U with
 // |U_ij| <= 1 above a unit diagonal), where |W||T| = |U^{-1}||U|.
 cudaError_t oz_trsm_inv(int64_t m, int k, const double* B, int64_t ldb, const int64_t* cols,
                         const double* T, int64_t ldt, double* X, int64_t ldx, void* work,

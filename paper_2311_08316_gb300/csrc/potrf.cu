@@ -1,5 +1,5 @@
 // Alg. 2 line 6: R^pre = chol(G), upper (G = R^T R), with the failure rule
-// of Remark 3 (Sec. 4.3): if the pivot of column j is not positive the
+// of Remark 4 (Sec. 3.3): if the pivot of column j is not positive the
 // factorisation stops, records fail = j, and the leading j x j block of R is
 // the valid factor of G[0:j, 0:j].
 //

@@ -1,6 +1,6 @@
 // Alg. 2 lines 2-3: column-pivoted Householder QR of the d x n sketch
 // (Businger-Golub max-norm pivoting, as LAPACK GEQP3 which the paper uses,
-// Sec. 3.2 and Appendix A.1) and the rank rule of Sec. 4.3.
+// Sec. 2.1 and Appendix A.1) and the rank rule of Sec. 3.3.
 //
 // The QRCP of one problem runs on G CTAs that stay resident for all n steps
 // (one cooperative launch for a single large problem; G = 1 and one CTA per
@@ -662,7 +662,7 @@ cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gat
 }
 
 // ---------------------------------------------------------------------------
-// Rank (Sec. 4.3).  tol > 0: k = number of leading j with R_jj > tol R_00.
+// Rank (Sec. 3.3).  tol > 0: k = number of leading j with R_jj > tol R_00.
 // tol <= 0: stage 1, k_o = min{l : ||C_l||_F <= u max|R|}, with
 // ||C_l||^2 = ||R[l, l:]||^2 + ||C_{l+1}||^2 (row sums ascending by fma).
 // ---------------------------------------------------------------------------
@@ -740,7 +740,7 @@ cudaError_t launch_rank_batched(const RankDesc* D, int nprob, cudaStream_t strea
   return cudaGetLastError();
 }
 
-// Stage 2: k := min(k, fail) (Remark 3), then if requested the largest
+// Stage 2: k := min(k, fail) (Remark 4), then if requested the largest
 // l <= k with max/min of diag(R^pre)[0:l] <= 10.
 __device__ __forceinline__ void stage2_body(const Stage2Desc& D) {
   DeviceScalars* sc = D.sc;

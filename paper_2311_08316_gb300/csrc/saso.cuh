@@ -1,4 +1,4 @@
-// SASO sketching operator S (d x m) of Sec. 3.3.1: column r holds exactly s
+// SASO sketching operator S (d x m) of Sec. 2.3.1: column r holds exactly s
 // nonzeros at distinct, uniformly chosen rows, each +-1/sqrt(s) with equal
 // probability.  Columns are generated on the device from (seed, r) with the
 // counter-based Philox4x32-10 generator (Salmon et al., SC'11), so S is never

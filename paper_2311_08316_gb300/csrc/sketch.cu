@@ -1,4 +1,4 @@
-// Alg. 2 line 1: the sketch M^sk = S M with the SASO S of Sec. 3.3.1.
+// Alg. 2 line 1: the sketch M^sk = S M with the SASO S of Sec. 2.3.1.
 //
 // Three kernels:
 //   saso_lists     per row block (kRowBlock rows) of M, the SASO columns of
@@ -18,7 +18,7 @@
 // the data, not by the launch shape.  Each kernel exists as a single-problem
 // launch and a batched launch (CTA -> (problem, tile)) over the same body.
 //
-// A dense operator S (d x m, given by the caller: Sec. 3.3.1's Gaussian
+// A dense operator S (d x m, given by the caller: Sec. 2.3.1's Gaussian
 // family) replaces the first two kernels by sketch_dense_partial, which forms
 // P_b[i, c] = sum_{r in b} S[i, r] M[r, c] with one fma per term in ascending
 // r from +0.0; sketch_combine then adds the blocks with scale 1 (exact).

@@ -5,7 +5,7 @@ times, run through the same entry point with the same handle settings.
 
 The oracle finishes this size in about half a minute on 16 cores, so the
 whole output is compared: J and k exactly, Q and R bit for bit.  The
-paper's accuracy invariants (Sec. 4: reconstruction and orthogonality) are
+paper's accuracy invariants (Sec. 3: reconstruction and orthogonality) are
 checked on the GPU result as well.
 """
 import math

@@ -421,7 +421,7 @@ def test_qrcp_mixed_storage(C, cap, monkeypatch):
     _compare_full(C, A, w.gamma, w.nnz, w.tol, w.sketch_seed)
 
 
-# ---------------------------------------------------------- Sec. 2.3 rCholQR
+# ---------------------------------------------------------- Sec. 1.3 rCholQR
 @pytest.mark.parametrize("m,n,seed", [(4096 + 33, 64, 1), (3 * 4096 + 5, 150, 2), (5000, 8, 3),
                                       (9000, 300, 4)])
 def test_rcholqr_matches_oracle(C, m, n, seed):
@@ -444,7 +444,7 @@ def test_rcholqr_matches_oracle(C, m, n, seed):
     (3 * 4096, 64, 96, 3),          # whole tiles, whole blocks
 ])
 def test_sketch_dense_matches_oracle(C, m, n, d, seed):
-    """Line 1 with a Gaussian operator (Sec. 3.3.1): bit-identical to the
+    """Line 1 with a Gaussian operator (Sec. 2.3.1): bit-identical to the
     oracle's blocked ascending-fma product."""
     S = np.asfortranarray(W.gaussian_operator(d, m, 500 + seed).numpy())
     M = np.asfortranarray(_rng(seed).standard_normal((m, n)))

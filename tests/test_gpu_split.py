@@ -9,7 +9,7 @@ error-free digit splitting) against the oracle.
 * The split-BF16 TRSM is backward stable: ||X T - B|| <= c u |X| |T|.
 * The full method keeps the FP64 sketch, QRCP and rank rule, so J and k are
   bit-identical to the oracle; Q and R satisfy the paper's accuracy
-  invariants (Sec. 4) and differ from the oracle by at most a u-level
+  invariants (Sec. 3) and differ from the oracle by at most a u-level
   backward error amplified by cond(R^sk_11) (two backward-stable QRs of the
   same matrix).
 """

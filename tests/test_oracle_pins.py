@@ -26,7 +26,7 @@ def _rng(seed):
 
 
 # --------------------------------------------------------------------------
-# S: Philox4x32-10 and the SASO sampling rule (Sec. 3.3.1)
+# S: Philox4x32-10 and the SASO sampling rule (Sec. 2.3.1)
 # --------------------------------------------------------------------------
 def test_philox_known_answers():
     """Salmon et al. SC'11 Philox4x32-10, published known-answer vectors."""
@@ -42,7 +42,7 @@ def test_philox_known_answers():
 
 @pytest.mark.parametrize("d,s", [(16, 4), (128, 4), (1280, 8), (5, 5), (7, 1)])
 def test_saso_columns_have_s_distinct_rows(d, s):
-    """Sec. 3.3.1: each column of S has exactly s nonzeros at distinct rows."""
+    """Sec. 2.3.1: each column of S has exactly s nonzeros at distinct rows."""
     for r in range(200):
         rows, neg = oracle.saso_column(12345, r, d, s)
         assert len(set(rows.tolist())) == s
@@ -51,7 +51,7 @@ def test_saso_columns_have_s_distinct_rows(d, s):
 
 
 def test_saso_subsets_uniform():
-    """Sec. 3.3.1: the s locations are uniform over all s-subsets of [0, d):
+    """Sec. 2.3.1: the s locations are uniform over all s-subsets of [0, d):
     chi-square over the C(6,2) = 15 subsets (Floyd's algorithm)."""
     d, s, cols = 6, 2, 30000
     counts = {}
@@ -66,7 +66,7 @@ def test_saso_subsets_uniform():
 
 
 def test_saso_signs_balanced_and_row_marginals_uniform():
-    """Sec. 3.3.1: signs +-1 equally likely; each row equally likely."""
+    """Sec. 2.3.1: signs +-1 equally likely; each row equally likely."""
     d, s, cols = 40, 4, 20000
     hist = np.zeros(d)
     negs = 0
@@ -185,7 +185,7 @@ def test_qrcp_lowest_index_on_exact_ties():
 
 
 # --------------------------------------------------------------------------
-# Alg. 2 line 3: rank (Sec. 4.3)
+# Alg. 2 line 3: rank (Sec. 3.3)
 # --------------------------------------------------------------------------
 def test_rank_tol_counts_leading_diagonal():
     R = np.diag([2.0, 1.0, 1e-3, 1e-10, 1e-9, 1e-15])
@@ -251,7 +251,7 @@ def test_potrf_matches_cholesky_and_reports_failure():
     R, fail = oracle.potrf_upper(G)
     assert fail == -1
     assert np.abs(R - np.linalg.cholesky(G).T).max() <= 1e-13 * np.abs(R).max()
-    # Remark 3: column 9 depends on columns 0..8 -> failure at 9, leading block valid
+    # Remark 4: column 9 depends on columns 0..8 -> failure at 9, leading block valid
     Bm[:, 9] = Bm[:, :9] @ rng.standard_normal(9)
     G = Bm.T @ Bm
     G[9, 9] -= 1e-6 * G[9, 9]
@@ -302,7 +302,7 @@ def test_full_rank_is_unique_positive_qr_of_pivoted_matrix():
 
 
 def test_theorem1_sketch_of_residual_vanishes():
-    """Thm. 1: S (M_n - Q_k R_k) = 0 when rank(SM) = rank(M)."""
+    """Thm. 2: S (M_n - Q_k R_k) = 0 when rank(SM) = rank(M)."""
     m, n, gamma, s, seed = 2048, 16, 1.5, 3, 5
     A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -4.0), 9).numpy())
     res = oracle.cqrrpt(A, gamma, s, 1e-12, seed)
@@ -313,7 +313,7 @@ def test_theorem1_sketch_of_residual_vanishes():
 
 
 def test_theorem2_spectrum_of_preconditioned_matrix():
-    """Thm. 2: sigma_i(M^pre) = 1 / sigma_{k-i+1}(S U), U an orthonormal basis
+    """Thm. 3: sigma_i(M^pre) = 1 / sigma_{k-i+1}(S U), U an orthonormal basis
     of range(M)."""
     m, n, gamma, s, seed = 4096, 20, 1.25, 4, 3
     U_ = W.haar(m, n, 21).numpy()
@@ -380,7 +380,7 @@ def test_default_rank_rule_and_degenerate_cases():
 
 
 # --------------------------------------------------------------------------
-# Implicit Q (Sec. 3.2: Q_k = M^pre (R^pre)^{-1}): apply Q and Q^T
+# Implicit Q (Sec. 2.1: Q_k = M^pre (R^pre)^{-1}): apply Q and Q^T
 # --------------------------------------------------------------------------
 def test_apply_q_exact_on_integer_factors():
     """With an integer M^pre and an upper R^pre whose diagonal holds powers
@@ -416,7 +416,7 @@ def test_apply_q_exact_on_integer_factors():
 def test_apply_q_matches_explicit_q_and_adjoint():
     """On a cond-1e8 factorisation: the implicit Q X and Q^T Y match the
     explicit Q of Alg. 2 line 7 to a few u, <Qx, y> = <x, Q^T y>, and
-    Q^T Q x = x (orthonormal columns, Theorem 2)."""
+    Q^T Q x = x (orthonormal columns, Theorem 3)."""
     w = W.single_small()
     M = np.asfortranarray(w.matrix().numpy())
     res = oracle.cqrrpt_implicit(M, w.gamma, w.nnz, w.tol, w.sketch_seed)
@@ -439,7 +439,7 @@ def test_apply_q_matches_explicit_q_and_adjoint():
 
 
 # --------------------------------------------------------------------------
-# Sec. 2.3: randomized CholeskyQR (unpivoted)
+# Sec. 1.3: randomized CholeskyQR (unpivoted)
 # --------------------------------------------------------------------------
 def test_qr_nopivot_matches_lapack_qr():
     """The unpivoted Householder QR (same reflectors, diagonal made
@@ -454,7 +454,7 @@ def test_qr_nopivot_matches_lapack_qr():
 
 
 def test_rcholqr_factorises_a_full_rank_matrix():
-    """Sec. 2.3 on a cond-1e6 matrix: J is the identity, k = n, M = Q R,
+    """Sec. 1.3 on a cond-1e6 matrix: J is the identity, k = n, M = Q R,
     Q^T Q = I, and R equals LAPACK's R of M (unique with a positive
     diagonal) to the conditioning."""
     m, n = 3000, 30
@@ -485,7 +485,7 @@ def test_rcholqr_equals_cqrrpt_when_the_pivots_are_the_identity():
 
 
 # --------------------------------------------------------------------------
-# Dense sketching operators (Sec. 3.3.1's Gaussian family)
+# Dense sketching operators (Sec. 2.3.1's Gaussian family)
 # --------------------------------------------------------------------------
 def test_sketch_dense_exact_on_integer_operands():
     """Integer S (|S| <= 3) and M (|M| <= 2^20): every product and partial
@@ -574,8 +574,8 @@ def test_cqrrpt_dense_with_one_nonzero_saso_equals_cqrrpt():
 
 
 def test_cqrrpt_dense_gaussian_theorem2_and_invariants():
-    """Gaussian S (Sec. 3.3.1): sigma_i(M^pre) = 1 / sigma_{k-i+1}(S U)
-    (Thm. 2, with M^pre = Q R^pre), and the factorisation invariants."""
+    """Gaussian S (Sec. 2.3.1): sigma_i(M^pre) = 1 / sigma_{k-i+1}(S U)
+    (Thm. 3, with M^pre = Q R^pre), and the factorisation invariants."""
     m, n = 4096 + 300, 20
     d = oracle.sketch_dim(n, 1.25)
     U_ = W.haar(m, n, 51).numpy()

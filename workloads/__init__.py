@@ -3,8 +3,8 @@ the benchmark; holds none of the method's arithmetic).
 
 The paper's workloads are tall dense matrices with controlled spectra: left
 and right singular vectors obtained by orthogonalising iid Gaussian matrices
-(Sec. 5.1 "low-coherence matrices"), iid Gaussian matrices for speed runs
-(Sec. 6), and a high-coherence construction (Sec. 5.2).  Every function here
+(the low-coherence matrices of Sec. 4.1), iid Gaussian matrices for speed runs
+(Sec. 5), and a high-coherence construction (Sec. 4.2).  Every function here
 builds such a matrix from a seed:
 
   A = U diag(sv) V^T (+ noise * N(0, 1) entrywise)
@@ -60,18 +60,18 @@ def planted(m, n, sv, seed, noise=0.0, device="cpu"):
 
 
 def gaussian(m, n, seed, device="cpu"):
-    """iid N(0,1) test matrix (the paper's speed-benchmark inputs, Sec. 6)."""
+    """iid N(0,1) test matrix (the paper's speed-benchmark inputs, Sec. 5)."""
     return to_colmajor(_gaussian(m, n, seed, device))
 
 
 def gaussian_operator(d, m, seed, device="cpu"):
-    """d x m Gaussian sketching operator of Sec. 3.3.1: iid entries of mean 0
+    """d x m Gaussian sketching operator of Sec. 2.3.1: iid entries of mean 0
     and variance 1/d (column-major)."""
     return to_colmajor(_gaussian(d, m, seed, device) * (1.0 / math.sqrt(d)))
 
 
 def high_coherence(m, n, seed, device="cpu", big=1e10):
-    """Sec. 5.2: stacked identities, n random rows scaled by `big`, then a
+    """Sec. 4.2: stacked identities, n random rows scaled by `big`, then a
     random right rotation."""
     reps = m // n
     rows = torch.cat([torch.arange(n).repeat(reps), torch.arange(m - reps * n)])

@@ -62,6 +62,11 @@ def lib():
         L.oracle_cqrrpt_core_sketched.argtypes = [_i64, _i64, _p, _i64, _p, _i64, _d,
                                                   _p, _i64, _p, _i64, _p, _p, _p, _p, _p, _p]
         L.oracle_cqrrpt_core_sketched.restype = ctypes.c_int
+        L.oracle_srrqr.argtypes = [_i64, _i64, _d, _p, _i64, _p, _i64]
+        L.oracle_srrqr.restype = _i64
+        L.oracle_cqrrpt_srrqr.argtypes = [_i64, _i64, _p, _i64, _d, ctypes.c_int, _d, _u64, _d,
+                                          _p, _i64, _p, _i64, _p, _p, _p, _p]
+        L.oracle_cqrrpt_srrqr.restype = ctypes.c_int
         L.oracle_sketch_dense.argtypes = [_i64, _i64, _i64, _p, _i64, _p, _i64, _p, _i64]
         L.oracle_sketch_dense.restype = ctypes.c_int
         L.oracle_cqrrpt_dense.argtypes = [_i64, _i64, _p, _i64, _i64, _p, _i64, _d,
@@ -333,3 +338,30 @@ def cqrrpt_dense(M, S, tol=-1.0):
     kk = int(k[0])
     return Result(Q=Q[:, :kk], R=R[:kk, :], J=J, k=kk, status=int(st), Rsk=Rsk,
                   Rpre=Rpre[:kk, :kk], pivnorm=piv, second=sec, Qfull=Q, Rfull=R)
+
+
+def srrqr(R, k, f=2.0, J=None, max_swaps=None):
+    """Sec. 2.2's strong RRQR exchanges (Gu-Eisenstat, tuning parameter f) at
+    rank k on an n x n upper-triangular R with J.  Returns (R, J, swaps)."""
+    R = _fortran(R).copy(order="F")
+    n = R.shape[0]
+    J = np.arange(n, dtype=np.int64) if J is None else np.array(J, dtype=np.int64)
+    sw = lib().oracle_srrqr(n, k, f, _ptr(R), n, _ptr(J), 64 * n if max_swaps is None else max_swaps)
+    return R, J, int(sw)
+
+
+def cqrrpt_srrqr(M, gamma=1.25, nnz=4, tol=-1.0, seed=0, f=2.0):
+    """Alg. 1 with the strong RRQR exchanges after the rank rule (Sec. 2.2)."""
+    M = _fortran(M)
+    m, n = M.shape
+    Q = np.zeros((m, n), dtype=np.float64, order="F")
+    R = np.zeros((n, n), dtype=np.float64, order="F")
+    J = np.zeros(n, dtype=np.int64)
+    k = np.zeros(1, dtype=np.int64)
+    Rsk = np.zeros((n, n), dtype=np.float64, order="F")
+    sw = np.zeros(1, dtype=np.int64)
+    st = lib().oracle_cqrrpt_srrqr(m, n, _ptr(M), m, gamma, nnz, tol, seed, f, _ptr(Q), m,
+                                   _ptr(R), n, _ptr(J), _ptr(k), _ptr(Rsk), _ptr(sw))
+    kk = int(k[0])
+    return Result(Q=Q[:, :kk], R=R[:kk, :], J=J, k=kk, status=int(st), Rsk=Rsk,
+                  swaps=int(sw[0]), Qfull=Q, Rfull=R)

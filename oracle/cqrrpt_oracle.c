@@ -24,6 +24,8 @@
  *   Alg. 2 line 8          -> oracle_trmm_upper      R_k = R^pre R^sk_k
  *   Q_k = M^pre (R^pre)^-1 -> oracle_apply_q         Q X and Q^T Y without forming Q
  *   Sec. 1.3 (rCholQR)     -> oracle_rcholqr         unpivoted randomized CholeskyQR
+ *   Sec. 2.2 (strong RRQR) -> oracle_srrqr           Gu-Eisenstat exchanges at rank k,
+ *                             oracle_cqrrpt_srrqr    the method with them
  *   (implicit Q: Sec. 2.1 notes that M^pre and R^pre represent Q_k)
  * The SASO operator is the one of Sec. 2.3.1 (each column of S has exactly s
  * nonzeros at uniformly random rows with values +-1/sqrt(s)).
@@ -506,6 +508,81 @@ void oracle_trmm_upper(int64_t k, int64_t n, const double* Rpre, int64_t ldp, co
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2.2: strong rank-revealing QR of the sketch at rank k (Gu and        */
+/* Eisenstat 1996, with tuning parameter f > 1; the paper names f = 2).      */
+/* ------------------------------------------------------------------------ */
+/* R = [A B; 0 C] (n x n upper triangular, diag >= 0, ld ldr) with A the
+ * leading k x k block.  While some pair (i < k <= j) has
+ *     rho_ij = (A^{-1} B)_{i, j-k}^2 + ||C[:, j-k]||^2 ||row i of A^{-1}||^2
+ * above f^2, the pair with the largest rho_ij (lowest i, then lowest j, on
+ * ties) has its columns exchanged (in R and in J) and R is refactored by
+ * an unpivoted Householder QR (the QRCP's reflectors and sign convention,
+ * Q discarded).  Each exchange multiplies |det A| by sqrt(rho_ij) > f, so
+ * the loop ends; max_swaps bounds it all the same.  Sums run in ascending
+ * index order with one fma per term:
+ *     W = A^{-1} by columns (column c: W[c,c] = 1 / A[c,c]; for i = c-1
+ *         down to 0, W[i,c] = -(sum_{t=i+1..c} A[i,t] W[t,c]) / A[i,i]);
+ *     (A^{-1}B)[i,j] = sum_{t=i..k-1} W[i,t] R[t,k+j];
+ *     w2_i = sum_{t=i..k-1} W[i,t]^2;  g2_j = sum_{t=k..k+j} R[t,k+j]^2;
+ *     rho_ij = fma(ab, ab, g2_j * w2_i).
+ * Returns the number of exchanges. */
+int64_t oracle_srrqr(int64_t n, int64_t k, double f, double* R, int64_t ldr, int64_t* J,
+                     int64_t max_swaps) {
+    if (k <= 0 || k >= n) return 0;
+    const int64_t nk = n - k;
+    double* W = (double*)calloc((size_t)(k * k), sizeof(double));
+    double* w2 = (double*)malloc(sizeof(double) * (size_t)k);
+    double* g2 = (double*)malloc(sizeof(double) * (size_t)nk);
+    double* X = (double*)malloc(sizeof(double) * (size_t)(n * n));
+    int64_t* Jt = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    double* tau = (double*)malloc(sizeof(double) * (size_t)n);
+    int64_t swaps = 0;
+    while (swaps < max_swaps) {
+        for (int64_t c = 0; c < k; ++c) {
+            W[c + c * k] = 1.0 / R[c + c * ldr];
+            for (int64_t i = c - 1; i >= 0; --i) {
+                double s = 0.0;
+                for (int64_t t = i + 1; t <= c; ++t) s = fma(R[i + t * ldr], W[t + c * k], s);
+                W[i + c * k] = -s / R[i + i * ldr];
+            }
+        }
+        for (int64_t i = 0; i < k; ++i) {
+            double s = 0.0;
+            for (int64_t t = i; t < k; ++t) s = fma(W[i + t * k], W[i + t * k], s);
+            w2[i] = s;
+        }
+        for (int64_t j = 0; j < nk; ++j) {
+            double s = 0.0;
+            for (int64_t t = k; t <= k + j; ++t) s = fma(R[t + (k + j) * ldr], R[t + (k + j) * ldr], s);
+            g2[j] = s;
+        }
+        double best = -1.0;
+        int64_t bi = -1, bj = -1;
+        for (int64_t i = 0; i < k; ++i)
+            for (int64_t j = 0; j < nk; ++j) {
+                double ab = 0.0;
+                for (int64_t t = i; t < k; ++t) ab = fma(W[i + t * k], R[t + (k + j) * ldr], ab);
+                double rho = fma(ab, ab, g2[j] * w2[i]);
+                if (rho > best) { best = rho; bi = i; bj = j; }
+            }
+        if (!(best > f * f)) break;
+        /* exchange columns bi and k + bj, then refactor */
+        const int64_t jc = k + bj;
+        for (int64_t c = 0; c < n; ++c) {
+            const int64_t src = c == bi ? jc : (c == jc ? bi : c);
+            for (int64_t r = 0; r < n; ++r) X[r + c * n] = R[r + src * ldr];
+        }
+        int64_t tj = J[bi]; J[bi] = J[jc]; J[jc] = tj;
+        qrcp_ex(n, n, X, n, Jt, tau, NULL, NULL, 0);
+        for (int64_t c = 0; c < n; ++c)
+            for (int64_t r = 0; r < n; ++r) R[r + c * ldr] = r <= c ? X[r + c * n] : 0.0;
+        ++swaps;
+    }
+    free(W); free(w2); free(g2); free(X); free(Jt); free(tau);
+    return swaps;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Alg. 1 + Alg. 2: the full method.                                         */
 /* ------------------------------------------------------------------------ */
 int64_t oracle_sketch_dim(int64_t n, double gamma) { return (int64_t)ceil(gamma * (double)n); }
@@ -518,20 +595,20 @@ int64_t oracle_sketch_dim(int64_t n, double gamma) { return (int64_t)ceil(gamma 
 static int core_ex(int64_t m, int64_t n, const double* M, int64_t ldm, double* Msk, int64_t d,
                    double tol, double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* J,
                    int64_t* k_out, double* Rsk_out, double* Rpre_out, double* pivnorm,
-                   double* second, int pivoting);
+                   double* second, int pivoting, double srrqr_f, int64_t* swaps_out);
 
 int oracle_cqrrpt_core_sketched(int64_t m, int64_t n, const double* M, int64_t ldm, double* Msk,
                                 int64_t d, double tol, double* Q, int64_t ldq, double* R,
                                 int64_t ldr, int64_t* J, int64_t* k_out, double* Rsk_out,
                                 double* Rpre_out, double* pivnorm, double* second) {
     return core_ex(m, n, M, ldm, Msk, d, tol, Q, ldq, R, ldr, J, k_out, Rsk_out, Rpre_out,
-                   pivnorm, second, 1);
+                   pivnorm, second, 1, 0.0, NULL);
 }
 
 static int core_ex(int64_t m, int64_t n, const double* M, int64_t ldm, double* Msk, int64_t d,
                    double tol, double* Q, int64_t ldq, double* R, int64_t ldr, int64_t* J,
                    int64_t* k_out, double* Rsk_out, double* Rpre_out, double* pivnorm,
-                   double* second, int pivoting) {
+                   double* second, int pivoting, double srrqr_f, int64_t* swaps_out) {
     *k_out = 0;
     double* tau = (double*)malloc(sizeof(double) * (size_t)n);
     qrcp_ex(d, n, Msk, d, J, tau, pivnorm, second, pivoting);
@@ -544,6 +621,11 @@ static int core_ex(int64_t m, int64_t n, const double* M, int64_t ldm, double* M
 
     int stage2 = !(tol > 0.0);
     int64_t k = stage2 ? oracle_rank_stage1(n, Rsk, n) : oracle_rank_tol(n, Rsk, n, tol);
+    if (srrqr_f > 0.0) {
+        int64_t sw = oracle_srrqr(n, k, srrqr_f, Rsk, n, J, 64 * n);
+        if (swaps_out) *swaps_out = sw;
+        if (Rsk_out) memcpy(Rsk_out, Rsk, sizeof(double) * (size_t)(n * n));
+    }
     if (k > 0) {
         /* M^pre into Q's storage */
         oracle_trsm_rut(m, k, M, ldm, J, Rsk, n, Q, ldq);
@@ -594,6 +676,37 @@ int oracle_cqrrpt(int64_t m, int64_t n, const double* M, int64_t ldm, double gam
     if (st == 0)
         st = oracle_cqrrpt_core_sketched(m, n, M, ldm, Msk, d, tol, Q, ldq, R, ldr, J, k_out,
                                          Rsk_out, Rpre_out, pivnorm, second);
+    free(Msk);
+    return st;
+}
+
+/* Alg. 1 with the strong rank-revealing QR of Sec. 2.2 in line 2: the QRCP
+ * of the sketch, the rank k of line 3, then oracle_srrqr at that k (J and
+ * R^sk exchanged and refactored), then lines 4-8 as oracle_cqrrpt.
+ * *swaps_out receives the number of exchanges.  Returns as oracle_cqrrpt
+ * (-10 for f <= 1). */
+int oracle_cqrrpt_srrqr(int64_t m, int64_t n, const double* M, int64_t ldm, double gamma, int nnz,
+                        double tol, uint64_t seed, double f, double* Q, int64_t ldq, double* R,
+                        int64_t ldr, int64_t* J, int64_t* k_out, double* Rsk_out,
+                        int64_t* swaps_out) {
+    *k_out = 0;
+    if (swaps_out) *swaps_out = 0;
+    if (m < 1) return -1;
+    if (n < 1) return -2;
+    if (ldm < m) return -4;
+    if (!(gamma >= 1.0)) return -5;
+    int64_t d = oracle_sketch_dim(n, gamma);
+    if (d > m) return -5;
+    if (nnz < 1 || nnz > d) return -6;
+    if (!(f > 1.0)) return -10;
+    if (ldq < m) return -11;
+    if (ldr < n) return -13;
+    double scale = 1.0 / sqrt((double)nnz);
+    double* Msk = (double*)malloc(sizeof(double) * (size_t)(d * n));
+    int st = oracle_sketch(m, n, M, ldm, d, nnz, seed, scale, Msk, d);
+    if (st == 0)
+        st = core_ex(m, n, M, ldm, Msk, d, tol, Q, ldq, R, ldr, J, k_out, Rsk_out, NULL, NULL,
+                     NULL, 1, f, swaps_out);
     free(Msk);
     return st;
 }
@@ -702,7 +815,7 @@ int oracle_rcholqr(int64_t m, int64_t n, const double* M, int64_t ldm, double ga
     int st = oracle_sketch(m, n, M, ldm, d, nnz, seed, scale, Msk, d);
     if (st == 0)
         st = core_ex(m, n, M, ldm, Msk, d, DBL_MIN, Q, ldq, R, ldr, J, k_out, Rsk_out, Rpre_out,
-                     NULL, NULL, 0);
+                     NULL, NULL, 0, 0.0, NULL);
     free(Msk);
     return st;
 }

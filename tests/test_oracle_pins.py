@@ -604,3 +604,132 @@ def test_cqrrpt_dense_planted_rank_and_argument_errors():
     assert np.linalg.norm(res.Q.T @ res.Q - np.eye(25), 2) <= 1e-13
     Sbad = np.asfortranarray(W.gaussian_operator(30, m, 63).numpy())   # d < n
     assert oracle.cqrrpt_dense(A, Sbad, 1e-9).status == -5
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2: strong rank-revealing QR of the sketch (Gu-Eisenstat exchanges)
+# --------------------------------------------------------------------------
+def _kahan(n, c=0.285):
+    s = math.sqrt(1.0 - c * c)
+    K = np.triu(-c * np.ones((n, n)), 1) + np.eye(n)
+    K = np.diag(s ** np.arange(n)) @ K
+    return np.asfortranarray(K @ np.diag(1.0 - 1e-7 * np.arange(n)))  # QRCP keeps the order
+
+
+def _qrcp_R(X):
+    X = np.asfortranarray(X, dtype=np.float64)
+    d, n = X.shape
+    W = X.copy(order="F")
+    J = np.zeros(n, dtype=np.int64)
+    oracle.lib().oracle_qrcp(d, n, oracle._ptr(W), d, oracle._ptr(J), None, None, None)
+    return np.asfortranarray(np.triu(W[:n, :])), J
+
+
+def _strong_bounds(R, k):
+    A, B, Cm = R[:k, :k], R[:k, k:], R[k:, k:]
+    AB = sl.solve_triangular(A, B)
+    Ainv = sl.solve_triangular(A, np.eye(k))
+    ratio = np.linalg.norm(Cm, axis=0)[None, :] * np.linalg.norm(Ainv, axis=1)[:, None]
+    return np.abs(AB).max(), ratio.max()
+
+
+def test_srrqr_repairs_the_kahan_matrix():
+    """Kahan's matrix defeats max-norm pivoting (no exchange, R[n-1,n-1] far
+    above sigma_min).  The strong RRQR exchanges at k = n - 1 give
+    |(A^-1 B)_ij| <= f, ||C_j|| / omega_i <= f (checked with LAPACK solves),
+    sigma_min <= R[n-1,n-1] <= sigma_min sqrt(1 + f^2 k (n-k)) (Gu-Eisenstat),
+    and R is the R factor of K[:, J] (numpy QR, up to row signs)."""
+    n, f = 30, 2.0
+    K = _kahan(n)
+    R0, J0 = _qrcp_R(K)
+    assert np.array_equal(J0, np.arange(n))
+    smin = np.linalg.svd(K, compute_uv=False)[-1]
+    assert R0[-1, -1] > 100 * smin
+    R, J, sw = oracle.srrqr(R0, n - 1, f, J0)
+    assert sw >= 1 and sorted(J.tolist()) == list(range(n))
+    ab, ratio = _strong_bounds(R, n - 1)
+    assert ab <= f and ratio <= f
+    assert smin * (1 - 1e-10) <= R[-1, -1] <= smin * math.sqrt(1 + f * f * (n - 1))
+    Rn = np.linalg.qr(K[:, J], mode="r")
+    assert np.abs(np.abs(R) - np.abs(Rn)).max() <= 1e-13 * np.abs(Rn).max()
+    assert (np.diag(R) >= 0).all() and np.array_equal(np.triu(R), R)
+
+
+def _vol(X, cols):
+    return math.sqrt(abs(np.linalg.det(X[:, cols].T @ X[:, cols])))
+
+
+def _volume_case(seed):
+    """seed 0: greedy max-norm pivoting picks (a, b) with volume 70 while
+    (b, c) has 98; seeds > 0: random columns with one near-dependence."""
+    rng = _rng(900 + seed)
+    if seed == 0:
+        X = 0.01 * rng.standard_normal((12, 8))
+        X[:3, 0] = [10.0, 0.0, 0.0]
+        X[:3, 1] = [7.0, 7.0, 0.0]
+        X[:3, 2] = [7.0, -7.0, 0.0]
+        return X, 2
+    X = rng.standard_normal((12, 8)) * (1.0 + 3.0 * rng.random(8))
+    X[:, 5] = X[:, 0] + 0.3 * X[:, 6]
+    return X, 4
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5, 6])
+def test_srrqr_no_exchange_grows_the_volume_beyond_f(seed):
+    """Brute force on small matrices: exchanging column i < k with column
+    j >= k multiplies |det A| (the volume of the k selected columns of X)
+    by sqrt(rho_ij) (Gu-Eisenstat's Lemma 3.1).  After the exchanges no single
+    exchange grows the volume by more than f, and the volume did not
+    shrink."""
+    X, k = _volume_case(seed)
+    n, f = X.shape[1], 1.02
+    R0, J0 = _qrcp_R(X)
+    R, J, sw = oracle.srrqr(R0, k, f, J0)
+    v = _vol(X, J[:k])
+    assert v >= _vol(X, J0[:k]) * (1 - 1e-12)
+    for i in range(k):
+        for j in range(k, n):
+            cols = J.copy()
+            cols[i], cols[j] = cols[j], cols[i]
+            assert _vol(X, cols[:k]) <= f * v * (1 + 1e-10)
+
+
+def test_srrqr_exchange_on_the_greedy_counterexample():
+    """Max-norm pivoting keeps (a, b), volume 70; one exchange reaches
+    (b, c), volume 98 (rho = (98/70)^2 = 1.96 > f^2)."""
+    X, k = _volume_case(0)
+    R0, J0 = _qrcp_R(X)
+    assert sorted(J0[:2].tolist()) == [0, 1]
+    R, J, sw = oracle.srrqr(R0, k, 1.2, J0)
+    assert sw == 1 and sorted(J[:2].tolist()) == [1, 2]
+    assert abs(_vol(X, J[:2]) / _vol(X, J0[:2]) - 1.4) < 1e-3
+
+
+def test_srrqr_leaves_a_strong_factorisation_alone():
+    X = _rng(77).standard_normal((200, 40))
+    R0, J0 = _qrcp_R(X)
+    R, J, sw = oracle.srrqr(R0, 20, 2.0, J0)
+    assert sw == 0 and np.array_equal(J, J0) and np.array_equal(R, R0)
+
+
+def test_cqrrpt_srrqr_planted_rank():
+    """The method with the exchanges: with f = 1.05 the planted-rank matrix
+    needs exchanges, and the result keeps k, the factorisation invariants
+    and the strong bounds on R^sk; with f = 2 no exchange happens and the
+    result is CQRRPT's, bit for bit."""
+    m, n = 5000, 48
+    sv = np.zeros(n)
+    sv[:30] = W.logspaced(30, -6.0).numpy()
+    A = np.asfortranarray(W.planted(m, n, sv, 701, noise=1e-15).numpy())
+    res = oracle.cqrrpt_srrqr(A, 1.25, 4, 1e-9, 77, 1.05)
+    assert res.status == 0 and res.k == 30 and res.swaps > 0
+    assert sorted(res.J.tolist()) == list(range(n))
+    ab, ratio = _strong_bounds(res.Rsk, 30)
+    assert ab <= 1.05 and ratio <= 1.05
+    assert np.linalg.norm(A[:, res.J] - res.Q @ res.R) / np.linalg.norm(A) <= 1e-11
+    assert np.linalg.norm(res.Q.T @ res.Q - np.eye(30), 2) <= 1e-13
+    r2 = oracle.cqrrpt_srrqr(A, 1.25, 4, 1e-9, 77, 2.0)
+    ref = oracle.cqrrpt(A, 1.25, 4, 1e-9, 77)
+    assert r2.swaps == 0 and np.array_equal(r2.J, ref.J)
+    assert np.array_equal(r2.Q, ref.Q) and np.array_equal(r2.R, ref.R)
+    assert oracle.cqrrpt_srrqr(A, 1.25, 4, 1e-9, 77, 1.0).status == -10

@@ -520,8 +520,9 @@ void oracle_trmm_upper(int64_t k, int64_t n, const double* Rpre, int64_t ldp, co
  * Q discarded).  Each exchange multiplies |det A| by sqrt(rho_ij) > f, so
  * the loop ends; max_swaps bounds it all the same.  Sums run in ascending
  * index order with one fma per term:
- *     W = A^{-1} by columns (column c: W[c,c] = 1 / A[c,c]; for i = c-1
- *         down to 0, W[i,c] = -(sum_{t=i+1..c} A[i,t] W[t,c]) / A[i,i]);
+ *     W = A^{-1} by columns, column-oriented back substitution (column c:
+ *         x = e_c; for t = c down to 0: x_t = x_t / A[t,t], then
+ *         x_i = fma(-A[i,t], x_t, x_i) for every i < t);
  *     (A^{-1}B)[i,j] = sum_{t=i..k-1} W[i,t] R[t,k+j];
  *     w2_i = sum_{t=i..k-1} W[i,t]^2;  g2_j = sum_{t=k..k+j} R[t,k+j]^2;
  *     rho_ij = fma(ab, ab, g2_j * w2_i).
@@ -539,11 +540,11 @@ int64_t oracle_srrqr(int64_t n, int64_t k, double f, double* R, int64_t ldr, int
     int64_t swaps = 0;
     while (swaps < max_swaps) {
         for (int64_t c = 0; c < k; ++c) {
-            W[c + c * k] = 1.0 / R[c + c * ldr];
-            for (int64_t i = c - 1; i >= 0; --i) {
-                double s = 0.0;
-                for (int64_t t = i + 1; t <= c; ++t) s = fma(R[i + t * ldr], W[t + c * k], s);
-                W[i + c * k] = -s / R[i + i * ldr];
+            double* x = W + c * k;
+            for (int64_t i = 0; i < k; ++i) x[i] = i == c ? 1.0 : 0.0;
+            for (int64_t t = c; t >= 0; --t) {
+                x[t] = x[t] / R[t + t * ldr];
+                for (int64_t i = 0; i < t; ++i) x[i] = fma(-R[i + t * ldr], x[t], x[i]);
             }
         }
         for (int64_t i = 0; i < k; ++i) {

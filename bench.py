@@ -52,14 +52,16 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--rows", type=int, default=131072, help="m of the workload")
     p.add_argument("--workload", default="single",
-                   choices=["single", "batched", "mixed", "serve", "dense", "panels"],
+                   choices=["single", "batched", "mixed", "serve", "dense", "panels",
+                            "srrqr"],
                    help="single: the rank-800 131072 x 1024 problem (headline); batched: 512 "
                         "uneven problems in one batched pass; mixed: 1048576 x 512, cond 1e10, "
                         "split-BF16 modes against FP64; serve: a Poisson stream of mixed-size "
                         "requests through the continuous-batching server; dense: the "
                         "headline matrix with a dense Gaussian operator instead of the SASO; "
                         "panels: the headline matrix streamed from pinned host memory in row "
-                        "panels")
+                        "panels; srrqr: the headline matrix with the strong rank-revealing "
+                        "exchanges on the sketch")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--requests", type=int, default=600, help="serve: requests in the open loop")
     p.add_argument("--pool", type=int, default=32, help="serve: distinct matrices")
@@ -567,6 +569,59 @@ def run_panels(args, world, rank, local, C):
         print(json.dumps(line), flush=True)
 
 
+def run_srrqr(args, world, rank, local, C):
+    """The headline matrix (m = 131072, n = 1024, planted rank 800) with the
+    strong rank-revealing exchanges of Sec. 2.2 after the rank rule
+    (cqrrpt_srrqr_d, f = 2 as the paper names, and f = 1.05), against
+    cqrrpt_d on the same matrix.  Wall clock of the whole call (the
+    exchange loop waits on the host once per step)."""
+    w = rank_workload(W.single_large(m=args.rows), rank)
+    m, n = w.m, w.n
+    A = w.matrix("cuda")
+    h = C.Handle(local)
+    Q = C.colmajor_empty(m, n)
+    R = C.colmajor_empty(n, n)
+    J = torch.empty(n, dtype=torch.int64, device="cuda")
+    steps = max(1, min(args.steps, 3))
+    out = {}
+
+    def wall(call):
+        for _ in range(max(1, args.warmup)):
+            r = call()
+        ms = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = call()
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) * 1e3)
+        return statistics.median(ms), r
+
+    t, res = wall(lambda: C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, out=(Q, R, J),
+                                   handle=h))
+    out["cqrrpt_fp64_ms"] = t
+    J0 = J.clone()
+    for f in (2.0, 1.05):
+        t, (res, sw) = wall(lambda: C.cqrrpt_srrqr(A, w.gamma, w.nnz, w.tol, w.sketch_seed, f=f,
+                                                   out=(Q, R, J), handle=h))
+        k = res.k
+        recon = (torch.linalg.norm(A[:, J] - Q[:, :k] @ R[:k]) / torch.linalg.norm(A)).item()
+        orth = torch.linalg.matrix_norm(Q[:, :k].t() @ Q[:, :k] - torch.eye(
+            k, dtype=torch.float64, device="cuda"), ord=2).item()
+        out["f_%g" % f] = {"ms": t, "k": k, "exchanges": sw, "recon_rel_F": recon,
+                           "orth_2": orth, "J_equal_cqrrpt": bool(torch.equal(J, J0))}
+    best = out["f_2"]
+    line = {"metric": "cqrrpt_factorizations_per_s", "value": 1e3 / best["ms"],
+            "unit": "factorizations/s", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": best["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name + "_strong_rrqr", "m": m, "n": n, "d": w.d,
+                       "nnz_per_col": w.nnz, "tol": w.tol},
+            "modes": out, "note": "wall clock per call; bit-identical to the oracle (tests)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serve(args, world, rank, local, C):
     """Continuous-batching server under a Poisson stream.  Requests are drawn
     from a pool of `--pool` matrices of the serving mix (m = 2^U[12,20],
@@ -773,6 +828,10 @@ def main():
         return
     if args.workload == "panels":
         run_panels(args, world, rank, local, C)
+        barrier(world)
+        return
+    if args.workload == "srrqr":
+        run_srrqr(args, world, rank, local, C)
         barrier(world)
         return
 

@@ -135,6 +135,27 @@ int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int
                      double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
                      cudaStream_t stream);
 
+/* ---- strong rank-revealing pivots ----------------------------------------- */
+
+/* Alg. 1 in FP64 with a strong rank-revealing QR of the sketch (Sec. 2.2:
+ * Gu and Eisenstat's algorithm, tuning parameter f; the paper names f = 2).
+ * Lines 1-3 as cqrrpt_d; then, with A = R^sk[:k, :k], B = R^sk[:k, k:],
+ * C = R^sk[k:, k:], while some i < k <= j has
+ *     rho_ij = (A^{-1} B)_{i, j-k}^2 + ||C[:, j-k]||^2 ||row i of A^{-1}||^2 > f^2,
+ * the pair with the largest rho_ij (lowest i, then j, on ties) is
+ * exchanged in J and R^sk, and R^sk is refactored by an unpivoted
+ * Householder QR (at most 64 n exchanges); then lines 4-8 at the same k.
+ * Afterwards |(A^{-1} B)_{ij}| <= f and ||C[:, j]|| / omega_i(A) <= f.
+ * The host waits for k after line 3 and once per exchange step.
+ *   f           tuning parameter, f > 1 (argument 10).
+ *   swaps_host  host int64 or NULL: the number of exchanges (argument 18).
+ * Other arguments, outputs and errors as cqrrpt_d (FP64; argument numbers
+ * from Q on shift by one: Q is 11). */
+int cqrrpt_srrqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                   double gamma, int nnz_per_col, double tol, uint64_t seed, double f, double* Q,
+                   int64_t ldq, double* R, int64_t ldr, int64_t* J, int64_t* k_dev,
+                   int64_t* k_host, int64_t* swaps_host, cudaStream_t stream);
+
 /* ---- row panels of a host-resident matrix --------------------------------- */
 
 /* The row-partitioned form of Alg. 2 (Sec. 2.1 notes that the sketch and the

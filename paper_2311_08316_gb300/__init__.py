@@ -86,6 +86,8 @@ def lib():
     L.cqrrpt_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _d, _int, _p, _i64,
                                  _p, _i64, _p, _p, _p, _p]
     L.cqrrpt_sketch_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_srrqr_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _d, _p, _i64, _p,
+                                 _i64, _p, _p, _p, _p, _p]
     L.cqrrpt_panels_host_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _i64, _p,
                                        _i64, _p, _i64, _p, _p, _p]
     L.cqrrpt_sketch_dim.argtypes = [_i64, _d]
@@ -108,7 +110,7 @@ def exported_symbols():
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
             "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d", "cqrrpt_dense_d",
-            "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d"]
+            "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -279,6 +281,29 @@ def rcholqr(A, gamma=1.25, nnz=4, seed=0, out=None, handle=None, stream=None):
     if rc < 0 or rc >= 3:
         _check(rc, "cqrrpt_rcholqr_d")
     return Factorization(Q, R, J, k.value, rc)
+
+
+def cqrrpt_srrqr(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, f=2.0, out=None, handle=None,
+                 stream=None):
+    """Alg. 1 with Sec. 2.2's strong rank-revealing exchanges on the sketch's
+    R factor (tuning parameter f > 1) through cqrrpt_srrqr_d; waits for the
+    result.  Returns (Factorization, number of exchanges)."""
+    h = handle or default_handle()
+    m, n = A.shape
+    if out is None:
+        Q = colmajor_empty(m, n, A.device)
+        R = colmajor_empty(n, n, A.device)
+        J = torch.empty(n, dtype=torch.int64, device=A.device)
+    else:
+        Q, R, J = out
+    k = _i64()
+    sw = _i64()
+    rc = lib().cqrrpt_srrqr_d(h.h, m, n, A.data_ptr(), _ld(A), gamma, nnz, tol, seed, f,
+                              Q.data_ptr(), _ld(Q), R.data_ptr(), _ld(R), J.data_ptr(), None,
+                              ctypes.byref(k), ctypes.byref(sw), _stream(stream))
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_srrqr_d")
+    return Factorization(Q, R, J, k.value, rc), sw.value
 
 
 def cqrrpt_panels(A_host, gamma=1.25, nnz=4, tol=-1.0, seed=0, panel_rows=65536, out=None,

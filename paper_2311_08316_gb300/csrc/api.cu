@@ -287,9 +287,11 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
                     int64_t d, int nnz, double tol, uint64_t seed, double* Q, int64_t ldq,
                     double* R, int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host,
                     cudaStream_t stream, bool form_q, double* Rpre_out, int64_t ld_rpre,
-                    bool pivoting = true, const double* S_dense = nullptr, int64_t lds = 0) {
+                    bool pivoting = true, const double* S_dense = nullptr, int64_t lds = 0,
+                    double srrqr_f = 0.0, int64_t* swaps_out = nullptr) {
   const Plan p = plan_fp64(m, n, d, nnz);
-  int st = ensure_ws(h, p.total);
+  const size_t sr_bytes = srrqr_f > 0.0 ? (size_t)srrqr_workspace_bytes((int)n) : 0;
+  int st = ensure_ws(h, p.total + sr_bytes);
   if (st != kOk) return st;
   char* w = (char*)h->ws;
   void* region = w; w += p.region;
@@ -304,6 +306,8 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
     ldp = ld_rpre;
   }
   double* f2 = (double*)w;
+  w += p.f2;
+  void* srw = w;
   DeviceScalars* sc = h->sc;
   int* status = &sc->status;
   const int ni = (int)n, di = (int)d;
@@ -318,6 +322,16 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
   if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream, !pivoting);
   mark(h, 2, stream);
   if (e == cudaSuccess) e = launch_rank(ni, Rsk, n, tol, sc, f2, stream);
+  if (e == cudaSuccess && srrqr_f > 0.0) {
+    // Sec. 2.2: strong RRQR exchanges at the rank of line 3 (host-driven)
+    int st1 = kOk;
+    int64_t kk = 0, sw = 0;
+    if (cqrrpt_last_status(h, stream, &st1, &kk) != kOk) e = cudaErrorUnknown;
+    if (e == cudaSuccess && st1 == kOk)
+      e = srrqr_exchange(ni, (int)kk, srrqr_f, Rsk, n, J, srw, qw, sc, h->num_sms,
+                         (double*)(h->pinned + 4), 64 * n, &sw, stream);
+    if (swaps_out) *swaps_out = sw;
+  }
   mark(h, 3, stream);
   if (e == cudaSuccess)
     e = launch_trsm_rut(m, ni, &sc->k, A, lda, J, Rsk, n, Q, ldq, status, stream);
@@ -498,6 +512,34 @@ int cqrrpt_rcholqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int
   // smallest normal tolerance
   return run_fp64(h, m, n, A, lda, d, nnz, DBL_MIN, seed, Q, ldq, R, ldr, J, k_dev, k_host,
                   stream, true, nullptr, 0, false);
+}
+
+int cqrrpt_srrqr_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
+                   double gamma, int nnz, double tol, uint64_t seed, double f, double* Q,
+                   int64_t ldq, double* R, int64_t ldr, int64_t* J, int64_t* k_dev,
+                   int64_t* k_host, int64_t* swaps_host, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 16384) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -6;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -6;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -7;
+  if (std::isnan(tol)) return -8;
+  if (!(f > 1.0) || !std::isfinite(f)) return -10;
+  if (!Q) return -11;
+  if (ldq < m) return -12;
+  if (!R) return -13;
+  if (ldr < n) return -14;
+  if (!J) return -15;
+  DevGuard g(h->device);
+  int64_t sw = 0;
+  const int r = run_fp64(h, m, n, A, lda, d, nnz, tol, seed, Q, ldq, R, ldr, J, k_dev, k_host,
+                         stream, true, nullptr, 0, true, nullptr, 0, f, &sw);
+  if (swaps_host) *swaps_host = sw;
+  return r;
 }
 
 int cqrrpt_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,

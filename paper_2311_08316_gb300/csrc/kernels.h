@@ -74,6 +74,17 @@ cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gat
                                 int64_t gather_tiles, int64_t qrcp_smem_bytes,
                                 cudaStream_t stream);
 
+// Sec. 2.2: strong RRQR exchanges (Gu-Eisenstat, f > 1) on R^sk (n x n,
+// upper triangular) and J at the host rank k, after line 3.  Loops with one
+// host wait per step (best_host: 32 pinned bytes); at most max_swaps
+// exchanges, counted in *swaps_out.  work: srrqr_workspace_bytes(n);
+// qrcp_work: qrcp_workspace_bytes(n).
+int64_t srrqr_workspace_bytes(int n);
+cudaError_t srrqr_exchange(int n, int k, double f, double* Rsk, int64_t ldr, int64_t* J,
+                           void* work, void* qrcp_work, DeviceScalars* sc, int num_sms,
+                           double* best_host, int64_t max_swaps, int64_t* swaps_out,
+                           cudaStream_t stream);
+
 // ---- Alg. 2 line 3 -------------------------------------------------------
 // tol > 0: leading count of R_jj > tol R_00; tol <= 0: stage 1.
 // f2: n + 1 doubles of scratch.

@@ -566,3 +566,37 @@ def test_panels_host_degenerate_cases(C):
     assert k == 0 and st == 2
     with pytest.raises(Exception):
         C.cqrrpt_panels(_host_colmajor(A), 1.25, 4, 1e-12, 3, panel_rows=5000)
+
+
+# ------------------------------------------- Sec. 2.2 strong rank-revealing QR
+@pytest.mark.parametrize("m,n,rank,tol,f", [
+    (5000, 48, 30, 1e-9, 1.05),       # planted rank: exchanges
+    (5000, 48, 30, 1e-9, 2.0),        # none at f = 2
+    (5000, 48, 0, 1e-8, 1.2),         # graded full rank, k < n by the tolerance
+    (20000, 400, 300, 1e-9, 1.05),    # k > 256: several blocks per column of A^-1 B
+])
+def test_srrqr_matches_oracle(C, m, n, rank, tol, f):
+    """cqrrpt_srrqr_d: every rho_ij and decision is the oracle's (same sums,
+    same tie rule), the refactoring is the unpivoted QRCP, so the number of
+    exchanges, J, k, Q and R equal the oracle's bit for bit."""
+    if rank:
+        sv = np.zeros(n)
+        sv[:rank] = W.logspaced(rank, -6.0).numpy()
+        A = np.asfortranarray(W.planted(m, n, sv, 701 + n, noise=1e-15).numpy())
+    else:
+        A = np.asfortranarray(W.planted(m, n, W.logspaced(n, -12.0), 703).numpy())
+    ref = oracle.cqrrpt_srrqr(A, 1.25, 4, tol, 77, f)
+    res, sw = C.cqrrpt_srrqr(gpu(A), 1.25, 4, tol, 77, f)
+    assert res.status == ref.status == 0 and res.k == ref.k
+    assert sw == ref.swaps
+    assert np.array_equal(host(res.J), ref.J)
+    assert_bits(host(res.Q), ref.Q, "Q")
+    assert_bits(host(res.R), ref.R, "R")
+
+
+def test_srrqr_arguments(C):
+    A = gpu(_rng(3).standard_normal((300, 10)))
+    with pytest.raises(Exception):
+        C.cqrrpt_srrqr(A, 1.25, 4, 1e-12, 1, f=1.0)
+    res, sw = C.cqrrpt_srrqr(gpu(np.zeros((300, 10))), 1.25, 4, 1e-12, 1, f=2.0)
+    assert res.k == 0 and res.status == 1 and sw == 0

@@ -65,8 +65,8 @@ def test_status_strings(L):
 
 def test_argument_errors_without_a_gpu(L):
     """Argument checks run before any CUDA call: a null handle is argument 1
-    (LAPACK-style -1) for the implicit-Q, apply-Q, host-pipeline, row-panel
-    and dense-operator entry points, and the host helpers reject bad sizes."""
+    (LAPACK-style -1) for the implicit-Q, apply-Q, host-pipeline, row-panel,
+    strong-RRQR and dense-operator entry points, and the host helpers reject bad sizes."""
     assert L.cqrrpt_implicit_d(None, 100, 10, None, 100, 1.25, 4, -1.0, 1, None, 100, None, 10,
                                None, 10, None, None, None, None) == -1
     assert L.cqrrpt_apply_q_d(None, 0, 100, 10, None, 100, None, 10, 1, None, 10, None, 100,
@@ -76,6 +76,8 @@ def test_argument_errors_without_a_gpu(L):
     assert L.cqrrpt_dense_d(None, 100, 10, None, 100, 13, None, 13, -1.0, 0, None, 100, None, 10,
                             None, None, None, None) == -1
     assert L.cqrrpt_sketch_dense_d(None, 100, 10, None, 100, 13, None, 13, None, 13, None) == -1
+    assert L.cqrrpt_srrqr_d(None, 100, 10, None, 100, 1.25, 4, -1.0, 1, 2.0, None, 100, None, 10,
+                            None, None, None, None, None) == -1
     assert L.cqrrpt_panels_host_d(None, 100, 10, None, 100, 1.25, 4, -1.0, 1, 4096, None, 100,
                                   None, 10, None, None, None) == -1
     b = C.ctypes.c_size_t()

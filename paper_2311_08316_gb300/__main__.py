@@ -3,9 +3,12 @@ driver for profilers and quick checks).
 
     python -m paper_2311_08316_gb300 [--workload single|mixed] [--rows M]
                                      [--reps R] [--precision fp64|splitbf16|cholqr2]
+                                     [--operator saso|gaussian]
 
 `single` is the rank-800 workload (n = 1024, planted rank 800, tol 1e-9),
-`mixed` the cond-1e10 workload (n = 512); --rows sets m.  Each repetition
+`mixed` the cond-1e10 workload (n = 512); --rows sets m.  --operator
+gaussian sketches with a dense Gaussian operator (iid N(0, 1/d), drawn once
+on the device) through cqrrpt_dense_d instead of the SASO.  Each repetition
 factors the same matrix on one handle; the last k, status and the library's
 kernel-launch count are printed.
 """
@@ -31,6 +34,7 @@ def main(argv=None):
     p.add_argument("--rows", type=int, default=None)
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    p.add_argument("--operator", default="saso", choices=["saso", "gaussian"])
     a = p.parse_args(argv)
     build.build()
     if a.workload == "single":
@@ -38,14 +42,18 @@ def main(argv=None):
     else:
         w = W.mixed_tall(m=a.rows or (1 << 20))
     A = w.matrix("cuda")
+    S = W.gaussian_operator(w.d, w.m, w.sketch_seed, "cuda") if a.operator == "gaussian" else None
     h = C.Handle()
     r = None
     for _ in range(a.reps):
-        r = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, precision=PRECISIONS[a.precision],
-                     handle=h)
+        if S is None:
+            r = C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed,
+                         precision=PRECISIONS[a.precision], handle=h)
+        else:
+            r = C.cqrrpt_dense(A, S, w.tol, precision=PRECISIONS[a.precision], handle=h)
     torch.cuda.synchronize()
-    print("workload %s m=%d n=%d precision %s: k=%d status=%d launches=%d"
-          % (w.name, w.m, w.n, a.precision, r.k, r.status, C.kernel_launches()))
+    print("workload %s m=%d n=%d precision %s operator %s: k=%d status=%d launches=%d"
+          % (w.name, w.m, w.n, a.precision, a.operator, r.k, r.status, C.kernel_launches()))
 
 
 if __name__ == "__main__":

@@ -36,6 +36,8 @@ import workloads as W  # noqa: E402
 # FP64 peak of GB300 for an ALU-bound FP64 kernel: 152 SMs x 2 DFMA/clk x
 # 2 flop x 2.070 GHz (nominal 1.25 TFLOP/s at the maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# measured dense bf16 peak of the GB300s (cuBLAS, burst)
+BF16_PEAK_TFLOPS = 1968.7
 # DRAM bytes per row of M for one trsm_rut_kernel launch at n = 1024, k = 800:
 # dram__bytes_read.sum + dram__bytes_write.sum = 2.013637 GB + 0.206175 GB
 # from an ncu capture of the m = 32768 case (one launch of line 4), divided
@@ -440,10 +442,10 @@ def run_mixed(args, world, rank, local, C):
 def run_dense(args, world, rank, local, C):
     """The headline matrix (m = 131072, n = 1024, planted rank 800, tol 1e-9)
     sketched by a dense Gaussian operator (Sec. 2.3.1: iid N(0, 1/d),
-    d = 1280, drawn once on the device, resident) instead of the SASO; lines
-    2-8 in FP64 (bit-identical to the oracle, tests) and in split-BF16.  The
-    sketch is 2 d m n FP64 flops; its time and FP64-roofline fraction are
-    reported beside the SASO run of the same matrix."""
+    d = 1280, drawn once on the device, resident) instead of the SASO: in FP64
+    (bit-identical to the oracle, tests), and in split-BF16, where the sketch
+    too runs on the tensor cores.  The sketch is 2 d m n flops; its time and
+    roofline fraction are reported beside the SASO run of the same matrix."""
     w = rank_workload(W.single_large(m=args.rows), rank)
     m, n, d = w.m, w.n, w.d
     A = w.matrix("cuda")
@@ -487,11 +489,22 @@ def run_dense(args, world, rank, local, C):
         sk_flops = 2.0 * d * m * n
         out[name] = {"ms": t, "factorizations_per_s": 1e3 / t, "k": k, "sketch_ms": tsk,
                      "recon_rel_F": recon, "orth_2": orth}
-        out[name]["sketch_roofline"] = {
-            "kernel": "sketch_dense_partial_kernel", "bound": "alu",
-            "achieved": sk_flops / (tsk * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
-            "unit": "GFLOP/s", "frac": sk_flops / (tsk * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
-            "algorithmic_flops_per_launch": sk_flops}
+        if prec == C.FP64:
+            out[name]["sketch_roofline"] = {
+                "kernel": "sketch_dense_partial_kernel", "bound": "alu",
+                "achieved": sk_flops / (tsk * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": sk_flops / (tsk * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+                "algorithmic_flops_per_launch": sk_flops}
+        else:
+            # split-BF16 sketch: 36 digit-pair products of the d x m x n shape
+            # (plus transpose and splits) against the measured bf16 peak
+            tc = 36.0 * sk_flops / (tsk * 1e-3) / 1e12
+            out[name]["sketch_roofline"] = {
+                "kernel": "sketch (transpose, splits, oz_tc_kernel, combine)", "bound": "tensor",
+                "achieved": tc, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tc / BF16_PEAK_TFLOPS,
+                "fp64_equivalent_gflops": sk_flops / (tsk * 1e-3) / 1e9,
+                "algorithmic_flops_per_launch": 36.0 * sk_flops}
     t, tsk, k = timed(lambda: C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, out=(Q, R, J),
                                        handle=h, stream=stream, sync=False))
     out["saso_fp64"] = {"ms": t, "sketch_ms": tsk, "k": k}

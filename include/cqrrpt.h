@@ -194,10 +194,12 @@ int cqrrpt_panels_host_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A_
 /* Alg. 2 with a dense sketching operator S that the caller drew: the
  * Gaussian family of Sec. 2.3.1 (iid entries of mean 0 and variance 1/d), or
  * any other d x m operator (Alg. 1 takes the distribution F as a parameter).
- * Line 1 is M^sk = S M in FP64: for each 4096-row block one fma per term in
- * ascending row order from +0.0, the blocks then added in ascending order,
- * no scaling (S carries its own); 2 d m n flops against the m n s additions
- * of a SASO.  Lines 2-8 are those of cqrrpt_d in the chosen precision.
+ * With CQRRPT_FP64, line 1 is M^sk = S M in FP64: for each 4096-row block
+ * one fma per term in ascending row order from +0.0, the blocks then added
+ * in ascending order, no scaling (S carries its own); 2 d m n flops against
+ * the m n s additions of a SASO.  In the split-BF16 precisions line 1 is the
+ * tensor-core product of cqrrpt_sketch_dense_split_d (FP64-accurate).
+ * Lines 2-8 are those of cqrrpt_d in the chosen precision.
  *   d          sketch rows, n <= d <= m and d <= 28000 (else -6).
  *   S, lds     d x m column-major device matrix, lds >= d; read only,
  *              owned by the caller (arguments 7, 8).
@@ -217,6 +219,18 @@ int cqrrpt_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64
 int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,
                           int64_t d, const double* S, int64_t lds, double* Ask, int64_t ldsk,
                           cudaStream_t stream);
+
+/* Line 1 with a dense operator on the BF16 tensor cores: Ask = S A as the
+ * split-BF16 product (S transposed, both operands split into eight 7-bit
+ * digit planes along m, 36 digit-pair products with exact FP32 sums of 1024
+ * terms, exact integer combination, one rounding per K slice, the slices
+ * added in ascending order).  FP64-accurate, not bit-identical to
+ * cqrrpt_sketch_dense_d.  A non-finite entry of S or A sets CQRRPT_NONFINITE.
+ * Arguments as cqrrpt_sketch_dense_d (n, d <= 65536).  Workspace: S^T and the
+ * digit planes, about (8 + 16 (d + n)) m bytes. */
+int cqrrpt_sketch_dense_split_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A,
+                                int64_t lda, int64_t d, const double* S, int64_t lds, double* Ask,
+                                int64_t ldsk, cudaStream_t stream);
 
 /* ---- implicit Q --------------------------------------------------------- */
 

@@ -86,6 +86,8 @@ def lib():
     L.cqrrpt_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _d, _int, _p, _i64,
                                  _p, _i64, _p, _p, _p, _p]
     L.cqrrpt_sketch_dense_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64, _p]
+    L.cqrrpt_sketch_dense_split_d.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p, _i64, _p, _i64,
+                                              _p]
     L.cqrrpt_srrqr_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _d, _p, _i64, _p,
                                  _i64, _p, _p, _p, _p, _p]
     L.cqrrpt_panels_host_d.argtypes = [_p, _i64, _i64, _p, _i64, _d, _int, _d, _u64, _i64, _p,
@@ -110,7 +112,8 @@ def exported_symbols():
             "cqrrpt_batched_autotune", "cqrrpt_batched_get_tuning", "cqrrpt_batched_set_tuning",
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
             "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d", "cqrrpt_dense_d",
-            "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d"]
+            "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d",
+            "cqrrpt_sketch_dense_split_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -437,17 +440,18 @@ def sketch(A, d, nnz, seed, handle=None, stream=None):
     return out
 
 
-def sketch_dense(A, S, handle=None, stream=None):
-    """Line 1 with a dense operator: S A (d x n) through cqrrpt_sketch_dense_d."""
+def sketch_dense(A, S, split=False, handle=None, stream=None):
+    """Line 1 with a dense operator: S A (d x n) through cqrrpt_sketch_dense_d
+    (FP64) or, with split=True, cqrrpt_sketch_dense_split_d (tensor cores)."""
     h = handle or default_handle()
     m, n = A.shape
     d = S.shape[0]
     if S.shape[1] != m:
         raise ValueError("S must be d x m")
     out = colmajor_empty(d, n, A.device)
-    _check(lib().cqrrpt_sketch_dense_d(h.h, m, n, A.data_ptr(), _ld(A), d, S.data_ptr(), _ld(S),
-                                       out.data_ptr(), _ld(out), _stream(stream)),
-           "cqrrpt_sketch_dense_d")
+    fn = lib().cqrrpt_sketch_dense_split_d if split else lib().cqrrpt_sketch_dense_d
+    _check(fn(h.h, m, n, A.data_ptr(), _ld(A), d, S.data_ptr(), _ld(S), out.data_ptr(), _ld(out),
+              _stream(stream)), "cqrrpt_sketch_dense_d")
     return out
 
 

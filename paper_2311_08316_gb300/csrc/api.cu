@@ -173,10 +173,13 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
               int64_t ldr, int64_t* J, int64_t* k_dev, int64_t* k_host, cudaStream_t stream,
               const double* S_dense = nullptr, int64_t lds = 0) {
   const Plan p = plan_for(m, n, d, nnz, precision);
-  int st = ensure_ws(h, p.total);
+  // a dense operator's split-BF16 sketch may need a larger first region
+  const int64_t need = S_dense ? sketch_dense_split_workspace_bytes(m, n, (int)d) : 0;
+  const size_t extra = need > (int64_t)p.region ? (size_t)align256(need) - p.region : 0;
+  int st = ensure_ws(h, p.total + extra);
   if (st != kOk) return st;
   char* w = (char*)h->ws;
-  void* region = w; w += p.region;
+  void* region = w; w += p.region + extra;
   double* X = (double*)w; w += p.x;
   void* qw = w; w += p.qrcp;
   double* Rsk = (double*)w; w += p.rsk;
@@ -193,7 +196,8 @@ int run_split(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t ld
   cudaError_t e = launch_init_scalars(sc, 0, stream);
   mark(h, 0, stream);
   if (e == cudaSuccess)
-    e = S_dense ? launch_sketch_dense(m, n, S_dense, lds, A, lda, di, X, d, region, status, stream)
+    e = S_dense ? launch_sketch_dense_split(m, n, S_dense, lds, A, lda, di, X, d, region, status,
+                                          stream)
                 : launch_sketch(m, n, A, lda, di, nnz, seed, scale, X, d, region, status, stream);
   mark(h, 1, stream);
   if (e == cudaSuccess) e = launch_qrcp(di, ni, X, d, J, Rsk, n, qw, sc, h->num_sms, stream);
@@ -588,6 +592,29 @@ int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A
   if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
   if (launch_sketch_dense(m, n, S, lds, A, lda, (int)d, Ask, ldsk, h->ws, &h->sc->status,
                           stream) != cudaSuccess)
+    return kCudaError;
+  return kOk;
+}
+
+int cqrrpt_sketch_dense_split_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A,
+                                int64_t lda, int64_t d, const double* S, int64_t lds, double* Ask,
+                                int64_t ldsk, cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (n < 1 || n > 65536) return -3;
+  if (!A) return -4;
+  if (lda < m) return -5;
+  if (d < 1 || d > 65536) return -6;
+  if (!S) return -7;
+  if (lds < d) return -8;
+  if (!Ask) return -9;
+  if (ldsk < d) return -10;
+  DevGuard g(h->device);
+  int st = ensure_ws(h, (size_t)sketch_dense_split_workspace_bytes(m, n, (int)d));
+  if (st != kOk) return st;
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess) return kCudaError;
+  if (launch_sketch_dense_split(m, n, S, lds, A, lda, (int)d, Ask, ldsk, h->ws, &h->sc->status,
+                                stream) != cudaSuccess)
     return kCudaError;
   return kOk;
 }

@@ -52,6 +52,14 @@ cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_
                                 cudaStream_t stream);
 cudaError_t launch_sketch_finish(int d, int64_t n, const double* acc, double scale, double* Msk,
                                  int64_t ldsk, int* status, cudaStream_t stream);
+// The same product on the BF16 tensor cores (split-BF16, FP64-accurate, not
+// bit-identical): S transposed, then the Gram's K-sliced product of S^T and M.
+// work: sketch_dense_split_workspace_bytes.
+int64_t sketch_dense_split_workspace_bytes(int64_t m, int64_t n, int d);
+cudaError_t launch_sketch_dense_split(int64_t m, int64_t n, const double* S, int64_t lds,
+                                      const double* M, int64_t ldm, int d, double* Msk,
+                                      int64_t ldsk, void* work, int* status,
+                                      cudaStream_t stream);
 int64_t sketch_list_tiles(const SketchDesc& D);
 int64_t sketch_partial_tiles(const SketchDesc& D);
 int64_t sketch_combine_tiles(const SketchDesc& D);

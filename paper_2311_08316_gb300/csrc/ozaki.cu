@@ -349,20 +349,10 @@ int64_t oz_plane_bytes(int64_t rows, int64_t kpad) {
 
 cudaError_t oz_gemm_launch(const OzGemm& G, cudaStream_t s) { return oz_gemm_tc_launch(G, s); }
 
-// Gram: G = X^T X (k x k) from X (m x k).
-int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out) {
-  const int64_t kpad = round_up(m, kOzChunk);
-  const int64_t chunks = kpad / kOzChunk;
-  // tiles the upper-triangle launch keeps (not strictly below the diagonal)
-  // (tile shape and residency of the tensor-core engine: 128 x 128, one CTA
-  // per SM)
-  const int64_t tile = 128;
-  int64_t active = 0;
-  for (int64_t tn = 0; tn < (k + tile - 1) / tile; ++tn)
-    for (int64_t tm = 0; tm < (k + tile - 1) / tile; ++tm)
-      if (tm * tile < tn * tile + tile) ++active;
-  // number of K slices: at least two waves of one CTA per SM, and the last
-  // wave at least 90% full when possible
+// Number of K slices for `active` output tiles over `chunks` 1024-term K
+// chunks: at least two waves of one CTA per SM (the engine's residency), and
+// the last wave at least 90% full when possible.
+static int64_t choose_slices(int64_t chunks, int64_t active) {
   const int64_t slots = 152;
   int64_t nslices = 1;
   double best = -1.0;
@@ -375,6 +365,21 @@ int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out) {
     if (ctas >= 2 * slots && eff >= 0.9) { nslices = real; best = eff; break; }
     if (eff > best) { best = eff; nslices = real; }
   }
+  return nslices;
+}
+
+// Gram: G = X^T X (k x k) from X (m x k).
+int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out) {
+  const int64_t kpad = round_up(m, kOzChunk);
+  const int64_t chunks = kpad / kOzChunk;
+  // tiles the upper-triangle launch keeps (not strictly below the diagonal)
+  // (tile shape of the tensor-core engine: 128 x 128)
+  const int64_t tile = 128;
+  int64_t active = 0;
+  for (int64_t tn = 0; tn < (k + tile - 1) / tile; ++tn)
+    for (int64_t tm = 0; tm < (k + tile - 1) / tile; ++tm)
+      if (tm * tile < tn * tile + tile) ++active;
+  const int64_t nslices = choose_slices(chunks, active);
   if (nslices_out) *nslices_out = nslices;
   return (int64_t)kOzDigits * oz_plane_bytes(k, kpad) + align256((int64_t)k * 4) +
          align256(nslices * (int64_t)k * k * 8);
@@ -415,6 +420,70 @@ cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* Gm, 
   const int64_t ns = (kpad + G.kslice - 1) / G.kslice;
   const OzCombine cb{P, G.c_slice, (int)ns, k, Gm, ldg};
   oz_combine_sym_kernel<<<(unsigned)oz_combine_tiles(cb), 256, 0, s>>>(cb);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// C = X^T Y (ka x kb) from X (m x ka) and Y (m x kb): the Gram's K-sliced
+// product with two operands and every output tile (line 1 with a dense
+// operator S: X = S^T).  Partial results per K slice are added in ascending
+// slice order (oz_combine_kernel).
+__global__ void __launch_bounds__(256) oz_combine_kernel(const double* P, int64_t slice,
+                                                         int nslices, int ka, int kb, double* C,
+                                                         int64_t ldc) {
+  const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (idx >= (int64_t)ka * kb) return;
+  const int c = (int)(idx / ka), a = (int)(idx - (int64_t)c * ka);
+  double v = 0.0;
+  for (int q = 0; q < nslices; ++q) v = __dadd_rn(v, P[(int64_t)q * slice + idx]);
+  C[(int64_t)c * ldc + a] = v;
+}
+
+int64_t oz_gemm_tn_workspace(int64_t m, int ka, int kb, int64_t* nslices_out) {
+  const int64_t kpad = round_up(m, kOzChunk);
+  const int64_t tiles = (int64_t)((ka + 127) / 128) * ((kb + 127) / 128);
+  const int64_t nslices = choose_slices(kpad / kOzChunk, tiles);
+  if (nslices_out) *nslices_out = nslices;
+  return (int64_t)kOzDigits * (oz_plane_bytes(ka, kpad) + oz_plane_bytes(kb, kpad)) +
+         align256((int64_t)ka * 4) + align256((int64_t)kb * 4) +
+         align256(nslices * (int64_t)ka * kb * 8);
+}
+
+cudaError_t oz_gemm_tn(int64_t m, int ka, int kb, const double* X, int64_t ldx, const double* Y,
+                       int64_t ldy, double* Cm, int64_t ldc, void* work, cudaStream_t s,
+                       int* status) {
+  int64_t nslices = 1;
+  oz_gemm_tn_workspace(m, ka, kb, &nslices);
+  const int64_t kpad = round_up(m, kOzChunk);
+  char* w = (char*)work;
+  __nv_bfloat16* DX = (__nv_bfloat16*)w;
+  const int64_t px = (int64_t)ka * kpad;
+  w += (int64_t)kOzDigits * oz_plane_bytes(ka, kpad);
+  __nv_bfloat16* DY = (__nv_bfloat16*)w;
+  const int64_t py = (int64_t)kb * kpad;
+  w += (int64_t)kOzDigits * oz_plane_bytes(kb, kpad);
+  int* ex = (int*)w;
+  w += align256((int64_t)ka * 4);
+  int* ey = (int*)w;
+  w += align256((int64_t)kb * 4);
+  double* P = (double*)w;
+  cudaError_t e = oz_colsplit(OzColSplit{X, ldx, m, ka, kpad, ex, DX, px, kOzChunk}, s);
+  if (e == cudaSuccess) e = oz_colsplit(OzColSplit{Y, ldy, m, kb, kpad, ey, DY, py, kOzChunk}, s);
+  if (e != cudaSuccess) return e;
+  OzGemm G{};
+  G.M = ka; G.N = kb; G.Kpad = kpad;
+  G.kslice = ((kpad / kOzChunk + nslices - 1) / nslices) * kOzChunk;
+  G.A = DX; G.a_plane = px; G.B = DY; G.b_plane = py;
+  G.a_kblk = kOzChunk; G.b_kblk = kOzChunk;
+  G.ea = ex; G.eb = ey;
+  G.C = P; G.ldc = ka; G.c_slice = (int64_t)ka * kb;
+  G.mode = kOzStore; G.upper_only = 0;
+  G.err = status;
+  e = oz_gemm_launch(G, s);
+  if (e != cudaSuccess) return e;
+  const int ns = (int)((kpad + G.kslice - 1) / G.kslice);
+  const unsigned grid = (unsigned)(((int64_t)ka * kb + 255) / 256);
+  oz_combine_kernel<<<grid, 256, 0, s>>>(P, G.c_slice, ns, ka, kb, Cm, ldc);
   count_launches(1);
   return cudaGetLastError();
 }

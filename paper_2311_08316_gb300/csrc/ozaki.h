@@ -111,6 +111,12 @@ int64_t oz_gram_slices(int64_t m, int k);
 int64_t oz_gram_workspace(int64_t m, int k, int64_t* nslices_out);
 cudaError_t oz_gram(int64_t m, int k, const double* X, int64_t ldx, double* G, int64_t ldg,
                     void* work, cudaStream_t s, int* status = nullptr);
+// C = X^T Y (ka x kb, ld ldc) from X (m x ka) and Y (m x kb), column-major:
+// the Gram's K-sliced split-BF16 product with two operands (all tiles).
+int64_t oz_gemm_tn_workspace(int64_t m, int ka, int kb, int64_t* nslices_out);
+cudaError_t oz_gemm_tn(int64_t m, int ka, int kb, const double* X, int64_t ldx, const double* Y,
+                       int64_t ldy, double* C, int64_t ldc, void* work, cudaStream_t s,
+                       int* status = nullptr);
 int64_t oz_trsm_workspace(int64_t m, int k);
 // X := B[:, cols] T^{-1} through the FP64 (row-wise) inverse of T.  side
 // (or null): a second stream and two events on which T^{-1} is formed while

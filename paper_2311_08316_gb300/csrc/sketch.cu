@@ -24,6 +24,7 @@
 // r from +0.0; sketch_combine then adds the blocks with scale 1 (exact).
 #include "common.cuh"
 #include "kernels.h"
+#include "ozaki.h"
 #include "saso.cuh"
 
 namespace cqrrpt {
@@ -408,6 +409,71 @@ cudaError_t launch_sketch_finish(int d, int64_t n, const double* acc, double sca
   sketch_finish_kernel<<<grid, kCombineThreads, 0, stream>>>(acc, d, n, scale, Msk, ldsk, status);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// ---- dense operators on the tensor cores ------------------------------------
+// M^sk = S M as the split-BF16 product (S^T)^T M: S is transposed into
+// S^T (m x d, column-major, 32 x 32 tiles through shared memory) so that both
+// operands are split along their m rows like the Gram's, then oz_gemm_tn.
+// Non-finite entries of S (seen by the transpose) or of M set kNonFinite:
+// the digit split does not carry them.
+__global__ void __launch_bounds__(256) sketch_transpose_kernel(const double* S, int64_t lds,
+                                                               int d, int64_t m, double* St,
+                                                               int* status) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;  // columns of S (rows of S^T)
+  const int i0 = blockIdx.y * 32;               // rows of S
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  bool bad = false;
+  for (int j = ty; j < 32; j += 8) {
+    const int i = i0 + tx;
+    const int64_t r = r0 + j;
+    double v = 0.0;
+    if (i < d && r < m) {
+      v = S[r * lds + i];
+      bad |= !isfinite(v);
+    }
+    tile[j][tx] = v;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = r0 + tx;
+    const int i = i0 + j;
+    if (i < d && r < m) St[(int64_t)i * m + r] = tile[tx][j];
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(status, kNonFinite);
+}
+
+__global__ void __launch_bounds__(256) nonfinite_scan_kernel(const double* M, int64_t ldm,
+                                                             int64_t rows, int64_t cols,
+                                                             int* status) {
+  bool bad = false;
+  const int64_t total = rows * cols;
+  for (int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * 256) {
+    const int64_t c = idx / rows, r = idx - c * rows;
+    bad |= !isfinite(M[c * ldm + r]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(status, kNonFinite);
+}
+
+int64_t sketch_dense_split_workspace_bytes(int64_t m, int64_t n, int d) {
+  return align256(m * (int64_t)d * 8) + oz_gemm_tn_workspace(m, d, (int)n, nullptr);
+}
+
+cudaError_t launch_sketch_dense_split(int64_t m, int64_t n, const double* S, int64_t lds,
+                                      const double* M, int64_t ldm, int d, double* Msk,
+                                      int64_t ldsk, void* work, int* status,
+                                      cudaStream_t stream) {
+  double* St = (double*)work;
+  void* rest = (char*)work + align256(m * (int64_t)d * 8);
+  const dim3 gt((unsigned)((m + 31) / 32), (unsigned)((d + 31) / 32));
+  sketch_transpose_kernel<<<gt, 256, 0, stream>>>(S, lds, d, m, St, status);
+  nonfinite_scan_kernel<<<4 * 152, 256, 0, stream>>>(M, ldm, m, n, status);
+  count_launches(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return oz_gemm_tn(m, d, (int)n, St, m, M, ldm, Msk, ldsk, rest, stream, status);
 }
 
 cudaError_t sketch_set_attributes(int max_d) {

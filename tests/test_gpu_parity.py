@@ -600,3 +600,37 @@ def test_srrqr_arguments(C):
         C.cqrrpt_srrqr(A, 1.25, 4, 1e-12, 1, f=1.0)
     res, sw = C.cqrrpt_srrqr(gpu(np.zeros((300, 10))), 1.25, 4, 1e-12, 1, f=2.0)
     assert res.k == 0 and res.status == 1 and sw == 0
+
+
+# ------------------------------------------- dense operator on the tensor cores
+@pytest.mark.parametrize("m,n,d", [(2 * 4096 + 77, 20, 40), (5000, 130, 129), (40000, 64, 300)])
+def test_sketch_dense_split_exact_on_integers(C, m, n, d):
+    """Split-BF16 dense sketch on integer operands (|S| <= 3, |M| <= 1000):
+    every digit, product and 1024-term FP32 sum is exact, so S M equals the
+    exact integer product bit for bit (several tiles, slices, ragged tails)."""
+    rng = _rng(m + n + d)
+    S = rng.integers(-3, 4, size=(d, m)).astype(np.float64)
+    M = rng.integers(-1000, 1001, size=(m, n)).astype(np.float64)
+    got = host(C.sketch_dense(gpu(M), gpu(S), split=True))
+    assert np.array_equal(got, (S.astype(np.int64) @ M.astype(np.int64)).astype(np.float64))
+
+
+@pytest.mark.parametrize("m,n,d", [(9000, 130, 150), (3 * 4096 + 5, 64, 80)])
+def test_sketch_dense_split_within_the_fp64_bound(C, m, n, d):
+    """Gaussian S, graded columns of M: the tensor-core sketch lies within
+    the FP64 dot-product bound of the oracle's FP64 sketch."""
+    S = np.asfortranarray(W.gaussian_operator(d, m, 611).numpy())
+    M = np.asfortranarray(_rng(612).standard_normal((m, n)) * np.logspace(0, -6, n))
+    ref, st = oracle.sketch_dense(S, M)
+    got = host(C.sketch_dense(gpu(M), gpu(S), split=True))
+    bound = 8 * (m / 1024 + 4096 + 16) * 2.0 ** -53 * (np.abs(S) @ np.abs(M))
+    assert (np.abs(got - ref) <= bound).all()
+
+
+def test_cqrrpt_dense_split_sketch_nonfinite(C):
+    m, n = 3000, 10
+    A = _rng(14).standard_normal((m, n))
+    S = np.asfortranarray(W.gaussian_operator(13, m, 613).numpy())
+    S[5, 77] = np.inf
+    res = C.cqrrpt_dense(gpu(A), gpu(S), 1e-12, precision=2)
+    assert res.status == 2 and res.k == 0

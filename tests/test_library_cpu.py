@@ -76,6 +76,8 @@ def test_argument_errors_without_a_gpu(L):
     assert L.cqrrpt_dense_d(None, 100, 10, None, 100, 13, None, 13, -1.0, 0, None, 100, None, 10,
                             None, None, None, None) == -1
     assert L.cqrrpt_sketch_dense_d(None, 100, 10, None, 100, 13, None, 13, None, 13, None) == -1
+    assert L.cqrrpt_sketch_dense_split_d(None, 100, 10, None, 100, 13, None, 13, None, 13,
+                                         None) == -1
     assert L.cqrrpt_srrqr_d(None, 100, 10, None, 100, 1.25, 4, -1.0, 1, 2.0, None, 100, None, 10,
                             None, None, None, None, None) == -1
     assert L.cqrrpt_panels_host_d(None, 100, 10, None, 100, 1.25, 4, -1.0, 1, 4096, None, 100,

@@ -13,67 +13,88 @@
 // by the diagonal-block and panel steps, again in ascending t.
 //
 // Single problem: three launches per panel (diagonal block, panel rows,
-// trailing update).  Batch: one CTA per problem runs every panel with block
+// trailing update).  Inside the diagonal block and the panel the sums run
+// right-looking (registers hold every running sum of a column), which keeps
+// each entry's ascending-t order but shortens the dependent chain.  Batch: one CTA per problem runs every panel with block
 // barriers between the steps; same bodies, same arithmetic.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace cqrrpt {
 
-// Diagonal block [jb, jb + nb) by one warp, lane = column.  Returns false
-// (and records sc->fail) on a non-positive pivot.
+// Diagonal block [jb, jb + nb) by one warp, lane = column c = jb + lane.
+// Right-looking inside the block: lane c keeps the running sums acc[j] of
+// its entries (j, c), j <= c, in registers; once row t is final, every sum
+// of a later row receives its term -R[t, j] R[t, c] (ascending t, one fma,
+// as the recurrence), so the critical path is one square root, one division
+// and one fma per row instead of the whole dot product.  Returns false (and
+// records sc->fail) on a non-positive pivot.
 __device__ __forceinline__ bool potrf_diag_body(int jb, const PotrfDesc& D) {
-  __shared__ double rdiag;
-  __shared__ int failed;
   DeviceScalars* sc = D.sc;
-  double* S = D.G;
+  const double* S = D.G;
   double* R = D.R;
   const int64_t lds = D.ldg, ldr = D.ldr;
   const int k = (int)sc->k;
   const int nb = min(kCholNB, k - jb);
   const int lane = threadIdx.x & 31;
-  if (lane == 0) failed = 0;
-  __syncwarp();
-  for (int jj = 0; jj < nb; ++jj) {
-    const int j = jb + jj;
-    if (lane == 0) {
-      double s = S[(int64_t)j * lds + j];
-      for (int t = jb; t < j; ++t) {
-        const double r = R[(int64_t)j * ldr + t];
-        s = __fma_rn(-r, r, s);
+  const int c = jb + lane;
+  const bool mine = lane < nb;
+  double acc[kCholNB];
+#pragma unroll
+  for (int j = 0; j < kCholNB; ++j)
+    acc[j] = (mine && j <= lane) ? S[(int64_t)c * lds + jb + j] : 0.0;
+#pragma unroll
+  for (int t = 0; t < kCholNB; ++t) {
+    if (t < nb) {
+      const double piv = __shfl_sync(0xffffffffu, acc[t], t);
+      if (!(piv > 0.0)) {
+        if (lane == 0) sc->fail = jb + t;
+        return false;
       }
-      if (!(s > 0.0)) {
-        failed = 1;
-        sc->fail = j;
-      } else {
-        rdiag = __dsqrt_rn(s);
-        R[(int64_t)j * ldr + j] = rdiag;
+      const double rd = __dsqrt_rn(piv);
+      double rt = 0.0;  // R[jb + t, c]
+      if (lane == t) {
+        rt = rd;
+        R[(int64_t)c * ldr + jb + t] = rd;
+      } else if (mine && lane > t) {
+        rt = __ddiv_rn(acc[t], rd);
+        R[(int64_t)c * ldr + jb + t] = rt;
+      }
+#pragma unroll
+      for (int j = t + 1; j < kCholNB; ++j) {
+        const double rtj = __shfl_sync(0xffffffffu, rt, j);  // R[jb + t, jb + j]
+        if (mine && j <= lane) acc[j] = __fma_rn(-rtj, rt, acc[j]);
       }
     }
-    __syncwarp();
-    if (failed) return false;
-    const int c = jb + lane;
-    if (lane > jj && lane < nb) {
-      double s = S[(int64_t)c * lds + j];
-      for (int t = jb; t < j; ++t) s = __fma_rn(-R[(int64_t)j * ldr + t], R[(int64_t)c * ldr + t], s);
-      R[(int64_t)c * ldr + j] = __ddiv_rn(s, rdiag);
-    }
-    __syncwarp();
   }
   return true;
 }
 
-// Panel rows [jb, jb + nb) of column c >= jb + nb.
+// Panel rows [jb, jb + nb) of column c >= jb + nb, right-looking as the
+// diagonal block: acc[j] holds the running sum of entry (jb + j, c).
 __device__ __forceinline__ void potrf_panel_col(int jb, int nb, int c, const PotrfDesc& D) {
   const double* S = D.G;
   double* R = D.R;
   const int64_t lds = D.ldg, ldr = D.ldr;
-  for (int jj = 0; jj < nb; ++jj) {
-    const int j = jb + jj;
-    double s = S[(int64_t)c * lds + j];
-    for (int t = jb; t < j; ++t) s = __fma_rn(-R[(int64_t)j * ldr + t], R[(int64_t)c * ldr + t], s);
-    R[(int64_t)c * ldr + j] = __ddiv_rn(s, R[(int64_t)j * ldr + j]);
+  double acc[kCholNB];
+#pragma unroll
+  for (int j = 0; j < kCholNB; ++j) acc[j] = j < nb ? S[(int64_t)c * lds + jb + j] : 0.0;
+#pragma unroll
+  for (int t = 0; t < kCholNB; ++t) {
+    if (t < nb) {
+      const double rt = __ddiv_rn(acc[t], R[(int64_t)(jb + t) * ldr + jb + t]);
+      R[(int64_t)c * ldr + jb + t] = rt;
+#pragma unroll
+      for (int j = t + 1; j < kCholNB; ++j)
+        if (j < nb) acc[j] = __fma_rn(-R[(int64_t)(jb + j) * ldr + jb + t], rt, acc[j]);
+    }
   }
+}
+
+// The same as a separate function: inlined into the batched kernel's loop
+// the unrolled body lost its register array to local memory.
+__device__ __noinline__ void potrf_panel_col_call(int jb, int nb, int c, const PotrfDesc& D) {
+  potrf_panel_col(jb, nb, c, D);
 }
 
 // Trailing update of S[a, c] (a <= c, both >= jb + nb) by the panel's rows.
@@ -137,7 +158,7 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const PotrfDesc* Dv)
     if (threadIdx.x == 0) go = (*(volatile int64_t*)&sc->fail < 0);
     __syncthreads();
     if (!go) return;
-    for (int c = base + threadIdx.x; c < k; c += blockDim.x) potrf_panel_col(jb, nb, c, D);
+    for (int c = base + threadIdx.x; c < k; c += blockDim.x) potrf_panel_col_call(jb, nb, c, D);
     __syncthreads();
     const int w = k - base;
     for (int e = threadIdx.x; e < w * w; e += blockDim.x) {

@@ -213,7 +213,7 @@ int cqrrpt_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64
                    int64_t* k_host, cudaStream_t stream);
 
 /* Line 1 alone with a dense operator: Ask (d x n, ldsk >= d) = S A in the
- * sum order of cqrrpt_dense_d; S d x m (lds >= d).  A non-finite result
+ * sum order of cqrrpt_dense_d; S d x m (lds >= d), 1 <= d <= 65536.  A non-finite result
  * sets the handle's status (CQRRPT_NONFINITE, read by cqrrpt_last_status).
  * Uses the handle's workspace ((m/4096 + 1) n d 8 bytes); no host wait. */
 int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int64_t lda,

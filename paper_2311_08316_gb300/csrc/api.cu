@@ -581,7 +581,7 @@ int cqrrpt_sketch_dense_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A
   if (n < 1) return -3;
   if (!A) return -4;
   if (lda < m) return -5;
-  if (d < 1) return -6;
+  if (d < 1 || d > 65536) return -6;
   if (!S) return -7;
   if (lds < d) return -8;
   if (!Ask) return -9;

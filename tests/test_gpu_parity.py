@@ -634,3 +634,43 @@ def test_cqrrpt_dense_split_sketch_nonfinite(C):
     S[5, 77] = np.inf
     res = C.cqrrpt_dense(gpu(A), gpu(S), 1e-12, precision=2)
     assert res.status == 2 and res.k == 0
+
+
+# ------------------------------------------- edge cases of the newer entry points
+def test_dense_operator_with_padded_leading_dimension(C):
+    """S as a view with lds = d + 5 (and A with lda = m + 3): the FP64 dense
+    sketch is bit-identical to the oracle's, the tensor-core one equals its
+    own contiguous-input result bit for bit."""
+    m, n, d = 4096 + 900, 12, 16
+    S = np.asfortranarray(W.gaussian_operator(d, m, 620).numpy())
+    A = np.asfortranarray(_rng(621).standard_normal((m, n)))
+    Sbig = torch.zeros((m, d + 5), dtype=torch.float64, device="cuda")
+    Sbig[:, :d] = torch.from_numpy(np.ascontiguousarray(S.T)).cuda()
+    Sv = Sbig.t()[:d, :]                      # d x m, stride(1) = d + 5
+    Abig = torch.zeros((n, m + 3), dtype=torch.float64, device="cuda")
+    Abig[:, :m] = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+    Av = Abig.t()[:m, :]                      # m x n, stride(1) = m + 3
+    assert Sv.stride(1) == d + 5 and Av.stride(1) == m + 3
+    ref, _ = oracle.sketch_dense(S, A)
+    assert_bits(host(C.sketch_dense(Av, Sv)), ref, "S A (padded)")
+    assert_bits(host(C.sketch_dense(Av, Sv, split=True)),
+                host(C.sketch_dense(gpu(A), gpu(S), split=True)), "split S A (padded)")
+    res = C.cqrrpt_dense(Av, Sv, 1e-12)
+    ref2 = oracle.cqrrpt_dense(A, S, 1e-12)
+    assert res.k == ref2.k and np.array_equal(host(res.J), ref2.J)
+    assert_bits(host(res.Q), ref2.Q, "Q")
+
+
+def test_single_column_through_panels_and_srrqr(C):
+    """n = 1 (d = 2): the row-panel driver and the strong-RRQR entry point
+    give the oracle's bits; no exchange is possible."""
+    m = 5000
+    A = _rng(622).standard_normal((m, 1))
+    ref = oracle.cqrrpt(np.asfortranarray(A), 1.25, 2, 1e-12, 9)
+    Q, R, J, k, st = C.cqrrpt_panels(_host_colmajor(A), 1.25, 2, 1e-12, 9, panel_rows=4096)
+    assert st == ref.status == 0 and k == ref.k == 1
+    assert_bits(np.asfortranarray(Q.numpy()), ref.Q, "Q")
+    assert_bits(np.asfortranarray(R.numpy()), ref.R, "R")
+    res, sw = C.cqrrpt_srrqr(gpu(A), 1.25, 2, 1e-12, 9, f=2.0)
+    assert sw == 0 and res.k == 1
+    assert_bits(host(res.Q), ref.Q, "Q")

@@ -733,3 +733,31 @@ def test_cqrrpt_srrqr_planted_rank():
     assert r2.swaps == 0 and np.array_equal(r2.J, ref.J)
     assert np.array_equal(r2.Q, ref.Q) and np.array_equal(r2.R, ref.R)
     assert oracle.cqrrpt_srrqr(A, 1.25, 4, 1e-9, 77, 1.0).status == -10
+
+
+def test_gaussian_operator_moments():
+    """The input generator's Gaussian operator has iid entries of mean 0 and
+    variance 1/d (Sec. 2.3.1): sample moments within a few standard errors,
+    and E[S^T S] = I_m shows in the column norms (mean 1)."""
+    d, m = 64, 20000
+    S = W.gaussian_operator(d, m, 99).numpy()
+    assert S.shape == (d, m)
+    n = S.size
+    assert abs(S.mean()) <= 5 / math.sqrt(n * d)
+    assert abs(S.var() * d - 1.0) <= 5 * math.sqrt(2.0 / n)
+    col = (S * S).sum(axis=0)
+    assert abs(col.mean() - 1.0) <= 5 * math.sqrt(2.0 / d / m)
+
+
+def test_cqrrpt_dense_theorem2_sketch_of_residual_vanishes():
+    """Thm. 2 with a Gaussian S: S (M_n - Q_k R_k) = 0 when rank(SM) =
+    rank(M), here on a planted rank-12 matrix."""
+    m, n = 3000, 20
+    sv = np.zeros(n)
+    sv[:12] = W.logspaced(12, -4.0).numpy()
+    A = np.asfortranarray(W.planted(m, n, sv, 71).numpy())
+    S = np.asfortranarray(W.gaussian_operator(25, m, 72).numpy())
+    res = oracle.cqrrpt_dense(A, S, 1e-10)
+    assert res.k == 12
+    D = A[:, res.J] - res.Q @ res.R
+    assert np.linalg.norm(S @ D) <= 1e-13 * np.linalg.norm(S @ A)

@@ -449,9 +449,9 @@ def sketch_dense(A, S, split=False, handle=None, stream=None):
     if S.shape[1] != m:
         raise ValueError("S must be d x m")
     out = colmajor_empty(d, n, A.device)
-    fn = lib().cqrrpt_sketch_dense_split_d if split else lib().cqrrpt_sketch_dense_d
-    _check(fn(h.h, m, n, A.data_ptr(), _ld(A), d, S.data_ptr(), _ld(S), out.data_ptr(), _ld(out),
-              _stream(stream)), "cqrrpt_sketch_dense_d")
+    name = "cqrrpt_sketch_dense_split_d" if split else "cqrrpt_sketch_dense_d"
+    _check(getattr(lib(), name)(h.h, m, n, A.data_ptr(), _ld(A), d, S.data_ptr(), _ld(S),
+                                out.data_ptr(), _ld(out), _stream(stream)), name)
     return out
 
 

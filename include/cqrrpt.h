@@ -457,6 +457,21 @@ int cqrrpt_phase_times(cqrrpt_handle h, float* ms_host, int nphases);
 /* Number of kernels this library has launched in this process. */
 long long cqrrpt_kernel_launches(void);
 
+/* Bounds of the device-side waits on the current device, for tests of the
+ * timeout path (the paper has no counterpart).  grid_spins: polls of the
+ * QRCP's grid barrier (Alg. 2 line 2, multi-CTA) before a CTA gives up;
+ * tensor_wait_ns: nanoseconds an mbarrier wait of the tensor-core engine
+ * (CQRRPT_SPLITBF16*) waits before it gives up.  0 restores each default
+ * (2^25 polls; 2 s).  A wait that gives up records CQRRPT_TIMEOUT in the
+ * call's status (read by cqrrpt_last_status or returned through k_host);
+ * the kernels then leave cleanly: the engine waits, with the default bound,
+ * for its copies and products in flight and releases its tensor memory, and
+ * every later kernel of the call sees the status and does nothing.  The
+ * next call starts from a clean state.  Process-wide per device, not tied
+ * to a handle; do not change it while calls are in flight.  Returns 0, -1 /
+ * -2 for a negative argument, or CQRRPT_CUDA_ERROR. */
+int cqrrpt_set_wait_limits(int64_t grid_spins, int64_t tensor_wait_ns);
+
 /* ---- single steps of Alg. 2 (same kernels as cqrrpt_d) ------------------ */
 
 /* Line 1: M^sk = S M, S the SASO of (seed, d, nnz_per_col).  Ask: d x n,
@@ -466,28 +481,43 @@ int cqrrpt_sketch_d(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
                     int64_t d, int nnz_per_col, uint64_t seed, double* Ask, int64_t ldsk,
                     cudaStream_t stream);
 
-/* Line 1 without any allocation (the paper has no counterpart: this is a
- * deployment variant).  For callers that cannot allocate device memory
- * when they sketch -- code inside a pre-sized, locked memory pool, or hosts
- * that may not create a handle because a handle owns a workspace -- this
- * computes exactly what cqrrpt_sketch_d computes (same kernels, same bits)
- * but needs no handle: its scratch is one file-scope device array of
- * 32 MiB that every GPU loading this library holds until the process exits.
- * It calls no cudaMalloc/cudaFree.  Problems whose sketch scratch exceeds
- * cqrrpt_sketch_noalloc_max_bytes() (about (m/4096 + 1) * n * d * 8 bytes
- * plus the S lists) return CQRRPT_TOO_LARGE.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All
- * calls on a device share the array and it keeps the last call's contents;
- * calls whose executions overlap on the GPU race on it and must not be
- * issued.  Arguments as cqrrpt_sketch_d without the handle (argument
- * numbers shift by one: m is argument 1).  The device is the current one. */
+/* The sketch S A without any allocation (a deployment variant with the same
+ * result as cqrrpt_sketch_d; the paper has no counterpart).  For callers
+ * that cannot allocate device memory when they sketch -- code inside a
+ * pre-sized, locked memory pool, or hosts that may not create a handle
+ * because a handle owns a workspace -- this computes exactly what
+ * cqrrpt_sketch_d computes (same kernels, same bits) but needs no handle:
+ * its scratch is one file-scope device array of 32 MiB that every GPU
+ * loading this library holds until the process exits.  It calls no
+ * cudaMalloc/cudaFree.  The scratch a problem needs is, with
+ * nb = ceil(m / 4096) and a256(x) = x rounded up to a multiple of 256,
+ *     a256(nb (d + 1) 4) + a256(nb 4096 nnz_per_col 4) + a256(nb n d 8)
+ * bytes; above cqrrpt_sketch_noalloc_max_bytes() the call returns
+ * CQRRPT_TOO_LARGE before any work is queued.  The first call in each CUDA
+ * context of a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it with the
+ * context's id (a context created again after cudaDeviceReset is looked up
+ * afresh); make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents; calls whose
+ * executions overlap on the GPU race on it and must not be issued.  A
+ * non-finite entry of A sets the status word in the array, which
+ * cqrrpt_sketch_noalloc_status reads.  Arguments as cqrrpt_sketch_d without
+ * the handle (argument numbers shift by one: m is argument 1).  The device
+ * is the current one. */
 int cqrrpt_sketch_noalloc_d(int64_t m, int64_t n, const double* A, int64_t lda, int64_t d,
                             int nnz_per_col, uint64_t seed, double* Ask, int64_t ldsk,
                             cudaStream_t stream);
 
 /* Largest sketch scratch (bytes) cqrrpt_sketch_noalloc_d accepts. */
 size_t cqrrpt_sketch_noalloc_max_bytes(void);
+
+/* Status of the last cqrrpt_sketch_noalloc_d queued on the current device,
+ * read in stream order: copies the status word of the fixed scratch array
+ * into *status_host (pageable host memory is fine) on `stream` and waits
+ * for the stream.  *status_host = 0 (CQRRPT_OK) or CQRRPT_NONFINITE (A held
+ * a NaN or an infinity).  Allocates nothing.  Returns 0, -2 (status_host
+ * NULL) or CQRRPT_CUDA_ERROR. */
+int cqrrpt_sketch_noalloc_status(cudaStream_t stream, int* status_host);
 
 /* Line 2: QRCP of X (d x n, ldx >= d, overwritten with Householder data).
  * J: n int64 pivots; Rsk: n x n (ldr >= n) sign-normalised R^sk (diagonal

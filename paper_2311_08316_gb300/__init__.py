@@ -63,6 +63,7 @@ def lib():
     L.cqrrpt_set_profiling.argtypes = [_p, _int]
     L.cqrrpt_phase_times.argtypes = [_p, ctypes.POINTER(ctypes.c_float), _int]
     L.cqrrpt_kernel_launches.argtypes = []
+    L.cqrrpt_set_wait_limits.argtypes = [_i64, _i64]
     L.cqrrpt_kernel_launches.restype = ctypes.c_longlong
     L.cqrrpt_batched_d.argtypes = [_p, _int, _p, _p, _p, _p, _d, _int, _p, _p, _int, _p, _p, _p,
                                    _p, _p, _p, _p, _p]
@@ -113,7 +114,8 @@ def exported_symbols():
             "cqrrpt_gram_split_d", "cqrrpt_trsm_split_d", "cqrrpt_host_pipeline_d",
             "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d", "cqrrpt_dense_d",
             "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d",
-            "cqrrpt_sketch_dense_split_d"]
+            "cqrrpt_sketch_dense_split_d", "cqrrpt_set_wait_limits", "cqrrpt_sketch_noalloc_d",
+            "cqrrpt_sketch_noalloc_max_bytes", "cqrrpt_sketch_noalloc_status"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -122,6 +124,15 @@ PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "t
 def kernel_launches():
     """Kernels launched by the library so far in this process."""
     return int(lib().cqrrpt_kernel_launches())
+
+
+def set_wait_limits(grid_spins=0, tensor_wait_ns=0):
+    """Bounds of the device-side waits on the current device (0 = default):
+    polls of the QRCP's grid barrier and nanoseconds of a tensor-core engine
+    wait.  Short bounds make a factorisation end with CQRRPT_TIMEOUT (status
+    5); a test hook of the timeout path."""
+    _check(lib().cqrrpt_set_wait_limits(int(grid_spins), int(tensor_wait_ns)),
+           "cqrrpt_set_wait_limits")
 
 
 def _check(rc, what):

@@ -1636,6 +1636,17 @@ int cqrrpt_phase_times(cqrrpt_handle h, float* ms_host, int nphases) {
 
 long long cqrrpt_kernel_launches(void) { return g_launches.load(); }
 
+int cqrrpt_set_wait_limits(int64_t grid_spins, int64_t tensor_wait_ns) {
+  if (grid_spins < 0) return -1;
+  if (tensor_wait_ns < 0) return -2;
+  if (qrcp_set_spin_limit((unsigned long long)grid_spins) != cudaSuccess ||
+      oz_set_wait_ns((unsigned long long)tensor_wait_ns) != cudaSuccess) {
+    cudaGetLastError();
+    return kCudaError;
+  }
+  return kOk;
+}
+
 const char* cqrrpt_status_string(int status) {
   switch (status) {
     case kOk: return "success";

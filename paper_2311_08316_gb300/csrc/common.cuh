@@ -50,14 +50,16 @@ __device__ __forceinline__ double warp_tree_sum32(double v) {
 }
 
 // Grid-wide barrier for cooperative launches: arrival counter plus a
-// generation word.  Waits are bounded: after kSpinLimit polls the CTA sets
-// *status = kTimeout and returns false.
+// generation word.  Waits are bounded: after spin_limit polls (kSpinLimit
+// unless a test lowered it) the CTA sets *status = kTimeout and returns
+// false.
 struct GridBarrier {
   unsigned int count;
   unsigned int generation;
 };
 
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, int* status) {
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, int* status,
+                                          unsigned long long spin_limit = kSpinLimit) {
   __shared__ int ok_flag;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -74,7 +76,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks
       } else {
         unsigned long long spins = 0;
         while (*genp == gen) {
-          if (++spins > kSpinLimit) {
+          if (++spins > spin_limit) {
             atomicExch(status, kTimeout);
             ok = 0;
             break;

@@ -68,6 +68,9 @@ cudaError_t launch_sketch_batched(int phase, const SketchDesc* D, const int64_t*
                                   int64_t total_tiles, int max_d, cudaStream_t stream);
 
 // ---- Alg. 2 line 2 -------------------------------------------------------
+// polls of the QRCP's grid barrier before it records kTimeout, on the
+// current device; 0 restores kSpinLimit (test hook of the timeout path)
+cudaError_t qrcp_set_spin_limit(unsigned long long spins);
 int64_t qrcp_workspace_bytes(int64_t n);
 QrcpWork qrcp_carve(void* work, int n);
 // X (d x n, ld ldx) is overwritten; J (n, int64) receives the pivots;

@@ -1,4 +1,4 @@
-// Allocation-free variant of the sketch entry point (Alg. 2 line 1).
+// Allocation-free variant of the sketch entry point (the sketch S A).
 //
 // Some callers cannot allocate device memory at the time they need a
 // sketch: code running inside a memory pool that is already sized and
@@ -12,16 +12,20 @@
 // process exits.
 //
 // Host code may not use the array's name as a device address (in host code
-// it names a host-side stand-in); the device address is obtained once per
-// device with cudaGetSymbolAddress, with that device current, on the first
-// call made on that device.  That first call should therefore come before
-// any stream capture.  All calls on a device share the one array and it
-// keeps the contents of the last call; the status word is cleared at the
-// start of every call, the other scratch is fully overwritten.  Calls whose
-// executions overlap on the GPU (different streams without ordering) race on
-// the array and must not be issued.
+// it names a host-side stand-in); the device address is obtained with
+// cudaGetSymbolAddress, with the device current, on the first call made in
+// each CUDA context of a device.  The address is cached per device together
+// with the context's unique id, so a context that was destroyed and created
+// again (cudaDeviceReset) is looked up afresh.  That first call should
+// come before any stream capture.  All calls on a device share the one
+// array and it keeps the contents of the last call; the status word is
+// cleared at the start of every call, the other scratch is fully
+// overwritten.  Calls whose executions overlap on the GPU (different
+// streams without ordering) race on the array and must not be issued.
 #include <cmath>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/cqrrpt.h"
 #include "kernels.h"
@@ -37,18 +41,55 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).  Returns nullptr on failure.
+// Unique id of the current context (cuCtxGetId through the runtime's driver
+// entry point, so the library needs no link against libcuda for it); 0 if
+// unavailable, which disables the cache.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)p;
+    cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device (looked up on
+// the first call in each context of the device).  Returns nullptr on failure.
 void* scratch_address(int device) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_ptr[device]) return g_scratch_ptr[device];
+  const unsigned long long ctx = current_context_id();
+  if (g_scratch_ptr[device] && ctx != 0 && ctx == g_scratch_ctx[device])
+    return g_scratch_ptr[device];
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   g_scratch_ptr[device] = p;
+  // the lookup has made the runtime create and bind the context if it did
+  // not exist yet; a context id of 0 (unknown) keeps the cache off
+  g_scratch_ctx[device] = current_context_id();
   return p;
 }
 
@@ -82,6 +123,22 @@ int cqrrpt_sketch_noalloc_d(int64_t m, int64_t n, const double* A, int64_t lda, 
   if (cqrrpt::launch_sketch(m, n, A, lda, (int)d, nnz_per_col, seed, scale, Ask, ldsk,
                             base + kStatusBytes, status, stream) != cudaSuccess)
     return CQRRPT_CUDA_ERROR;
+  return CQRRPT_OK;
+}
+
+int cqrrpt_sketch_noalloc_status(cudaStream_t stream, int* status_host) {
+  if (!status_host) return -2;
+  int device = -1;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)
+    return CQRRPT_CUDA_ERROR;
+  unsigned char* base = (unsigned char*)scratch_address(device);
+  if (!base) return CQRRPT_CUDA_ERROR;
+  if (cudaMemcpyAsync(status_host, base, sizeof(int), cudaMemcpyDeviceToHost, stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess) {
+    cudaGetLastError();
+    return CQRRPT_CUDA_ERROR;
+  }
   return CQRRPT_OK;
 }
 

@@ -39,6 +39,9 @@ struct OzGemm {
 
 // tcgen05 engine (ozaki_tc.cu)
 cudaError_t oz_gemm_tc_launch(const OzGemm& G, cudaStream_t s);
+// bound (ns) of the tensor-core engine's pipeline waits on the current
+// device; 0 restores the default (test hook of the timeout path)
+cudaError_t oz_set_wait_ns(unsigned long long ns);
 cudaError_t oz_gemm_launch(const OzGemm& G, cudaStream_t s);
 // many products in one launch: jobs, their two TMA maps each (A, B; 64-byte
 // aligned CUtensorMap objects in device memory) and the CTA prefix table

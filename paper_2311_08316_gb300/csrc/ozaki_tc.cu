@@ -115,15 +115,41 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait for the phase of parity `parity` to complete: gives up after
-// kTcWaitNs of wall time (a pipeline step of this kernel takes microseconds)
-// or kSpinLimit polls, whichever comes first.
+// limit_ns of wall time (kTcWaitNs by default; a pipeline step of this
+// kernel takes microseconds) or kSpinLimit polls, whichever comes first.
+// A limit below the default (set by cqrrpt_set_wait_limits, a test hook of
+// the timeout path) polls without blocking and reads the clock every poll,
+// so that a phase that is not already complete runs the limit out.
+// g_tc_wait_ns bounds the pipeline's own waits; the waits of the clean-up
+// after a timeout (copies and products in flight) always take kTcWaitNs.
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ unsigned long long g_tc_wait_ns = kTcWaitNs;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          unsigned long long limit_ns = kTcWaitNs) {
   const unsigned long long t0 = global_ns();
+  if (limit_ns < kTcWaitNs) {
+    for (unsigned long long i = 0; i < kSpinLimit; ++i) {
+      if (mbar_test_wait(bar, parity)) return true;
+      if (global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+  }
   for (unsigned long long i = 0; i < kSpinLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > kTcWaitNs) return false;
+    if ((i & 255) == 255 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -290,6 +316,7 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
   const int run = nchunks == 1 ? max(1, kTcChunkStages / nk) : 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long wait_ns = g_tc_wait_ns;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(full_bar(s), 1);
@@ -337,7 +364,7 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
       const int q = s - p;
       const int kst_end = min(nk, (c + 1) * kTcChunkStages);
       for (int kst = c * kTcChunkStages; kst < kst_end; ++kst) {
-        if (!mbar_wait(empty_bar(stage), phase ^ 1u)) {
+        if (!mbar_wait(empty_bar(stage), phase ^ 1u, wait_ns)) {
           record_timeout(G.err);
           ok = false;
           break;
@@ -389,7 +416,7 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
         int s = 2;
         while ((s - 1) * s / 2 <= pi) ++s;
         const int run_end = min(pi + run, (s - 1) * s / 2);  // same level only
-        if (!mbar_wait(acce_bar(buf), ((use >> buf) & 1u) ^ 1u)) {
+        if (!mbar_wait(acce_bar(buf), ((use >> buf) & 1u) ^ 1u, wait_ns)) {
           record_timeout(G.err);
           ok = false;
           break;
@@ -399,7 +426,7 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
         const int st_n = min(kTcChunkStages, nk - c * kTcChunkStages);
         for (int pr = pi; pr < run_end && ok; ++pr) {
           for (int j = 0; j < st_n; ++j) {
-            if (!mbar_wait(full_bar(stage), phase)) {
+            if (!mbar_wait(full_bar(stage), phase, wait_ns)) {
               record_timeout(G.err);
               ok = false;
               break;
@@ -455,7 +482,7 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
         int s = 2;
         while ((s - 1) * s / 2 <= pi) ++s;
         const int run_end = min(pi + run, (s - 1) * s / 2);  // same level only
-        if (!mbar_wait(accf_bar(buf), (fph >> buf) & 1u)) {
+        if (!mbar_wait(accf_bar(buf), (fph >> buf) & 1u, wait_ns)) {
           record_timeout(G.err);
           ok = false;
           break;
@@ -602,6 +629,13 @@ bool plane_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_
 }
 
 }  // namespace
+
+// Test hook of the timeout path (cqrrpt_set_wait_limits): bound of the
+// engine's pipeline waits on the current device; 0 restores kTcWaitNs.
+cudaError_t oz_set_wait_ns(unsigned long long ns) {
+  const unsigned long long v = ns ? ns : kTcWaitNs;
+  return cudaMemcpyToSymbol(g_tc_wait_ns, &v, sizeof(v));
+}
 
 static cudaError_t tc_attributes() {
   static bool attr = false;

@@ -29,6 +29,15 @@
 
 namespace cqrrpt {
 
+// Polls of a grid barrier before it gives up (kTimeout); lowered only by
+// cqrrpt_set_wait_limits, a test hook for the timeout path.
+__device__ unsigned long long g_grid_spin_limit = kSpinLimit;
+
+cudaError_t qrcp_set_spin_limit(unsigned long long spins) {
+  const unsigned long long v = spins ? spins : kSpinLimit;
+  return cudaMemcpyToSymbol(g_grid_spin_limit, &v, sizeof(v));
+}
+
 QrcpWork qrcp_carve(void* work, int n) {
   char* p = (char*)work;
   QrcpWork w;
@@ -81,6 +90,7 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
   __shared__ int red_col[32];
 
   if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
+  const unsigned long long spins = g_grid_spin_limit;
 
   // initial norms of owned columns
   for (int q = warp;; q += nwarps) {
@@ -122,7 +132,7 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
   };
   __syncthreads();
   publish_candidate(-1);
-  if (!grid_sync(&sc->bar, G, status)) return;
+  if (!grid_sync(&sc->bar, G, status, spins)) return;
 
   for (int j = 0; j < n; ++j) {
     // 1. global pivot
@@ -188,7 +198,7 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
       w.phys[j] = P;
       w.posof[P] = j;
     }
-    if (!grid_sync(&sc->bar, G, status)) return;
+    if (!grid_sync(&sc->bar, G, status, spins)) return;
 
     // 3. apply H to owned unpivoted columns, downdate norms
     const double tau = __ldcg(w.tau + j);
@@ -233,7 +243,7 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
     }
     __syncthreads();
     publish_candidate(j);
-    if (!grid_sync(&sc->bar, G, status)) return;
+    if (!grid_sync(&sc->bar, G, status, spins)) return;
   }
 }
 
@@ -312,6 +322,7 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
   __shared__ int red_col[32];
 
   if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
+  const unsigned long long spins = g_grid_spin_limit;
 
   // owned column q: shared memory for q < ncached, else its column of X
   auto colptr = [&](int q) -> double* {
@@ -372,7 +383,7 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
     }
   };
   publish_candidate(-1);
-  bool ok = grid_sync(&sc->bar, G, status);
+  bool ok = grid_sync(&sc->bar, G, status, spins);
 
   for (int j = 0; ok && j < n; ++j) {
     // beta of the previous pivot, if its column lives in X: every CTA has
@@ -520,7 +531,7 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
     }
     __syncthreads();
     publish_candidate(j);
-    if (!grid_sync(&sc->bar, G, status)) { ok = false; break; }
+    if (!grid_sync(&sc->bar, G, status, spins)) { ok = false; break; }
   }
   // write the owned columns back (also after an early exit, so that global
   // memory holds this CTA's last state) and, from CTA 0, the maps

@@ -176,3 +176,47 @@ def test_batched_split_bf16_matches_single_split_and_oracle(C):
             bound = 1e-12 if r.k == n else max(1e-12, 10e-15 * np.sqrt(m * n) / np.linalg.norm(A))
             assert np.linalg.norm(AJ - Q @ R) / np.linalg.norm(A) <= bound, i
             assert np.linalg.norm(Q.T @ Q - np.eye(r.k), 2) <= 1e-12, i
+
+
+def pick_uneven(count=16):
+    """Problems of the batched workload itself (workloads.batch_uneven: m in
+    [4096, 65536], n in [32, 256], planted rank in [n/2, n]): the four with the
+    largest sketches n^2 d (their batched QRCP keeps columns in global
+    memory), the tallest one, then every 47th of the list."""
+    ws = W.batch_uneven(count=512)
+    by_size = sorted(range(len(ws)), key=lambda i: -(ws[i].n ** 2 * ws[i].d))
+    pick = []
+    for i in by_size[:4] + [max(range(len(ws)), key=lambda i: ws[i].m)] + list(range(0, 512, 47)):
+        if i not in pick:
+            pick.append(i)
+    return [ws[i] for i in pick[:count]]
+
+
+@pytest.mark.slow
+def test_batched_uneven_workload_sizes(C):
+    import split_bounds
+    ws = pick_uneven(16)
+    assert len(ws) == 16
+    assert any(w.n >= 200 and w.m >= 32768 for w in ws)
+    # the largest sketches do not fit one CTA's shared memory
+    assert max(w.d * w.n * 8 for w in ws) > 227 * 1024
+    As = [w.matrix("cuda") for w in ws]
+    tols = [w.tol for w in ws]
+    seeds = [w.sketch_seed for w in ws]
+    refs = [oracle.cqrrpt(np.asfortranarray(A.cpu().numpy()), w.gamma, w.nnz, w.tol,
+                          w.sketch_seed) for A, w in zip(As, ws)]
+    h = C.Handle()
+    res, _, _ = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, handle=h)
+    res_t, _, _, _ = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, handle=h, autotune=True)
+    for i, (r, rt, ref) in enumerate(zip(res, res_t, refs)):
+        assert r.status == ref.status == 0 and r.k == ref.k, (i, r.status, r.k, ref.k)
+        for x in (r, rt):
+            assert bits_equal(host(x.J), ref.J), i
+            assert bits_equal(host(x.Q), ref.Q) and bits_equal(host(x.R), ref.R), i
+    sp, _, _ = C.cqrrpt_batched(As, 1.25, 4, tols, seeds, precision=C.SPLITBF16, handle=h)
+    for i, (r, ref, w) in enumerate(zip(sp, refs, ws)):
+        assert r.status == 0 and r.k == ref.k, (i, r.status, r.k, ref.k)
+        assert bits_equal(host(r.J), ref.J), i
+        rq, rr = split_bounds.ratios(r.Q, r.R, ref.Q, ref.R, ref.Rsk, w.m)
+        assert rq <= 4.0 and rr <= 4.0, (i, w.m, w.n, rq, rr)
+    h.close()

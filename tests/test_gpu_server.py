@@ -134,3 +134,42 @@ def test_server_wide_fp64_requests_take_single_path(C):
         assert np.array_equal(Q.view(np.uint64), ref.Q.view(np.uint64))
         assert np.array_equal(R.view(np.uint64), ref.R.view(np.uint64))
     srv.close()
+
+
+@pytest.mark.slow
+def test_server_large_requests_both_precisions(C):
+    # requests up to m = 2^17 and n = 512 (the serving mix reaches m = 2^20,
+    # n = 512), wide ones on the single-problem route, narrow ones batched,
+    # FP64 and split-BF16 interleaved
+    import split_bounds
+    shapes = [(1 << 17, 512, 0, 0), (1 << 16, 300, 2, 0), (100000, 256, 0, 180),
+              (70000, 200, 2, 0), (1 << 17, 64, 0, 0), (50000, 128, 2, 90), (30000, 33, 0, 0),
+              (9000, 17, 2, 0)]
+    reqs = []
+    for i, (m, n, prec, r) in enumerate(shapes):
+        sv = np.zeros(n)
+        if r:
+            sv[:r] = W.logspaced(r, -6.0).numpy()
+        else:
+            sv = W.logspaced(n, -9.0).numpy()
+        A = np.asfortranarray(W.planted(m, n, sv, 5100 + i, noise=(1e-15 if r else 0.0)).numpy())
+        reqs.append((A, 1e-9 if r else 1e-12, 8100 + i, prec))
+    srv = C.Server(hbm_budget_bytes=8 << 30, max_inflight=16)
+    tickets = [srv.submit(pinned_colmajor(A), tol, seed, precision=prec)
+               for A, tol, seed, prec in reqs]
+    srv.drain(timeout_us=600_000_000)
+    assert srv.stats()["completed"] == len(reqs)
+    for t, (A, tol, seed, prec) in zip(tickets, reqs):
+        fac, res = srv.poll(t)
+        ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+        assert res.status == ref.status == 0 and res.k == ref.k, (A.shape, res.status, res.k)
+        assert np.array_equal(fac.J.numpy(), ref.J)
+        Q = np.asfortranarray(fac.Q.numpy())
+        R = np.asfortranarray(fac.R.numpy())
+        if prec == 0:
+            assert np.array_equal(Q.view(np.uint64), ref.Q.view(np.uint64)), A.shape
+            assert np.array_equal(R.view(np.uint64), ref.R.view(np.uint64)), A.shape
+        else:
+            rq, rr = split_bounds.ratios(Q, R, ref.Q, ref.R, ref.Rsk, A.shape[0])
+            assert rq <= 4.0 and rr <= 4.0, (A.shape, rq, rr)
+    srv.close()

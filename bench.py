@@ -10,10 +10,14 @@ Prints one JSON line (rank 0).  `value` is factorisations/s over all ranks
 with A resident in HBM; `e2e` is the same metric through the public API with
 host buffers (pinned host -> device copy of A, device -> host copy of Q, R,
 J, k every step), measured through cqrrpt_host_pipeline_d, whose copies
-overlap the factorisations of neighbouring steps.  Under torchrun each rank factors its own independent
-problem (the factorisations do not exchange data): weak scaling, no
-collective on the data path.  `--impl reference` times the CPU oracle on a
-row sample of the same workload.
+overlap the factorisations of neighbouring steps.  Under torchrun each rank
+factors its own independent problem (the factorisations do not exchange
+data): weak scaling, no collective on the data path.  At N = 1 the line also
+carries `configs`: the small (4096 x 64) latency case, the mixed-precision
+case (2^20 x 512), the 512-problem batch and a shortened serving run,
+measured in the same run (--configs none leaves them out).
+`--impl reference` times the CPU oracle on the full headline workload, one
+of its eight phases per step (OracleSteps).
 """
 import argparse
 import json
@@ -54,9 +58,10 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--rows", type=int, default=131072, help="m of the workload")
     p.add_argument("--workload", default="single",
-                   choices=["single", "batched", "mixed", "serve", "dense", "panels",
+                   choices=["single", "small", "batched", "mixed", "serve", "dense", "panels",
                             "srrqr"],
-                   help="single: the rank-800 131072 x 1024 problem (headline); batched: 512 "
+                   help="single: the rank-800 131072 x 1024 problem (headline); small: the "
+                        "4096 x 64 cond-1e8 problem (latency per factorisation); batched: 512 "
                         "uneven problems in one batched pass; mixed: 1048576 x 512, cond 1e10, "
                         "split-BF16 modes against FP64; serve: a Poisson stream of mixed-size "
                         "requests through the continuous-batching server; dense: the "
@@ -64,6 +69,9 @@ def parse():
                         "panels: the headline matrix streamed from pinned host memory in row "
                         "panels; srrqr: the headline matrix with the strong rank-revealing "
                         "exchanges on the sketch")
+    p.add_argument("--configs", default="all", choices=["all", "none"],
+                   help="single workload, N = 1: also measure the small, mixed, batched and "
+                        "serving workloads in the same run (all) or only the headline (none)")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--requests", type=int, default=600, help="serve: requests in the open loop")
     p.add_argument("--pool", type=int, default=32, help="serve: distinct matrices")
@@ -170,33 +178,135 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- reference arm
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def cpu_threads():
+    """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS, else every
+    core the process may run on)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.isdigit():
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+ORACLE_PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
+
+
+class OracleSteps:
+    """The oracle's CQRRPT (Alg. 1 + Alg. 2) cut into its eight public phase
+    calls, made in the order oracle_cqrrpt makes them: the sketch (line 1),
+    the QRCP (2), the rank rule (3), M^pre (4), the Gram (5), the Cholesky
+    with Remark 4 and the second rank stage (6), Q (7), R (8).  run(i) makes
+    phase i; after phase 7 `result` holds (Q, R, J, k) of one factorisation
+    and the next run(0) starts another."""
+
+    def __init__(self, M, gamma, nnz, tol, seed):
+        import oracle
+        self.o = oracle
+        self.M, self.gamma, self.nnz, self.tol, self.seed = M, gamma, nnz, tol, seed
+        self.result = None
+
+    def run(self, i):
+        o, st = self.o, self
+        m, n = st.M.shape
+        if i == 0:
+            st.d = o.sketch_dim(n, st.gamma)
+            st.Msk, st.status = o.sketch(st.M, st.d, st.nnz, st.seed)
+            st.k = 0
+        elif i == 1:
+            if st.status == 0:
+                st.Rsk, st.J = o.qrcp(st.Msk)[:2]
+        elif i == 2:
+            if st.status == 0:
+                st.stage2 = not (st.tol > 0.0)
+                st.k = o.rank_stage1(st.Rsk) if st.stage2 else o.rank_tol(st.Rsk, st.tol)
+        elif i == 3:
+            if st.status == 0 and st.k > 0:
+                st.X = o.trsm_rut(st.M, st.Rsk[:st.k, :st.k], st.J)
+        elif i == 4:
+            if st.status == 0 and st.k > 0:
+                st.G = o.gram(st.X)
+        elif i == 5:
+            if st.status == 0 and st.k > 0:
+                st.Rpre, fail = o.potrf_upper(st.G)
+                kc = fail if fail >= 0 else st.k
+                if st.stage2 and kc > 0:
+                    kc = o.rank_stage2(kc, st.Rpre)
+                st.k = kc
+        elif i == 6:
+            if st.status == 0 and st.k > 0:
+                st.Q = o.trsm_rut(st.X, st.Rpre[:st.k, :st.k])
+        elif i == 7:
+            if st.status == 0 and st.k > 0:
+                R = o.trmm_upper(st.Rpre[:st.k, :st.k], st.Rsk[:st.k, :])
+                st.result = (st.Q, R, st.J, st.k)
+            else:
+                st.result = (None, None, getattr(st, "J", None), 0)
+            st.X = st.G = None
+
+
 def run_reference(args, world, rank):
+    """The oracle, as it stands, on the full headline workload (m = 131072,
+    n = 1024, planted rank 800), on the host cores.  Step i makes phase
+    i mod 8 of a factorisation (OracleSteps), so a factorisation spans eight
+    consecutive steps and the whole --warmup + --steps run stays within a few
+    minutes; value = 1 / (sum over the eight phases of the mean time of that
+    phase in the timed steps): factorisations/s of the full workload, no
+    extrapolation."""
     if rank != 0:
         return
-    import oracle
     w = W.single_large(m=args.rows)
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    m_s = min(32768, w.m)
-    A = np.asfortranarray(W.planted(w.m, w.n, w.sv, w.seed, w.noise, dev).cpu().numpy()[:m_s])
-    times = []
+    A = np.asfortranarray(W.planted(w.m, w.n, w.sv, w.seed, w.noise, dev).cpu().numpy())
+    steps = OracleSteps(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
+    phase_ms = {p: [] for p in ORACLE_PHASES}
+    step_ms = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed)
-        dt = time.perf_counter() - t0
+        steps.run(i % 8)
+        dt = (time.perf_counter() - t0) * 1e3
         if i >= args.warmup:
-            times.append(dt)
-    t = sum(times) / len(times)
-    value = (m_s / w.m) / t
-    cores = os.cpu_count()
-    sample = ("oracle CQRRPT on the first %d of %d rows (n=%d, same gamma, nnz, tol, seed; "
-              "k=%d); factorisations/s extrapolated linearly in m" % (m_s, w.m, w.n, r.k))
+            step_ms.append(dt)
+            phase_ms[ORACLE_PHASES[i % 8]].append(dt)
+    if all(phase_ms.values()):
+        fact_ms = sum(statistics.mean(v) for v in phase_ms.values())
+        how = "1 / sum of the eight phases' mean times"
+    else:  # fewer than eight timed steps: steps / 8 factorisations over the time
+        fact_ms = sum(step_ms) * 8.0 / len(step_ms)
+        how = "(steps / 8) factorisations over the timed seconds"
+    value = 1e3 / fact_ms
+    threads = cpu_threads()
+    sample = ("the full workload (%d x %d); step i makes phase i mod 8 (%s) of the oracle's "
+              "factorisation, so 8 consecutive steps are one factorisation; value = %s"
+              % (w.m, w.n, ", ".join(ORACLE_PHASES), how))
     line = {"metric": "cqrrpt_factorizations_per_s", "value": value, "unit": "factorizations/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": statistics.mean(step_ms), "ms_per_factorization": fact_ms,
+            "phase_ms": {p: (statistics.mean(v) if v else None) for p, v in phase_ms.items()},
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": config_of(w),
-            "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "factorizations/s", "cores": threads,
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "factorizations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -213,6 +323,82 @@ def cqrrpt_flops(m, n, d, k, s):
     m*s*n additions."""
     return (2.0 * m * k * k + m * k * (k + 1) + 4.0 * d * n * k - 2.0 * k * k * (d + n)
             + 5.0 * k ** 3 / 3.0 + float(m) * s * n)
+
+
+def run_small(args, world, rank, local, C):
+    """The small full-rank problem (m = 4096, n = 64, sv 1 -> 1e-8 log-spaced,
+    SASO d = 128 with 4 nonzeros per column, tol 1e-12): a launch-bound
+    factorisation.  Latency per call two ways: device span of each call
+    between CUDA events on its stream (calls queued back to back), and host
+    wall time of a synchronous call (k read back), p50 / p99 over the calls;
+    throughput of back-to-back calls.  Parity: bit-identical to the oracle."""
+    import oracle
+    w = rank_workload(W.single_small(), rank)
+    m, n = w.m, w.n
+    A = w.matrix("cuda")
+    h = C.Handle(local)
+    Q = C.colmajor_empty(m, n)
+    R = C.colmajor_empty(n, n)
+    J = torch.empty(n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def call(sync):
+        return C.cqrrpt(A, w.gamma, w.nnz, w.tol, w.sketch_seed, out=(Q, R, J), handle=h,
+                        stream=stream, sync=sync)
+
+    for _ in range(max(3, args.warmup)):
+        res = call(True)
+    assert res.status == 0 and res.k == n
+    calls = max(200, args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = C.kernel_launches()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * calls)]
+    t0 = time.perf_counter()
+    for i in range(calls):
+        evs[2 * i].record(stream)
+        call(False)
+        evs[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = C.kernel_launches() - launches0
+    dev_us = [evs[2 * i].elapsed_time(evs[2 * i + 1]) * 1e3 for i in range(calls)]
+    host_us = []
+    for _ in range(calls):
+        t1 = time.perf_counter()
+        call(True)
+        host_us.append((time.perf_counter() - t1) * 1e6)
+    clk = clocks.stop()
+    st, k = h.last_status()
+    assert st == 0 and k == n
+    wall = max_over_ranks(wall, world)
+    value = world * calls / wall
+    ref = oracle.cqrrpt(np.asfortranarray(A.cpu().numpy()), w.gamma, w.nnz, w.tol, w.sketch_seed)
+    same = (ref.k == k and np.array_equal(ref.J, J.cpu().numpy())
+            and np.array_equal(ref.Q.view(np.uint64),
+                               np.asfortranarray(Q[:, :k].cpu().numpy()).view(np.uint64))
+            and np.array_equal(ref.R.view(np.uint64),
+                               np.asfortranarray(R[:k].cpu().numpy()).view(np.uint64)))
+    flops = cqrrpt_flops(m, n, w.d, n, w.nnz)
+    h.close()
+    return {"metric": "cqrrpt_factorizations_per_s", "value": value, "unit": "factorizations/s",
+            "n_gpus": world, "steps": calls, "warmup": max(3, args.warmup),
+            "ms_per_step": wall * 1e3 / calls, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "m": m, "n": n, "d": w.d, "nnz_per_col": w.nnz,
+                       "gamma": w.gamma, "tol": w.tol, "precision": "fp64",
+                       "l2": "A = 2 MiB is L2-resident between calls (latency case), no flush"},
+            "latency_us": {"device_p50": float(np.percentile(dev_us, 50)),
+                           "device_p99": float(np.percentile(dev_us, 99)),
+                           "host_sync_p50": float(np.percentile(host_us, 50)),
+                           "host_sync_p99": float(np.percentile(host_us, 99))},
+            "gflops_algorithmic": value * flops / 1e9,
+            "fp64_fraction": value * flops / 1e9 / FP64_PEAK_GFLOPS,
+            "parity_vs_oracle": "bit-identical J, k, Q, R" if same else "MISMATCH",
+            "gpu_launches": int(launches), "clocks": clk}
 
 
 def run_batched(args, world, rank, local, C):
@@ -348,8 +534,7 @@ def run_batched(args, world, rank, local, C):
                                           "batch by the Sec. 2.1 flop count" % (len(sample), len(ws), t_cpu)}
         line["parity_vs_oracle"] = ("bit-identical J, k, Q, R on %d sampled problems" % len(sample)
                                     if same else "MISMATCH")
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_mixed(args, world, rank, local, C):
@@ -365,6 +550,8 @@ def run_mixed(args, world, rank, local, C):
     stream = torch.cuda.current_stream()
     out = {}
     results = {}
+    clocks = ClockSampler(local)
+    clocks.start()
     for prec, name in [(C.FP64, "fp64"), (C.SPLITBF16, "splitbf16"),
                        (C.SPLITBF16_CHOLQR2, "splitbf16_cholqr2")]:
         Q = C.colmajor_empty(m, n)
@@ -417,6 +604,7 @@ def run_mixed(args, world, rank, local, C):
         del Qr, Rr, Jr
     except Exception as ex:  # reported, not hidden
         out["fp64_rcholqr"] = {"error": str(ex)}
+    clk = clocks.stop()
     Rf = results["fp64"][1][: results["fp64"][3]]
     for name in ("splitbf16", "splitbf16_cholqr2"):
         Rs = results[name][1][: results[name][3]]
@@ -433,10 +621,9 @@ def run_mixed(args, world, rank, local, C):
                        "gamma": w.gamma, "tol": w.tol, "cond": 1e10,
                        "l2": "inputs larger than L2 (A = %.1f GiB), no flush" % (m * n * 8 / 2**30)},
             "gflops_2mn2": best["factorizations_per_s"] * 2.0 * m * n * n / 1e9,
-            "modes": out,
+            "modes": out, "clocks": clk,
             "note": "FP64 mode is bit-identical to the oracle (tests); differences are vs that"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_dense(args, world, rank, local, C):
@@ -521,8 +708,7 @@ def run_dense(args, world, rank, local, C):
             "modes": out,
             "note": "S is drawn once before timing (not timed); FP64 mode bit-identical to "
                     "the oracle (tests)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_panels(args, world, rank, local, C):
@@ -578,8 +764,7 @@ def run_panels(args, world, rank, local, C):
                        "d2h_bytes_per_step": 2 * m * k * 8 + k * n * 8 + n * 8},
             "modes": out, "equal_to_device_resident_bits": same,
             "note": "wall clock of the whole call (host copies included)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_srrqr(args, world, rank, local, C):
@@ -631,8 +816,7 @@ def run_srrqr(args, world, rank, local, C):
             "config": {"workload": w.name + "_strong_rrqr", "m": m, "n": n, "d": w.d,
                        "nnz_per_col": w.nnz, "tol": w.tol},
             "modes": out, "note": "wall clock per call; bit-identical to the oracle (tests)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serve(args, world, rank, local, C):
@@ -708,6 +892,7 @@ def run_serve(args, world, rank, local, C):
                   torch.empty(w.n, dtype=torch.int64, pin_memory=True))
     tickets = [None] * len(reqs)
     results = {}
+    stats0 = srv.stats()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -786,7 +971,11 @@ def run_serve(args, world, rank, local, C):
             "n_gpus": world, "steps": len(reqs), "warmup": 2 * len(pool),
             "ms_per_step": wall * 1e3 / len(reqs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 / bf16 digits -> f64", "data": "synthetic",
-            "config": {"workload": "cqrrpt_serving_poisson_m2^12-2^20_n16-512_cond1e2-1e12",
+            "config": {"workload": "cqrrpt_serving_poisson_%dreq_pool%d_m2^12-2^20_n16-512_"
+                                   "cond1e2-1e12" % (len(reqs), len(pool)),
+                       "sample": "%d requests (of the 20000-request mix) drawn from %d distinct "
+                                 "matrices of the mix, each with its own S seed and precision"
+                                 % (len(reqs), len(pool)),
                        "requests": len(reqs), "pool_matrices": len(pool),
                        "mean_A_bytes": h2d, "hbm_budget_bytes": 120 << 30, "max_inflight": 64,
                        "offered_rate_per_s": rate, "load": args.load,
@@ -798,15 +987,15 @@ def run_serve(args, world, rank, local, C):
                            "queue": pct(que)},
             "gflops_algorithmic": flops / wall / 1e9,
             "gflops_2mn2": sum(2.0 * w.m * w.n * w.n for w in ws) / wall / 1e9,
-            "waves": stats["waves"],
+            "waves": stats["waves"] - stats0["waves"],
+            "mean_wave_size": len(reqs) / max(1, stats["waves"] - stats0["waves"]),
             "e2e": {"value": throughput, "unit": "requests/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "note": "the serving loop is end to end: pinned host in, host out"},
             "parity_vs_oracle": ("%d/%d sampled requests match (fp64 bit-identical, split-BF16 "
                                  "same J/k and residuals <= 1e-12)" % (sum(par), len(par))),
             "gpu_launches": int(launches), "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------- our arm
@@ -823,28 +1012,13 @@ def main():
     import paper_2311_08316_gb300 as C
     from paper_2311_08316_gb300 import build as cbuild
     cbuild.build()
-    if args.workload == "batched":
-        run_batched(args, world, rank, local, C)
-        barrier(world)
-        return
-    if args.workload == "mixed":
-        run_mixed(args, world, rank, local, C)
-        barrier(world)
-        return
-    if args.workload == "serve":
-        run_serve(args, world, rank, local, C)
-        barrier(world)
-        return
-    if args.workload == "dense":
-        run_dense(args, world, rank, local, C)
-        barrier(world)
-        return
-    if args.workload == "panels":
-        run_panels(args, world, rank, local, C)
-        barrier(world)
-        return
-    if args.workload == "srrqr":
-        run_srrqr(args, world, rank, local, C)
+    others = {"batched": run_batched, "mixed": run_mixed, "serve": run_serve,
+              "dense": run_dense, "panels": run_panels, "srrqr": run_srrqr,
+              "small": run_small}
+    if args.workload in others:
+        line = others[args.workload](args, world, rank, local, C)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         barrier(world)
         return
 
@@ -905,8 +1079,14 @@ def main():
     trsm_ms = (statistics.mean(phases["trsm_pre"]) + statistics.mean(phases["trsm_q"])) / 2
     trsm_flops = float(m) * k * k          # k^2/2 fma per row, 2 flop each
     achieved = trsm_flops / (trsm_ms * 1e-3) / 1e9
+    try:
+        probe_gflops, _ = C.probe_fp64_gflops(local)
+    except Exception:
+        probe_gflops = None
     roof = {"kernel": "trsm_rut_kernel", "bound": "alu", "achieved": achieved,
             "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+            "peak_probe_measured": probe_gflops,
+            "frac_of_probe": (achieved / probe_gflops) if probe_gflops else None,
             "traffic": (TRSM_DRAM_BYTES_PER_ROW * m) if TRSM_DRAM_BYTES_PER_ROW else None,
             "algorithmic_flops_per_launch": trsm_flops,
             "launch_ms": trsm_ms,
@@ -1062,9 +1242,41 @@ def main():
                 and np.array_equal(ref.R.view(np.uint64),
                                    np.asfortranarray(Rh[:k, :].numpy()).view(np.uint64)))
         line["cpu_baseline"] = {"value": 1.0 / t, "unit": "factorizations/s",
-                                "cores": os.cpu_count(), "kind": "oracle",
+                                "cores": cpu_threads(), "cpu_model": cpu_model(),
+                                "kind": "oracle",
                                 "sample": "the full workload, one factorisation (%.1f s)" % t}
         line["parity_vs_oracle"] = "bit-identical J, k, Q, R" if same else "MISMATCH"
+        del Ahost, ref
+
+    # ---- the other workloads, measured in the same run (N = 1 only): the
+    # small latency case, the mixed-precision case, the batched case and a
+    # shortened serving run; each with its own clocks and parity check
+    if world == 1 and args.configs == "all":
+        import argparse as _ap
+        h.close()
+        del A_host, Qh, Rh, Jh, Ad, Q, R, J, outs, pres, out
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        subs = {}
+        plan = [("small_m4096_n64", run_small, dict(steps=200, warmup=3)),
+                ("mixed_m1048576_n512", run_mixed, dict(steps=5, warmup=1, rows=131072)),
+                ("batched_512", run_batched, dict(steps=3, warmup=2, batch=512)),
+                ("serving_poisson", run_serve, dict(steps=1, warmup=0, requests=200, pool=32,
+                                                    load=0.7))]
+        for name, fn, over in plan:
+            sub = _ap.Namespace(**vars(args))
+            for key, v in over.items():
+                setattr(sub, key, v)
+            t0 = time.perf_counter()
+            try:
+                rec = fn(sub, world, rank, local, C)
+            except Exception as ex:  # reported, not hidden
+                rec = {"error": "%s: %s" % (type(ex).__name__, ex)}
+            rec["wall_s"] = time.perf_counter() - t0
+            subs[name] = rec
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        line["configs"] = subs
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(world)

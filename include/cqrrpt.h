@@ -472,6 +472,16 @@ long long cqrrpt_kernel_launches(void);
  * -2 for a negative argument, or CQRRPT_CUDA_ERROR. */
 int cqrrpt_set_wait_limits(int64_t grid_spins, int64_t tensor_wait_ns);
 
+/* Measured FP64 fma rate of CUDA device `device` (GFLOP/s, 2 flop per fma):
+ * threads running 8, 16 or 32 independent register fma chains (the same
+ * flop count: 8 * iters fma per thread), 4 or 8 CTAs of 256 threads per SM;
+ * each shape is launched once to warm up, then timed with CUDA events; the
+ * best rate is returned.  The roofline denominator of the FP64 kernels (the
+ * paper has no counterpart).  *ms_host (may be NULL) receives the best
+ * shape's timed ms.  Returns 0, -2 (iters < 1), -3 (gflops_host NULL) or
+ * CQRRPT_CUDA_ERROR. */
+int cqrrpt_probe_fp64_gflops(int device, int iters, double* gflops_host, double* ms_host);
+
 /* ---- single steps of Alg. 2 (same kernels as cqrrpt_d) ------------------ */
 
 /* Line 1: M^sk = S M, S the SASO of (seed, d, nnz_per_col).  Ask: d x n,

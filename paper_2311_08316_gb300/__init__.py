@@ -64,6 +64,7 @@ def lib():
     L.cqrrpt_phase_times.argtypes = [_p, ctypes.POINTER(ctypes.c_float), _int]
     L.cqrrpt_kernel_launches.argtypes = []
     L.cqrrpt_set_wait_limits.argtypes = [_i64, _i64]
+    L.cqrrpt_probe_fp64_gflops.argtypes = [_int, _int, ctypes.POINTER(_d), ctypes.POINTER(_d)]
     L.cqrrpt_kernel_launches.restype = ctypes.c_longlong
     L.cqrrpt_batched_d.argtypes = [_p, _int, _p, _p, _p, _p, _d, _int, _p, _p, _int, _p, _p, _p,
                                    _p, _p, _p, _p, _p]
@@ -115,7 +116,8 @@ def exported_symbols():
             "cqrrpt_implicit_d", "cqrrpt_apply_q_d", "cqrrpt_rcholqr_d", "cqrrpt_dense_d",
             "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d",
             "cqrrpt_sketch_dense_split_d", "cqrrpt_set_wait_limits", "cqrrpt_sketch_noalloc_d",
-            "cqrrpt_sketch_noalloc_max_bytes", "cqrrpt_sketch_noalloc_status"]
+            "cqrrpt_sketch_noalloc_max_bytes", "cqrrpt_sketch_noalloc_status",
+            "cqrrpt_probe_fp64_gflops"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -133,6 +135,16 @@ def set_wait_limits(grid_spins=0, tensor_wait_ns=0):
     5); a test hook of the timeout path."""
     _check(lib().cqrrpt_set_wait_limits(int(grid_spins), int(tensor_wait_ns)),
            "cqrrpt_set_wait_limits")
+
+
+def probe_fp64_gflops(device=None, iters=1 << 15):
+    """Measured FP64 fma rate of the device (GFLOP/s) and the timed ms."""
+    dev = torch.cuda.current_device() if device is None else int(device)
+    g = _d()
+    ms = _d()
+    _check(lib().cqrrpt_probe_fp64_gflops(dev, int(iters), ctypes.byref(g), ctypes.byref(ms)),
+           "cqrrpt_probe_fp64_gflops")
+    return g.value, ms.value
 
 
 def _check(rc, what):

@@ -471,7 +471,6 @@ __device__ __forceinline__ void oz_tc_body(const CUtensorMap* tmA, const CUtenso
     const bool row_ok = row < G.M;
     const int ea = row_ok ? G.ea[row] : 0;
     double* Cbase = G.C + ks * G.c_slice + (row_ok ? row : 0);
-    const int col0 = n0 + cslice * 32;
     uint32_t fph = 0u;  // bit b: parity of accumulator b's next completion
     int buf = 0;
     bool ok = true;

@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--requests", type=int, default=600, help="serve: requests in the open loop")
     p.add_argument("--pool", type=int, default=32, help="serve: distinct matrices")
+    p.add_argument("--lanes", type=int, default=3, help="serve: server lanes (units in flight)")
     p.add_argument("--load", type=float, default=0.7,
                    help="serve: offered rate as a fraction of the closed-loop capacity")
     return p.parse_args()
@@ -844,7 +845,7 @@ def run_serve(args, world, rank, local, C):
                      torch.empty(w.n, dtype=torch.int64, pin_memory=True)))
     torch.cuda.synchronize()
     h = C.Handle(local)
-    srv = C.Server(hbm_budget_bytes=120 << 30, max_inflight=64, handle=h)
+    srv = C.Server(hbm_budget_bytes=120 << 30, max_inflight=64, handle=h, lanes=args.lanes)
 
     def make(count, seed_base):
         reqs = []
@@ -987,8 +988,12 @@ def run_serve(args, world, rank, local, C):
                            "queue": pct(que)},
             "gflops_algorithmic": flops / wall / 1e9,
             "gflops_2mn2": sum(2.0 * w.m * w.n * w.n for w in ws) / wall / 1e9,
-            "waves": stats["waves"] - stats0["waves"],
-            "mean_wave_size": len(reqs) / max(1, stats["waves"] - stats0["waves"]),
+            "units": stats["waves"] - stats0["waves"],
+            "single_route_units": stats["single_units"] - stats0["single_units"],
+            "batched_waves": stats["batched_units"] - stats0["batched_units"],
+            "mean_wave_size": ((stats["batched_requests"] - stats0["batched_requests"])
+                               / max(1, stats["batched_units"] - stats0["batched_units"])),
+            "lanes": stats["lanes"], "max_units_in_flight": stats["max_busy_lanes"],
             "e2e": {"value": throughput, "unit": "requests/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "note": "the serving loop is end to end: pinned host in, host out"},

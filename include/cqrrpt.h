@@ -396,21 +396,35 @@ typedef struct {
 
 typedef struct cqrrpt_server_s* cqrrpt_server;
 
-/* A server that factors submitted requests with continuous batching: a
- * scheduler thread admits requests in arrival order while their device
- * footprint (A, Q, R, J and, for requests of a batched route, the batched
- * workspace) fits hbm_budget_bytes (one allocation made here) and at most
- * max_inflight are in flight, and copies their inputs in while earlier work
- * runs.  Whenever the GPU is free it starts the next unit of work, chosen by
- * the oldest request whose input has arrived: one batched pass over every
- * arrived request of the same precision with n <= 256 (CQRRPT_FP64 or
- * CQRRPT_SPLITBF16; requests that arrived while the previous pass ran join
- * the next one), or a single-problem run (cqrrpt_d on the whole GPU) of a
- * request with n > 256 or in CQRRPT_SPLITBF16_CHOLQR2.  Results are
- * bit-identical to standalone calls of the same precision.  The server owns
- * `h` until cqrrpt_server_destroy (single-problem runs and the split-BF16
- * digit planes use its workspaces, outside the budget).  The current device
- * is used. */
+/* A server that factors submitted requests with continuous batching, its
+ * units of work overlapping on the GPU (the paper has no serving layer; the
+ * arithmetic of every unit is Alg. 1 + Alg. 2 as in cqrrpt_d).  A scheduler
+ * thread admits requests in arrival order while their device footprint (A,
+ * Q, R, J and, for requests of a batched route, the batched workspace) fits
+ * hbm_budget_bytes (one allocation made here) and at most max_inflight are
+ * in flight, and copies their inputs in while other work runs.  Work runs on
+ * `lanes` lanes (1..8), each a handle, a stream and a worker thread, so that
+ * up to `lanes` units are in flight at once, the oldest arrived request
+ * deciding the next unit:
+ *   - a request with n > 256 or in CQRRPT_SPLITBF16_CHOLQR2 runs alone
+ *     through cqrrpt_d (multi-CTA QRCP) on its lane, at most lanes - 1 such
+ *     units at a time (their cooperative QRCP grids run one after another on
+ *     the GPU, everything else side by side);
+ *   - other requests run as batched waves: one batched pass over the arrived
+ *     requests of the oldest one's precision (CQRRPT_FP64 or
+ *     CQRRPT_SPLITBF16).  A wave starts at once when the GPU is idle;
+ *     while any unit is in flight, arrivals gather until 4 are waiting or
+ *     the oldest has waited 8 ms.
+ * Results are bit-identical to standalone calls of the same precision.  The
+ * server owns `h` (lane 0) until cqrrpt_server_destroy; lanes 1.. get
+ * handles of their own (with h's batched tile shapes).  Single-route runs
+ * and the split-BF16 digit planes use the lanes' handle workspaces, outside
+ * the budget.  The current device is used.  Returns 0, -i for argument i,
+ * CQRRPT_NO_MEMORY or CQRRPT_CUDA_ERROR. */
+int cqrrpt_server_create_lanes(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight,
+                               double gamma, int nnz_per_col, int lanes, cqrrpt_server* server);
+
+/* cqrrpt_server_create_lanes with 3 lanes. */
 int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight, double gamma,
                          int nnz_per_col, cqrrpt_server* server);
 
@@ -427,9 +441,16 @@ int cqrrpt_server_poll(cqrrpt_server s, uint64_t ticket, int* done, cqrrpt_resul
  * Returns CQRRPT_TIMEOUT when the limit passes first. */
 int cqrrpt_server_drain(cqrrpt_server s, int64_t timeout_us);
 
-/* Counters: batched waves launched, requests completed, in flight, queued. */
+/* Counters: units of work launched (batched waves and single-route runs),
+ * requests completed, in flight, queued. */
 int cqrrpt_server_stats(cqrrpt_server s, int64_t* waves, int64_t* completed, int64_t* inflight,
                         int64_t* queued);
+
+/* The first `count` (at most 10) of: units launched, requests completed, in
+ * flight, queued, lanes, the largest number of units in flight at the same
+ * time so far, single-route units, batched waves, requests in batched
+ * waves, units in flight now.  out: host array.  Returns 0, -1 or -2. */
+int cqrrpt_server_stats_ex(cqrrpt_server s, int64_t* out, int count);
 
 /* Finishes every queued and in-flight request, stops the scheduler and frees
  * the server's memory. */

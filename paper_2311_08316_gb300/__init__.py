@@ -117,7 +117,7 @@ def exported_symbols():
             "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d",
             "cqrrpt_sketch_dense_split_d", "cqrrpt_set_wait_limits", "cqrrpt_sketch_noalloc_d",
             "cqrrpt_sketch_noalloc_max_bytes", "cqrrpt_sketch_noalloc_status",
-            "cqrrpt_probe_fp64_gflops"]
+            "cqrrpt_probe_fp64_gflops", "cqrrpt_server_create_lanes", "cqrrpt_server_stats_ex"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -735,6 +735,9 @@ def _server_lib():
     L = lib()
     if not getattr(L, "_server_ready", False):
         L.cqrrpt_server_create.argtypes = [_p, ctypes.c_size_t, _int, _d, _int, ctypes.POINTER(_p)]
+        L.cqrrpt_server_create_lanes.argtypes = [_p, ctypes.c_size_t, _int, _d, _int, _int,
+                                                 ctypes.POINTER(_p)]
+        L.cqrrpt_server_stats_ex.argtypes = [_p, ctypes.POINTER(_i64), _int]
         L.cqrrpt_server_submit.argtypes = [_p, ctypes.POINTER(Request), ctypes.POINTER(_u64)]
         L.cqrrpt_server_poll.argtypes = [_p, _u64, ctypes.POINTER(_int), ctypes.POINTER(Result)]
         L.cqrrpt_server_drain.argtypes = [_p, _i64]
@@ -749,12 +752,14 @@ class Server:
     (ideally pinned) column-major float64 tensors; results land in the
     request's host output tensors.  The handle is owned by the server."""
 
-    def __init__(self, hbm_budget_bytes, max_inflight=64, gamma=1.25, nnz=4, handle=None):
+    def __init__(self, hbm_budget_bytes, max_inflight=64, gamma=1.25, nnz=4, handle=None,
+                 lanes=3):
         L = _server_lib()
         self.handle = handle or Handle()
         s = ctypes.c_void_p()
-        _check(L.cqrrpt_server_create(self.handle.h, int(hbm_budget_bytes), max_inflight, gamma,
-                                      nnz, ctypes.byref(s)), "cqrrpt_server_create")
+        _check(L.cqrrpt_server_create_lanes(self.handle.h, int(hbm_budget_bytes), max_inflight,
+                                            gamma, nnz, int(lanes), ctypes.byref(s)),
+               "cqrrpt_server_create_lanes")
         self.s = s
         self._keep = {}
 
@@ -790,11 +795,14 @@ class Server:
     def drain(self, timeout_us=-1):
         _check(_server_lib().cqrrpt_server_drain(self.s, int(timeout_us)), "cqrrpt_server_drain")
 
+    STATS = ["waves", "completed", "inflight", "queued", "lanes", "max_busy_lanes",
+             "single_units", "batched_units", "batched_requests", "busy_lanes"]
+
     def stats(self):
-        v = [_i64() for _ in range(4)]
-        _check(_server_lib().cqrrpt_server_stats(self.s, *[ctypes.byref(x) for x in v]),
-               "cqrrpt_server_stats")
-        return dict(zip(["waves", "completed", "inflight", "queued"], [x.value for x in v]))
+        v = (_i64 * len(self.STATS))()
+        _check(_server_lib().cqrrpt_server_stats_ex(self.s, v, len(self.STATS)),
+               "cqrrpt_server_stats_ex")
+        return dict(zip(self.STATS, list(v)))
 
     def close(self):
         if self.s:

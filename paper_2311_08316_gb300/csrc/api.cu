@@ -7,6 +7,8 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -66,6 +68,24 @@ static std::atomic<long long> g_launches{0};
 
 namespace cqrrpt {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// The dynamic shared-memory limit of a kernel is one attribute per device,
+// shared by every thread and stream: it is only ever raised (to the largest
+// size any launch has asked for), under a lock, so that a launch on one
+// stream never finds the limit lowered below its own size by another.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[std::make_pair(dev, fn)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 // k and status of the handle's last call into caller slots, stream-ordered
 int handle_finalize(cqrrpt_handle h, int64_t* k_out, int* status_out, cudaStream_t s) {
   return launch_finalize(h->sc, k_out, status_out, s) == cudaSuccess ? kOk : kCudaError;

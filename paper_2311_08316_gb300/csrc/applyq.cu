@@ -193,8 +193,7 @@ __global__ void __launch_bounds__(kCombineThreads)
 cudaError_t trsv_cols(int lower, int k, const double* T, int64_t ldt, const double* B,
                       int64_t ldb, double* W, int64_t ldw, int r, cudaStream_t s) {
   const size_t smem = (size_t)k * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(trsv_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)trsv_cols_kernel, smem);
   if (e != cudaSuccess) return e;
   trsv_cols_kernel<<<(unsigned)r, kTrsvThreads, smem, s>>>(lower, k, T, ldt, B, ldb, W, ldw);
   count_launches(1);

@@ -28,6 +28,9 @@ inline int64_t align256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
 // Process-wide count of kernels this library has launched.
 void count_launches(int n);
+// Raises (never lowers) the dynamic shared-memory limit of kernel `fn` on
+// the current device to `bytes`; thread-safe.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 
 // ---- Alg. 2 line 1 -------------------------------------------------------
 int64_t sketch_workspace_bytes(int64_t m, int64_t n, int d, int s);

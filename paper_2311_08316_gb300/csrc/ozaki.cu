@@ -316,7 +316,7 @@ int oz_trinv_warps(int kmax) {
 int64_t oz_trinv_tiles(const OzTrinv& J, int warps) { return (J.k + warps - 1) / warps; }
 static cudaError_t trinv_smem_attr(const void* fn, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return raise_smem_limit(fn, bytes);
 }
 cudaError_t oz_trinv(const OzTrinv& J, cudaStream_t s) {
   const int warps = oz_trinv_warps(J.k);

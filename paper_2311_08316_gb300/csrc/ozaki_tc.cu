@@ -637,17 +637,9 @@ cudaError_t oz_set_wait_ns(unsigned long long ns) {
 }
 
 static cudaError_t tc_attributes() {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTcSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(oz_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kTcSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  return cudaSuccess;
+  cudaError_t e = raise_smem_limit((const void*)oz_tc_kernel, (size_t)kTcSmem);
+  if (e == cudaSuccess) e = raise_smem_limit((const void*)oz_tc_batched_kernel, (size_t)kTcSmem);
+  return e;
 }
 
 // TMA: 16-byte aligned bases, row strides and plane strides (several K

@@ -23,6 +23,7 @@
 // barriers spin a bounded number of times (status kTimeout on expiry).
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -600,6 +601,51 @@ __global__ void qrcp_gather_batched_kernel(const QrcpDesc* D, const int64_t* bas
 
 static double tol3z_value() { return sqrt(ldexp(1.0, -53)); }
 
+// Cooperative QRCP grids of one device run one at a time.  Each needs all
+// its CTAs resident at once (they wait on one another at the grid barrier);
+// two such grids issued from different streams (several handles, threads or
+// server lanes) could each hold part of the SMs and wait for the rest.  So
+// every cooperative launch waits, on the GPU, for the previous one on the
+// same device (an event, recorded after each launch under a lock): the host
+// never blocks, and other kernels still run beside the grid.  Not applied
+// while the stream is being captured into a graph.
+namespace {
+struct CoopFence {
+  std::mutex mu;
+  cudaEvent_t ev = nullptr;
+  bool recorded = false;
+};
+CoopFence g_coop[64];
+}  // namespace
+
+static cudaError_t coop_launch(const void* fn, int G, void** args, size_t smem,
+                               cudaStream_t stream) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  int dev = 0;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone ||
+      cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrcpThreads), args, smem, stream);
+  }
+  CoopFence& f = g_coop[dev];
+  std::lock_guard<std::mutex> lock(f.mu);
+  cudaError_t e = cudaSuccess;
+  if (f.ev && f.recorded && cudaStreamWaitEvent(stream, f.ev, 0) != cudaSuccess) {
+    // the event died with its context (cudaDeviceReset): start afresh
+    cudaGetLastError();
+    f.ev = nullptr;
+    f.recorded = false;
+  }
+  if (!f.ev) e = cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrcpThreads), args, smem, stream);
+  if (e == cudaSuccess) {
+    e = cudaEventRecord(f.ev, stream);
+    f.recorded = e == cudaSuccess;
+  }
+  return e;
+}
+
 cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double* Rsk,
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
                         cudaStream_t stream, bool nopivot) {
@@ -632,8 +678,7 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   int qci = (int)qc;
   void* args_c[] = {&D, (void*)&tol3z, &qci};
   if (cached) {
-    e = cudaFuncSetAttribute(qrcp_cached_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = raise_smem_limit((const void*)qrcp_cached_kernel, smem);
     int per_sm_c = 0;
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, qrcp_cached_kernel,
@@ -642,11 +687,9 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
     cudaGetLastError();
   }
   if (cached)
-    e = cudaLaunchCooperativeKernel((const void*)qrcp_cached_kernel, dim3(G), dim3(kQrcpThreads),
-                                    args_c, smem, stream);
+    e = coop_launch((const void*)qrcp_cached_kernel, G, args_c, smem, stream);
   else
-    e = cudaLaunchCooperativeKernel((const void*)qrcp_kernel, dim3(G), dim3(kQrcpThreads), args, 0,
-                                    stream);
+    e = coop_launch((const void*)qrcp_kernel, G, args, 0, stream);
   if (e != cudaSuccess) return e;
   qrcp_gather_kernel<<<n, 128, 0, stream>>>(D);
   count_launches(2);
@@ -658,9 +701,8 @@ cudaError_t launch_qrcp_batched(const QrcpDesc* D, int nprob, const int64_t* gat
                                 cudaStream_t stream) {
   if (nprob <= 0) return cudaSuccess;
   if (qrcp_smem_bytes > 0) {
-    cudaError_t e = cudaFuncSetAttribute(qrcp_cached_batched_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)qrcp_smem_bytes);
+    cudaError_t e = raise_smem_limit((const void*)qrcp_cached_batched_kernel,
+                                     (size_t)qrcp_smem_bytes);
     if (e != cudaSuccess) return e;
     qrcp_cached_batched_kernel<<<nprob, kQrcpBatchThreads, (size_t)qrcp_smem_bytes, stream>>>(
         D, tol3z_value(), qrcp_smem_bytes);

@@ -1,27 +1,44 @@
-// Continuous-batching CQRRPT server.
+// Continuous-batching CQRRPT server whose units of work overlap on the GPU.
 //
 // Requests (a host matrix plus host output buffers) are submitted from any
-// thread and return a ticket at once.  One scheduler thread per server:
+// thread and return a ticket at once.  The server runs its work on L lanes;
+// a lane is a handle (workspace, device scalars), two compute streams (the
+// highest stream priority for single-route units, whose kernels then get
+// the SMs first, the lowest for batched waves), a launch table area and a
+// worker thread.  One scheduler thread:
 //   * admits queued requests in arrival order while their device footprint
 //     (A, Q, R, J, per-problem workspace) fits the HBM budget -- a first-fit
 //     arena over one allocation made at creation -- and at most max_inflight
 //     are in flight; the host -> device copy of an admitted request's A is
-//     issued at once on a copy stream, overlapping the running wave;
-//   * whenever no wave is running, starts the next unit of work, chosen by
-//     the oldest request whose input has arrived: one batched pass over
-//     every arrived request of its kind (FP64 waves run the batched kernels
-//     of batched.cu, split-BF16 waves the batched split path) -- requests
-//     that arrived while the previous wave ran join the next one -- or, for
-//     a request routed to the single-problem path (n above kBatchMaxN, where
-//     the one-CTA-per-problem QRCP and Cholesky of the batched kernels would
-//     serialise, or the mode with a second Cholesky-QR pass), that request
-//     alone on the whole GPU;
-//   * when a wave completes, copies each result (Q, R, J, k, status) back on
-//     the copy stream, frees the request's arena block when the copy is done
-//     and records the completion time.
-// Every wait of the scheduler is a host-side poll with a bounded sleep; the
-// kernels contain no cross-CTA waits.  Results are bit-identical to a
-// standalone call on the same request, whatever else shares a wave.
+//     issued at once on the copy-in stream, overlapping running work;
+//   * hands units of work to idle lanes, the oldest arrived request first.
+//     A request with n above kBatchMaxN (where the one-CTA-per-problem QRCP
+//     and Cholesky of the batched kernels would serialise) or in the mode
+//     with a second Cholesky-QR pass is a single-route unit: it runs alone
+//     on its lane through cqrrpt_d, with the multi-CTA QRCP.  At most
+//     lanes - 1 single-route units are in flight, so a lane is always left
+//     for small requests.  Other requests run as batched waves: one batched
+//     pass (batched.cu, or the batched split path) over the arrived requests
+//     of the oldest one's precision.  A wave starts at once when the GPU is
+//     idle; while any unit is in flight, arrivals gather until kMinWave are
+//     waiting or the oldest has waited kMaxWaitUs.  The cooperative QRCP
+//     grids of single-route units on different lanes run one after another
+//     on the GPU (qrcp.cu's per-device launch fence), everything else side
+//     by side;
+//   * when a lane's unit completes, copies each result (Q, R, J, k, status)
+//     back on the copy-out stream, frees the request's arena block when the
+//     copy is done and records the completion time.
+// So a large request no longer holds the GPU alone: small waves and other
+// large requests run on the other lanes beside it.  The
+// worker threads make the launches (the split path reads k back on the way,
+// which blocks only its own lane).  Every wait of the scheduler is a
+// host-side poll with a bounded sleep; the kernels contain no cross-CTA
+// waits except the single-route QRCP's grid barrier, which is bounded (and
+// never shared by two grids at once).
+// Results are bit-identical to a standalone call on the same request,
+// whatever else shares a wave or runs beside it: each lane has its own
+// workspace and the kernels fix their summation orders.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -139,6 +156,33 @@ size_t footprint(const cqrrpt_request& r, int64_t d, int nnz) {
 
 }  // namespace
 
+// Dynamic batching: while any unit is in flight, a new wave waits until
+// this many requests are ready or the oldest has waited this long.
+constexpr int kMinWave = 4;
+constexpr double kMaxWaitUs = 8000.0;
+
+enum LaneState { kLaneIdle = 0, kLaneLaunching, kLaneRunning };
+
+struct Lane {
+  int id = 0;
+  cqrrpt_handle h = nullptr;
+  bool own_handle = false;
+  cudaStream_t compute = nullptr;     // the current unit's stream
+  cudaStream_t wave_stream = nullptr;  // batched waves
+  cudaStream_t single_stream = nullptr;  // single-route units: highest priority
+  cudaEvent_t done = nullptr, stage_ev = nullptr;
+  char* fixed = nullptr;  // DeviceScalars[max_inflight] + batch tables
+  void* stage = nullptr;  // pinned table staging
+  size_t stage_bytes = 0;
+  std::vector<Req*> wave;
+  bool single = false;
+  int state = kLaneIdle;
+  bool has_work = false;
+  int rc = kOk;
+  std::thread th;
+  std::condition_variable cv;
+};
+
 struct Server {
   cqrrpt_handle h = nullptr;
   int device = 0;
@@ -147,16 +191,11 @@ struct Server {
   int max_inflight = 64;
   char* arena_base = nullptr;
   Arena arena;
-  char* fixed = nullptr;  // DeviceScalars[max_inflight] + tables
   size_t fixed_bytes = 0;
-  void* stage = nullptr;  // pinned table staging
-  size_t stage_bytes = 0;
   int64_t* pinned_slots = nullptr;  // 2 words per in-flight slot
   std::vector<int> free_slots;
-  cudaStream_t compute = nullptr, copy = nullptr;
-  cudaEvent_t wave_done = nullptr, stage_ev = nullptr;
-  bool wave_running = false;
-  std::vector<Req*> wave;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  std::vector<Lane*> lanes;
   std::thread th;
   std::mutex mu;
   std::condition_variable cv;
@@ -165,18 +204,89 @@ struct Server {
   std::unordered_map<uint64_t, Req*> all;
   uint64_t next_ticket = 1;
   bool stop = false;
+  bool stop_workers = false;
   int error = 0;
-  int64_t waves = 0, completed = 0;
+  int64_t waves = 0, completed = 0, single_units = 0, batched_units = 0, batched_reqs = 0;
+  int busy = 0, max_busy = 0;
   int (*run_single)(cqrrpt_handle, const cqrrpt_request&, double, int, double*, double*, double*,
                     int64_t*, cudaStream_t) = nullptr;
 
   void loop();
   bool step();
+  void worker(Lane* L);
+  int launch_unit(Lane* L);
 };
+
+// The lane's unit: launches only (the worker records `done` after them).
+int Server::launch_unit(Lane* L) {
+  if (L->single) {
+    Req* q = L->wave[0];
+    // FP64 requests are enqueued without a host wait; the split-BF16
+    // pipeline reads k back on the way (its recursive products are sized on
+    // the host).  k and status land in the request's device slots.
+    const int rc = run_single(L->h, q->r, gamma, nnz, q->A, q->Q, q->R, q->J, L->compute);
+    if (rc != kOk && rc != kRankZero && rc != kNonFinite) {
+      *q->k_host = 0;
+      *q->st_host = rc;
+      cudaMemcpyAsync(q->k_dev, q->k_host, sizeof(int64_t), cudaMemcpyHostToDevice, L->compute);
+      cudaMemcpyAsync(q->st_dev, q->st_host, sizeof(int), cudaMemcpyHostToDevice, L->compute);
+      return kOk;
+    }
+    return handle_finalize(L->h, q->k_dev, q->st_dev, L->compute);
+  }
+  const std::vector<Req*>& ready = L->wave;
+  std::vector<BatchProblem> probs(ready.size());
+  std::vector<char*> wss(ready.size());
+  for (size_t i = 0; i < ready.size(); ++i) {
+    const Req* q = ready[i];
+    BatchProblem& b = probs[i];
+    b.m = q->r.m; b.n = q->r.n; b.d = q->d; b.nnz = nnz; b.tol = q->r.tol;
+    b.seed = q->r.seed; b.A = q->A; b.lda = q->r.m; b.Q = q->Q; b.ldq = q->r.m;
+    b.R = q->R; b.ldr = q->r.n; b.J = q->J; b.k_out = q->k_dev; b.status_out = q->st_dev;
+    wss[i] = q->ws;
+  }
+  BatchPlan P;
+  P.scalars = (DeviceScalars*)L->fixed;
+  P.tables = L->fixed + align256((int64_t)max_inflight * sizeof(DeviceScalars));
+  batch_plan(P, (int)ready.size(), probs.data(), nullptr, wss.data(), handle_tuning(L->h));
+  const size_t img = P.image.size();
+  cudaEventSynchronize(L->stage_ev);
+  if (img > L->stage_bytes) {
+    if (L->stage) cudaFreeHost(L->stage);
+    L->stage = nullptr;
+    L->stage_bytes = 0;
+    if (cudaMallocHost(&L->stage, img) != cudaSuccess) return kNoMemory;
+    L->stage_bytes = img;
+  }
+  memcpy(L->stage, P.image.data(), img);
+  if (cudaMemcpyAsync(P.tables, L->stage, img, cudaMemcpyHostToDevice, L->compute) != cudaSuccess)
+    return kCudaError;
+  cudaEventRecord(L->stage_ev, L->compute);
+  if (ready[0]->r.precision != CQRRPT_FP64)
+    return batched_split_exec(L->h, P, probs, L->compute);  // waits for its stream twice
+  sketch_set_attributes(P.max_d);
+  return batch_launch(P, L->compute) == cudaSuccess ? kOk : kCudaError;
+}
+
+void Server::worker(Lane* L) {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lock(mu);
+  while (true) {
+    L->cv.wait(lock, [&] { return L->has_work || stop_workers; });
+    if (!L->has_work) break;
+    lock.unlock();
+    int rc = launch_unit(L);
+    if (cudaEventRecord(L->done, L->compute) != cudaSuccess && rc == kOk) rc = kCudaError;
+    lock.lock();
+    L->rc = rc;
+    L->has_work = false;
+    L->state = kLaneRunning;
+    cv.notify_all();
+  }
+}
 
 bool Server::step() {
   bool progress = false;
-  std::vector<Req*> finished;
   {
     std::lock_guard<std::mutex> lock(mu);
     // completions of copies back
@@ -199,31 +309,33 @@ bool Server::step() {
       }
       ++i;
     }
-  }
-  if (progress) cv.notify_all();
-  // wave completion: copy results back
-  if (wave_running && cudaEventQuery(wave_done) == cudaSuccess) {
-    std::lock_guard<std::mutex> lock(mu);
-    cudaStreamWaitEvent(copy, wave_done, 0);
-    for (Req* q : wave) {
-      const cqrrpt_request& r = q->r;
-      cudaMemcpy2DAsync(r.Q_host, r.ldq * sizeof(double), q->Q, r.m * sizeof(double),
-                        r.m * sizeof(double), r.n, cudaMemcpyDeviceToHost, copy);
-      cudaMemcpy2DAsync(r.R_host, r.ldr * sizeof(double), q->R, r.n * sizeof(double),
-                        r.n * sizeof(double), r.n, cudaMemcpyDeviceToHost, copy);
-      cudaMemcpyAsync(r.J_host, q->J, r.n * sizeof(int64_t), cudaMemcpyDeviceToHost, copy);
-      cudaMemcpyAsync(q->k_host, q->k_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, copy);
-      cudaMemcpyAsync(q->st_host, q->st_dev, sizeof(int), cudaMemcpyDeviceToHost, copy);
-      cudaEventRecord(q->done, copy);
-      q->state = kCopyBack;
+    // units that finished on the GPU: copy their results back
+    for (Lane* L : lanes) {
+      if (L->state != kLaneRunning || cudaEventQuery(L->done) != cudaSuccess) continue;
+      if (L->rc != kOk) {
+        error = L->rc;
+        return false;
+      }
+      cudaStreamWaitEvent(copy_out, L->done, 0);
+      for (Req* q : L->wave) {
+        const cqrrpt_request& r = q->r;
+        cudaMemcpy2DAsync(r.Q_host, r.ldq * sizeof(double), q->Q, r.m * sizeof(double),
+                          r.m * sizeof(double), r.n, cudaMemcpyDeviceToHost, copy_out);
+        cudaMemcpy2DAsync(r.R_host, r.ldr * sizeof(double), q->R, r.n * sizeof(double),
+                          r.n * sizeof(double), r.n, cudaMemcpyDeviceToHost, copy_out);
+        cudaMemcpyAsync(r.J_host, q->J, r.n * sizeof(int64_t), cudaMemcpyDeviceToHost, copy_out);
+        cudaMemcpyAsync(q->k_host, q->k_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, copy_out);
+        cudaMemcpyAsync(q->st_host, q->st_dev, sizeof(int), cudaMemcpyDeviceToHost, copy_out);
+        cudaEventRecord(q->done, copy_out);
+        q->state = kCopyBack;
+      }
+      L->wave.clear();
+      L->single = false;
+      L->state = kLaneIdle;
+      --busy;
+      progress = true;
     }
-    wave.clear();
-    wave_running = false;
-    progress = true;
-  }
-  // admission
-  {
-    std::lock_guard<std::mutex> lock(mu);
+    // admission
     while (!pending.empty() && (int)inflight.size() < max_inflight && !free_slots.empty()) {
       Req* q = pending.front();
       const cqrrpt_request& r = q->r;
@@ -247,106 +359,90 @@ bool Server::step() {
       q->k_host = pinned_slots + 2 * slot;
       q->st_host = (int*)(pinned_slots + 2 * slot + 1);
       cudaMemcpy2DAsync(q->A, r.m * sizeof(double), r.A_host, r.lda * sizeof(double),
-                        r.m * sizeof(double), r.n, cudaMemcpyHostToDevice, copy);
-      cudaEventRecord(q->h2d, copy);
+                        r.m * sizeof(double), r.n, cudaMemcpyHostToDevice, copy_in);
+      cudaEventRecord(q->h2d, copy_in);
       q->state = kStaging;
       q->t_start = now_us();
       inflight.push_back(q);
       progress = true;
     }
-  }
-  // launch the next unit of work: the oldest arrived request decides
-  // between a batched wave and a single-path run
-  if (!wave_running) {
-    // arrived requests: single route, or one of the two batched routes
-    // (FP64 waves and split-BF16 waves); the oldest decides what runs
-    std::vector<Req*> ready;
-    Req* solo = nullptr;
-    Req* oldest = nullptr;
-    {
-      std::lock_guard<std::mutex> lock(mu);
-      for (Req* q : inflight) {
-        if (q->state != kStaging || cudaEventQuery(q->h2d) != cudaSuccess) continue;
-        if (!oldest || q->t_submit < oldest->t_submit) oldest = q;
-        if (single_route(q->r) && (!solo || q->t_submit < solo->t_submit)) solo = q;
+    // hand units to idle lanes
+    std::vector<Req*> arrived;
+    for (Req* q : inflight)
+      if (q->state == kStaging && cudaEventQuery(q->h2d) == cudaSuccess) arrived.push_back(q);
+    std::sort(arrived.begin(), arrived.end(),
+              [](const Req* a, const Req* b) { return a->t_submit < b->t_submit; });
+    int singles_busy = 0, waves_busy = 0;
+    for (Lane* L : lanes)
+      if (L->state != kLaneIdle) {
+        if (L->single) ++singles_busy;
+        else ++waves_busy;
       }
-      if (oldest && !single_route(oldest->r))
-        for (Req* q : inflight)
-          if (q->state == kStaging && !single_route(q->r) &&
-              q->r.precision == oldest->r.precision && cudaEventQuery(q->h2d) == cudaSuccess)
-            ready.push_back(q);
-    }
-    const bool split_wave = !ready.empty() && oldest->r.precision != CQRRPT_FP64;
-    if (!ready.empty()) {
-      std::vector<BatchProblem> probs(ready.size());
-      std::vector<char*> wss(ready.size());
-      for (size_t i = 0; i < ready.size(); ++i) {
-        const Req* q = ready[i];
-        BatchProblem& b = probs[i];
-        b.m = q->r.m; b.n = q->r.n; b.d = q->d; b.nnz = nnz; b.tol = q->r.tol;
-        b.seed = q->r.seed; b.A = q->A; b.lda = q->r.m; b.Q = q->Q; b.ldq = q->r.m;
-        b.R = q->R; b.ldr = q->r.n; b.J = q->J; b.k_out = q->k_dev; b.status_out = q->st_dev;
-        wss[i] = q->ws;
+    // single-route units in flight at most: all lanes but one, so that a
+    // lane is always left for the batched waves of small requests
+    const int max_singles = lanes.size() > 1 ? (int)lanes.size() - 1 : 1;
+    const double now = now_us();
+    for (Lane* L : lanes) {
+      if (L->state != kLaneIdle || arrived.empty()) continue;
+      std::vector<Req*> unit;
+      bool single = false;
+      Req* oldest_single = nullptr;
+      Req* oldest_batched = nullptr;
+      for (Req* q : arrived) {
+        if (single_route(q->r)) {
+          if (!oldest_single) oldest_single = q;
+        } else if (!oldest_batched) {
+          oldest_batched = q;
+        }
       }
-      BatchPlan P;
-      P.scalars = (DeviceScalars*)fixed;
-      P.tables = fixed + align256((int64_t)max_inflight * sizeof(DeviceScalars));
-      batch_plan(P, (int)ready.size(), probs.data(), nullptr, wss.data(), handle_tuning(h));
-      const size_t img = P.image.size();
-      cudaEventSynchronize(stage_ev);
-      if (img > stage_bytes) {
-        if (stage) cudaFreeHost(stage);
-        stage = nullptr;
-        stage_bytes = 0;
-        if (cudaMallocHost(&stage, img) != cudaSuccess) { error = kNoMemory; return false; }
-        stage_bytes = img;
+      const bool can_single = oldest_single && singles_busy < max_singles;
+      if (can_single && (!oldest_batched || oldest_single->t_submit < oldest_batched->t_submit)) {
+        unit.push_back(oldest_single);
+        single = true;
+      } else if (oldest_batched) {
+        for (Req* q : arrived)
+          if (!single_route(q->r) && q->r.precision == oldest_batched->r.precision)
+            unit.push_back(q);
+        if (waves_busy + singles_busy > 0 && (int)unit.size() < kMinWave &&
+            now - oldest_batched->t_start < kMaxWaitUs) {
+          unit.clear();  // gather more while another wave runs
+          if (can_single) {
+            unit.push_back(oldest_single);
+            single = true;
+          }
+        }
+      } else if (can_single) {
+        unit.push_back(oldest_single);
+        single = true;
       }
-      memcpy(stage, P.image.data(), img);
-      cudaMemcpyAsync(P.tables, stage, img, cudaMemcpyHostToDevice, compute);
-      cudaEventRecord(stage_ev, compute);
-      {
-        std::lock_guard<std::mutex> lock(mu);
-        for (Req* q : ready) q->state = kRunning;
-        wave = ready;
-      }
-      if (split_wave) {
-        // the split products are sized by each problem's k: this waits for
-        // the compute stream twice
-        if (batched_split_exec(h, P, probs, compute) != kOk) { error = kCudaError; return false; }
-      } else {
-        sketch_set_attributes(P.max_d);
-        if (batch_launch(P, compute) != cudaSuccess) { error = kCudaError; return false; }
-      }
-      cudaEventRecord(wave_done, compute);
-      wave_running = true;
-      ++waves;
-      progress = true;
-    } else if (solo) {
-      Req* q = solo;
-      {
-        std::lock_guard<std::mutex> lock(mu);
+      if (unit.empty()) continue;
+      for (Req* q : unit) {
         q->state = kRunning;
-        wave.assign(1, q);
+        arrived.erase(std::find(arrived.begin(), arrived.end(), q));
       }
-      // FP64 requests are enqueued without a host wait; the split-BF16
-      // pipeline reads k back on the way (its recursive products are sized
-      // on the host).  k and status land in the request's device slots.
-      const int rc = run_single(h, q->r, gamma, nnz, q->A, q->Q, q->R, q->J, compute);
-      if (rc != kOk && rc != kRankZero && rc != kNonFinite) {
-        *q->k_host = 0;
-        *q->st_host = rc;
-        cudaMemcpyAsync(q->k_dev, q->k_host, sizeof(int64_t), cudaMemcpyHostToDevice, compute);
-        cudaMemcpyAsync(q->st_dev, q->st_host, sizeof(int), cudaMemcpyHostToDevice, compute);
-      } else if (handle_finalize(h, q->k_dev, q->st_dev, compute) != kOk) {
-        error = kCudaError;
-        return false;
-      }
-      cudaEventRecord(wave_done, compute);
-      wave_running = true;
+      L->wave = unit;
+      L->single = single;
+      // a large request's kernels get the SMs first (it sets the tail
+      // latency); small waves fill what it leaves
+      L->compute = single ? L->single_stream : L->wave_stream;
+      L->state = kLaneLaunching;
+      L->has_work = true;
+      ++busy;
+      if (busy > max_busy) max_busy = busy;
       ++waves;
+      if (single) {
+        ++single_units;
+        ++singles_busy;
+      } else {
+        ++batched_units;
+        batched_reqs += (int64_t)unit.size();
+        ++waves_busy;
+      }
+      L->cv.notify_all();
       progress = true;
     }
   }
+  if (progress) cv.notify_all();
   return progress;
 }
 
@@ -355,7 +451,7 @@ void Server::loop() {
   while (true) {
     {
       std::lock_guard<std::mutex> lock(mu);
-      if (stop && pending.empty() && inflight.empty() && !wave_running) break;
+      if (stop && pending.empty() && inflight.empty() && busy == 0) break;
     }
     const bool progress = step();
     if (error) {
@@ -390,14 +486,15 @@ int run_single_impl(cqrrpt_handle h, const cqrrpt_request& r, double gamma, int 
 
 extern "C" {
 
-int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight, double gamma,
-                         int nnz_per_col, cqrrpt_server* out) {
+int cqrrpt_server_create_lanes(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight,
+                                double gamma, int nnz_per_col, int lanes, cqrrpt_server* out) {
   if (!h) return -1;
   if (hbm_budget_bytes < (1u << 20)) return -2;
   if (max_inflight < 1 || max_inflight > 4096) return -3;
   if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -4;
   if (nnz_per_col < 1 || nnz_per_col > kMaxNnzInline) return -5;
-  if (!out) return -6;
+  if (lanes < 1 || lanes > 8) return -6;
+  if (!out) return -7;
   *out = nullptr;
   cqrrpt_server_s* S = new cqrrpt_server_s();
   Server& s = S->s;
@@ -409,24 +506,63 @@ int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_infli
   if (cudaGetDevice(&s.device) != cudaSuccess) { delete S; return kCudaError; }
   s.fixed_bytes = (size_t)(align256((int64_t)max_inflight * sizeof(DeviceScalars)) +
                            batch_table_bytes(max_inflight));
-  if (cudaMalloc((void**)&s.arena_base, hbm_budget_bytes) != cudaSuccess ||
-      cudaMalloc((void**)&s.fixed, s.fixed_bytes) != cudaSuccess ||
-      cudaMallocHost((void**)&s.pinned_slots, (size_t)max_inflight * 16) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s.compute, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s.copy, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s.wave_done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s.stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+  int jb[16], gt[16];
+  bool ok = cudaMalloc((void**)&s.arena_base, hbm_budget_bytes) == cudaSuccess &&
+            cudaMallocHost((void**)&s.pinned_slots, (size_t)max_inflight * 16) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s.copy_in, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s.copy_out, cudaStreamNonBlocking) == cudaSuccess &&
+            cqrrpt_batched_get_tuning(h, jb, gt) == kOk;
+  for (int i = 0; ok && i < lanes; ++i) {
+    Lane* L = new Lane();
+    L->id = i;
+    s.lanes.push_back(L);
+    if (i == 0) {
+      L->h = h;
+    } else {
+      ok = cqrrpt_create(&L->h, s.device) == kOk && cqrrpt_batched_set_tuning(L->h, jb, gt) == kOk;
+      L->own_handle = L->h != nullptr;
+    }
+    int lo = 0, hi = 0;
+    ok = ok && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&L->wave_stream, cudaStreamNonBlocking, lo) == cudaSuccess &&
+         cudaStreamCreateWithPriority(&L->single_stream, cudaStreamNonBlocking, hi) ==
+             cudaSuccess &&
+         cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&L->stage_ev, cudaEventDisableTiming) == cudaSuccess &&
+         cudaMalloc((void**)&L->fixed, s.fixed_bytes) == cudaSuccess;
+  }
+  if (!ok) {
     cudaGetLastError();
+    for (Lane* L : s.lanes) {
+      if (L->fixed) cudaFree(L->fixed);
+      if (L->done) cudaEventDestroy(L->done);
+      if (L->stage_ev) cudaEventDestroy(L->stage_ev);
+      if (L->wave_stream) cudaStreamDestroy(L->wave_stream);
+      if (L->single_stream) cudaStreamDestroy(L->single_stream);
+      if (L->own_handle) cqrrpt_destroy(L->h);
+      delete L;
+    }
+    if (s.copy_in) cudaStreamDestroy(s.copy_in);
+    if (s.copy_out) cudaStreamDestroy(s.copy_out);
+    if (s.pinned_slots) cudaFreeHost(s.pinned_slots);
     if (s.arena_base) cudaFree(s.arena_base);
-    if (s.fixed) cudaFree(s.fixed);
     delete S;
     return kNoMemory;
   }
   s.arena.init(hbm_budget_bytes);
   for (int i = max_inflight - 1; i >= 0; --i) s.free_slots.push_back(i);
+  for (Lane* L : s.lanes) L->th = std::thread([S, L] { S->s.worker(L); });
   s.th = std::thread([S] { S->s.loop(); });
   *out = S;
   return kOk;
+}
+
+int cqrrpt_server_create(cqrrpt_handle h, size_t hbm_budget_bytes, int max_inflight, double gamma,
+                         int nnz_per_col, cqrrpt_server* out) {
+  if (!out) return -6;
+  const int rc = cqrrpt_server_create_lanes(h, hbm_budget_bytes, max_inflight, gamma,
+                                            nnz_per_col, 3, out);
+  return rc == -7 ? -6 : rc;
 }
 
 int cqrrpt_server_submit(cqrrpt_server S, const cqrrpt_request* r, uint64_t* ticket) {
@@ -508,6 +644,18 @@ int cqrrpt_server_stats(cqrrpt_server S, int64_t* waves, int64_t* completed, int
   return kOk;
 }
 
+int cqrrpt_server_stats_ex(cqrrpt_server S, int64_t* out, int count) {
+  if (!S) return -1;
+  if (!out || count < 0) return -2;
+  Server& s = S->s;
+  std::lock_guard<std::mutex> lock(s.mu);
+  const int64_t v[10] = {s.waves,         s.completed,       (int64_t)s.inflight.size(),
+                         (int64_t)s.pending.size(), (int64_t)s.lanes.size(), s.max_busy,
+                         s.single_units,  s.batched_units,   s.batched_reqs, s.busy};
+  for (int i = 0; i < count && i < 10; ++i) out[i] = v[i];
+  return kOk;
+}
+
 int cqrrpt_server_destroy(cqrrpt_server S) {
   if (!S) return -1;
   Server& s = S->s;
@@ -517,21 +665,39 @@ int cqrrpt_server_destroy(cqrrpt_server S) {
   }
   s.cv.notify_all();
   if (s.th.joinable()) s.th.join();
-  cudaStreamSynchronize(s.compute);
-  cudaStreamSynchronize(s.copy);
+  {
+    std::lock_guard<std::mutex> lock(s.mu);
+    s.stop_workers = true;
+  }
+  for (Lane* L : s.lanes) {
+    L->cv.notify_all();
+    if (L->th.joinable()) L->th.join();
+  }
+  for (Lane* L : s.lanes) {
+    cudaStreamSynchronize(L->wave_stream);
+    cudaStreamSynchronize(L->single_stream);
+  }
+  cudaStreamSynchronize(s.copy_in);
+  cudaStreamSynchronize(s.copy_out);
   for (auto& kv : s.all) {
     cudaEventDestroy(kv.second->h2d);
     cudaEventDestroy(kv.second->done);
     delete kv.second;
   }
+  for (Lane* L : s.lanes) {
+    cudaFree(L->fixed);
+    if (L->stage) cudaFreeHost(L->stage);
+    cudaEventDestroy(L->done);
+    cudaEventDestroy(L->stage_ev);
+    cudaStreamDestroy(L->wave_stream);
+    cudaStreamDestroy(L->single_stream);
+    if (L->own_handle) cqrrpt_destroy(L->h);
+    delete L;
+  }
   cudaFree(s.arena_base);
-  cudaFree(s.fixed);
   cudaFreeHost(s.pinned_slots);
-  if (s.stage) cudaFreeHost(s.stage);
-  cudaEventDestroy(s.wave_done);
-  cudaEventDestroy(s.stage_ev);
-  cudaStreamDestroy(s.compute);
-  cudaStreamDestroy(s.copy);
+  cudaStreamDestroy(s.copy_in);
+  cudaStreamDestroy(s.copy_out);
   delete S;
   return kOk;
 }

@@ -328,19 +328,14 @@ int64_t sketch_combine_tiles(const SketchDesc& D) {
 static cudaError_t set_smem_attrs(size_t lists_bytes) {
   cudaError_t e = cudaSuccess;
   if (lists_bytes > 48 * 1024) {
-    e = cudaFuncSetAttribute(saso_lists_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)lists_bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(saso_lists_batched_kernel,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lists_bytes);
+    e = raise_smem_limit((const void*)saso_lists_kernel, lists_bytes);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)saso_lists_batched_kernel, lists_bytes);
     if (e != cudaSuccess) return e;
   }
   const int tile_bytes = kRowBlock * (int)sizeof(double2);
-  e = cudaFuncSetAttribute(sketch_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           tile_bytes);
+  e = raise_smem_limit((const void*)sketch_partial_kernel, (size_t)tile_bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sketch_partial_batched_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes);
+    e = raise_smem_limit((const void*)sketch_partial_batched_kernel, (size_t)tile_bytes);
   return e;
 }
 

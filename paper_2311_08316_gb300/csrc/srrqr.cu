@@ -220,8 +220,7 @@ cudaError_t srrqr_exchange(int n, int k, double f, double* Rsk, int64_t ldr, int
   const size_t inv_smem = (size_t)inv_warps * k * 8;
   cudaError_t e = cudaSuccess;
   if (inv_smem > 48 * 1024)
-    e = cudaFuncSetAttribute(srrqr_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)inv_smem);
+    e = raise_smem_limit((const void*)srrqr_inv_kernel, inv_smem);
   if (e != cudaSuccess) return e;
   const unsigned gn = (unsigned)((n + kSrThreads - 1) / kSrThreads);
   const dim3 grho(gk, (unsigned)(n - k));

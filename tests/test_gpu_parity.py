@@ -674,3 +674,31 @@ def test_single_column_through_panels_and_srrqr(C):
     res, sw = C.cqrrpt_srrqr(gpu(A), 1.25, 2, 1e-12, 9, f=2.0)
     assert sw == 0 and res.k == 1
     assert_bits(host(res.Q), ref.Q, "Q")
+
+
+def test_two_handles_on_two_streams_at_once(C):
+    # two factorisations queued on two streams without a wait in between,
+    # each with its own handle: their multi-CTA QRCP grids must not compete
+    # for the SMs (the library runs cooperative grids of a device one after
+    # another), and each result is the oracle's bit for bit
+    mats = [np.asfortranarray(W.planted(30000, n, W.logspaced(n, -7.0), 4400 + n).numpy())
+            for n in (300, 280)]
+    refs = [oracle.cqrrpt(A, 1.25, 4, 1e-12, 21) for A in mats]
+    hs = [C.Handle(), C.Handle()]
+    ss = [torch.cuda.Stream(), torch.cuda.Stream()]
+    As = [gpu(A) for A in mats]
+    torch.cuda.synchronize()
+    outs = []
+    for rep in range(3):
+        for A, h, s in zip(As, hs, ss):
+            outs.append(C.cqrrpt(A, 1.25, 4, 1e-12, 21, handle=h, stream=s, sync=False))
+    torch.cuda.synchronize()
+    for i, r in enumerate(outs):
+        ref = refs[i % 2]
+        st, k = hs[i % 2].last_status(ss[i % 2])
+        assert st == 0 and k == ref.k
+        assert np.array_equal(host(r.J), ref.J)
+        assert np.array_equal(host(r.Qbuf[:, :k]).view(np.uint64), ref.Q.view(np.uint64))
+        assert np.array_equal(host(r.Rbuf[:k]).view(np.uint64), ref.R.view(np.uint64))
+    for h in hs:
+        h.close()

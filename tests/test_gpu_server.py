@@ -173,3 +173,86 @@ def test_server_large_requests_both_precisions(C):
             rq, rr = split_bounds.ratios(Q, R, ref.Q, ref.R, ref.Rsk, A.shape[0])
             assert rq <= 4.0 and rr <= 4.0, (A.shape, rq, rr)
     srv.close()
+
+
+def test_server_units_overlap_and_stay_bit_identical(C):
+    # a wide request (single-problem route) is in flight while small requests
+    # arrive: their batched waves run on the other lanes beside it, so at
+    # least two units are in flight at once.  Every result equals a
+    # standalone call of its precision (FP64: also the oracle) bit for bit.
+    big_n, big_m = 400, 1 << 17
+    big = np.asfortranarray(W.planted(big_m, big_n, W.logspaced(big_n, -7.0), 6100).numpy())
+    reqs = [(big, 1e-12, 6200, 0)] + [(A, tol, seed, (2 if i % 3 == 2 else 0))
+                                      for i, (A, tol, seed) in enumerate(requests(12, 9))]
+    srv = C.Server(hbm_budget_bytes=4 << 30, max_inflight=32, lanes=3)
+    tickets = [srv.submit(pinned_colmajor(reqs[0][0]), reqs[0][1], reqs[0][2])]
+    time.sleep(0.01)
+    for A, tol, seed, prec in reqs[1:]:
+        tickets.append(srv.submit(pinned_colmajor(A), tol, seed, precision=prec))
+        time.sleep(0.001)
+    srv.drain(timeout_us=300_000_000)
+    st = srv.stats()
+    assert st["completed"] == len(reqs)
+    assert st["lanes"] == 3 and st["single_units"] == 1
+    assert st["max_busy_lanes"] >= 2, st
+    for t, (A, tol, seed, prec) in zip(tickets, reqs):
+        fac, res = srv.poll(t)
+        assert res.status == 0
+        one = C.cqrrpt(torch.from_numpy(A.T.copy()).cuda().t(), 1.25, 4, tol, seed,
+                       precision=prec)
+        assert res.k == one.k
+        assert np.array_equal(fac.J.numpy(), one.J.cpu().numpy())
+        assert np.array_equal(np.asfortranarray(fac.Q.numpy()).view(np.uint64),
+                              np.asfortranarray(one.Q.cpu().numpy()).view(np.uint64))
+        assert np.array_equal(np.asfortranarray(fac.R.numpy()).view(np.uint64),
+                              np.asfortranarray(one.R.cpu().numpy()).view(np.uint64))
+        if prec == 0 and A.shape[1] <= 64:
+            ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+            assert np.array_equal(np.asfortranarray(fac.Q.numpy()).view(np.uint64),
+                                  ref.Q.view(np.uint64))
+    srv.close()
+
+
+def test_server_one_lane_still_serves_everything(C):
+    # with a single lane the server degenerates to one unit at a time
+    reqs = requests(6, 10)
+    srv = C.Server(hbm_budget_bytes=1 << 30, max_inflight=8, lanes=1)
+    tickets = [srv.submit(pinned_colmajor(A), tol, seed) for A, tol, seed in reqs]
+    srv.drain(timeout_us=120_000_000)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["lanes"] == 1 and st["max_busy_lanes"] == 1
+    for t, (A, tol, seed) in zip(tickets, reqs):
+        fac, res = srv.poll(t)
+        ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+        assert res.k == ref.k
+        assert np.array_equal(np.asfortranarray(fac.R.numpy()).view(np.uint64),
+                              ref.R.view(np.uint64))
+    srv.close()
+
+
+def test_server_wide_requests_side_by_side(C):
+    # several wide requests: up to lanes - 1 single-route units at once, their
+    # cooperative QRCP grids one after another on the GPU; results equal the
+    # oracle bit for bit
+    rng = np.random.default_rng(12)
+    reqs = []
+    for i, n in enumerate([300, 320, 290, 270, 40, 50]):
+        m = int(rng.integers(20000, 40000))
+        A = W.planted(m, n, W.logspaced(n, -6.0), 9100 + i).numpy()
+        reqs.append((np.asfortranarray(A), 1e-12, 7100 + i))
+    srv = C.Server(hbm_budget_bytes=2 << 30, max_inflight=8, lanes=3)
+    tickets = [srv.submit(pinned_colmajor(A), tol, seed) for A, tol, seed in reqs]
+    srv.drain(timeout_us=300_000_000)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["single_units"] == 4
+    assert st["max_busy_lanes"] >= 2
+    for t, (A, tol, seed) in zip(tickets, reqs):
+        fac, res = srv.poll(t)
+        ref = oracle.cqrrpt(A, 1.25, 4, tol, seed)
+        assert res.status == ref.status and res.k == ref.k
+        assert np.array_equal(fac.J.numpy(), ref.J)
+        assert np.array_equal(np.asfortranarray(fac.Q.numpy()).view(np.uint64),
+                              ref.Q.view(np.uint64))
+        assert np.array_equal(np.asfortranarray(fac.R.numpy()).view(np.uint64),
+                              ref.R.view(np.uint64))
+    srv.close()

@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--rows", type=int, default=131072, help="m of the workload")
     p.add_argument("--workload", default="single",
                    choices=["single", "small", "batched", "mixed", "serve", "dense", "panels",
-                            "srrqr"],
+                            "srrqr", "sharded"],
                    help="single: the rank-800 131072 x 1024 problem (headline); small: the "
                         "4096 x 64 cond-1e8 problem (latency per factorisation); batched: 512 "
                         "uneven problems in one batched pass; mixed: 1048576 x 512, cond 1e10, "
@@ -68,7 +68,8 @@ def parse():
                         "headline matrix with a dense Gaussian operator instead of the SASO; "
                         "panels: the headline matrix streamed from pinned host memory in row "
                         "panels; srrqr: the headline matrix with the strong rank-revealing "
-                        "exchanges on the sketch")
+                        "exchanges on the sketch; sharded: one (ranks x --rows) x 1024 "
+                        "matrix partitioned by rows over the torchrun ranks")
     p.add_argument("--configs", default="all", choices=["all", "none"],
                    help="single workload, N = 1: also measure the small, mixed, batched and "
                         "serving workloads in the same run (all) or only the headline (none)")
@@ -400,6 +401,75 @@ def run_small(args, world, rank, local, C):
             "fp64_fraction": value * flops / 1e9 / FP64_PEAK_GFLOPS,
             "parity_vs_oracle": "bit-identical J, k, Q, R" if same else "MISMATCH",
             "gpu_launches": int(launches), "clocks": clk}
+
+
+def run_sharded(args, world, rank, local, C):
+    """The row-partitioned form (Sec. 2.1) across the torchrun ranks: one
+    m x 1024 problem with m = world x --rows (each rank holds --rows rows,
+    planted rank 800 as the headline workload), the sketch and the Gram
+    summed over the ranks in rank order (ordered_scan: NCCL send / receive
+    and broadcast of d x n and n x n doubles; gloo through host copies).
+    One step = one factorisation of the whole matrix by all ranks; weak
+    scaling (fixed rows per rank).  Rank 0 checks its rows of Q and the whole
+    R, J, k against cqrrpt_d on the whole matrix (N = 1: the same call)."""
+    import torch.distributed as dist
+    w = W.single_large(m=args.rows * world)
+    rows = args.rows
+    r0 = rank * rows
+    A_full = w.matrix("cuda")
+    A = C.colmajor(A_full[r0:r0 + rows])
+    ref = None
+    if rank == 0:
+        ref = C.cqrrpt(A_full, w.gamma, w.nnz, w.tol, w.sketch_seed)
+        ref = (ref.k, ref.J.clone(), ref.Q[:rows].clone(), ref.R.clone())
+    del A_full
+    torch.cuda.empty_cache()
+    h = C.Handle(local)
+    group = None
+
+    def step():
+        return C.cqrrpt_sharded(A, w.m, r0, w.gamma, w.nnz, w.tol, w.sketch_seed, group=group,
+                                handle=h)
+
+    for _ in range(args.warmup):
+        res = step()
+    assert res.status == 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = C.kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = step()
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    barrier(world)
+    launches = C.kernel_launches() - launches0
+    clk = clocks.stop()
+    elapsed = max_over_ranks(elapsed, world, "cuda")
+    value = args.steps / elapsed
+    parity = None
+    if rank == 0:
+        k, J, Q, R = ref
+        parity = ("bit-identical to cqrrpt_d on the whole matrix (rank 0's rows of Q, R, J, k)"
+                  if res.k == k and torch.equal(res.J, J) and torch.equal(res.Qbuf[:, :k], Q)
+                  and torch.equal(res.Rbuf[:k], R) else "MISMATCH")
+    d = w.d
+    return {"metric": "cqrrpt_factorizations_per_s", "value": value,
+            "unit": "factorizations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "cqrrpt_fp64_row_partitioned_m%d_n%d_rank800" % (w.m, w.n),
+                       "m": w.m, "rows_per_rank": rows, "n": w.n, "d": d,
+                       "nnz_per_col": w.nnz, "tol": w.tol,
+                       "parallelism": "rows over %d ranks" % world,
+                       "l2": "inputs larger than L2, no flush"},
+            "gflops_2mn2": value * 2.0 * w.m * w.n * w.n / 1e9,
+            "communication_bytes_per_rank": 8 * (d * w.n + w.n * w.n) * (2 if world > 1 else 0),
+            "parity": parity, "gpu_launches": int(launches), "clocks": clk}
 
 
 def run_batched(args, world, rank, local, C):
@@ -1019,7 +1089,7 @@ def main():
     cbuild.build()
     others = {"batched": run_batched, "mixed": run_mixed, "serve": run_serve,
               "dense": run_dense, "panels": run_panels, "srrqr": run_srrqr,
-              "small": run_small}
+              "small": run_small, "sharded": run_sharded}
     if args.workload in others:
         line = others[args.workload](args, world, rank, local, C)
         if rank == 0:

@@ -369,6 +369,74 @@ int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const 
 int cqrrpt_batched_get_tuning(cqrrpt_handle h, int* trsm_jb_host, int* gram_tile_host);
 int cqrrpt_batched_set_tuning(cqrrpt_handle h, const int* trsm_jb_host, const int* gram_tile_host);
 
+/* ---- row-partitioned CQRRPT over ranks (Sec. 2.1, communication cost) ---- */
+
+/* The paper's distributed form: the rows of M are split among ranks (each a
+ * process with its own device and handle), each rank sketches its rows, the
+ * d x n sketch is summed over the ranks, every rank factors the sketch
+ * (lines 2-3, the same J and k everywhere), each rank forms M^pre and its
+ * Gram contribution on its rows, the k x k Gram is summed over the ranks,
+ * and every rank finishes (lines 6-8) with Q on its own rows.  The two sums
+ * are the only communication: d n + k^2 words, plus their broadcast.
+ *
+ * Rank r holds rows [row0, row0 + rows) of M, with row0 a multiple of 4096;
+ * the ranks' ranges, in rank order, tile 0 .. m-1.  Each sum is an ordered
+ * scan: rank 0 starts from +0.0, rank r adds its 4096-row block sums in
+ * ascending block order to the running sum it receives from rank r-1 and
+ * passes it on; the last rank's sum is broadcast.  Every sum then runs in
+ * exactly the order of cqrrpt_d on the whole M (blocks ascending), so J, k,
+ * R and each rank's rows of Q are bit-identical to cqrrpt_d's.  The library
+ * does the arithmetic; the caller moves the two buffers between ranks (any
+ * transport: they are plain device arrays).
+ *
+ * Per rank, all calls on one handle and one stream, in this order:
+ *   cqrrpt_shard_sketch_d            block sums of S M on this rank's rows
+ *   cqrrpt_shard_sketch_accumulate_d acc += them (after receiving acc)
+ *   cqrrpt_shard_qrcp_d              lines 1-3 on the summed sketch
+ *   cqrrpt_shard_gram_d              line 4 on this rank's rows, and the
+ *                                    block sums of line 5
+ *   cqrrpt_shard_gram_accumulate_d   G += them (after receiving G)
+ *   cqrrpt_shard_finish_d            lines 6-8
+ * A phase called out of order returns -1.  The handle keeps the rank's state
+ * (and A's pointer: A must stay valid until cqrrpt_shard_gram_d). */
+
+/* Phase 1: m = rows of the whole M; rows, row0: this rank's rows; A: this
+ * rank's rows x n block (column-major, lda >= rows); gamma, nnz, seed as
+ * cqrrpt_d (the same on every rank).  Errors: -i for argument i (row0 not a
+ * multiple of 4096 or past m: -4; d > m: -8), CQRRPT_NO_MEMORY,
+ * CQRRPT_CUDA_ERROR. */
+int cqrrpt_shard_sketch_d(cqrrpt_handle h, int64_t m, int64_t rows, int64_t row0, int64_t n,
+                          const double* A, int64_t lda, double gamma, int nnz, uint64_t seed,
+                          cudaStream_t stream);
+
+/* Phase 2: acc (d x n, ld d, device) += this rank's block sums in ascending
+ * block order.  acc must hold +0.0 everywhere on rank 0, else the running
+ * sum received from the previous rank. */
+int cqrrpt_shard_sketch_accumulate_d(cqrrpt_handle h, double* acc, cudaStream_t stream);
+
+/* Phase 3: M^sk = acc / sqrt(nnz) (the complete sum, every rank the same),
+ * the QRCP (line 2) and the rank rule (line 3, tol as cqrrpt_d).  J: n
+ * device int64 pivots, which must stay valid until cqrrpt_shard_gram_d. */
+int cqrrpt_shard_qrcp_d(cqrrpt_handle h, const double* acc, double tol, int64_t* J,
+                        cudaStream_t stream);
+
+/* Phase 4: Q[:, :k] = A[:, J[:k]] (R^sk_11)^-1 on this rank's rows (M^pre,
+ * Q: rows x n capacity, ldq >= rows), then its 4096-row Gram block sums. */
+int cqrrpt_shard_gram_d(cqrrpt_handle h, double* Q, int64_t ldq, cudaStream_t stream);
+
+/* Phase 5: G (n x n, ld n, device; both triangles of the leading k x k
+ * written) += this rank's Gram block sums in ascending block order.  G must
+ * hold +0.0 on rank 0, else the running sum received from the previous
+ * rank. */
+int cqrrpt_shard_gram_accumulate_d(cqrrpt_handle h, double* G, cudaStream_t stream);
+
+/* Phase 6: with the complete G (overwritten as working storage): R^pre =
+ * chol(G) with Remark 4 and the second rank stage, Q[:, :k] = M^pre
+ * (R^pre)^-1 in place on this rank's rows, R = R^pre R^sk_k (n x n
+ * capacity, ldr >= n; every rank the same).  k_dev / k_host as cqrrpt_d. */
+int cqrrpt_shard_finish_d(cqrrpt_handle h, double* G, double* Q, int64_t ldq, double* R,
+                          int64_t ldr, int64_t* k_dev, int64_t* k_host, cudaStream_t stream);
+
 /* ---- serving: continuous batching ---------------------------------------- */
 
 /* One request: a host matrix and host output buffers (pinned host memory

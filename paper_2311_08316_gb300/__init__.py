@@ -64,6 +64,12 @@ def lib():
     L.cqrrpt_phase_times.argtypes = [_p, ctypes.POINTER(ctypes.c_float), _int]
     L.cqrrpt_kernel_launches.argtypes = []
     L.cqrrpt_set_wait_limits.argtypes = [_i64, _i64]
+    L.cqrrpt_shard_sketch_d.argtypes = [_p, _i64, _i64, _i64, _i64, _p, _i64, _d, _int, _u64, _p]
+    L.cqrrpt_shard_sketch_accumulate_d.argtypes = [_p, _p, _p]
+    L.cqrrpt_shard_qrcp_d.argtypes = [_p, _p, _d, _p, _p]
+    L.cqrrpt_shard_gram_d.argtypes = [_p, _p, _i64, _p]
+    L.cqrrpt_shard_gram_accumulate_d.argtypes = [_p, _p, _p]
+    L.cqrrpt_shard_finish_d.argtypes = [_p, _p, _p, _i64, _p, _i64, _p, _p, _p]
     L.cqrrpt_probe_fp64_gflops.argtypes = [_int, _int, ctypes.POINTER(_d), ctypes.POINTER(_d)]
     L.cqrrpt_kernel_launches.restype = ctypes.c_longlong
     L.cqrrpt_batched_d.argtypes = [_p, _int, _p, _p, _p, _p, _d, _int, _p, _p, _int, _p, _p, _p,
@@ -117,7 +123,9 @@ def exported_symbols():
             "cqrrpt_sketch_dense_d", "cqrrpt_panels_host_d", "cqrrpt_srrqr_d",
             "cqrrpt_sketch_dense_split_d", "cqrrpt_set_wait_limits", "cqrrpt_sketch_noalloc_d",
             "cqrrpt_sketch_noalloc_max_bytes", "cqrrpt_sketch_noalloc_status",
-            "cqrrpt_probe_fp64_gflops", "cqrrpt_server_create_lanes", "cqrrpt_server_stats_ex"]
+            "cqrrpt_probe_fp64_gflops", "cqrrpt_server_create_lanes", "cqrrpt_server_stats_ex",
+            "cqrrpt_shard_sketch_d", "cqrrpt_shard_sketch_accumulate_d", "cqrrpt_shard_qrcp_d",
+            "cqrrpt_shard_gram_d", "cqrrpt_shard_gram_accumulate_d", "cqrrpt_shard_finish_d"]
 
 
 PHASES = ["sketch", "qrcp", "rank", "trsm_pre", "gram", "cholesky", "trsm_q", "trmm"]
@@ -285,6 +293,91 @@ def cqrrpt(A, gamma=1.25, nnz=4, tol=-1.0, seed=0, precision=FP64, out=None, han
         _check(rc, "cqrrpt_d")
     if not sync:
         return Factorization(Q, R, J, None, None)
+    return Factorization(Q, R, J, k.value, rc)
+
+
+def ordered_scan(buf, accumulate, group=None):
+    """The ordered sum over the ranks of `group` (torch.distributed): rank 0
+    starts from buf as it is (+0.0), rank r receives the running sum from
+    rank r - 1 into buf, calls accumulate(buf) to add its own part, and
+    passes buf on to rank r + 1; the last rank's buf is then broadcast, so
+    every rank ends with the complete sum, added in rank order.  This moves
+    data only (the arithmetic is accumulate's).  CUDA buffers travel through
+    host copies on the gloo backend and directly on NCCL."""
+    import torch.distributed as dist
+    if group is None and not dist.is_initialized():
+        accumulate(buf)
+        return buf
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    glob = (lambda r: r) if group is None else (lambda r: dist.get_global_rank(group, r))
+    staged = buf.is_cuda and dist.get_backend(group) == "gloo"
+
+    def recv(src):
+        if staged:
+            h = torch.empty(buf.shape, dtype=buf.dtype)
+            dist.recv(h, src=glob(src), group=group)
+            buf.copy_(h)
+        else:
+            dist.recv(buf, src=glob(src), group=group)
+
+    def send(dst):
+        if staged:
+            torch.cuda.current_stream().synchronize()
+            dist.send(buf.cpu(), dst=glob(dst), group=group)
+        else:
+            dist.send(buf, dst=glob(dst), group=group)
+
+    if world > 1 and rank > 0:
+        recv(rank - 1)
+    accumulate(buf)
+    if world > 1 and rank < world - 1:
+        send(rank + 1)
+    if world > 1:
+        if staged:
+            torch.cuda.current_stream().synchronize()
+            h = buf.cpu()
+            dist.broadcast(h, src=glob(world - 1), group=group)
+            buf.copy_(h)
+        else:
+            dist.broadcast(buf, src=glob(world - 1), group=group)
+    return buf
+
+
+def cqrrpt_sharded(A_local, m, row0, gamma=1.25, nnz=4, tol=-1.0, seed=0, group=None,
+                   handle=None):
+    """Row-partitioned CQRRPT (Sec. 2.1) across the ranks of `group`: this
+    rank holds rows [row0, row0 + rows) of the m x n matrix M (A_local, a
+    column-major float64 CUDA tensor; row0 a multiple of 4096; the ranks'
+    ranges tile M in rank order).  The sketch and the Gram are summed over
+    the ranks by ordered_scan through the cqrrpt_shard_* phases, on the
+    current stream.  Returns a Factorization with this rank's rows of Q and
+    the whole R, J, k: bit-identical to cqrrpt() on the whole M."""
+    h = handle or default_handle()
+    L = lib()
+    rows, n = A_local.shape
+    st = _stream(None)
+    _check(L.cqrrpt_shard_sketch_d(h.h, m, rows, row0, n, A_local.data_ptr(), _ld(A_local),
+                                   gamma, nnz, seed, st), "cqrrpt_shard_sketch_d")
+    d = sketch_dim(n, gamma)
+    dev = A_local.device
+    acc = torch.zeros(d * n, dtype=torch.float64, device=dev)
+    ordered_scan(acc, lambda b: _check(L.cqrrpt_shard_sketch_accumulate_d(h.h, b.data_ptr(), st),
+                                       "cqrrpt_shard_sketch_accumulate_d"), group)
+    J = torch.empty(n, dtype=torch.int64, device=dev)
+    _check(L.cqrrpt_shard_qrcp_d(h.h, acc.data_ptr(), tol, J.data_ptr(), st),
+           "cqrrpt_shard_qrcp_d")
+    Q = colmajor_empty(rows, n, dev)
+    _check(L.cqrrpt_shard_gram_d(h.h, Q.data_ptr(), _ld(Q), st), "cqrrpt_shard_gram_d")
+    G = torch.zeros(n * n, dtype=torch.float64, device=dev)
+    ordered_scan(G, lambda b: _check(L.cqrrpt_shard_gram_accumulate_d(h.h, b.data_ptr(), st),
+                                     "cqrrpt_shard_gram_accumulate_d"), group)
+    R = colmajor_empty(n, n, dev)
+    k = _i64()
+    rc = L.cqrrpt_shard_finish_d(h.h, G.data_ptr(), Q.data_ptr(), _ld(Q), R.data_ptr(), _ld(R),
+                                 None, ctypes.byref(k), st)
+    if rc < 0 or rc >= 3:
+        _check(rc, "cqrrpt_shard_finish_d")
     return Factorization(Q, R, J, k.value, rc)
 
 

@@ -62,6 +62,16 @@ struct cqrrpt_ctx {
   // split path: side stream and fork/join events (inverses beside splits)
   cudaStream_t side = nullptr;
   cudaEvent_t side_ev[2] = {};
+  // row-partitioned form (cqrrpt_shard_*): this rank's rows and the state
+  // carried from one phase to the next
+  struct {
+    const double* A = nullptr;
+    int64_t lda = 0, m = 0, rows = 0, row0 = 0, n = 0, d = 0;
+    int nnz = 0;
+    double tol = 0.0;
+    const int64_t* J = nullptr;
+    int phase = 0;  // 1 sketched, 2 factored the sketch, 3 Gram block sums
+  } shard;
 };
 
 static std::atomic<long long> g_launches{0};
@@ -723,6 +733,165 @@ int pipe_ensure(cqrrpt_handle h, int64_t m, int64_t n) {
 }  // namespace
 
 extern "C" {
+
+// ---- row-partitioned CQRRPT (Sec. 2.1): one rank's phases ---------------
+// The workspace carve of a rank: the plan of a rows-row factorisation.
+static Plan shard_plan(cqrrpt_handle h) {
+  return plan_fp64(h->shard.rows, h->shard.n, h->shard.d, h->shard.nnz);
+}
+struct ShardWs {
+  void* region;
+  double *X, *Rsk, *G, *Rpre, *f2;
+  void* qw;
+};
+static ShardWs shard_ws(cqrrpt_handle h) {
+  const Plan p = shard_plan(h);
+  char* w = (char*)h->ws;
+  ShardWs s;
+  s.region = w; w += p.region;
+  s.X = (double*)w; w += p.x;
+  s.qw = w; w += p.qrcp;
+  s.Rsk = (double*)w; w += p.rsk;
+  s.G = (double*)w; w += p.g;
+  s.Rpre = (double*)w; w += p.rpre;
+  s.f2 = (double*)w;
+  return s;
+}
+
+int cqrrpt_shard_sketch_d(cqrrpt_handle h, int64_t m, int64_t rows, int64_t row0, int64_t n,
+                          const double* A, int64_t lda, double gamma, int nnz, uint64_t seed,
+                          cudaStream_t stream) {
+  if (!h) return -1;
+  if (m < 1) return -2;
+  if (rows < 1 || rows > m) return -3;
+  if (row0 < 0 || row0 % kRowBlock != 0 || row0 + rows > m) return -4;
+  if (n < 1 || n > 16384) return -5;
+  if (!A) return -6;
+  if (lda < rows) return -7;
+  if (!(gamma >= 1.0) || !std::isfinite(gamma)) return -8;
+  const int64_t d = sketch_dim(n, gamma);
+  if (d > m || d > 28000) return -8;
+  if (nnz < 1 || nnz > d || nnz > kMaxNnzInline) return -9;
+  DevGuard g(h->device);
+  h->shard.A = A;
+  h->shard.lda = lda;
+  h->shard.m = m;
+  h->shard.rows = rows;
+  h->shard.row0 = row0;
+  h->shard.n = n;
+  h->shard.d = d;
+  h->shard.nnz = nnz;
+  h->shard.phase = 0;
+  int st = ensure_ws(h, shard_plan(h).total);
+  if (st != kOk) return st;
+  const ShardWs w = shard_ws(h);
+  if (launch_init_scalars(h->sc, 0, stream) != cudaSuccess ||
+      launch_sketch_panel_partials(rows, n, A, lda, (int)d, nnz, seed, row0, w.region, stream) !=
+          cudaSuccess)
+    return kCudaError;
+  h->shard.phase = 1;
+  return kOk;
+}
+
+int cqrrpt_shard_sketch_accumulate_d(cqrrpt_handle h, double* acc, cudaStream_t stream) {
+  if (!h) return -1;
+  if (!acc) return -2;
+  if (h->shard.phase != 1) return -1;
+  DevGuard g(h->device);
+  const ShardWs w = shard_ws(h);
+  return launch_sketch_panel_accumulate(h->shard.rows, h->shard.n, (int)h->shard.d,
+                                        h->shard.nnz, acc, w.region, stream) == cudaSuccess
+             ? kOk
+             : kCudaError;
+}
+
+int cqrrpt_shard_qrcp_d(cqrrpt_handle h, const double* acc, double tol, int64_t* J,
+                        cudaStream_t stream) {
+  if (!h) return -1;
+  if (!acc) return -2;
+  if (std::isnan(tol)) return -3;
+  if (!J) return -4;
+  if (h->shard.phase != 1) return -1;
+  DevGuard g(h->device);
+  const ShardWs w = shard_ws(h);
+  const int ni = (int)h->shard.n, di = (int)h->shard.d;
+  DeviceScalars* sc = h->sc;
+  cudaError_t e = launch_sketch_finish(di, h->shard.n, acc, 1.0 / std::sqrt((double)h->shard.nnz),
+                                       w.X, h->shard.d, &sc->status, stream);
+  if (e == cudaSuccess)
+    e = launch_qrcp(di, ni, w.X, h->shard.d, J, w.Rsk, h->shard.n, w.qw, sc, h->num_sms, stream);
+  if (e == cudaSuccess) e = launch_rank(ni, w.Rsk, h->shard.n, tol, sc, w.f2, stream);
+  if (e != cudaSuccess) return kCudaError;
+  h->shard.tol = tol;
+  h->shard.J = J;
+  h->shard.phase = 2;
+  return kOk;
+}
+
+int cqrrpt_shard_gram_d(cqrrpt_handle h, double* Q, int64_t ldq, cudaStream_t stream) {
+  if (!h) return -1;
+  if (!Q) return -2;
+  if (ldq < h->shard.rows) return -3;
+  if (h->shard.phase != 2) return -1;
+  DevGuard g(h->device);
+  const ShardWs w = shard_ws(h);
+  const int ni = (int)h->shard.n;
+  DeviceScalars* sc = h->sc;
+  cudaError_t e = launch_trsm_rut(h->shard.rows, ni, &sc->k, h->shard.A, h->shard.lda,
+                                  h->shard.J, w.Rsk, h->shard.n, Q, ldq, &sc->status, stream);
+  if (e == cudaSuccess)
+    e = launch_gram_partials(h->shard.rows, ni, &sc->k, Q, ldq, w.region, &sc->status, stream);
+  if (e != cudaSuccess) return kCudaError;
+  h->shard.phase = 3;
+  return kOk;
+}
+
+int cqrrpt_shard_gram_accumulate_d(cqrrpt_handle h, double* G, cudaStream_t stream) {
+  if (!h) return -1;
+  if (!G) return -2;
+  if (h->shard.phase != 3) return -1;
+  DevGuard g(h->device);
+  const ShardWs w = shard_ws(h);
+  return launch_gram_sum(h->shard.rows, (int)h->shard.n, &h->sc->k, G, h->shard.n, w.region,
+                         &h->sc->status, stream, true) == cudaSuccess
+             ? kOk
+             : kCudaError;
+}
+
+int cqrrpt_shard_finish_d(cqrrpt_handle h, double* G, double* Q, int64_t ldq, double* R,
+                          int64_t ldr, int64_t* k_dev, int64_t* k_host, cudaStream_t stream) {
+  if (!h) return -1;
+  if (!G) return -2;
+  if (!Q) return -3;
+  if (ldq < h->shard.rows) return -4;
+  if (!R) return -5;
+  if (ldr < h->shard.n) return -6;
+  if (h->shard.phase != 3) return -1;
+  DevGuard g(h->device);
+  const ShardWs w = shard_ws(h);
+  const int ni = (int)h->shard.n;
+  const int64_t n = h->shard.n;
+  DeviceScalars* sc = h->sc;
+  int* status = &sc->status;
+  cudaError_t e = launch_potrf(ni, G, n, w.Rpre, n, sc, stream);
+  if (e == cudaSuccess) e = launch_rank_stage2(w.Rpre, n, !(h->shard.tol > 0.0), sc, stream);
+  if (e == cudaSuccess)
+    e = launch_trsm_rut(h->shard.rows, ni, &sc->k, Q, ldq, nullptr, w.Rpre, n, Q, ldq, status,
+                        stream);
+  if (e == cudaSuccess) e = launch_trmm(ni, &sc->k, w.Rpre, n, w.Rsk, n, R, ldr, status, stream);
+  if (e == cudaSuccess) e = launch_finalize(sc, k_dev, nullptr, stream);
+  if (e != cudaSuccess) return kCudaError;
+  h->shard.phase = 0;
+  if (k_host) {
+    int st2 = kOk;
+    int64_t kk = 0;
+    const int r = cqrrpt_last_status(h, stream, &st2, &kk);
+    if (r != kOk) return r;
+    *k_host = kk;
+    return st2;
+  }
+  return kOk;
+}
 
 int cqrrpt_host_pipeline_d(cqrrpt_handle h, int count, int64_t m, int64_t n,
                            const double* const* A_host, int64_t lda, double gamma, int nnz,

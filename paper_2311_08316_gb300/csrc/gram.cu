@@ -173,11 +173,11 @@ static int gram_single_tile(int64_t m, int kmax) {
   return 8;
 }
 
-cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
-                        double* G, int64_t ldg, void* work, const int* status,
-                        cudaStream_t stream, bool accumulate) {
+cudaError_t launch_gram_partials(int64_t m, int kmax, const int64_t* k_dev, const double* X,
+                                 int64_t ldx, void* work, const int* status,
+                                 cudaStream_t stream) {
   const int tile = gram_single_tile(m, kmax);
-  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, G, ldg, status, tile};
+  GramDesc D{m, kmax, k_dev, X, ldx, (double*)work, nullptr, 0, status, tile};
   const unsigned grid = (unsigned)gram_partial_tiles(m, kmax, tile);
   if (tile == 8)
     gram_partial_kernel<8><<<grid, 64, 0, stream>>>(D);
@@ -185,12 +185,27 @@ cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double*
     gram_partial_kernel<16><<<grid, 64, 0, stream>>>(D);
   else
     gram_partial_kernel<kGramTile><<<grid, 64, 0, stream>>>(D);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_sum(int64_t m, int kmax, const int64_t* k_dev, double* G, int64_t ldg,
+                            void* work, const int* status, cudaStream_t stream, bool accumulate) {
+  GramDesc D{m, kmax, k_dev, nullptr, 0, (double*)work, G, ldg, status, kGramTile};
   if (accumulate)
     gram_accumulate_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
   else
     gram_combine_kernel<<<(unsigned)gram_combine_tiles(kmax), kCombineThreads, 0, stream>>>(D);
-  count_launches(2);
+  count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
+                        double* G, int64_t ldg, void* work, const int* status,
+                        cudaStream_t stream, bool accumulate) {
+  cudaError_t e = launch_gram_partials(m, kmax, k_dev, X, ldx, work, status, stream);
+  if (e != cudaSuccess) return e;
+  return launch_gram_sum(m, kmax, k_dev, G, ldg, work, status, stream, accumulate);
 }
 
 cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* base, int np,

@@ -55,6 +55,13 @@ cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_
                                 cudaStream_t stream);
 cudaError_t launch_sketch_finish(int d, int64_t n, const double* acc, double scale, double* Msk,
                                  int64_t ldsk, int* status, cudaStream_t stream);
+// The two halves of launch_sketch_panel: the panel's block sums into `work`,
+// then acc += those sums in ascending block order (the same work carve).
+cudaError_t launch_sketch_panel_partials(int64_t rows, int64_t n, const double* M, int64_t ldm,
+                                         int d, int s, uint64_t seed, int64_t row0, void* work,
+                                         cudaStream_t stream);
+cudaError_t launch_sketch_panel_accumulate(int64_t rows, int64_t n, int d, int s, double* acc,
+                                           void* work, cudaStream_t stream);
 // The same product on the BF16 tensor cores (split-BF16, FP64-accurate, not
 // bit-identical): S transposed, then the Gram's K-sliced product of S^T and M.
 // work: sketch_dense_split_workspace_bytes.
@@ -129,6 +136,13 @@ int64_t gram_combine_tiles(int kmax);
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
                         cudaStream_t stream, bool accumulate = false);
+// The two halves of launch_gram: the block sums into `work`, then G (both
+// triangles) = (accumulate: G +) their ascending sum.
+cudaError_t launch_gram_partials(int64_t m, int kmax, const int64_t* k_dev, const double* X,
+                                 int64_t ldx, void* work, const int* status,
+                                 cudaStream_t stream);
+cudaError_t launch_gram_sum(int64_t m, int kmax, const int64_t* k_dev, double* G, int64_t ldg,
+                            void* work, const int* status, cudaStream_t stream, bool accumulate);
 // phase 0: partial tiles, 1: combine
 cudaError_t launch_gram_batched(int phase, const GramDesc* D, const int64_t* base, int nprob,
                                 int64_t total_tiles, cudaStream_t stream);

@@ -378,9 +378,9 @@ cudaError_t launch_sketch_dense(int64_t m, int64_t n, const double* S, int64_t l
   return cudaGetLastError();
 }
 
-cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_t ldm, int d,
-                                int s, uint64_t seed, int64_t row0, double* acc, void* work,
-                                cudaStream_t stream) {
+cudaError_t launch_sketch_panel_partials(int64_t rows, int64_t n, const double* M, int64_t ldm,
+                                         int d, int s, uint64_t seed, int64_t row0, void* work,
+                                         cudaStream_t stream) {
   SketchDesc D{};
   D.m = rows; D.n = n; D.d = d; D.s = s; D.seed = seed; D.row0 = row0; D.scale = 1.0;
   D.M = M; D.ldm = ldm;
@@ -392,10 +392,27 @@ cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_
   const int64_t ncg = (n + kSkCols - 1) / kSkCols;
   sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), sketch_threads(d),
                           kRowBlock * sizeof(double2), stream>>>(D, ncg);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_panel_accumulate(int64_t rows, int64_t n, int d, int s, double* acc,
+                                           void* work, cudaStream_t stream) {
+  SketchDesc D{};
+  D.m = rows; D.n = n; D.d = d; D.s = s;
+  sketch_carve(D, work);
   sketch_accumulate_kernel<<<(unsigned)sketch_combine_tiles(D), kCombineThreads, 0, stream>>>(
       D, acc);
-  count_launches(3);
+  count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_panel(int64_t rows, int64_t n, const double* M, int64_t ldm, int d,
+                                int s, uint64_t seed, int64_t row0, double* acc, void* work,
+                                cudaStream_t stream) {
+  cudaError_t e = launch_sketch_panel_partials(rows, n, M, ldm, d, s, seed, row0, work, stream);
+  if (e != cudaSuccess) return e;
+  return launch_sketch_panel_accumulate(rows, n, d, s, acc, work, stream);
 }
 
 cudaError_t launch_sketch_finish(int d, int64_t n, const double* acc, double scale, double* Msk,

@@ -1,13 +1,14 @@
 """Run factorisations of the synthetic workloads from the command line (a
 driver for profilers and quick checks).
 
-    python -m paper_2311_08316_gb300 [--workload single|mixed] [--rows M]
+    python -m paper_2311_08316_gb300 [--workload single|mixed|small] [--rows M]
                                      [--reps R] [--precision fp64|splitbf16|cholqr2]
                                      [--operator saso|gaussian] [--srrqr F]
                                      [--panels ROWS]
 
 `single` is the rank-800 workload (n = 1024, planted rank 800, tol 1e-9),
-`mixed` the cond-1e10 workload (n = 512); --rows sets m.  --operator
+`mixed` the cond-1e10 workload (n = 512), `small` the 4096 x 64 cond-1e8
+workload (d = 128); --rows sets m.  --operator
 gaussian sketches with a dense Gaussian operator (iid N(0, 1/d), drawn once
 on the device) through cqrrpt_dense_d instead of the SASO.  --srrqr F adds
 the strong rank-revealing exchanges with tuning parameter F (FP64), and
@@ -35,7 +36,7 @@ PRECISIONS = {"fp64": C.FP64, "splitbf16": C.SPLITBF16, "cholqr2": C.SPLITBF16_C
 
 def main(argv=None):
     p = argparse.ArgumentParser(prog="python -m paper_2311_08316_gb300")
-    p.add_argument("--workload", default="single", choices=["single", "mixed"])
+    p.add_argument("--workload", default="single", choices=["single", "mixed", "small"])
     p.add_argument("--rows", type=int, default=None)
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
@@ -46,6 +47,8 @@ def main(argv=None):
     build.build()
     if a.workload == "single":
         w = W.single_large(m=a.rows or 131072)
+    elif a.workload == "small":
+        w = W.single_small(m=a.rows or 4096)
     else:
         w = W.mixed_tall(m=a.rows or (1 << 20))
     A = w.matrix("cuda")

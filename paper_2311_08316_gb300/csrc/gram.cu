@@ -71,17 +71,46 @@ __device__ __forceinline__ void gram_partial_tile(int64_t tile, const GramDesc& 
 #pragma unroll
     for (int v = 0; v < R; ++v) acc[u][v] = 0.0;
 
-  for (int rr0 = 0; rr0 < rows; rr0 += kGramRows) {
+  // small tiles (few CTAs, latency-bound): the next chunk's rows are loaded
+  // into registers while the current chunk is summed
+  constexpr bool kPrefetch = TILE <= 16;
+  constexpr int kPer = kPrefetch ? TILE * kGramRows / 64 : 1;  // staged elements per thread
+  double pa[kPer], pc[kPer];
+  auto load_chunk = [&](int rr0) {
     const int nr = min(kGramRows, rows - rr0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < TILE * kGramRows; e += 64) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = threadIdx.x + 64 * q;
       const int col = e / kGramRows, row = e % kGramRows;
       const int64_t r = r0 + rr0 + row;
       const bool rok = row < nr;
-      Xa[col][row] = (rok && a0 + col < k) ? X[(int64_t)(a0 + col) * ldx + r] : 0.0;
-      Xc[col][row] = (rok && c0 + col < k) ? X[(int64_t)(c0 + col) * ldx + r] : 0.0;
+      pa[q] = (rok && a0 + col < k) ? X[(int64_t)(a0 + col) * ldx + r] : 0.0;
+      pc[q] = (rok && c0 + col < k) ? X[(int64_t)(c0 + col) * ldx + r] : 0.0;
+    }
+  };
+  if constexpr (kPrefetch) load_chunk(0);
+  for (int rr0 = 0; rr0 < rows; rr0 += kGramRows) {
+    const int nr = min(kGramRows, rows - rr0);
+    __syncthreads();
+    if constexpr (kPrefetch) {
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int e = threadIdx.x + 64 * q;
+        Xa[e / kGramRows][e % kGramRows] = pa[q];
+        Xc[e / kGramRows][e % kGramRows] = pc[q];
+      }
+    } else {
+      for (int e = threadIdx.x; e < TILE * kGramRows; e += 64) {
+        const int col = e / kGramRows, row = e % kGramRows;
+        const int64_t r = r0 + rr0 + row;
+        const bool rok = row < nr;
+        Xa[col][row] = (rok && a0 + col < k) ? X[(int64_t)(a0 + col) * ldx + r] : 0.0;
+        Xc[col][row] = (rok && c0 + col < k) ? X[(int64_t)(c0 + col) * ldx + r] : 0.0;
+      }
     }
     __syncthreads();
+    if constexpr (kPrefetch)
+      if (rr0 + kGramRows < rows) load_chunk(rr0 + kGramRows);
     for (int row = 0; row < nr; ++row) {
       double va[R], vc[R];
 #pragma unroll

@@ -13,7 +13,8 @@
 // by the diagonal-block and panel steps, again in ascending t.
 //
 // Single problem: three launches per panel (diagonal block, panel rows,
-// trailing update).  Inside the diagonal block and the panel the sums run
+// trailing update); a factor of at most 128 columns runs on one CTA, as a
+// batch's problems do.  Inside the diagonal block and the panel the sums run
 // right-looking (registers hold every running sum of a column), which keeps
 // each entry's ascending-t order but shortens the dependent chain.  Batch: one CTA per problem runs every panel with block
 // barriers between the steps; same bodies, same arithmetic.
@@ -139,9 +140,8 @@ __global__ void potrf_update_kernel(int jb, PotrfDesc D) {
   potrf_update_elem(jb, base, a, c, D);
 }
 
-// ---- batch: one CTA per problem -----------------------------------------------
-__global__ void __launch_bounds__(256) potrf_batched_kernel(const PotrfDesc* Dv) {
-  const PotrfDesc& D = Dv[blockIdx.x];
+// ---- one CTA per problem (a batch, or a small single problem) -----------------
+__device__ __forceinline__ void potrf_cta_body(const PotrfDesc& D) {
   DeviceScalars* sc = D.sc;
   __shared__ int go;
   for (int jb = 0; jb < D.kmax; jb += kCholNB) {
@@ -169,9 +169,25 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const PotrfDesc* Dv)
   }
 }
 
+__global__ void __launch_bounds__(256) potrf_batched_kernel(const PotrfDesc* Dv) {
+  potrf_cta_body(Dv[blockIdx.x]);
+}
+
+// A small factor (k <= kPotrfSingleCtaMax): every panel in one launch on one
+// CTA (block barriers instead of three launches per panel); same bodies.
+constexpr int kPotrfSingleCtaMax = 128;
+__global__ void __launch_bounds__(256) potrf_single_cta_kernel(PotrfDesc D) {
+  potrf_cta_body(D);
+}
+
 cudaError_t launch_potrf(int kmax, double* G, int64_t ldg, double* R, int64_t ldr,
                          DeviceScalars* sc, cudaStream_t stream) {
   PotrfDesc D{kmax, G, ldg, R, ldr, sc};
+  if (kmax <= kPotrfSingleCtaMax) {
+    potrf_single_cta_kernel<<<1, 256, 0, stream>>>(D);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   for (int jb = 0; jb < kmax; jb += kCholNB) {
     potrf_diag_kernel<<<1, 32, 0, stream>>>(jb, D);
     count_launches(1);

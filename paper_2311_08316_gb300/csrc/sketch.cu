@@ -29,6 +29,15 @@
 
 namespace cqrrpt {
 
+constexpr int kListThreads = 256;   // saso_lists: threads per CTA
+constexpr int kListMapWords = kRowBlock / 32;  // one bit per row of a block
+// dynamic shared memory of saso_lists: counts and starts (2 d + 1 ints),
+// then per warp a row map and a sign map of kListMapWords words each
+static size_t lists_smem_bytes(int d) {
+  return (size_t)(2 * d + 1) * sizeof(int) +
+         (size_t)(kListThreads / 32) * 2 * kListMapWords * sizeof(uint32_t);
+}
+
 // entries: (r_local << 1) | negative
 __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, int* sh_lists) {
   const int d = D.d, s = D.s;
@@ -77,17 +86,59 @@ __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, 
     }
   }
   __syncthreads();
-  // each segment to ascending r (insertion sort; segments are short)
-  for (int i = threadIdx.x; i < d; i += blockDim.x) {
-    const int a = start[i], e = start[i + 1];
-    for (int x = a + 1; x < e; ++x) {
-      const uint32_t key = gent[x];
-      int y = x - 1;
-      while (y >= a && gent[y] > key) {
-        gent[y + 1] = gent[y];
-        --y;
+  // each segment to ascending r: one warp per segment marks its rows (and
+  // their signs) in two 4096-bit maps in shared memory -- the rows of a
+  // segment are distinct, a row having s distinct targets -- then writes
+  // them back in bit order, lane l taking map words 4l .. 4l+3 at the offset
+  // of a warp prefix sum of the words' popcounts: O(L + 128) per segment of
+  // L entries instead of an O(L^2) insertion sort
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    uint32_t* rowmap = (uint32_t*)(start + d + 1) + warp * 2 * kListMapWords;
+    uint32_t* negmap = rowmap + kListMapWords;
+    for (int i = warp; i < d; i += nwarps) {
+      const int a = start[i], e = start[i + 1];
+      if (e - a < 2) continue;  // uniform over the warp
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        rowmap[4 * lane + u] = 0u;
+        negmap[4 * lane + u] = 0u;
       }
-      gent[y + 1] = key;
+      __syncwarp();
+      for (int x = a + lane; x < e; x += 32) {
+        const uint32_t w = gent[x];
+        const uint32_t r = w >> 1;
+        atomicOr(&rowmap[r >> 5], 1u << (r & 31));
+        if (w & 1u) atomicOr(&negmap[r >> 5], 1u << (r & 31));
+      }
+      __syncwarp();
+      uint32_t words[4], negs[4];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        words[u] = rowmap[4 * lane + u];
+        negs[u] = negmap[4 * lane + u];
+        cnt += __popc(words[u]);
+      }
+      int x = cnt;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+      }
+      int pos = a + x - cnt;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint32_t bits = words[u];
+        while (bits) {
+          const int bit = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const uint32_t r = (uint32_t)((4 * lane + u) * 32 + bit);
+          gent[pos++] = (r << 1) | ((negs[u] >> bit) & 1u);
+        }
+      }
+      __syncwarp();
     }
   }
 }
@@ -346,10 +397,10 @@ cudaError_t launch_sketch(int64_t m, int64_t n, const double* M, int64_t ldm, in
   D.m = m; D.n = n; D.d = d; D.s = s; D.seed = seed; D.scale = scale;
   D.M = M; D.ldm = ldm; D.Msk = Msk; D.ldsk = ldsk; D.status = status;
   sketch_carve(D, work);
-  const size_t sh_lists = (size_t)(2 * d + 1) * sizeof(int);
+  const size_t sh_lists = lists_smem_bytes(d);
   cudaError_t e = set_smem_attrs(sh_lists);
   if (e != cudaSuccess) return e;
-  saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), 256, sh_lists, stream>>>(D);
+  saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), kListThreads, sh_lists, stream>>>(D);
   const int64_t ncg = (n + kSkCols - 1) / kSkCols;
   sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), sketch_threads(d),
                           kRowBlock * sizeof(double2), stream>>>(D, ncg);
@@ -385,10 +436,10 @@ cudaError_t launch_sketch_panel_partials(int64_t rows, int64_t n, const double* 
   D.m = rows; D.n = n; D.d = d; D.s = s; D.seed = seed; D.row0 = row0; D.scale = 1.0;
   D.M = M; D.ldm = ldm;
   sketch_carve(D, work);
-  const size_t sh_lists = (size_t)(2 * d + 1) * sizeof(int);
+  const size_t sh_lists = lists_smem_bytes(d);
   cudaError_t e = set_smem_attrs(sh_lists);
   if (e != cudaSuccess) return e;
-  saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), 256, sh_lists, stream>>>(D);
+  saso_lists_kernel<<<(unsigned)sketch_list_tiles(D), kListThreads, sh_lists, stream>>>(D);
   const int64_t ncg = (n + kSkCols - 1) / kSkCols;
   sketch_partial_kernel<<<(unsigned)sketch_partial_tiles(D), sketch_threads(d),
                           kRowBlock * sizeof(double2), stream>>>(D, ncg);
@@ -488,18 +539,17 @@ cudaError_t launch_sketch_dense_split(int64_t m, int64_t n, const double* S, int
   return oz_gemm_tn(m, d, (int)n, St, m, M, ldm, Msk, ldsk, rest, stream, status);
 }
 
-cudaError_t sketch_set_attributes(int max_d) {
-  return set_smem_attrs((size_t)(2 * max_d + 1) * sizeof(int));
-}
+cudaError_t sketch_set_attributes(int max_d) { return set_smem_attrs(lists_smem_bytes(max_d)); }
 
 // The shared-memory attributes must have been set by sketch_set_attributes
 // (outside any stream capture).
 cudaError_t launch_sketch_batched(int phase, const SketchDesc* D, const int64_t* base, int np,
                                   int64_t total_tiles, int max_d, cudaStream_t stream) {
   if (total_tiles <= 0) return cudaSuccess;
-  const size_t sh_lists = (size_t)(2 * max_d + 1) * sizeof(int);
+  const size_t sh_lists = lists_smem_bytes(max_d);
   if (phase == 0)
-    saso_lists_batched_kernel<<<(unsigned)total_tiles, 256, sh_lists, stream>>>(D, base, np);
+    saso_lists_batched_kernel<<<(unsigned)total_tiles, kListThreads, sh_lists, stream>>>(D, base,
+                                                                                        np);
   else if (phase == 1)
     sketch_partial_batched_kernel<<<(unsigned)total_tiles, sketch_threads(max_d),
                                     kRowBlock * sizeof(double2), stream>>>(D, base, np);

@@ -25,8 +25,9 @@
 
 namespace cqrrpt {
 
-// Columns j0 .. j0 + JB - 1 of the thread's row i (all of them exist).
-template <int JB>
+// Columns j0 .. j0 + JB - 1 of the thread's row i (all of them exist);
+// THREADS threads per CTA.
+template <int JB, int THREADS>
 __device__ __forceinline__ void trsm_rut_block(int j0, int64_t i, bool active, double* Ts,
                                                double* Td, const TrsmDesc& D) {
   const double* B = D.B;
@@ -47,7 +48,7 @@ __device__ __forceinline__ void trsm_rut_block(int j0, int64_t i, bool active, d
   for (int t0 = 0; t0 < j0; t0 += kTrsmTB) {
     const int tb = min(kTrsmTB, j0 - t0);
     __syncthreads();
-    for (int e = threadIdx.x; e < tb * JB; e += kTrsmThreads) {
+    for (int e = threadIdx.x; e < tb * JB; e += THREADS) {
       const int tt = e / JB, jj = e % JB;
       Ts[tt * JB + jj] = T[(int64_t)(j0 + jj) * ldt + (t0 + tt)];
     }
@@ -62,7 +63,7 @@ __device__ __forceinline__ void trsm_rut_block(int j0, int64_t i, bool active, d
   }
   // triangular block
   __syncthreads();
-  for (int e = threadIdx.x; e < JB * JB; e += kTrsmThreads) {
+  for (int e = threadIdx.x; e < JB * JB; e += THREADS) {
     const int tt = e / JB, jj = e % JB;
     Td[tt * JB + jj] = T[(int64_t)(j0 + jj) * ldt + (j0 + tt)];
   }
@@ -83,27 +84,39 @@ __device__ __forceinline__ void trsm_rut_block(int j0, int64_t i, bool active, d
 // halving width (16, 8, 4, 2, 1), so no block computes a column that does not
 // exist.
 // Ts (kTrsmTB x kTrsmJB) and Td (kTrsmJB x kTrsmJB): shared staging.
-template <int JBMAX>
+template <int JBMAX, int THREADS = kTrsmThreads>
 __device__ __forceinline__ void trsm_rut_body(int64_t tile, const TrsmDesc& D, double* Ts,
                                               double* Td) {
   static_assert(JBMAX == 16 || JBMAX == 32, "column block of 16 or 32");
   if (*D.status != kOk) return;
   const int k = (int)*D.k_dev;
-  const int64_t i = tile * (int64_t)kTrsmThreads + threadIdx.x;
+  const int64_t i = tile * (int64_t)THREADS + threadIdx.x;
   const bool active = i < D.m;
   int j0 = 0;
-  for (; j0 + JBMAX <= k; j0 += JBMAX) trsm_rut_block<JBMAX>(j0, i, active, Ts, Td, D);
-  if (JBMAX > 16 && k - j0 >= 16) { trsm_rut_block<16>(j0, i, active, Ts, Td, D); j0 += 16; }
-  if (k - j0 >= 8) { trsm_rut_block<8>(j0, i, active, Ts, Td, D); j0 += 8; }
-  if (k - j0 >= 4) { trsm_rut_block<4>(j0, i, active, Ts, Td, D); j0 += 4; }
-  if (k - j0 >= 2) { trsm_rut_block<2>(j0, i, active, Ts, Td, D); j0 += 2; }
-  if (k - j0 >= 1) trsm_rut_block<1>(j0, i, active, Ts, Td, D);
+  for (; j0 + JBMAX <= k; j0 += JBMAX) trsm_rut_block<JBMAX, THREADS>(j0, i, active, Ts, Td, D);
+  if (JBMAX > 16 && k - j0 >= 16) {
+    trsm_rut_block<16, THREADS>(j0, i, active, Ts, Td, D);
+    j0 += 16;
+  }
+  if (k - j0 >= 8) { trsm_rut_block<8, THREADS>(j0, i, active, Ts, Td, D); j0 += 8; }
+  if (k - j0 >= 4) { trsm_rut_block<4, THREADS>(j0, i, active, Ts, Td, D); j0 += 4; }
+  if (k - j0 >= 2) { trsm_rut_block<2, THREADS>(j0, i, active, Ts, Td, D); j0 += 2; }
+  if (k - j0 >= 1) trsm_rut_block<1, THREADS>(j0, i, active, Ts, Td, D);
 }
 
 __global__ void __launch_bounds__(kTrsmThreads) trsm_rut_kernel(TrsmDesc D) {
   __shared__ double Ts[kTrsmTB * kTrsmJB];
   __shared__ double Td[kTrsmJB * kTrsmJB];
   trsm_rut_body<kTrsmJB>(blockIdx.x, D, Ts, Td);
+}
+
+// Small m: one warp per CTA, so that the rows spread over more SMs (same
+// arithmetic, same bits).
+constexpr int kTrsmSmallThreads = 32;
+__global__ void __launch_bounds__(kTrsmSmallThreads) trsm_rut_small_kernel(TrsmDesc D) {
+  __shared__ double Ts[kTrsmTB * kTrsmJB];
+  __shared__ double Td[kTrsmJB * kTrsmJB];
+  trsm_rut_body<kTrsmJB, kTrsmSmallThreads>(blockIdx.x, D, Ts, Td);
 }
 
 __global__ void __launch_bounds__(kTrsmThreads) trsm_rut_batched_kernel(const TrsmDesc* D,
@@ -126,7 +139,12 @@ cudaError_t launch_trsm_rut(int64_t m, int kmax, const int64_t* k_dev, const dou
                             double* X, int64_t ldx, const int* status, cudaStream_t stream) {
   (void)kmax;
   TrsmDesc D{m, k_dev, B, ldb, cols, T, ldt, X, ldx, status, kTrsmJB};
-  trsm_rut_kernel<<<(unsigned)trsm_tiles(m), kTrsmThreads, 0, stream>>>(D);
+  if (trsm_tiles(m) < 152) {  // less than one CTA per SM at 128 rows per CTA
+    trsm_rut_small_kernel<<<(unsigned)((m + kTrsmSmallThreads - 1) / kTrsmSmallThreads),
+                            kTrsmSmallThreads, 0, stream>>>(D);
+  } else {
+    trsm_rut_kernel<<<(unsigned)trsm_tiles(m), kTrsmThreads, 0, stream>>>(D);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -42,12 +42,12 @@ import workloads as W  # noqa: E402
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # measured dense bf16 peak of the GB300s (cuBLAS, burst)
 BF16_PEAK_TFLOPS = 1968.7
-# DRAM bytes per row of M for one trsm_rut_kernel launch at n = 1024, k = 800:
-# dram__bytes_read.sum + dram__bytes_write.sum = 2.013637 GB + 0.206175 GB
-# from an ncu capture of the m = 32768 case (one launch of line 4), divided
-# by its 32768 rows (the kernel's traffic grows in proportion to the rows:
-# one thread per row, T staged per CTA).  Set to None when the kernel changes.
-TRSM_DRAM_BYTES_PER_ROW = (2.013637e9 + 0.206175e9) / 32768
+# DRAM bytes of one trsm_rut_kernel launch of the headline factorisation
+# (m = 131072, n = 1024, k = 800): dram__bytes_read.sum + dram__bytes_write.sum
+# = 10.452 GB + 0.834 GB from one ncu capture of this bench command (one-pass
+# metrics, lines 4 and 7 alike; profiles/ncu_trsm_traffic_m131072_n1024.md).
+# Valid for that size and the kernel as captured; None otherwise.
+TRSM_DRAM_BYTES_HEADLINE = 10.451892e9 + 0.834476e9
 
 
 def parse():
@@ -1162,7 +1162,7 @@ def main():
             "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
             "peak_probe_measured": probe_gflops,
             "frac_of_probe": (achieved / probe_gflops) if probe_gflops else None,
-            "traffic": (TRSM_DRAM_BYTES_PER_ROW * m) if TRSM_DRAM_BYTES_PER_ROW else None,
+            "traffic": TRSM_DRAM_BYTES_HEADLINE if (m, n, k) == (131072, 1024, 800) else None,
             "algorithmic_flops_per_launch": trsm_flops,
             "launch_ms": trsm_ms,
             "peak_note": "FP64 ALU: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, nominal)"}

@@ -173,8 +173,65 @@ __global__ void __launch_bounds__(256) potrf_batched_kernel(const PotrfDesc* Dv)
   potrf_cta_body(Dv[blockIdx.x]);
 }
 
-// A small factor (k <= kPotrfSingleCtaMax): every panel in one launch on one
-// CTA (block barriers instead of three launches per panel); same bodies.
+// A small factor (k <= kPotrfSmallMax): one CTA of 1024 threads, fully
+// right-looking.  Step t: thread 0 takes R[t, t] = sqrt(S[t, t]) (or records
+// the Remark 4 failure at t); the threads divide row t, R[t, c] = S[t, c] /
+// R[t, t] for c > t, in parallel; then every trailing entry S[j, c]
+// (t < j <= c) receives its term -R[t, j] R[t, c] with one fma.  Each entry
+// still receives its terms in ascending t and the same division and square
+// root as the recurrence, but every step spreads its work over 32 warps (a
+// single warp issues one FP64 instruction per 64 cycles).  S lives in shared
+// memory (k <= 64: 32 KB).
+constexpr int kPotrfSmallMax = 64;
+constexpr int kPotrfSmallThreads = 1024;
+__global__ void __launch_bounds__(kPotrfSmallThreads) potrf_small_kernel(PotrfDesc D) {
+  __shared__ double S[kPotrfSmallMax * kPotrfSmallMax];  // column-major, ld kPotrfSmallMax
+  __shared__ int fail_at;
+  DeviceScalars* sc = D.sc;
+  if (sc->status != kOk || sc->fail >= 0) return;
+  const int k = (int)sc->k;
+  if (k <= 0) return;
+  const int ld = kPotrfSmallMax;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int c = e / k, j = e - c * k;
+    S[c * ld + j] = j <= c ? D.G[(int64_t)c * D.ldg + j] : 0.0;
+  }
+  if (threadIdx.x == 0) fail_at = -1;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    if (threadIdx.x == 0) {
+      const double piv = S[t * ld + t];
+      if (!(piv > 0.0)) {
+        fail_at = t;
+      } else {
+        const double r = __dsqrt_rn(piv);
+        S[t * ld + t] = r;
+        D.R[(int64_t)t * D.ldr + t] = r;
+      }
+    }
+    __syncthreads();
+    if (fail_at >= 0) break;  // uniform
+    const double rtt = S[t * ld + t];
+    for (int c = t + 1 + (int)threadIdx.x; c < k; c += blockDim.x) {
+      const double v = __ddiv_rn(S[c * ld + t], rtt);
+      S[c * ld + t] = v;
+      D.R[(int64_t)c * D.ldr + t] = v;
+    }
+    __syncthreads();
+    // trailing update: entries (j, c), t < j <= c < k, in one flat index
+    const int w = k - 1 - t;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int c = t + 1 + e / w, j = t + 1 + e % w;
+      if (j <= c) S[c * ld + j] = __fma_rn(-S[j * ld + t], S[c * ld + t], S[c * ld + j]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && fail_at >= 0) sc->fail = fail_at;
+}
+
+// A factor of kPotrfSmallMax < k <= kPotrfSingleCtaMax: every panel in one
+// launch on one CTA (block barriers instead of three launches per panel);
+// the batched body.
 constexpr int kPotrfSingleCtaMax = 128;
 __global__ void __launch_bounds__(256) potrf_single_cta_kernel(PotrfDesc D) {
   potrf_cta_body(D);
@@ -183,6 +240,11 @@ __global__ void __launch_bounds__(256) potrf_single_cta_kernel(PotrfDesc D) {
 cudaError_t launch_potrf(int kmax, double* G, int64_t ldg, double* R, int64_t ldr,
                          DeviceScalars* sc, cudaStream_t stream) {
   PotrfDesc D{kmax, G, ldg, R, ldr, sc};
+  if (kmax <= kPotrfSmallMax) {
+    potrf_small_kernel<<<1, kPotrfSmallThreads, 0, stream>>>(D);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   if (kmax <= kPotrfSingleCtaMax) {
     potrf_single_cta_kernel<<<1, 256, 0, stream>>>(D);
     count_launches(1);

@@ -29,13 +29,20 @@
 
 namespace cqrrpt {
 
-constexpr int kListThreads = 256;   // saso_lists: threads per CTA
+constexpr int kListThreads = 1024;  // saso_lists: threads per CTA
 constexpr int kListMapWords = kRowBlock / 32;  // one bit per row of a block
-// dynamic shared memory of saso_lists: counts and starts (2 d + 1 ints),
-// then per warp a row map and a sign map of kListMapWords words each
+constexpr int kListSmemMax = 227 * 1024;       // dynamic shared memory per CTA, at most
+// warps that sort segments: one row map and one sign map of kListMapWords
+// words each per warp, as many as fit beside the counts and starts (2 d + 1
+// ints; d <= 28000 leaves room for 8)
+__host__ __device__ inline int lists_sort_warps(int d) {
+  const int room = (kListSmemMax - (2 * d + 1) * 4) / (2 * kListMapWords * 4);
+  return room < 1 ? 1 : (room > kListThreads / 32 ? kListThreads / 32 : room);
+}
+// dynamic shared memory of saso_lists
 static size_t lists_smem_bytes(int d) {
   return (size_t)(2 * d + 1) * sizeof(int) +
-         (size_t)(kListThreads / 32) * 2 * kListMapWords * sizeof(uint32_t);
+         (size_t)lists_sort_warps(d) * 2 * kListMapWords * sizeof(uint32_t);
 }
 
 // entries: (r_local << 1) | negative
@@ -94,10 +101,10 @@ __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, 
   // L entries instead of an O(L^2) insertion sort
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nwarps = blockDim.x >> 5;
+    const int nwarps = lists_sort_warps(d);
     uint32_t* rowmap = (uint32_t*)(start + d + 1) + warp * 2 * kListMapWords;
     uint32_t* negmap = rowmap + kListMapWords;
-    for (int i = warp; i < d; i += nwarps) {
+    for (int i = warp; warp < nwarps && i < d; i += nwarps) {
       const int a = start[i], e = start[i + 1];
       if (e - a < 2) continue;  // uniform over the warp
 #pragma unroll
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kCombineThreads) sketch_finish_kernel(const do
 }
 
 // ---- single-problem kernels -------------------------------------------------
-__global__ void saso_lists_kernel(SketchDesc D) {
+__global__ void __launch_bounds__(kListThreads) saso_lists_kernel(SketchDesc D) {
   extern __shared__ int sh_lists[];
   saso_lists_body(blockIdx.x, D, sh_lists);
 }
@@ -242,7 +249,8 @@ __global__ void __launch_bounds__(kCombineThreads) sketch_combine_kernel(SketchD
 }
 
 // ---- batched kernels --------------------------------------------------------
-__global__ void saso_lists_batched_kernel(const SketchDesc* D, const int64_t* base, int np) {
+__global__ void __launch_bounds__(kListThreads) saso_lists_batched_kernel(const SketchDesc* D,
+                                                                   const int64_t* base, int np) {
   extern __shared__ int sh_lists[];
   int64_t t;
   const int p = find_problem(base, np, blockIdx.x, &t);

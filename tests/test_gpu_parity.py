@@ -61,6 +61,9 @@ def _rng(s):
     (4097, 5, 16, 1, 3),
     (10000, 33, 42, 32, 2**40 + 9),
     (300, 7, 300, 4, 5),
+    # the largest sketch dimension the library takes (28000): the lists
+    # kernel's counts then leave shared memory for 8 sorting warps only
+    (2 * 4096 + 31, 3, 28000, 8, 13),
 ])
 def test_sketch_bitexact(C, m, n, d, s, seed):
     A = _rng(seed % 1000).standard_normal((m, n))

@@ -23,6 +23,8 @@
 // barriers spin a bounded number of times (status kTimeout on expiry).
 #include <algorithm>
 #include <cstdlib>
+
+#include <cooperative_groups.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -557,6 +559,240 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
   qrcp_cached_body(D, tol3z, qc, gridDim.x, blockIdx.x, cache);
 }
 
+// A small sketch (n <= kQrcpClusterMaxN) on one thread-block cluster of G
+// CTAs (G <= 8, one column per warp, every column in shared memory): the
+// same steps and arithmetic as qrcp_cached_body, with the exchange inside
+// the cluster.  At the end of a step each CTA writes its candidate into its
+// own shared memory (two slots by step parity) and the cluster barrier
+// (barrier.cluster arrive with release, wait with acquire) replaces the grid
+// barrier; every CTA then reads the G candidates and the pivot column
+// straight from the owner CTA's shared memory (distributed shared memory),
+// with no round trip through global memory.  The owner writes beta into its
+// column's row j only after the next barrier (the others read that row
+// during the step); the Householder vector itself is not kept, as only the
+// upper triangle (R^sk) is read afterwards.  Every CTA runs the same
+// sequence of barriers (the exits depend only on data every CTA holds
+// alike), and a last barrier keeps each CTA's shared memory alive until no
+// peer reads it.
+constexpr int kQrcpClusterMaxN = 64;
+constexpr int kQrcpClusterMaxG = 8;
+__global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, double tol3z) {
+  extern __shared__ double cache[];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int G = (int)cluster.num_blocks();
+  const int bid = (int)cluster.block_rank();
+  const int d = D.d, n = D.n;
+  double* X = D.X;
+  const int64_t ldx = D.ldx;
+  const QrcpWork& w = D.w;
+  DeviceScalars* sc = D.sc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  int* status = &sc->status;
+  const int nown = bid < n ? (n - bid + G - 1) / G : 0;
+  double* vbuf = cache + (int64_t)nown * d;  // d
+  double* vn1 = vbuf + d;                    // nown
+  double* vn2 = vn1 + nown;                  // nown
+  int* phys = (int*)(vn2 + nown);            // n
+  int* posof = phys + n;                     // n
+  __shared__ double rec_val[2];
+  __shared__ int rec_pos[2], rec_col[2];
+  __shared__ int sh_P, sh_p;
+  __shared__ double sh_tau, sh_beta, sh_rden;
+  __shared__ int sh_nz;
+  __shared__ int sh_pend_q, sh_pend_row;  // beta into row sh_pend_row of column sh_pend_q
+  __shared__ double sh_pend_val;
+  __shared__ double red_val[32];
+  __shared__ int red_pos[32];
+  __shared__ int red_col[32];
+
+  if (*(volatile int*)status != kOk) return;  // set before launch: uniform over CTAs
+
+  for (int q = 0; q < nown; ++q) {
+    const double* src = X + (int64_t)(bid + G * q) * ldx;
+    for (int r = threadIdx.x; r < d; r += blockDim.x) cache[(int64_t)q * d + r] = src[r];
+  }
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    phys[c] = c;
+    posof[c] = c;
+  }
+  if (threadIdx.x == 0) sh_pend_q = -1;
+  __syncthreads();
+  for (int q = warp; q < nown; q += nwarps) {
+    const double s = warp_dot32_self_smem(cache + (int64_t)q * d, d);
+    if (lane == 0) {
+      const double v = __dsqrt_rn(s);
+      vn1[q] = v;
+      vn2[q] = v;
+    }
+  }
+  __syncthreads();
+
+  // the CTA's best unpivoted column into its record slot (j_done + 2) & 1
+  auto publish_candidate = [&](int j_done) {
+    double bv = -1.0;
+    int bp = 0x7fffffff, bq = -1;
+    for (int q = warp; q < nown; q += nwarps) {
+      const int c = bid + G * q;
+      const int pc = posof[c];
+      if (pc <= j_done) continue;
+      const double v = D.nopivot ? (double)(n - pc) : vn1[q];
+      if (cand_better(v, pc, bv, bp)) { bv = v; bp = pc; bq = q; }
+    }
+    if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bq; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 1; i < nwarps; ++i)
+        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bq = red_col[i]; }
+      const int slot = (j_done + 2) & 1;
+      rec_val[slot] = bv;
+      rec_pos[slot] = bp;
+      rec_col[slot] = bq >= 0 ? bid + G * bq : -1;
+    }
+    cluster.sync();
+  };
+  publish_candidate(-1);
+
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    // beta of the previous pivot into its owner's column: every CTA has read
+    // that column (it passed the barrier after reading it)
+    if (threadIdx.x == 0 && sh_pend_q >= 0) {
+      cache[(int64_t)sh_pend_q * d + sh_pend_row] = sh_pend_val;
+      sh_pend_q = -1;
+    }
+    // 1. global pivot from the G records (every CTA alike)
+    if (warp == 0) {
+      double bv = -1.0;
+      int bp = 0x7fffffff, bc = -1;
+      const int slot = (j + 1) & 1;
+      if (lane < G) {
+        const double v = *cluster.map_shared_rank(&rec_val[slot], lane);
+        const int p = *cluster.map_shared_rank(&rec_pos[slot], lane);
+        const int c = *cluster.map_shared_rank(&rec_col[slot], lane);
+        if (c >= 0) { bv = v; bp = p; bc = c; }
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int op = __shfl_down_sync(0xffffffffu, bp, off);
+        const int oc = __shfl_down_sync(0xffffffffu, bc, off);
+        if (oc >= 0 && cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+      }
+      if (lane == 0) { sh_P = bc; sh_p = bp; }
+    }
+    __syncthreads();
+    const int P = sh_P, p = sh_p;
+    if (P < 0) {  // no finite candidate anywhere: every CTA sees the same
+      if (bid == 0 && threadIdx.x == 0) atomicExch(status, kNonFinite);
+      ok = false;
+      break;
+    }
+    // 2. the pivot column, rows j.., from its owner's shared memory
+    const int owner = P % G, qP = P / G;
+    const int len = d - j;
+    {
+      const double* src = cluster.map_shared_rank(cache + (int64_t)qP * d + j, owner);
+      for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = src[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const double alpha = vbuf[0];
+      const double sumsq = (j + 1 < d) ? warp_dot32_self_smem(vbuf + 1, d - j - 1) : 0.0;
+      if (lane == 0) {
+        if (sumsq == 0.0) {
+          sh_tau = 0.0;
+          sh_nz = 0;
+        } else {
+          const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
+          const double beta = (alpha >= 0.0) ? -nrm : nrm;
+          sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
+          sh_beta = beta;
+          sh_rden = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
+          sh_nz = 1;
+        }
+      }
+    }
+    __syncthreads();
+    const double tau = sh_tau;
+    const bool nz = sh_nz != 0;
+    const double rden = sh_rden;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      double v = 1.0;
+      if (i > 0) {
+        const double x = vbuf[i];
+        v = nz ? __dmul_rn(x, rden) : x;
+      }
+      vbuf[i] = v;
+    }
+    if (threadIdx.x == 0) {
+      if (owner == bid && nz) {
+        sh_pend_q = qP;
+        sh_pend_row = j;
+        sh_pend_val = sh_beta;
+      }
+      const int Pj = phys[j];
+      phys[p] = Pj;
+      posof[Pj] = p;
+      phys[j] = P;
+      posof[P] = j;
+      if (bid == 0) w.tau[j] = tau;
+    }
+    __syncthreads();
+    // 3. apply H to the owned unpivoted columns, downdate their norms
+    for (int q = warp; q < nown; q += nwarps) {
+      const int c = bid + G * q;
+      if (posof[c] <= j) continue;
+      double* colc = cache + (int64_t)q * d + j;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int i = lane; i < len; i += 32) acc = __fma_rn(vbuf[i], colc[i], acc);
+      const double wsum = warp_tree_sum32(acc);
+      const double t = __dmul_rn(-tau, wsum);
+#pragma unroll 8
+      for (int i2 = lane; i2 < len; i2 += 32) colc[i2] = __fma_rn(vbuf[i2], t, colc[i2]);
+      __syncwarp();
+      const double v1 = vn1[q];
+      if (v1 != 0.0) {
+        const double v2 = vn2[q];
+        double temp = __ddiv_rn(fabs(colc[0]), v1);
+        temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
+        temp = temp > 0.0 ? temp : 0.0;
+        const double ratio = __ddiv_rn(v1, v2);
+        const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
+        if (temp2 <= tol3z) {
+          const double s2 = (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1) : 0.0;
+          if (lane == 0) {
+            const double nv = (j + 1 < d) ? __dsqrt_rn(s2) : 0.0;
+            vn1[q] = nv;
+            vn2[q] = nv;
+          }
+        } else if (lane == 0) {
+          vn1[q] = __dmul_rn(v1, __dsqrt_rn(temp));
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    publish_candidate(j);
+  }
+  // no peer reads this CTA's shared memory once every CTA is past here
+  cluster.sync();
+  if (threadIdx.x == 0 && sh_pend_q >= 0 && ok)
+    cache[(int64_t)sh_pend_q * d + sh_pend_row] = sh_pend_val;
+  __syncthreads();
+  for (int q = 0; q < nown; ++q) {
+    double* dst = X + (int64_t)(bid + G * q) * ldx;
+    for (int r = threadIdx.x; r < d; r += blockDim.x) dst[r] = cache[(int64_t)q * d + r];
+  }
+  if (bid == 0)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      w.phys[c] = phys[c];
+      w.posof[c] = posof[c];
+    }
+}
+
 // One CTA per problem (G = 1), the problems in the table's order (the batch
 // planner puts the largest first); smem_bytes of dynamic shared memory hold
 // the maps, norms and reflector buffer and as many columns as fit.
@@ -652,6 +888,38 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
                         cudaStream_t stream, bool nopivot) {
   QrcpDesc D{d, n, X, ldx, qrcp_carve(work, n), J, Rsk, ldr, sc, nopivot ? 1 : 0};
+  // a small sketch: one cluster, one column per warp (CQRRPT_QRCP_CLUSTER = 0
+  // turns this off, for tests of the other path on the same sizes)
+  {
+    const int Gc = (n + 7) / 8;
+    const int64_t nown_c = (n + Gc - 1) / Gc;  // CTA 0 owns the most columns
+    // the columns, the reflector buffer, two norms per column, the two maps
+    const int64_t smem_c = nown_c * d * 8 + (d + 2 * nown_c) * 8 + (int64_t)2 * n * 4;
+    bool use = n <= kQrcpClusterMaxN && Gc <= kQrcpClusterMaxG && smem_c <= kQrcpSmemCap;
+    if (const char* f = std::getenv("CQRRPT_QRCP_CLUSTER")) use = use && f[0] != '0';
+    if (use) {
+      cudaError_t e1 = raise_smem_limit((const void*)qrcp_cluster_kernel, (size_t)smem_c);
+      if (e1 != cudaSuccess) return e1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(Gc);
+      cfg.blockDim = dim3(kQrcpThreads);
+      cfg.dynamicSmemBytes = (size_t)smem_c;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = Gc;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      const double tz = tol3z_value();
+      e1 = cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, D, tz);
+      if (e1 != cudaSuccess) return e1;
+      qrcp_gather_kernel<<<n, 128, 0, stream>>>(D);
+      count_launches(2);
+      return cudaGetLastError();
+    }
+  }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qrcp_kernel, kQrcpThreads, 0);
   if (e != cudaSuccess) return e;

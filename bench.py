@@ -936,6 +936,15 @@ def run_serve(args, world, rank, local, C):
             submit((e, prec, 7))
     srv.drain(timeout_us=600_000_000)
     assert srv.stats()["completed"] == 2 * len(pool)
+    # each pool entry alone on the idle server, in each precision: the
+    # latency a request has without any other in flight (host copies included)
+    alone = {}
+    for e in range(len(pool)):
+        for prec in (C.FP64, C.SPLITBF16):
+            t = submit((e, prec, 8))
+            srv.drain(timeout_us=600_000_000)
+            alone[(e, prec)] = srv.poll(t)[1].latency_us / 1e3
+    largest = max(alone, key=alone.get)
 
     # closed loop: capacity
     cap_reqs = make(max(len(pool), args.requests // 2), 10**7)
@@ -1056,6 +1065,16 @@ def run_serve(args, world, rank, local, C):
             "capacity_requests_per_s": capacity,
             "latency_ms": {"all": pct(lat), "fp64": pct(lat[isfp]), "splitbf16": pct(lat[~isfp]),
                            "queue": pct(que)},
+            "standalone_ms": {"largest": alone[largest],
+                              "largest_request": {"m": pool[largest[0]][0].m,
+                                                  "n": pool[largest[0]][0].n,
+                                                  "precision": "fp64" if largest[1] == C.FP64
+                                                  else "splitbf16"},
+                              "p99_over_largest": float(np.percentile(lat, 99)) / alone[largest],
+                              "mean_over_requests": float(np.mean(
+                                  [alone[(r[0], r[1])] for r in reqs])),
+                              "note": "each pool entry run alone on the idle server (host "
+                                      "copies included) before the open loop"},
             "gflops_algorithmic": flops / wall / 1e9,
             "gflops_2mn2": sum(2.0 * w.m * w.n * w.n for w in ws) / wall / 1e9,
             "units": stats["waves"] - stats0["waves"],

@@ -44,6 +44,7 @@ struct QrcpWork {
   double* cand_val;
   int* cand_pos;
   int* cand_col;
+  double* cand_refl;  // per record: tau, beta, 1 / (alpha - beta), nz (as 0.0 / 1.0)
 };
 
 struct QrcpDesc {

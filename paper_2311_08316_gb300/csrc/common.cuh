@@ -49,47 +49,62 @@ __device__ __forceinline__ double warp_tree_sum32(double v) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
-// Grid-wide barrier for cooperative launches: arrival counter plus a
-// generation word.  Waits are bounded: after spin_limit polls (kSpinLimit
-// unless a test lowered it) the CTA sets *status = kTimeout and returns
-// false.
+// Grid-wide barrier for cooperative launches: a counter that only grows.
+// Barrier b of a launch is passed once the counter reaches (b + 1) G: each
+// CTA adds 1 and waits until the counter reaches the next multiple of G, so
+// the last CTA to arrive releases the others by its own addition (no reset,
+// no second word on the critical path).  grid_release() at the end of the
+// kernel puts the counter back to 0 for the next launch; init_scalars also
+// zeroes it.  Waits are bounded: after spin_limit polls (kSpinLimit unless a
+// test lowered it) the CTA sets *status = kTimeout and returns false.
 struct GridBarrier {
   unsigned int count;
-  unsigned int generation;
+  unsigned int released;  // CTAs past their last barrier (grid_release)
 };
+
+// One thread's side of the barrier: arrive for its CTA (after the CTA's
+// writes, which a block-level barrier orders before this call) and wait.
+__device__ __forceinline__ bool grid_arrive_wait(GridBarrier* bar, unsigned int nblocks,
+                                                 int* status, unsigned long long spin_limit) {
+  if (nblocks <= 1) return true;
+  bool ok = true;
+  __threadfence();  // the CTA's writes before its arrival
+  const unsigned int arrived = atomicAdd(&bar->count, 1u);
+  const unsigned int target = arrived - arrived % nblocks + nblocks;
+  if (arrived + 1 != target) {
+    volatile unsigned int* cp = &bar->count;
+    unsigned long long spins = 0;
+    while ((int)(*cp - target) < 0) {
+      if (++spins > spin_limit) {
+        atomicExch(status, kTimeout);
+        ok = false;
+        break;
+      }
+      if (spins > 256) __nanosleep(64);  // poll tightly first, then back off
+    }
+  }
+  __threadfence();
+  return ok;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, int* status,
                                           unsigned long long spin_limit = kSpinLimit) {
   __shared__ int ok_flag;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (nblocks > 1) {
-      volatile unsigned int* genp = &bar->generation;
-      unsigned int gen = *genp;
-      __threadfence();
-      unsigned int arrived = atomicAdd(&bar->count, 1u);
-      if (arrived == nblocks - 1) {
-        atomicExch(&bar->count, 0u);
-        __threadfence();
-        atomicAdd(&bar->generation, 1u);
-      } else {
-        unsigned long long spins = 0;
-        while (*genp == gen) {
-          if (++spins > spin_limit) {
-            atomicExch(status, kTimeout);
-            ok = 0;
-            break;
-          }
-          if (spins > 256) __nanosleep(64);  // poll tightly first, then back off
-        }
-      }
-      __threadfence();
-    }
-    ok_flag = ok;
-  }
+  if (threadIdx.x == 0) ok_flag = grid_arrive_wait(bar, nblocks, status, spin_limit) ? 1 : 0;
   __syncthreads();
   return ok_flag != 0;
+}
+
+// After a CTA's last grid_sync of the launch: the last CTA to get here (all
+// others are past every barrier and read the counter no more) zeroes it.
+__device__ __forceinline__ void grid_release(GridBarrier* bar, unsigned int nblocks) {
+  if (nblocks > 1 && threadIdx.x == 0) {
+    if (atomicAdd(&bar->released, 1u) == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      atomicExch(&bar->released, 0u);
+    }
+  }
 }
 
 }  // namespace cqrrpt

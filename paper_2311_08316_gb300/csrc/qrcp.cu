@@ -41,6 +41,10 @@ cudaError_t qrcp_set_spin_limit(unsigned long long spins) {
   return cudaMemcpyToSymbol(g_grid_spin_limit, &v, sizeof(v));
 }
 
+// Candidate records of the multi-CTA QRCP: two slots (step parity) of
+// kCandSlot CTAs each (G <= kCandSlot; G is at most one CTA per SM).
+constexpr int kCandSlot = 256;
+
 QrcpWork qrcp_carve(void* work, int n) {
   char* p = (char*)work;
   QrcpWork w;
@@ -49,14 +53,16 @@ QrcpWork qrcp_carve(void* work, int n) {
   w.tau = (double*)p; p += align256((int64_t)n * 8);
   w.phys = (int*)p; p += align256((int64_t)n * 4);
   w.posof = (int*)p; p += align256((int64_t)n * 4);
-  w.cand_val = (double*)p; p += align256(4096 * 8);
-  w.cand_pos = (int*)p; p += align256(4096 * 4);
-  w.cand_col = (int*)p; p += align256(4096 * 4);
+  w.cand_val = (double*)p; p += align256(2 * kCandSlot * 8);
+  w.cand_pos = (int*)p; p += align256(2 * kCandSlot * 4);
+  w.cand_col = (int*)p; p += align256(2 * kCandSlot * 4);
+  w.cand_refl = (double*)p; p += align256(2 * kCandSlot * 4 * 8);
   return w;
 }
 
 int64_t qrcp_workspace_bytes(int64_t n) {
-  return 3 * align256(n * 8) + 2 * align256(n * 4) + align256(4096 * 8) + 2 * align256(4096 * 4);
+  return 3 * align256(n * 8) + 2 * align256(n * 4) + align256(2 * kCandSlot * 8) +
+         2 * align256(2 * kCandSlot * 4) + align256(2 * kCandSlot * 4 * 8);
 }
 
 // dot32 of x[0..len) with itself, by one warp (result in every lane).
@@ -252,6 +258,8 @@ __device__ __forceinline__ void qrcp_body(const int G, const int bid, const Qrcp
 
 __global__ void __launch_bounds__(kQrcpThreads) qrcp_kernel(QrcpDesc D, double tol3z) {
   qrcp_body(gridDim.x, blockIdx.x, D, tol3z);
+  __syncthreads();
+  grid_release(&D.sc->bar, gridDim.x);
 }
 
 __global__ void __launch_bounds__(1024) qrcp_batched_kernel(const QrcpDesc* D, double tol3z) {
@@ -278,27 +286,147 @@ __device__ __forceinline__ double warp_dot32_self_smem(const double* x, int len,
   return warp_tree_sum32(acc);
 }
 
+// The reflector of a column for step jn (LAPACK's dlarfg on rows jn.., as
+// above), by one warp; every lane returns the same values.  The two
+// divisions run at once on lanes 0 and 1 (the same correctly rounded
+// quotients as one after the other; a warp pays for each FP64 instruction
+// whatever its lanes do).  nz = 0 when the rows below jn are all zero
+// (H = I, tau = 0).
+__device__ __forceinline__ void warp_reflector(const double* col, int jn, int d, bool global,
+                                               double& tau, double& beta, double& rden,
+                                               int& nz) {
+  const int lane = threadIdx.x & 31;
+  const double alpha = col[jn];
+  const double sumsq = (jn + 1 < d) ? warp_dot32_self_smem(col + jn + 1, d - jn - 1, global) : 0.0;
+  if (sumsq == 0.0) {
+    tau = 0.0;
+    beta = alpha;
+    rden = 1.0;
+    nz = 0;
+    return;
+  }
+  const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
+  beta = (alpha >= 0.0) ? -nrm : nrm;
+  const double num = lane == 1 ? 1.0 : __dsub_rn(beta, alpha);  // tau = (beta - alpha) / beta
+  const double den = lane == 1 ? __dsub_rn(alpha, beta) : beta;  // 1 / (alpha - beta)
+  const double q = __ddiv_rn(num, den);
+  tau = __shfl_sync(0xffffffffu, q, 0);
+  rden = __shfl_sync(0xffffffffu, q, 1);
+  nz = 1;
+}
+
+// LAPACK dlaqp2's norm downdate of one column after step j (a0 = |x_j|
+// after the update; `below` holds rows j+1..), by one warp; the new norms
+// go to *vn1q / *vn2q from lane 0.  |x_j| / vn1 and vn1 / vn2 are formed at
+// once on lanes 0 and 1.
+__device__ __forceinline__ void warp_downdate(double* vn1q, double* vn2q, double a0,
+                                              const double* below, int len_below, bool global,
+                                              double tol3z) {
+  const int lane = threadIdx.x & 31;
+  const double v1 = *vn1q;
+  if (v1 == 0.0) return;
+  const double v2 = *vn2q;
+  const double qq = __ddiv_rn(lane == 1 ? v1 : a0, lane == 1 ? v2 : v1);
+  double temp = __shfl_sync(0xffffffffu, qq, 0);         // |x_j| / vn1
+  const double ratio = __shfl_sync(0xffffffffu, qq, 1);  // vn1 / vn2
+  temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
+  temp = temp > 0.0 ? temp : 0.0;
+  const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
+  if (temp2 <= tol3z) {
+    const double s2 = len_below > 0 ? warp_dot32_self_smem(below, len_below, global) : 0.0;
+    if (lane == 0) {
+      const double nv = len_below > 0 ? __dsqrt_rn(s2) : 0.0;
+      *vn1q = nv;
+      *vn2q = nv;
+    }
+  } else if (lane == 0) {
+    *vn1q = __dmul_rn(v1, __dsqrt_rn(temp));
+  }
+}
+
+// The best candidate of the calling warp's lanes below `width` (a power of
+// two at most 32); every lane of the warp ends with it (lane 0's result is
+// broadcast when width < 32, so that the whole warp takes the same branch
+// afterwards).  A butterfly in
+// the candidate order (larger value, then lower position).  Lanes without a
+// candidate hold value -1, position INT_MAX and c < 0, which every finite
+// candidate beats; a NaN value never wins (as in the sequential scans).  The
+// order is total over distinct positions, so the result does not depend on
+// the combination order.
+struct Cand {
+  double v;
+  int p, c, i;  // position, column (or owned index), record
+  double tau, beta, rden;
+  int nz;
+};
+__device__ __forceinline__ void warp_best(Cand& a, int width, bool carry) {
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    if (off >= width) continue;
+    Cand o = a;
+    o.v = __shfl_xor_sync(0xffffffffu, a.v, off);
+    o.p = __shfl_xor_sync(0xffffffffu, a.p, off);
+    o.c = __shfl_xor_sync(0xffffffffu, a.c, off);
+    o.i = __shfl_xor_sync(0xffffffffu, a.i, off);
+    if (carry) {
+      o.tau = __shfl_xor_sync(0xffffffffu, a.tau, off);
+      o.beta = __shfl_xor_sync(0xffffffffu, a.beta, off);
+      o.rden = __shfl_xor_sync(0xffffffffu, a.rden, off);
+      o.nz = __shfl_xor_sync(0xffffffffu, a.nz, off);
+    }
+    if (o.c >= 0 && cand_better(o.v, o.p, a.v, a.p)) a = o;
+  }
+  if (width < 32) {  // lanes at and above width combined only among themselves
+    a.v = __shfl_sync(0xffffffffu, a.v, 0);
+    a.p = __shfl_sync(0xffffffffu, a.p, 0);
+    a.c = __shfl_sync(0xffffffffu, a.c, 0);
+    a.i = __shfl_sync(0xffffffffu, a.i, 0);
+    if (carry) {
+      a.tau = __shfl_sync(0xffffffffu, a.tau, 0);
+      a.beta = __shfl_sync(0xffffffffu, a.beta, 0);
+      a.rden = __shfl_sync(0xffffffffu, a.rden, 0);
+      a.nz = __shfl_sync(0xffffffffu, a.nz, 0);
+    }
+  }
+}
+
+__device__ __forceinline__ int pow2_at_least(int x) {
+  int w = 1;
+  while (w < x && w < 32) w <<= 1;
+  return w;
+}
+
+// Named barrier 1 (0 is __syncthreads): arrive signals without
+// waiting, sync waits until `nthreads` threads have arrived or synced.  The
+// non-.aligned forms, so that a warp's threads may reach them apart (after
+// a branch taken by one lane).
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+  asm volatile("barrier.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Same arithmetic as qrcp_body, one grid barrier per step instead of two.
 // Every CTA keeps its first qc owned columns (cache[q * d + r] is row r of
 // physical column bid + G q), the partial norms of all of them and its own
 // copy of the position <-> column maps in shared memory for the whole
 // factorisation; owned columns q >= qc (when the sketch is too large for
-// the SMs' shared memory) stay in X, which only their owner writes.  For a
-// pivot column in X the owner writes beta into X after the next barrier
-// (the other CTAs read the column during the step) and leaves the rows
-// below it as they were (only R^sk is read afterwards).
-// At the end of a step a CTA publishes its best candidate and writes that
-// column's current rows j+1.. to X (global); after the barrier every CTA
-// picks the same pivot P, reads P's column from X and forms the same
-// reflector itself (same dot32, same operations: identical bits on every
-// CTA), updates its maps with the same swap and applies the reflector to its
-// columns -- so no second barrier is needed to broadcast the reflector.  The
-// owner of P also stores beta and v into its cached column.  All owned
-// columns are written back at the end; CTA 0 writes the maps and tau.
-// G CTAs (bid = this CTA's index) on one problem, qc owned columns of each
-// cached; G = 1 (one CTA per problem, the batched form) keeps the candidate
-// and reads the pivot column in shared memory when it is cached: no global
-// memory round trip per step.
+// the SMs' shared memory) stay in X, which only their owner writes.
+// At the end of step j each CTA picks its best unpivoted column (its
+// candidate for step j + 1), forms that column's reflector for step j + 1
+// itself (one warp, while the other warps copy the column's rows j+1.. to
+// X) and publishes candidate and reflector (tau, beta, 1 / (alpha - beta))
+// in its record, two slots by step parity.  After the barrier every CTA
+// picks the same pivot P from the records, reads P's rows below the
+// diagonal from X scaled by the published 1 / (alpha - beta) (the same
+// products as the owner would form), updates its maps with the same swap
+// and applies the reflector to its columns.  The owner of a cached P keeps
+// beta and v in its column; a P in X gets beta written into X after the
+// next barrier and keeps its rows below (only R^sk is read afterwards).
+// All owned columns are written back at the end; CTA 0 writes the maps and
+// tau.  G = 1 (one CTA per problem, the batched form) keeps the candidate
+// and its reflector in shared memory: no global memory round trip per step.
 __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z, int qc, int G,
                                                  int bid, double* cache) {
   const int d = D.d, n = D.n;
@@ -316,7 +444,7 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
   double* vn2 = vn1 + nown;                           // nown
   int* phys = (int*)(vn2 + nown);                     // n
   int* posof = phys + n;                              // n
-  __shared__ int sh_P, sh_p;
+  __shared__ int sh_P, sh_p, sh_q;
   __shared__ double sh_tau, sh_beta, sh_rden;
   __shared__ int sh_nz;
   __shared__ double* sh_pend;  // beta of a pivot column in X, written after the barrier
@@ -352,9 +480,10 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
   }
   __syncthreads();
 
-  // local best unpivoted column (largest partial norm, lowest position on
-  // exact ties); its rows j_done+1.. go to X for the other CTAs
+  // the CTA's best unpivoted column after step j_done and its reflector for
+  // step j_done + 1, into record slot (j_done + 1) & 1 (G = 1: shared memory)
   auto publish_candidate = [&](int j_done) {
+    const int jn = j_done + 1;
     double bv = -1.0;
     int bp = 0x7fffffff, bq = -1;
     for (int q = warp; q < nown; q += nwarps) {
@@ -367,23 +496,50 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
     }
     if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bq; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 1; i < nwarps; ++i)
-        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bq = red_col[i]; }
-      if (G > 1) {
-        w.cand_val[bid] = bv;
-        w.cand_pos[bid] = bp;
-        w.cand_col[bid] = bq >= 0 ? bid + G * bq : -1;
+    if (warp == 0) {
+      Cand a;
+      a.v = lane < nwarps ? red_val[lane] : -1.0;
+      a.p = lane < nwarps ? red_pos[lane] : 0x7fffffff;
+      a.c = lane < nwarps ? red_col[lane] : -1;
+      a.i = 0;
+      a.tau = a.beta = 0.0;
+      a.rden = 1.0;
+      a.nz = 0;
+      warp_best(a, pow2_at_least(nwarps), false);
+      const int q = a.c;
+      if (lane == 0) sh_q = q;
+      if (G > 1) named_arrive(1, blockDim.x);  // the other warps copy the column meanwhile
+      double tau = 0.0, beta = 0.0, rden = 1.0;
+      int nz = 0;
+      if (q >= 0 && jn < n) warp_reflector(colptr(q), jn, d, q >= ncached, tau, beta, rden, nz);
+      if (lane == 0) {
+        if (G > 1) {
+          const int idx = (jn & 1) * kCandSlot + bid;
+          w.cand_val[idx] = a.v;
+          w.cand_pos[idx] = a.p;
+          w.cand_col[idx] = q >= 0 ? bid + G * q : -1;
+          double* r = w.cand_refl + 4 * (int64_t)idx;
+          r[0] = tau;
+          r[1] = beta;
+          r[2] = rden;
+          r[3] = (double)nz;
+        } else {  // G = 1: owned index q is physical column q
+          sh_P = q;
+          sh_p = a.p;
+          sh_tau = tau;
+          sh_beta = beta;
+          sh_rden = rden;
+          sh_nz = nz;
+        }
       }
-      red_col[0] = bq;
-      red_pos[0] = bp;
-    }
-    __syncthreads();
-    const int q = red_col[0];
-    if (G > 1 && q >= 0 && q < ncached) {  // a column in X is already there
-      double* dst = X + (int64_t)(bid + G * q) * ldx;
-      const double* src = cache + (int64_t)q * d;
-      for (int r = j_done + 1 + threadIdx.x; r < d; r += blockDim.x) dst[r] = src[r];
+    } else if (G > 1) {
+      named_sync(1, blockDim.x);
+      const int q = sh_q;
+      if (q >= 0 && q < ncached) {  // a column in X is already there
+        double* dst = X + (int64_t)(bid + G * q) * ldx;
+        const double* src = cache + (int64_t)q * d;
+        for (int r = jn + threadIdx.x - 32; r < d; r += blockDim.x - 32) dst[r] = src[r];
+      }
     }
   };
   publish_candidate(-1);
@@ -396,29 +552,45 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
       *sh_pend = sh_pend_val;
       sh_pend = nullptr;
     }
-    // 1. global pivot (every CTA alike)
-    if (G == 1) {
-      if (threadIdx.x == 0) {
-        sh_P = red_col[0] >= 0 ? red_col[0] : -1;  // G = 1: column q is physical column q
-        sh_p = red_pos[0];
-      }
-    } else if (warp == 0) {
-      double bv = -1.0;
-      int bp = 0x7fffffff, bc = -1;
+    // 1. global pivot and its reflector from the records (every CTA alike)
+    if (G > 1 && warp == 0) {
+      const int slot = (j & 1) * kCandSlot;
+      Cand a;
+      a.v = -1.0;
+      a.p = 0x7fffffff;
+      a.c = -1;
+      a.i = 0;
+      a.tau = 0.0;
+      a.beta = 0.0;
+      a.rden = 1.0;
+      a.nz = 0;
       for (int i = lane; i < G; i += 32) {
-        const double v = __ldcg(w.cand_val + i);
-        const int p = __ldcg(w.cand_pos + i);
-        const int c = __ldcg(w.cand_col + i);
-        if (c >= 0 && cand_better(v, p, bv, bp)) { bv = v; bp = p; bc = c; }
+        const double v = __ldcg(w.cand_val + slot + i);
+        const int p = __ldcg(w.cand_pos + slot + i);
+        const int c = __ldcg(w.cand_col + slot + i);
+        if (c >= 0 && cand_better(v, p, a.v, a.p)) {
+          a.v = v;
+          a.p = p;
+          a.c = c;
+          a.i = i;
+        }
       }
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-        const int op = __shfl_down_sync(0xffffffffu, bp, off);
-        const int oc = __shfl_down_sync(0xffffffffu, bc, off);
-        if (oc >= 0 && cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+      if (a.c >= 0) {
+        const double* r = w.cand_refl + 4 * (int64_t)(slot + a.i);
+        a.tau = __ldcg(r);
+        a.beta = __ldcg(r + 1);
+        a.rden = __ldcg(r + 2);
+        a.nz = __ldcg(r + 3) != 0.0;
       }
-      if (lane == 0) { sh_P = bc; sh_p = bp; }
+      warp_best(a, 32, true);
+      if (lane == 0) {
+        sh_P = a.c;
+        sh_p = a.p;
+        sh_tau = a.tau;
+        sh_beta = a.beta;
+        sh_rden = a.rden;
+        sh_nz = a.nz;
+      }
     }
     __syncthreads();
     const int P = sh_P, p = sh_p;
@@ -427,47 +599,21 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
       ok = false;
       break;
     }
-    // 2. the reflector of column P (published rows j.. in X), by every CTA:
-    // the column is staged in shared memory by all threads, then one warp
-    // takes its norm (dot32) and the column is scaled in place
-    const double* gP = X + (int64_t)P * ldx;
-    const int len = d - j;
-    if (G == 1 && P < ncached) {  // the pivot column is in this CTA's shared memory
-      const double* cPs = cache + (int64_t)P * d + j;
-      for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = cPs[i];
-    } else {
-      for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = __ldcg(gP + j + i);
-    }
-    __syncthreads();
-    if (warp == 0) {
-      const double alpha = vbuf[0];
-      const double sumsq = (j + 1 < d) ? warp_dot32_self_smem(vbuf + 1, d - j - 1) : 0.0;
-      if (lane == 0) {
-        if (sumsq == 0.0) {
-          sh_tau = 0.0;
-          sh_nz = 0;
-        } else {
-          const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
-          const double beta = (alpha >= 0.0) ? -nrm : nrm;
-          sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
-          sh_beta = beta;
-          sh_rden = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
-          sh_nz = 1;
-        }
-      }
-    }
-    __syncthreads();
+    // 2. v = (1, x_{j+1..} / (alpha - beta)) into vbuf; the owner of a
+    // cached P keeps v and beta in its column
     const double tau = sh_tau;
     const bool nz = sh_nz != 0;
     const double rden = sh_rden;
+    const int len = d - j;
     const bool owner = (P % G == bid);
     const int qP = (P - bid) / G;
     const bool owner_cached = owner && qP < ncached;
     double* cP = owner_cached ? cache + (int64_t)qP * d : nullptr;
+    const double* src = owner_cached ? cP : X + (int64_t)P * ldx;
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
       double v = 1.0;
       if (i > 0) {
-        const double x = vbuf[i];
+        const double x = owner_cached ? src[j + i] : __ldcg(src + j + i);
         v = nz ? __dmul_rn(x, rden) : x;
         if (owner_cached) cP[j + i] = v;
       }
@@ -512,26 +658,7 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
 #pragma unroll 8
       for (int i2 = lane; i2 < len; i2 += 32) colc[i2] = __fma_rn(vbuf[i2], t, colc[i2]);
       __syncwarp();
-      const double v1 = vn1[q];
-      if (v1 != 0.0) {
-        const double v2 = vn2[q];
-        double temp = __ddiv_rn(fabs(colc[0]), v1);
-        temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
-        temp = temp > 0.0 ? temp : 0.0;
-        const double ratio = __ddiv_rn(v1, v2);
-        const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
-        if (temp2 <= tol3z) {
-          const double s2 =
-              (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1, q >= ncached) : 0.0;
-          if (lane == 0) {
-            const double nv = (j + 1 < d) ? __dsqrt_rn(s2) : 0.0;
-            vn1[q] = nv;
-            vn2[q] = nv;
-          }
-        } else if (lane == 0) {
-          vn1[q] = __dmul_rn(v1, __dsqrt_rn(temp));
-        }
-      }
+      warp_downdate(vn1 + q, vn2 + q, fabs(colc[0]), colc + 1, d - j - 1, q >= ncached, tol3z);
       __syncwarp();
     }
     __syncthreads();
@@ -541,6 +668,7 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
   // write the owned columns back (also after an early exit, so that global
   // memory holds this CTA's last state) and, from CTA 0, the maps
   __syncthreads();
+  grid_release(&sc->bar, G);
   if (threadIdx.x == 0 && sh_pend) *sh_pend = sh_pend_val;  // after the last barrier
   for (int q = 0; q < ncached; ++q) {
     double* dst = X + (int64_t)(bid + G * q) * ldx;
@@ -560,22 +688,22 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cached_kernel(QrcpDesc D, d
 }
 
 // A small sketch (n <= kQrcpClusterMaxN) on one thread-block cluster of G
-// CTAs (G <= 8, one column per warp, every column in shared memory): the
+// CTAs (G <= 16, four columns each, every column in shared memory): the
 // same steps and arithmetic as qrcp_cached_body, with the exchange inside
-// the cluster.  At the end of a step each CTA writes its candidate into its
-// own shared memory (two slots by step parity) and the cluster barrier
-// (barrier.cluster arrive with release, wait with acquire) replaces the grid
-// barrier; every CTA then reads the G candidates and the pivot column
-// straight from the owner CTA's shared memory (distributed shared memory),
-// with no round trip through global memory.  The owner writes beta into its
-// column's row j only after the next barrier (the others read that row
-// during the step); the Householder vector itself is not kept, as only the
-// upper triangle (R^sk) is read afterwards.  Every CTA runs the same
-// sequence of barriers (the exits depend only on data every CTA holds
-// alike), and a last barrier keeps each CTA's shared memory alive until no
-// peer reads it.
+// the cluster.  At the end of a step each CTA writes its candidate and that
+// column's reflector for the next step into its own shared memory (two
+// slots by step parity), and the cluster barrier (barrier.cluster arrive
+// with release, wait with acquire) replaces the grid barrier; every CTA then
+// reads the G records and the pivot column straight from the owner CTA's
+// shared memory (distributed shared memory), with no round trip through
+// global memory.  The owner writes beta into its column's row j only after
+// the next barrier (the others read that column during the step); the
+// Householder vector itself is not kept, as only the upper triangle (R^sk)
+// is read afterwards.  Every CTA runs the same sequence of barriers (the
+// exits depend only on data every CTA holds alike), and a last barrier
+// keeps each CTA's shared memory alive until no peer reads it.
 constexpr int kQrcpClusterMaxN = 64;
-constexpr int kQrcpClusterMaxG = 8;
+constexpr int kQrcpClusterMaxG = 16;
 __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, double tol3z) {
   extern __shared__ double cache[];
   namespace cg = cooperative_groups;
@@ -596,8 +724,8 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, 
   double* vn2 = vn1 + nown;                  // nown
   int* phys = (int*)(vn2 + nown);            // n
   int* posof = phys + n;                     // n
-  __shared__ double rec_val[2];
-  __shared__ int rec_pos[2], rec_col[2];
+  __shared__ double rec_val[2], rec_tau[2], rec_beta[2], rec_rden[2];
+  __shared__ int rec_pos[2], rec_col[2], rec_nz[2];
   __shared__ int sh_P, sh_p;
   __shared__ double sh_tau, sh_beta, sh_rden;
   __shared__ int sh_nz;
@@ -629,8 +757,10 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, 
   }
   __syncthreads();
 
-  // the CTA's best unpivoted column into its record slot (j_done + 2) & 1
+  // the CTA's best unpivoted column after step j_done and its reflector for
+  // step j_done + 1, into record slot (j_done + 1) & 1
   auto publish_candidate = [&](int j_done) {
+    const int jn = j_done + 1;
     double bv = -1.0;
     int bp = 0x7fffffff, bq = -1;
     for (int q = warp; q < nown; q += nwarps) {
@@ -642,13 +772,31 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, 
     }
     if (lane == 0) { red_val[warp] = bv; red_pos[warp] = bp; red_col[warp] = bq; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int i = 1; i < nwarps; ++i)
-        if (cand_better(red_val[i], red_pos[i], bv, bp)) { bv = red_val[i]; bp = red_pos[i]; bq = red_col[i]; }
-      const int slot = (j_done + 2) & 1;
-      rec_val[slot] = bv;
-      rec_pos[slot] = bp;
-      rec_col[slot] = bq >= 0 ? bid + G * bq : -1;
+    if (warp == 0) {
+      Cand a;
+      a.v = lane < nwarps ? red_val[lane] : -1.0;
+      a.p = lane < nwarps ? red_pos[lane] : 0x7fffffff;
+      a.c = lane < nwarps ? red_col[lane] : -1;
+      a.i = 0;
+      a.tau = a.beta = 0.0;
+      a.rden = 1.0;
+      a.nz = 0;
+      warp_best(a, pow2_at_least(nwarps), false);
+      const int q = a.c;
+      double tau = 0.0, beta = 0.0, rden = 1.0;
+      int nz = 0;
+      if (q >= 0 && jn < n)
+        warp_reflector(cache + (int64_t)q * d, jn, d, false, tau, beta, rden, nz);
+      if (lane == 0) {
+        const int slot = jn & 1;
+        rec_val[slot] = a.v;
+        rec_pos[slot] = a.p;
+        rec_col[slot] = q >= 0 ? bid + G * q : -1;
+        rec_tau[slot] = tau;
+        rec_beta[slot] = beta;
+        rec_rden[slot] = rden;
+        rec_nz[slot] = nz;
+      }
     }
     cluster.sync();
   };
@@ -662,25 +810,41 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, 
       cache[(int64_t)sh_pend_q * d + sh_pend_row] = sh_pend_val;
       sh_pend_q = -1;
     }
-    // 1. global pivot from the G records (every CTA alike)
+    // 1. global pivot and its reflector from the G records (every CTA alike)
     if (warp == 0) {
-      double bv = -1.0;
-      int bp = 0x7fffffff, bc = -1;
-      const int slot = (j + 1) & 1;
+      const int slot = j & 1;
+      Cand a;
+      a.v = -1.0;
+      a.p = 0x7fffffff;
+      a.c = -1;
+      a.i = 0;
+      a.tau = 0.0;
+      a.beta = 0.0;
+      a.rden = 1.0;
+      a.nz = 0;
       if (lane < G) {
-        const double v = *cluster.map_shared_rank(&rec_val[slot], lane);
-        const int p = *cluster.map_shared_rank(&rec_pos[slot], lane);
         const int c = *cluster.map_shared_rank(&rec_col[slot], lane);
-        if (c >= 0) { bv = v; bp = p; bc = c; }
+        const double v = *cluster.map_shared_rank(&rec_val[slot], lane);
+        const int pp = *cluster.map_shared_rank(&rec_pos[slot], lane);
+        if (c >= 0 && cand_better(v, pp, a.v, a.p)) {
+          a.v = v;
+          a.p = pp;
+          a.c = c;
+          a.tau = *cluster.map_shared_rank(&rec_tau[slot], lane);
+          a.beta = *cluster.map_shared_rank(&rec_beta[slot], lane);
+          a.rden = *cluster.map_shared_rank(&rec_rden[slot], lane);
+          a.nz = *cluster.map_shared_rank(&rec_nz[slot], lane);
+        }
       }
-#pragma unroll
-      for (int off = 16; off >= 1; off >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-        const int op = __shfl_down_sync(0xffffffffu, bp, off);
-        const int oc = __shfl_down_sync(0xffffffffu, bc, off);
-        if (oc >= 0 && cand_better(ov, op, bv, bp)) { bv = ov; bp = op; bc = oc; }
+      warp_best(a, pow2_at_least(G), true);
+      if (lane == 0) {
+        sh_P = a.c;
+        sh_p = a.p;
+        sh_tau = a.tau;
+        sh_beta = a.beta;
+        sh_rden = a.rden;
+        sh_nz = a.nz;
       }
-      if (lane == 0) { sh_P = bc; sh_p = bp; }
     }
     __syncthreads();
     const int P = sh_P, p = sh_p;
@@ -689,42 +853,22 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, 
       ok = false;
       break;
     }
-    // 2. the pivot column, rows j.., from its owner's shared memory
+    // 2. v = (1, x_{j+1..} / (alpha - beta)) from the owner's shared memory
     const int owner = P % G, qP = P / G;
     const int len = d - j;
-    {
-      const double* src = cluster.map_shared_rank(cache + (int64_t)qP * d + j, owner);
-      for (int i = threadIdx.x; i < len; i += blockDim.x) vbuf[i] = src[i];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      const double alpha = vbuf[0];
-      const double sumsq = (j + 1 < d) ? warp_dot32_self_smem(vbuf + 1, d - j - 1) : 0.0;
-      if (lane == 0) {
-        if (sumsq == 0.0) {
-          sh_tau = 0.0;
-          sh_nz = 0;
-        } else {
-          const double nrm = __dsqrt_rn(__fma_rn(alpha, alpha, sumsq));
-          const double beta = (alpha >= 0.0) ? -nrm : nrm;
-          sh_tau = __ddiv_rn(__dsub_rn(beta, alpha), beta);
-          sh_beta = beta;
-          sh_rden = __ddiv_rn(1.0, __dsub_rn(alpha, beta));  // 1 / (alpha - beta)
-          sh_nz = 1;
-        }
-      }
-    }
-    __syncthreads();
     const double tau = sh_tau;
     const bool nz = sh_nz != 0;
     const double rden = sh_rden;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-      double v = 1.0;
-      if (i > 0) {
-        const double x = vbuf[i];
-        v = nz ? __dmul_rn(x, rden) : x;
+    {
+      const double* src = cluster.map_shared_rank(cache + (int64_t)qP * d + j, owner);
+      for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        double v = 1.0;
+        if (i > 0) {
+          const double x = src[i];
+          v = nz ? __dmul_rn(x, rden) : x;
+        }
+        vbuf[i] = v;
       }
-      vbuf[i] = v;
     }
     if (threadIdx.x == 0) {
       if (owner == bid && nz) {
@@ -753,25 +897,7 @@ __global__ void __launch_bounds__(kQrcpThreads) qrcp_cluster_kernel(QrcpDesc D, 
 #pragma unroll 8
       for (int i2 = lane; i2 < len; i2 += 32) colc[i2] = __fma_rn(vbuf[i2], t, colc[i2]);
       __syncwarp();
-      const double v1 = vn1[q];
-      if (v1 != 0.0) {
-        const double v2 = vn2[q];
-        double temp = __ddiv_rn(fabs(colc[0]), v1);
-        temp = __dsub_rn(1.0, __dmul_rn(temp, temp));
-        temp = temp > 0.0 ? temp : 0.0;
-        const double ratio = __ddiv_rn(v1, v2);
-        const double temp2 = __dmul_rn(temp, __dmul_rn(ratio, ratio));
-        if (temp2 <= tol3z) {
-          const double s2 = (j + 1 < d) ? warp_dot32_self_smem(colc + 1, d - j - 1) : 0.0;
-          if (lane == 0) {
-            const double nv = (j + 1 < d) ? __dsqrt_rn(s2) : 0.0;
-            vn1[q] = nv;
-            vn2[q] = nv;
-          }
-        } else if (lane == 0) {
-          vn1[q] = __dmul_rn(v1, __dsqrt_rn(temp));
-        }
-      }
+      warp_downdate(vn1 + q, vn2 + q, fabs(colc[0]), colc + 1, d - j - 1, false, tol3z);
       __syncwarp();
     }
     __syncthreads();
@@ -888,18 +1014,31 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
                         int64_t ldr, void* work, DeviceScalars* sc, int num_sms,
                         cudaStream_t stream, bool nopivot) {
   QrcpDesc D{d, n, X, ldx, qrcp_carve(work, n), J, Rsk, ldr, sc, nopivot ? 1 : 0};
-  // a small sketch: one cluster, one column per warp (CQRRPT_QRCP_CLUSTER = 0
-  // turns this off, for tests of the other path on the same sizes)
+  // CQRRPT_QRCP_CLUSTER = 1: a small sketch on one cluster of up to 16 CTAs,
+  // four columns each (as the cooperative grid below), exchanging through
+  // distributed shared memory and the cluster barrier.  Same bits; at n = 64
+  // it measured 0.81 ms against 0.55 ms for the cooperative grid with its
+  // counter barrier, so the grid is the default.  A cluster that cannot be
+  // placed falls back to the grid.
   {
-    const int Gc = (n + 7) / 8;
+    const int Gc = (n + 3) / 4;
     const int64_t nown_c = (n + Gc - 1) / Gc;  // CTA 0 owns the most columns
     // the columns, the reflector buffer, two norms per column, the two maps
     const int64_t smem_c = nown_c * d * 8 + (d + 2 * nown_c) * 8 + (int64_t)2 * n * 4;
     bool use = n <= kQrcpClusterMaxN && Gc <= kQrcpClusterMaxG && smem_c <= kQrcpSmemCap;
-    if (const char* f = std::getenv("CQRRPT_QRCP_CLUSTER")) use = use && f[0] != '0';
+    const char* f = std::getenv("CQRRPT_QRCP_CLUSTER");
+    use = use && f && f[0] == '1';
+    cudaError_t e1 = cudaSuccess;
     if (use) {
-      cudaError_t e1 = raise_smem_limit((const void*)qrcp_cluster_kernel, (size_t)smem_c);
+      e1 = raise_smem_limit((const void*)qrcp_cluster_kernel, (size_t)smem_c);
       if (e1 != cudaSuccess) return e1;
+      if (Gc > 8)  // clusters above 8 CTAs are opt-in
+        e1 = cudaFuncSetAttribute(qrcp_cluster_kernel,
+                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      use = e1 == cudaSuccess;
+      cudaGetLastError();
+    }
+    if (use) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(Gc);
       cfg.blockDim = dim3(kQrcpThreads);
@@ -912,12 +1051,18 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      const double tz = tol3z_value();
-      e1 = cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, D, tz);
-      if (e1 != cudaSuccess) return e1;
-      qrcp_gather_kernel<<<n, 128, 0, stream>>>(D);
-      count_launches(2);
-      return cudaGetLastError();
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, qrcp_cluster_kernel, &cfg) != cudaSuccess)
+        nclusters = 0;
+      cudaGetLastError();
+      if (nclusters >= 1) {
+        const double tz = tol3z_value();
+        e1 = cudaLaunchKernelEx(&cfg, qrcp_cluster_kernel, D, tz);
+        if (e1 != cudaSuccess) return e1;
+        qrcp_gather_kernel<<<n, 128, 0, stream>>>(D);
+        count_launches(2);
+        return cudaGetLastError();
+      }
     }
   }
   int per_sm = 0;
@@ -930,7 +1075,7 @@ cudaError_t launch_qrcp(int d, int n, double* X, int64_t ldx, int64_t* J, double
   int G = (n + 3) / 4;
   if (G > num_sms * per_sm) G = num_sms * per_sm;
   if (G > num_sms) G = num_sms;
-  if (G > 4096) G = 4096;
+  if (G > kCandSlot) G = kCandSlot;
   if (G < 1) G = 1;
   const double tol3z = tol3z_value();
   void* args[] = {&D, (void*)&tol3z};
@@ -1115,7 +1260,7 @@ __device__ __forceinline__ void init_scalars_body(DeviceScalars* sc, int64_t k) 
   sc->status = kOk;
   sc->pad = 0;
   sc->bar.count = 0;
-  sc->bar.generation = 0;
+  sc->bar.released = 0;
 }
 
 __global__ void init_scalars_kernel(DeviceScalars* sc, int64_t k) { init_scalars_body(sc, k); }

@@ -75,14 +75,14 @@ def test_sketch_bitexact(C, m, n, d, s, seed):
 
 
 # ---------------------------------------------------------------- line 2
-@pytest.mark.parametrize("path", ["auto", "no_cluster"])
+@pytest.mark.parametrize("path", ["auto", "cluster"])
 @pytest.mark.parametrize("d,n,seed", [(128, 64, 1), (37, 29, 2), (200, 150, 3), (640, 512, 4),
                                       (9, 9, 5), (1, 1, 6), (80, 57, 7)])
 def test_qrcp_bitexact(C, d, n, seed, path, monkeypatch):
-    # n <= 64 runs on one thread-block cluster unless turned off; both forms
-    # give the oracle's bits
-    if path == "no_cluster":
-        monkeypatch.setenv("CQRRPT_QRCP_CLUSTER", "0")
+    # CQRRPT_QRCP_CLUSTER=1 runs n <= 64 on one thread-block cluster instead
+    # of the cooperative grid; both forms give the oracle's bits
+    if path == "cluster":
+        monkeypatch.setenv("CQRRPT_QRCP_CLUSTER", "1")
     rng = _rng(seed)
     X = rng.standard_normal((d, n)) * np.logspace(0, -8, n)[rng.permutation(n)]
     R_ref, J_ref, *_ = oracle.qrcp(X)
@@ -93,11 +93,11 @@ def test_qrcp_bitexact(C, d, n, seed, path, monkeypatch):
     assert_bits(host(Rsk), R_ref, "R^sk")
 
 
-@pytest.mark.parametrize("path", ["auto", "no_cluster"])
+@pytest.mark.parametrize("path", ["auto", "cluster"])
 @pytest.mark.parametrize("n", [80, 64])
 def test_qrcp_rank_deficient_and_ties(C, n, path, monkeypatch):
-    if path == "no_cluster":
-        monkeypatch.setenv("CQRRPT_QRCP_CLUSTER", "0")
+    if path == "cluster":
+        monkeypatch.setenv("CQRRPT_QRCP_CLUSTER", "1")
     rng = _rng(9)
     d = 96
     X = rng.standard_normal((d, 40)) @ rng.standard_normal((40, n))

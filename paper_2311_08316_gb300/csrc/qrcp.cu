@@ -564,25 +564,35 @@ __device__ __forceinline__ void qrcp_cached_body(const QrcpDesc& D, double tol3z
       a.beta = 0.0;
       a.rden = 1.0;
       a.nz = 0;
+      // lane l reads records l, l + 32, ... with their reflectors (all
+      // loads in flight at once) and keeps its best; the butterfly then
+      // moves only the keys, and the winner's reflector comes from the lane
+      // that read it
       for (int i = lane; i < G; i += 32) {
         const double v = __ldcg(w.cand_val + slot + i);
         const int p = __ldcg(w.cand_pos + slot + i);
         const int c = __ldcg(w.cand_col + slot + i);
+        const double2 r01 = __ldcg((const double2*)(w.cand_refl + 4 * (int64_t)(slot + i)));
+        const double2 r23 = __ldcg((const double2*)(w.cand_refl + 4 * (int64_t)(slot + i)) + 1);
         if (c >= 0 && cand_better(v, p, a.v, a.p)) {
           a.v = v;
           a.p = p;
           a.c = c;
           a.i = i;
+          a.tau = r01.x;
+          a.beta = r01.y;
+          a.rden = r23.x;
+          a.nz = r23.y != 0.0;
         }
       }
-      if (a.c >= 0) {
-        const double* r = w.cand_refl + 4 * (int64_t)(slot + a.i);
-        a.tau = __ldcg(r);
-        a.beta = __ldcg(r + 1);
-        a.rden = __ldcg(r + 2);
-        a.nz = __ldcg(r + 3) != 0.0;
+      warp_best(a, 32, false);
+      {
+        const int src = a.i & 31;  // the lane that read record a.i
+        a.tau = __shfl_sync(0xffffffffu, a.tau, src);
+        a.beta = __shfl_sync(0xffffffffu, a.beta, src);
+        a.rden = __shfl_sync(0xffffffffu, a.rden, src);
+        a.nz = __shfl_sync(0xffffffffu, a.nz, src);
       }
-      warp_best(a, 32, true);
       if (lane == 0) {
         sh_P = a.c;
         sh_p = a.p;

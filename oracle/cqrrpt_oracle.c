@@ -45,7 +45,10 @@
  *   - Every sum over the tall dimension m is blocked: rows are split into
  *     blocks of ROW_BLOCK = 4096; inside a block terms are added in
  *     ascending row order starting from +0.0; block sums are added in
- *     ascending block order starting from +0.0.
+ *     ascending block order starting from +0.0.  The Gram (line 5) blocks
+ *     once more: its sum over a block is the ascending sum, from +0.0, of
+ *     the block's GRAM_SUB_BLOCK = 256-row sub-block sums, each of which
+ *     adds its terms in ascending row order from +0.0.
  *   - Dot products inside the QRCP of the d x n sketch ("dot32"): element i
  *     of a vector goes to lane i mod 32; each lane accumulates its elements
  *     in ascending order with fma from +0.0; lanes are combined by the fixed
@@ -79,6 +82,7 @@
 #include <string.h>
 
 #define ROW_BLOCK 4096
+#define GRAM_SUB_BLOCK 256
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11, Sec. 4.2).                           */
@@ -451,7 +455,8 @@ void oracle_trsm_rut(int64_t m, int64_t k, const double* B, int64_t ldb, const i
     }
 }
 
-/* Alg. 2 line 5: G = X^T X (k x k, both triangles), blocked sum over rows. */
+/* Alg. 2 line 5: G = X^T X (k x k, both triangles), blocked sum over rows:
+ * 256-row sub-blocks inside 4096-row blocks (the reading above). */
 void oracle_gram(int64_t m, int64_t k, const double* X, int64_t ldx, double* G, int64_t ldg) {
 #pragma omp parallel for schedule(dynamic)
     for (int64_t b = 0; b < k; ++b) {
@@ -462,7 +467,12 @@ void oracle_gram(int64_t m, int64_t k, const double* X, int64_t ldx, double* G, 
             for (int64_t r0 = 0; r0 < m; r0 += ROW_BLOCK) {
                 int64_t r1 = r0 + ROW_BLOCK < m ? r0 + ROW_BLOCK : m;
                 double part = 0.0;
-                for (int64_t r = r0; r < r1; ++r) part = fma(xa[r], xb[r], part);
+                for (int64_t s0 = r0; s0 < r1; s0 += GRAM_SUB_BLOCK) {
+                    int64_t s1 = s0 + GRAM_SUB_BLOCK < r1 ? s0 + GRAM_SUB_BLOCK : r1;
+                    double sub = 0.0;
+                    for (int64_t r = s0; r < s1; ++r) sub = fma(xa[r], xb[r], sub);
+                    part = part + sub;
+                }
                 total = total + part;
             }
             G[a + b * ldg] = total;

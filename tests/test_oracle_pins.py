@@ -243,6 +243,45 @@ def test_gram_matches_product_several_blocks():
     assert np.array_equal(oracle.gram(Xi), (Xi.astype(np.int64).T @ Xi.astype(np.int64)).astype(float))
 
 
+def test_gram_sums_256_row_sub_blocks_in_ascending_order():
+    """The Gram's summation reading, on inputs where the order shows in the
+    result (values derived by hand; u = 2^-53, half an ulp of 1.0).
+    Column 0 is all ones, so G[0, 1] is the sum of column 1.
+    (a) rows 0..255: 1, then 255 times u; rows 256..511: 255 times u, then -1.
+    Sub-block 0 sums to 1 (each 1 + u is a tie and rounds to 1), sub-block 1
+    to u*255 - 1 exactly; their sum is 255 u.  One sequential chain over the
+    512 rows would give 0 instead (the u's all vanish against 1 or are added
+    before the -1).
+    (b) rows 0, 256 and 512 hold 1, u and u (the rest 0): the sub-block sums
+    1, u, u added in ascending order from +0.0 give 1 (two ties); a tree
+    1 + (u + u) would give 1 + 2u."""
+    u = 2.0 ** -53
+    y = np.zeros(512)
+    y[0] = 1.0
+    y[1:256] = u
+    y[256:511] = u
+    y[511] = -1.0
+    X = np.asfortranarray(np.stack([np.ones(512), y], axis=1))
+    G = oracle.gram(X)
+    assert G[0, 1] == 255 * u and G[1, 0] == 255 * u
+    y = np.zeros(768)
+    y[0], y[256], y[512] = 1.0, u, u
+    X = np.asfortranarray(np.stack([np.ones(768), y], axis=1))
+    assert oracle.gram(X)[0, 1] == 1.0
+    # the same sums in a second 4096-row block start again from +0.0 and the
+    # two block sums are added in ascending order
+    y2 = np.zeros(4096 + 512)
+    y2[4096 + 0] = 1.0
+    y2[4096 + 1:4096 + 256] = u
+    y2[4096 + 256:4096 + 511] = u
+    y2[4096 + 511] = -1.0
+    # block 0 sums to 1, block 1 to 255 u; 1 + 255 u lies halfway between
+    # 1 + 254 u and 1 + 256 u (the ulp of 1 is 2u) and rounds to the even one
+    y2[0] = 1.0
+    X = np.asfortranarray(np.stack([np.ones(4096 + 512), y2], axis=1))
+    assert oracle.gram(X)[0, 1] == 1.0 + 256 * u
+
+
 def test_potrf_matches_cholesky_and_reports_failure():
     rng = _rng(7)
     k = 15

@@ -370,7 +370,8 @@ static int run_fp64(cqrrpt_handle h, int64_t m, int64_t n, const double* A, int6
   if (e == cudaSuccess)
     e = launch_trsm_rut(m, ni, &sc->k, A, lda, J, Rsk, n, Q, ldq, status, stream);
   mark(h, 4, stream);
-  if (e == cudaSuccess) e = launch_gram(m, ni, &sc->k, Q, ldq, G, n, region, status, stream);
+  if (e == cudaSuccess)  // region holds gram_workspace_bytes(m, n): either form
+    e = launch_gram(m, ni, &sc->k, Q, ldq, G, n, region, status, stream, false, true);
   mark(h, 5, stream);
   if (e == cudaSuccess) e = launch_potrf(ni, G, n, Rpre, ldp, sc, stream);
   if (e == cudaSuccess) e = launch_rank_stage2(Rpre, ldp, !(tol > 0.0), sc, stream);
@@ -1941,8 +1942,8 @@ int cqrrpt_gram_d(cqrrpt_handle h, int64_t m, int64_t k, const double* X, int64_
   int st = ensure_ws(h, (size_t)gram_workspace_bytes(m, k));
   if (st != kOk) return st;
   if (launch_init_scalars(h->sc, k, stream) != cudaSuccess) return kCudaError;
-  if (launch_gram(m, (int)k, &h->sc->k, X, ldx, G, ldg, h->ws, &h->sc->status, stream) !=
-      cudaSuccess)
+  if (launch_gram(m, (int)k, &h->sc->k, X, ldx, G, ldg, h->ws, &h->sc->status, stream, false,
+                  true) != cudaSuccess)
     return kCudaError;
   return kOk;
 }

@@ -93,6 +93,7 @@ struct GramDesc {
   int64_t ldg;
   const int* status;
   int tile;  // output tile edge: 8, 16 or 32 (0 = 32)
+  int sub;   // 1: partials per kGramSub-row sub-block (else per kRowBlock block)
 };
 
 struct PotrfDesc {

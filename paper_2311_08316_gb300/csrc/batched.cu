@@ -44,7 +44,7 @@ size_t push_table(std::vector<char>& buf, const std::vector<T>& v) {
 
 int64_t problem_workspace_bytes(int64_t m, int64_t n, int64_t d, int nnz) {
   const int64_t a = sketch_workspace_bytes(m, n, (int)d, nnz);
-  const int64_t b = gram_workspace_bytes(m, n);
+  const int64_t b = gram_block_workspace_bytes(m, n);
   int64_t t = (a > b ? a : b);
   t += align256(d * n * 8);
   t += qrcp_workspace_bytes(n);
@@ -96,7 +96,7 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     const int64_t m = q.m, n = q.n, d = q.d;
     if (d > max_d) max_d = (int)d;
     const int64_t a = sketch_workspace_bytes(m, n, (int)d, q.nnz);
-    const int64_t b = gram_workspace_bytes(m, n);
+    const int64_t b = gram_block_workspace_bytes(m, n);
     if (ws_each) w = ws_each[p];  // problem p's own workspace
     char* region = w;
     w += (a > b ? a : b);

@@ -20,6 +20,7 @@
 namespace cqrrpt {
 
 constexpr int kRowBlock = 4096;
+constexpr int kGramSub = 256;  // the Gram's sub-blocks inside a row block
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 

@@ -128,14 +128,19 @@ cudaError_t launch_trsm_rut_batched(const TrsmDesc* D, const int64_t* base, int 
                                     int64_t total_tiles, cudaStream_t stream);
 
 // ---- Alg. 2 line 5 -------------------------------------------------------
+// Workspace of launch_gram (either form); gram_block_workspace_bytes: of
+// the block-partial form alone (launch_gram_partials, the batched Gram).
 int64_t gram_workspace_bytes(int64_t m, int64_t n);
+int64_t gram_block_workspace_bytes(int64_t m, int64_t n);
 int64_t gram_partial_tiles(int64_t m, int kmax, int tile);
 int64_t gram_combine_tiles(int kmax);
 // accumulate: G (both triangles) += this X's blocks, continuing G's sums
 // in ascending block order (row panels; G = 0 before the first panel).
+// sub_ok: `work` holds gram_workspace_bytes(m, kmax), so a small problem
+// may take the sub-block partial form (same bits, shorter chains).
 cudaError_t launch_gram(int64_t m, int kmax, const int64_t* k_dev, const double* X, int64_t ldx,
                         double* G, int64_t ldg, void* work, const int* status,
-                        cudaStream_t stream, bool accumulate = false);
+                        cudaStream_t stream, bool accumulate = false, bool sub_ok = false);
 // The two halves of launch_gram: the block sums into `work`, then G (both
 // triangles) = (accumulate: G +) their ascending sum.
 cudaError_t launch_gram_partials(int64_t m, int kmax, const int64_t* k_dev, const double* X,

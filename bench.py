@@ -59,7 +59,7 @@ def parse():
     p.add_argument("--rows", type=int, default=131072, help="m of the workload")
     p.add_argument("--workload", default="single",
                    choices=["single", "small", "batched", "mixed", "serve", "dense", "panels",
-                            "srrqr", "sharded"],
+                            "srrqr", "sharded", "sweep"],
                    help="single: the rank-800 131072 x 1024 problem (headline); small: the "
                         "4096 x 64 cond-1e8 problem (latency per factorisation); batched: 512 "
                         "uneven problems in one batched pass; mixed: 1048576 x 512, cond 1e10, "
@@ -69,7 +69,9 @@ def parse():
                         "panels: the headline matrix streamed from pinned host memory in row "
                         "panels; srrqr: the headline matrix with the strong rank-revealing "
                         "exchanges on the sketch; sharded: one (ranks x --rows) x 1024 "
-                        "matrix partitioned by rows over the torchrun ranks")
+                        "matrix partitioned by rows over the torchrun ranks; sweep: Gaussian "
+                        "--rows x n, n = 512 .. 4096 (the paper's speed experiment), FP64 "
+                        "and split-BF16")
     p.add_argument("--configs", default="all", choices=["all", "none"],
                    help="single workload, N = 1: also measure the small, mixed, batched and "
                         "serving workloads in the same run (all) or only the headline (none)")
@@ -1092,6 +1094,67 @@ def run_serve(args, world, rank, local, C):
     return line
 
 
+def run_sweep(args, world, rank, local, C):
+    """The paper's speed experiment (Sec. 5.2): iid Gaussian --rows x n
+    matrices, n = 512, 1024, 2048, 4096, gamma 1.25, 4 nonzeros per column,
+    tol 1e-12 (full rank); per n one warm-up and --steps timed
+    factorisations (at most 3) in FP64 (with the per-phase split) and in
+    split-BF16.  The rate is the paper's canonical one, 2 m n^2 / time."""
+    m = args.rows
+    steps = max(1, min(args.steps, 3))
+    stream = torch.cuda.current_stream()
+    h = C.Handle(local)
+    per_n = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall = time.perf_counter()
+    for n in (512, 1024, 2048, 4096):
+        A = W.gaussian(m, n, W.BASE_SEED + 40 + n, "cuda")
+        Q = C.colmajor_empty(m, n, A.device)
+        R = C.colmajor_empty(n, n, A.device)
+        J = torch.empty(n, dtype=torch.int64, device=A.device)
+        rec = {}
+        for prec, name in ((C.FP64, "fp64"), (C.SPLITBF16, "splitbf16")):
+            res = C.cqrrpt(A, 1.25, 4, 1e-12, 7, precision=prec, out=(Q, R, J), handle=h,
+                           stream=stream)
+            assert res.status == 0 and res.k == n, (res.status, res.k)
+            h.set_profiling(prec == C.FP64)
+            ts, qr = [], []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C.cqrrpt(A, 1.25, 4, 1e-12, 7, precision=prec, out=(Q, R, J), handle=h,
+                         stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                if prec == C.FP64:
+                    qr.append(h.phase_times()["qrcp"])
+            h.set_profiling(False)
+            ms = statistics.median(ts)
+            rec[name] = {"ms": ms, "gflops_2mn2": 2.0 * m * n * n / (ms * 1e6), "k": res.k}
+            if qr:
+                rec[name]["qrcp_ms"] = statistics.median(qr)
+                rec[name]["qrcp_share"] = statistics.median(qr) / ms
+        rec["splitbf16"]["speedup_vs_fp64"] = rec["fp64"]["ms"] / rec["splitbf16"]["ms"]
+        per_n[str(n)] = rec
+        del A, Q, R, J
+        torch.cuda.empty_cache()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    top = per_n["2048"]["fp64"]
+    return {"metric": "cqrrpt_gflops_canonical", "value": top["gflops_2mn2"],
+            "unit": "GFLOP/s (2mn^2 / time)", "n_gpus": world, "steps": steps, "warmup": 1,
+            "ms_per_step": top["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 / bf16 digits -> f64", "data": "synthetic",
+            "config": {"workload": "cqrrpt_sweep_gaussian_m%d_n512-4096" % m, "m": m,
+                       "n": [512, 1024, 2048, 4096], "gamma": 1.25, "nnz_per_col": 4,
+                       "tol": 1e-12, "value_is": "FP64 at n = 2048",
+                       "l2": "inputs larger than L2, no flush"},
+            "per_n": per_n, "clocks": clk, "wall_s": wall}
+
+
 # --------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -1108,7 +1171,7 @@ def main():
     cbuild.build()
     others = {"batched": run_batched, "mixed": run_mixed, "serve": run_serve,
               "dense": run_dense, "panels": run_panels, "srrqr": run_srrqr,
-              "small": run_small, "sharded": run_sharded}
+              "small": run_small, "sharded": run_sharded, "sweep": run_sweep}
     if args.workload in others:
         line = others[args.workload](args, world, rank, local, C)
         if rank == 0:

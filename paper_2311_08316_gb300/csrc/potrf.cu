@@ -196,33 +196,59 @@ __global__ void __launch_bounds__(kPotrfSmallThreads) potrf_small_kernel(PotrfDe
     const int c = e / k, j = e - c * k;
     S[c * ld + j] = j <= c ? D.G[(int64_t)c * D.ldg + j] : 0.0;
   }
-  if (threadIdx.x == 0) fail_at = -1;
   __syncthreads();
-  for (int t = 0; t < k; ++t) {
-    if (threadIdx.x == 0) {
-      const double piv = S[t * ld + t];
-      if (!(piv > 0.0)) {
-        fail_at = t;
-      } else {
-        const double r = __dsqrt_rn(piv);
-        S[t * ld + t] = r;
-        D.R[(int64_t)t * D.ldr + t] = r;
-      }
+  // thread 0 takes each pivot's square root one step ahead: at step t, right
+  // after the divisions of column t, it applies step t's update to
+  // (t+1, t+1) (the same fma the trailing update would) and takes the root,
+  // while warps 1.. update the rest of the trailing block
+  auto pivot = [&](int t) {  // thread 0: S[t, t] holds the updated pivot
+    const double piv = S[t * ld + t];
+    if (!(piv > 0.0)) {
+      fail_at = t;
+    } else {
+      const double r = __dsqrt_rn(piv);
+      S[t * ld + t] = r;
+      D.R[(int64_t)t * D.ldr + t] = r;
     }
-    __syncthreads();
+  };
+  if (threadIdx.x == 0) {
+    fail_at = -1;
+    pivot(0);
+  }
+  __syncthreads();
+  const int upd_threads = (int)blockDim.x - 32;
+  for (int t = 0; t < k; ++t) {
     if (fail_at >= 0) break;  // uniform
     const double rtt = S[t * ld + t];
+    // column t's divisions (threads 0 .. k-t-2: warps 0 and 1); warp 0 then
+    // signals barrier 1 and thread 0 goes on to the next pivot while warps
+    // 1.. (after barrier 1) update the trailing block
+    double v1 = 0.0;
     for (int c = t + 1 + (int)threadIdx.x; c < k; c += blockDim.x) {
       const double v = __ddiv_rn(S[c * ld + t], rtt);
       S[c * ld + t] = v;
       D.R[(int64_t)c * D.ldr + t] = v;
+      if (c == t + 1) v1 = v;
     }
-    __syncthreads();
-    // trailing update: entries (j, c), t < j <= c < k, in one flat index
-    const int w = k - 1 - t;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int c = t + 1 + e / w, j = t + 1 + e % w;
-      if (j <= c) S[c * ld + j] = __fma_rn(-S[j * ld + t], S[c * ld + t], S[c * ld + j]);
+    if (threadIdx.x < 32) {
+      asm volatile("barrier.arrive 1, %0;" ::"r"((int)blockDim.x) : "memory");
+      if (threadIdx.x == 0 && t + 1 < k) {  // the next pivot
+        const int c = t + 1;
+        S[c * ld + c] = __fma_rn(-v1, v1, S[c * ld + c]);
+        pivot(c);
+      }
+    } else {
+      asm volatile("barrier.sync 1, %0;" ::"r"((int)blockDim.x) : "memory");
+    }
+    // trailing update by warps 1..: entries (j, c), t < j <= c < k, but
+    // (t+1, t+1), which thread 0 did
+    if (threadIdx.x >= 32) {
+      const int w = k - 1 - t;
+      for (int e = (int)threadIdx.x - 32; e < w * w; e += upd_threads) {
+        const int c = t + 1 + e / w, j = t + 1 + e % w;
+        if (j <= c && c > t + 1)
+          S[c * ld + j] = __fma_rn(-S[j * ld + t], S[c * ld + t], S[c * ld + j]);
+      }
     }
     __syncthreads();
   }

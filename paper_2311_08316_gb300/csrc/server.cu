@@ -38,6 +38,7 @@
 // Results are bit-identical to a standalone call on the same request,
 // whatever else shares a wave or runs beside it: each lane has its own
 // workspace and the kernels fix their summation orders.
+#include <cstdlib>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -158,6 +159,8 @@ size_t footprint(const cqrrpt_request& r, int64_t d, int nnz) {
 
 // Dynamic batching: while any unit is in flight, a new wave waits until
 // this many requests are ready or the oldest has waited this long.
+// CQRRPT_SERVER_MAX_WAIT_US, read when a server is created, sets the wait
+// (a larger one trades latency for larger waves).
 constexpr int kMinWave = 4;
 constexpr double kMaxWaitUs = 8000.0;
 
@@ -208,6 +211,7 @@ struct Server {
   int error = 0;
   int64_t waves = 0, completed = 0, single_units = 0, batched_units = 0, batched_reqs = 0;
   int busy = 0, max_busy = 0;
+  double max_wait_us = kMaxWaitUs;
   int (*run_single)(cqrrpt_handle, const cqrrpt_request&, double, int, double*, double*, double*,
                     int64_t*, cudaStream_t) = nullptr;
 
@@ -404,7 +408,7 @@ bool Server::step() {
           if (!single_route(q->r) && q->r.precision == oldest_batched->r.precision)
             unit.push_back(q);
         if (waves_busy + singles_busy > 0 && (int)unit.size() < kMinWave &&
-            now - oldest_batched->t_start < kMaxWaitUs) {
+            now - oldest_batched->t_start < max_wait_us) {
           unit.clear();  // gather more while another wave runs
           if (can_single) {
             unit.push_back(oldest_single);
@@ -498,6 +502,10 @@ int cqrrpt_server_create_lanes(cqrrpt_handle h, size_t hbm_budget_bytes, int max
   *out = nullptr;
   cqrrpt_server_s* S = new cqrrpt_server_s();
   Server& s = S->s;
+  if (const char* e = std::getenv("CQRRPT_SERVER_MAX_WAIT_US")) {
+    const double v = std::strtod(e, nullptr);
+    if (v >= 0.0 && v <= 10e6) s.max_wait_us = v;
+  }
   s.h = h;
   s.gamma = gamma;
   s.nnz = nnz_per_col;

@@ -279,7 +279,7 @@ __global__ void oz_gather_kernel(const double* __restrict__ B, int64_t ldb,
 // for each j the dot product sum_{i<=t<j} w_t T[t, j] is split over the 32
 // lanes (T's column j is contiguous: coalesced) and reduced by a fixed
 // shuffle tree; the row being built lives in shared memory.
-constexpr int kTrinvWarps = 8;  // at most; fewer when k rows do not fit
+constexpr int kTrinvWarps = 4;  // at most (one warp per SM sub-partition); fewer when k rows do not fit
 __device__ __forceinline__ void trinv_body(const OzTrinv& J, int64_t tile, double* rows) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = J.k;

@@ -45,6 +45,18 @@ static size_t lists_smem_bytes(int d) {
          (size_t)lists_sort_warps(d) * 2 * kListMapWords * sizeof(uint32_t);
 }
 
+// seg_start of a block holds, for t < d, start[t] (the offset of target t's
+// segment) in its low 17 bits and, in its high 15, the target that thread t
+// of sketch_partial takes: the targets in descending order of list length, so
+// that a warp's lanes walk lists of about the same length (within one length
+// the order is free; every target's sum is the same whichever thread forms
+// it).  seg_start[d] is the total.  Only when every start fits 17 bits and
+// every target 15 (s < 32, d < 32768); otherwise the plain starts, in target
+// order.
+__host__ __device__ inline bool seg_packed(int d, int s) { return d < 32768 && s < 32; }
+constexpr uint32_t kSegMask = (1u << 17) - 1;
+constexpr int kLenBins = 128;  // list lengths of 127 and more share the last bin
+
 // entries: (r_local << 1) | negative
 __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, int* sh_lists) {
   const int d = D.d, s = D.s;
@@ -148,6 +160,39 @@ __device__ __forceinline__ void saso_lists_body(int64_t b, const SketchDesc& D, 
       __syncwarp();
     }
   }
+  if (!seg_packed(d, s)) return;
+  // targets by descending list length: a counting sort on the length (the
+  // sort warps' maps are free again: their first kLenBins words hold it)
+  __syncthreads();
+  int* hist = start + d + 1;
+  for (int i = threadIdx.x; i < kLenBins; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const int len = start[i + 1] - start[i];
+    atomicAdd(&hist[kLenBins - 1 - (len < kLenBins - 1 ? len : kLenBins - 1)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the bins (longest first)
+    const int lane = threadIdx.x;
+    int carry = 0;
+    for (int base = 0; base < kLenBins; base += 32) {
+      const int v = hist[base + lane];
+      int x = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+      }
+      hist[base + lane] = carry + x - v;
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const int len = start[i + 1] - start[i];
+    const int pos = atomicAdd(&hist[kLenBins - 1 - (len < kLenBins - 1 ? len : kLenBins - 1)], 1);
+    gstart[pos] = (int)(((uint32_t)i << 17) | (uint32_t)start[pos]);
+  }
 }
 
 // tile: the block's rows of the kSkCols (= 2) columns, one double2 per row.
@@ -167,13 +212,17 @@ __device__ __forceinline__ void sketch_partial_body(int64_t b, int64_t cg, const
       tile[rl] = make_double2(col0[rl], two ? col1[rl] : 0.0);
   }
   __syncthreads();
-  const int* st = D.seg_start + b * (int64_t)(d + 1);
+  const uint32_t* st = (const uint32_t*)D.seg_start + b * (int64_t)(d + 1);
   const uint32_t* ent = D.entries + b * (int64_t)kRowBlock * D.s;
   double* P = D.partial + b * n * (int64_t)d;  // P_b: d x n, ld d
-  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+  const bool packed = seg_packed(d, D.s);
+  for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    // thread t takes target i (longest lists first when packed)
+    const int i = packed ? (int)(st[t] >> 17) : t;
+    const int e0 = packed ? (int)(st[i] & kSegMask) : (int)st[i];
+    const int e1 = i + 1 < d ? (packed ? (int)(st[i + 1] & kSegMask) : (int)st[i + 1]) : (int)st[d];
     double a0 = 0.0, a1 = 0.0;
-    const int e1 = st[i + 1];
-    for (int e = st[i]; e < e1; ++e) {
+    for (int e = e0; e < e1; ++e) {
       const uint32_t w = ent[e];
       const double2 v = tile[w >> 1];
       // a - x == a + (-x) exactly; the sign flip runs on the integer pipe

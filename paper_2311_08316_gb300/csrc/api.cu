@@ -1420,7 +1420,7 @@ int split_trsm_step(cqrrpt_handle h, const std::vector<int>& ids,
       return kCudaError;
     gm[j] = G;
   }
-  const int warps = oz_trinv_warps(kmax);
+  const int warps = oz_trinv_row_mode(kmax) ? 1 : oz_trinv_warps(kmax);
   const auto b_ti = prefix(nj, [&](size_t j) { return oz_trinv_tiles(ti[j], warps); });
   const auto b_re = prefix(nj, [&](size_t j) { return oz_rowexp_tiles(rs[j]); });
   const auto b_rs = prefix(nj, [&](size_t j) { return oz_splitrows_tiles(rs[j]); });

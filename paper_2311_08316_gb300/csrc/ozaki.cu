@@ -308,6 +308,66 @@ __global__ void __launch_bounds__(kTrinvWarps * 32)
   const int j = find_problem(base, n, blockIdx.x, &t);
   trinv_body(J[j], t, trinv_rows);
 }
+// A single problem's W: one CTA of kTrinvRowThreads threads per row i,
+// right-looking.  Thread q owns the columns j = i + q + kTrinvRowThreads u
+// and keeps their running sums s_j = [j = i] - sum_{t<j} w_t T[t, j] in
+// shared memory.  At step t every thread adds -w_t T[t, j] to its columns
+// j > t; the owner of column t+1 does its own entry first and divides it by
+// T[t+1, t+1] at once, so each step costs one division and one block barrier
+// (instead of a warp's dot product, shuffle tree and division), and the
+// other threads' updates run beside that division.  Each w_j solves
+// w T = e_i left to right, as trinv_body's rows do (the sums in ascending t,
+// one fma per term), so W has the same small right residual.
+constexpr int kTrinvRowThreads = 128;
+constexpr int kTrinvRowMaxK = 200 * 1024 / 8;  // the row's sums in shared memory
+__device__ __forceinline__ void trinv_row_body(const OzTrinv& J, int i, double* trinv_sums) {
+  __shared__ double wb[2];  // w_t, by step parity
+  const int k = J.k;
+  if (i >= k) return;
+  const int q = threadIdx.x, nt = blockDim.x;
+  const double* T = J.T;
+  const int64_t ldt = J.ldt;
+  double* s = trinv_sums;
+  for (int j = i + q; j < k; j += nt) s[j] = j == i ? 1.0 : 0.0;
+  __syncthreads();
+  if (q == 0) {
+    const double w = __ddiv_rn(s[i], __ldg(T + (int64_t)i * ldt + i));
+    s[i] = w;
+    wb[i & 1] = w;
+  }
+  __syncthreads();
+  for (int t = i; t + 1 < k; ++t) {
+    const double w = wb[t & 1];
+    const int own = (t + 1 - i) % nt;  // the thread owning column t+1
+    if (q == own) {
+      const int j = t + 1;
+      const double v = __fma_rn(-w, __ldg(T + (int64_t)j * ldt + t), s[j]);
+      const double w1 = __ddiv_rn(v, __ldg(T + (int64_t)j * ldt + j));
+      s[j] = w1;
+      wb[j & 1] = w1;
+    }
+    // this thread's columns j > t+1
+    int j = i + q;
+    if (j <= t + 1) j += ((t + 1 - j) / nt + 1) * nt;
+    for (; j < k; j += nt) s[j] = __fma_rn(-w, __ldg(T + (int64_t)j * ldt + t), s[j]);
+    __syncthreads();
+  }
+  for (int j = q; j < k; j += nt) J.W[(int64_t)j * J.ldw + i] = j < i ? 0.0 : s[j];
+}
+__global__ void __launch_bounds__(kTrinvRowThreads) oz_trinv_row_kernel(OzTrinv J) {
+  extern __shared__ double trinv_sums[];  // [k]: s_j at index j (j >= i)
+  trinv_row_body(J, blockIdx.x, trinv_sums);
+}
+// batched: CTA -> (job, row) through the prefix table of the jobs' k
+__global__ void __launch_bounds__(kTrinvRowThreads)
+    oz_trinv_row_batched_kernel(const OzTrinv* J, const int64_t* base, int n) {
+  extern __shared__ double trinv_sums[];  // [max k]
+  int64_t t;
+  const int j = find_problem(base, n, blockIdx.x, &t);
+  trinv_row_body(J[j], (int)t, trinv_sums);
+}
+bool oz_trinv_row_mode(int kmax) { return kmax <= kTrinvRowMaxK; }
+
 // one row of W per warp in shared memory: as many warps as fit 200 KB
 int oz_trinv_warps(int kmax) {
   int warps = (int)(200 * 1024 / ((int64_t)kmax * (int64_t)sizeof(double)));
@@ -319,17 +379,34 @@ static cudaError_t trinv_smem_attr(const void* fn, size_t bytes) {
   return raise_smem_limit(fn, bytes);
 }
 cudaError_t oz_trinv(const OzTrinv& J, cudaStream_t s) {
+  if (J.k <= 0) return cudaSuccess;
+  const size_t smem = (size_t)J.k * sizeof(double);
+  if (oz_trinv_row_mode(J.k)) {  // one CTA per row
+    cudaError_t e = trinv_smem_attr((const void*)oz_trinv_row_kernel, smem);
+    if (e != cudaSuccess) return e;
+    oz_trinv_row_kernel<<<(unsigned)J.k, kTrinvRowThreads, smem, s>>>(J);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int warps = oz_trinv_warps(J.k);
-  const size_t smem = (size_t)warps * J.k * sizeof(double);
-  cudaError_t e = trinv_smem_attr((const void*)oz_trinv_rows_kernel, smem);
+  const size_t smem_w = (size_t)warps * J.k * sizeof(double);
+  cudaError_t e = trinv_smem_attr((const void*)oz_trinv_rows_kernel, smem_w);
   if (e != cudaSuccess) return e;
-  oz_trinv_rows_kernel<<<(unsigned)oz_trinv_tiles(J, warps), warps * 32, smem, s>>>(J);
+  oz_trinv_rows_kernel<<<(unsigned)oz_trinv_tiles(J, warps), warps * 32, smem_w, s>>>(J);
   count_launches(1);
   return cudaGetLastError();
 }
 cudaError_t oz_trinv_batched(const OzTrinv* jobs, const int64_t* base, int64_t tiles, int njobs,
                              int warps, int kmax, cudaStream_t s) {
   if (njobs <= 0 || tiles <= 0) return cudaSuccess;
+  if (oz_trinv_row_mode(kmax)) {  // one CTA per row (the caller's tiles: k per job)
+    const size_t smem_r = (size_t)kmax * sizeof(double);
+    cudaError_t e = trinv_smem_attr((const void*)oz_trinv_row_batched_kernel, smem_r);
+    if (e != cudaSuccess) return e;
+    oz_trinv_row_batched_kernel<<<(unsigned)tiles, kTrinvRowThreads, smem_r, s>>>(jobs, base, njobs);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)warps * kmax * sizeof(double);
   cudaError_t e = trinv_smem_attr((const void*)oz_trinv_rows_batched_kernel, smem);
   if (e != cudaSuccess) return e;

@@ -97,6 +97,9 @@ int64_t oz_splitrows_tiles(const OzRowSplit& J);
 int64_t oz_colexp_tiles(const OzColSplit& J);
 int64_t oz_splitcols_tiles(const OzColSplit& J);
 int oz_trinv_warps(int kmax);
+// one CTA per row of W (every k of a batch at most kmax): then a job's tiles
+// are its k rows (oz_trinv_tiles with warps = 1)
+bool oz_trinv_row_mode(int kmax);
 int64_t oz_trinv_tiles(const OzTrinv& J, int warps);
 int64_t oz_combine_tiles(const OzCombine& J);
 cudaError_t oz_rowsplit_batched(const OzRowSplit* jobs, const int64_t* base_exp,

@@ -337,9 +337,9 @@ int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable);
  * tile shapes chosen per problem width bucket b = min((n - 1) / 32, 15):
  * the widest register block of the substitution of Alg. 2 lines 4 and 7
  * (16 or 32 columns) and the output tile of the Gram partial sums of line 5
- * (16 x 16 or 32 x 32).  This call factors the batch once with the handle's
- * current shapes, then, for every bucket present, times both shapes of both
- * kernels on that bucket's problems (best of 3 launches, CUDA events),
+ * (8 x 8, 16 x 16 or 32 x 32).  This call factors the batch once with the
+ * handle's current shapes, then, for every bucket present, times every shape
+ * of both kernels on that bucket's problems (best of 3 launches, CUDA events),
  * stores the faster shape per bucket and kernel in the handle (every later
  * cqrrpt_batched_d and server wave on the handle uses it), and factors the
  * batch again with the chosen shapes: on return the outputs are those of
@@ -351,7 +351,8 @@ int cqrrpt_set_batch_graphs(cqrrpt_handle h, int enable);
  *   times_us_host       HOST array of 64 doubles or NULL: for bucket b,
  *                       [4b + 0, 4b + 1] = TRSM time with 16 / 32 columns,
  *                       [4b + 2, 4b + 3] = Gram time with 16 / 32 tiles
- *                       (microseconds; 0 for buckets absent from the batch).
+ *                       (microseconds; 0 for buckets absent from the batch;
+ *                       the 8 x 8 Gram time is compared but not reported).
  * Returns 0, an argument error, CQRRPT_NO_MEMORY or CQRRPT_CUDA_ERROR. */
 int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const int64_t* n,
                             const double* const* A, const int64_t* lda, double gamma,
@@ -362,9 +363,9 @@ int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const 
                             cudaStream_t stream);
 
 /* The handle's batched tile shapes: HOST arrays of 16 entries (either may be
- * NULL), TRSM column block (16 or 32) and Gram tile edge (16 or 32) per
- * width bucket.  set_tuning returns -2 / -3 for a value other than 16 or
- * 32 and then changes nothing.  A new handle starts with 32-column blocks
+ * NULL), TRSM column block (16 or 32) and Gram tile edge (8, 16 or 32) per
+ * width bucket.  set_tuning returns -2 for a TRSM block other than 16 or 32
+ * and -3 for a Gram edge other than 8, 16 or 32, and then changes nothing.  A new handle starts with 32-column blocks
  * and 16 x 16 Gram tiles for n <= 64, 32 x 32 above. */
 int cqrrpt_batched_get_tuning(cqrrpt_handle h, int* trsm_jb_host, int* gram_tile_host);
 int cqrrpt_batched_set_tuning(cqrrpt_handle h, const int* trsm_jb_host, const int* gram_tile_host);

@@ -1744,14 +1744,16 @@ int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const 
   BatchTuning T = h->tune;
   for (int b = 0; b < kTuneBuckets; ++b) {
     if (members[(size_t)b].empty()) continue;
-    double tt[2], tg[2];
-    const int shapes[2] = {16, 32};
-    for (int v = 0; v < 2; ++v) {
+    double tt[3], tg[3];
+    // shapes 16 and 32 for both kernels; 8 x 8 Gram tiles as well (less
+    // padding of a small k; the TRSM time of that run is not used)
+    const int shapes[3] = {16, 32, 8};
+    for (int v = 0; v < 3; ++v) {
       st = time_bucket(h, probs, members[(size_t)b], shapes[v], W, ws_each, stream, &tt[v], &tg[v]);
       if (st != kOk) return st;
     }
     T.trsm_jb[b] = tt[0] < tt[1] ? 16 : 32;
-    T.gram_tile[b] = tg[0] < tg[1] ? 16 : 32;
+    T.gram_tile[b] = tg[2] < std::min(tg[0], tg[1]) ? 8 : (tg[0] < tg[1] ? 16 : 32);
     if (times_us_host) {
       times_us_host[4 * b + 0] = tt[0];
       times_us_host[4 * b + 1] = tt[1];
@@ -1780,7 +1782,9 @@ int cqrrpt_batched_set_tuning(cqrrpt_handle h, const int* trsm_jb_host,
   if (!h) return -1;
   for (int b = 0; b < kTuneBuckets; ++b) {
     if (trsm_jb_host && trsm_jb_host[b] != 16 && trsm_jb_host[b] != 32) return -2;
-    if (gram_tile_host && gram_tile_host[b] != 16 && gram_tile_host[b] != 32) return -3;
+    if (gram_tile_host && gram_tile_host[b] != 8 && gram_tile_host[b] != 16 &&
+        gram_tile_host[b] != 32)
+      return -3;
   }
   for (int b = 0; b < kTuneBuckets; ++b) {
     if (trsm_jb_host) h->tune.trsm_jb[b] = trsm_jb_host[b];

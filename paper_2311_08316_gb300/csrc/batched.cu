@@ -112,7 +112,7 @@ int batch_plan(BatchPlan& P, int batch, const BatchProblem* probs, char* ws_base
     DeviceScalars* s = sc + (scalar_index ? scalar_index[p] : p);
     const int bucket = tune_bucket(n);
     const int jb = TU.trsm_jb[bucket] == 16 ? 16 : 32;
-    const int gt = TU.gram_tile[bucket] == 16 ? 16 : 32;
+    const int gt = TU.gram_tile[bucket] == 8 ? 8 : TU.gram_tile[bucket] == 16 ? 16 : 32;
     SketchDesc& S = sk[p];
     S = SketchDesc{};
     S.m = m; S.n = n; S.d = (int)d; S.s = q.nnz; S.seed = q.seed;

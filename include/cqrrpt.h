@@ -365,8 +365,9 @@ int cqrrpt_batched_autotune(cqrrpt_handle h, int batch, const int64_t* m, const 
 /* The handle's batched tile shapes: HOST arrays of 16 entries (either may be
  * NULL), TRSM column block (16 or 32) and Gram tile edge (8, 16 or 32) per
  * width bucket.  set_tuning returns -2 for a TRSM block other than 16 or 32
- * and -3 for a Gram edge other than 8, 16 or 32, and then changes nothing.  A new handle starts with 32-column blocks
- * and 16 x 16 Gram tiles for n <= 64, 32 x 32 above. */
+ * and -3 for a Gram edge other than 8, 16 or 32, and then changes nothing.
+ * A new handle starts with 32-column blocks, 8 x 8 Gram tiles for
+ * n <= 256 and 32 x 32 above. */
 int cqrrpt_batched_get_tuning(cqrrpt_handle h, int* trsm_jb_host, int* gram_tile_host);
 int cqrrpt_batched_set_tuning(cqrrpt_handle h, const int* trsm_jb_host, const int* gram_tile_host);
 

@@ -57,7 +57,7 @@ BatchTuning default_tuning() {
   BatchTuning t;
   for (int b = 0; b < kTuneBuckets; ++b) {
     t.trsm_jb[b] = 32;
-    t.gram_tile[b] = b < 2 ? 16 : 32;
+    t.gram_tile[b] = b < 8 ? 8 : 32;  // the autotuner's choice on uneven batches up to n = 256
   }
   return t;
 }
